@@ -1,0 +1,8 @@
+"""FP64 CPU oracle of the box-least-squares periodogram (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may
+import this package. It shares no code with the CUDA library and never imports it.
+"""
+from .oracle import (  # noqa: F401
+    OraclePeak, build, kminmax, freq, fold, prep, bins, power, bls, bls_many, lib_path,
+)

@@ -1,0 +1,209 @@
+"""ctypes binding of ``bls_oracle.c``, the plain FP64 BLS oracle (test infrastructure).
+
+Every function mirrors one C function; see that file for the definition each one
+follows (Sec. 2.2.2 of the paper and the BLS method it cites).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bls_oracle.c")
+_LIB = os.path.join(_HERE, "libbls_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc: -O2, no FMA contraction, no fast-math."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-Wall", "-o", tmp, _SRC, "-lm", "-lpthread"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Peak(C.Structure):
+    _fields_ = [("j", C.c_int), ("freq", C.c_double), ("period", C.c_double),
+                ("epoch", C.c_double), ("duration", C.c_double), ("depth", C.c_double),
+                ("snr", C.c_double), ("sr", C.c_double), ("power", C.c_double),
+                ("i1", C.c_int), ("k", C.c_int)]
+
+
+class _Curve(C.Structure):
+    _fields_ = [("t", C.c_void_p), ("y", C.c_void_p), ("dy", C.c_void_p), ("n", C.c_int),
+                ("freqs", C.c_void_p), ("nf", C.c_int), ("fmin", C.c_double),
+                ("df", C.c_double), ("nb", C.c_int), ("kmin", C.c_int), ("kmax", C.c_int)]
+
+
+@dataclass
+class OraclePeak:
+    j: int
+    freq: float
+    period: float
+    epoch: float
+    duration: float
+    depth: float
+    snr: float
+    sr: float
+    power: float
+    i1: int
+    k: int
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = C.CDLL(_LIB)
+            D, I, P = C.c_double, C.c_int, C.c_void_p
+            lib.oracle_kminmax.argtypes = [I, D, D, C.POINTER(I), C.POINTER(I)]
+            lib.oracle_freq.argtypes = [I, D, D]
+            lib.oracle_freq.restype = D
+            lib.oracle_fold.argtypes = [D, D, I]
+            lib.oracle_prep.argtypes = [I, P, P, P, P, P, P, P]
+            lib.oracle_bins.argtypes = [I, P, I, P, I, P]
+            lib.oracle_power.argtypes = [I, P, P, P, D, I, I, I, I, C.POINTER(D),
+                                         C.POINTER(I), C.POINTER(I), C.POINTER(D),
+                                         C.POINTER(D)]
+            lib.oracle_bls.argtypes = [C.POINTER(_Curve), I, P, P, P, I, P]
+            lib.oracle_bls_many.argtypes = [I, C.POINTER(_Curve), I, I, P, I, P]
+            _lib = lib
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+def kminmax(nb: int, qmin: float, qmax: float):
+    lo, hi = C.c_int(), C.c_int()
+    if _load().oracle_kminmax(nb, qmin, qmax, C.byref(lo), C.byref(hi)) != 0:
+        raise ValueError("invalid nb/q range")
+    return lo.value, hi.value
+
+
+def freq(j: int, fmin: float, df: float) -> float:
+    return _load().oracle_freq(int(j), float(fmin), float(df))
+
+
+def fold(dt: float, f: float, nb: int) -> int:
+    return _load().oracle_fold(float(dt), float(f), int(nb))
+
+
+def _arrays(t, y, dy):
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    dy = None if dy is None else np.ascontiguousarray(dy, dtype=np.float32)
+    return t, y, dy
+
+
+def prep(t, y, dy):
+    """Returns dt, w, x (FP64) and (t_ref, W, ybar, sum w x^2)."""
+    t, y, dy = _arrays(t, y, dy)
+    n = len(t)
+    dt, w, x = np.empty(n), np.empty(n), np.empty(n)
+    scal = np.empty(4)
+    if _load().oracle_prep(n, _p(t), _p(y), _p(dy), _p(dt), _p(w), _p(x), _p(scal)) != 0:
+        raise ValueError("invalid curve")
+    return dt, w, x, tuple(scal)
+
+
+def bins(t, freqs: Sequence[float], nb: int) -> np.ndarray:
+    """Per-point phase bins, shape (len(freqs), n)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    f = np.ascontiguousarray(freqs, dtype=np.float64)
+    out = np.empty((len(f), len(t)), dtype=np.int32)
+    if _load().oracle_bins(len(t), _p(t), len(f), _p(f), nb, _p(out)) != 0:
+        raise ValueError("invalid input")
+    return out
+
+
+def power(dt, w, x, f: float, nb: int, kmin: int, kmax: int, sign: int = 0):
+    """Best box at one frequency: (P, i1, k, r, s)."""
+    dt = np.ascontiguousarray(dt, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    P, r, s = C.c_double(), C.c_double(), C.c_double()
+    i1, k = C.c_int(), C.c_int()
+    rc = _load().oracle_power(len(dt), _p(dt), _p(w), _p(x), float(f), nb, kmin, kmax, sign,
+                              C.byref(P), C.byref(i1), C.byref(k), C.byref(r), C.byref(s))
+    if rc != 0:
+        raise ValueError("invalid input")
+    return P.value, i1.value, k.value, r.value, s.value
+
+
+def _curve_struct(t, y, dy, nb, kmin, kmax, freqs=None, fmin=0.0, df=0.0, nf=None):
+    keep = [t, y, dy, freqs]
+    cs = _Curve(_p(t), _p(y), _p(dy), len(t), _p(freqs),
+                int(len(freqs) if freqs is not None else nf), float(fmin), float(df),
+                int(nb), int(kmin), int(kmax))
+    return cs, keep
+
+
+def _peaks(arr) -> List[OraclePeak]:
+    return [OraclePeak(p.j, p.freq, p.period, p.epoch, p.duration, p.depth, p.snr, p.sr,
+                       p.power, p.i1, p.k) for p in arr]
+
+
+def bls(t, y, dy, nb: int, kmin: int, kmax: int, *, freqs=None, fmin=0.0, df=0.0,
+        nf: Optional[int] = None, sign: int = 0, topk: int = 1):
+    """Full periodogram of one curve: (P[nf], i1[nf], k[nf], peaks[topk])."""
+    t, y, dy = _arrays(t, y, dy)
+    if freqs is not None:
+        freqs = np.ascontiguousarray(freqs, dtype=np.float64)
+        nf = len(freqs)
+    cs, keep = _curve_struct(t, y, dy, nb, kmin, kmax, freqs, fmin, df, nf)
+    P = np.empty(nf)
+    i1 = np.empty(nf, dtype=np.int32)
+    k = np.empty(nf, dtype=np.int32)
+    pk = (_Peak * max(topk, 1))()
+    rc = _load().oracle_bls(C.byref(cs), sign, _p(P), _p(i1), _p(k), topk, pk)
+    if rc != 0:
+        raise ValueError(f"oracle_bls failed ({rc})")
+    del keep
+    return P, i1, k, _peaks(pk[:topk])
+
+
+def bls_many(curves, nthreads: int = 1, sign: int = 0, topk: int = 1,
+             want_power: bool = False):
+    """Periodograms of many curves on POSIX threads.
+
+    ``curves`` is a sequence of dicts with keys t, y, dy, nb, kmin, kmax and either
+    freqs or (fmin, df, nf).  Returns (peaks per curve, concatenated powers or None).
+    """
+    structs = (_Curve * len(curves))()
+    keep = []
+    total_nf = 0
+    for i, c in enumerate(curves):
+        t, y, dy = _arrays(c["t"], c["y"], c.get("dy"))
+        fr = c.get("freqs")
+        if fr is not None:
+            fr = np.ascontiguousarray(fr, dtype=np.float64)
+        cs, kp = _curve_struct(t, y, dy, c["nb"], c["kmin"], c["kmax"], fr,
+                               c.get("fmin", 0.0), c.get("df", 0.0), c.get("nf"))
+        structs[i] = cs
+        keep.append(kp)
+        total_nf += cs.nf
+    P = np.empty(total_nf) if want_power else None
+    pk = (_Peak * (len(curves) * max(topk, 1)))()
+    rc = _load().oracle_bls_many(len(curves), structs, sign, nthreads, _p(P), topk, pk)
+    if rc != 0:
+        raise ValueError(f"oracle_bls_many failed ({rc})")
+    del keep
+    out = _peaks(pk)
+    return [out[i * topk:(i + 1) * topk] for i in range(len(curves))], P
