@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the batched BLS search on one B300 (or N independent replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: the batched search of 1024 survey-shaped light curves (N log-uniform in
+[500, 5000], nightly windows over 60 days, FP64 times, FP32 flux), 50,000 trial
+frequencies uniform in [0.1, 5] 1/d, nb = 200 phase bins, q in [0.005, 0.15].
+A step is one bls_search over the whole batch: prep, fold-bin-sweep, peak reduction.
+
+Metric: point x frequency evaluations per second (sum over curves of N * nf per step,
+divided by the step time).  `value` is timed with CUDA events on the plan's stream with
+inputs resident in device memory; L2 is flushed (256 MiB write) before every step inside
+the timed region.  `e2e` is the same metric through the C ABI with pinned host buffers:
+host-to-device copies of t, y, dy and the device-to-host copy of the peaks are inside.
+
+Roofline of the dominant kernel (fold-bin-sweep): FP32-issue / shared-memory model.
+  loop A (fold + bin), per point x frequency: 2 shared-memory read-modify-writes of 8 B,
+      16 B per unit at 128 B/clk/SM  -> 8 units/clk/SM, i.e. 16 FP32 lane-op equivalents;
+  loop B (box sweep), per box evaluation: 7 FP32 ops (2 adds, r(1-r), s^2, compare)
+      -> 128/7 units/clk/SM, i.e. 7 lane-op equivalents.
+  peak = SMs x 128 lanes x clock (max SM clock of the measured peaks).
+Multi-GPU (torchrun, N > 1): each rank searches its own 1024 curves (weak scaling);
+value = all ranks' units / max over ranks of the step time.  No data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1112_1701_b300 import synth  # noqa: E402
+
+METRIC = "BLS point x freq evals/s"
+UNIT = "point*freq/s"
+NB, QMIN, QMAX = 200, 0.005, 0.15
+
+# DRAM traffic of one fold-bin-sweep launch on this workload, from one ncu capture of the
+# kernel source with the given SHA-256 (reported as null once the source changes).
+NCU_TRAFFIC = {"kernel_sha256": None, "bytes_per_launch": None}
+
+
+def kernel_sha():
+    p = os.path.join(ROOT, "paper_1112_1701_b300", "csrc", "bls_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                          f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons)}
+
+
+def box_evals(batch):
+    from paper_1112_1701_b300 import bls
+    tot = 0
+    for g, nb in zip(batch.grids, batch.nb):
+        kmin, kmax = bls.kminmax(nb, batch.qmin, batch.qmax)
+        tot += nb * (kmax - kmin + 1) * g.nf
+    return tot
+
+
+def cpu_baseline(batch, seconds_hint=15.0, max_curves=1024):
+    """The FP64 oracle as it stands, on all host cores, on a bounded sample of curves
+    (full grid each); returns the CPU-baseline object."""
+    import oracle
+    cores = os.cpu_count() or 1
+    kmin, kmax = oracle.kminmax(NB, batch.qmin, batch.qmax)
+
+    def run(idx):
+        cur = [dict(t=batch.curves[i].t, y=batch.curves[i].y, dy=batch.curves[i].dy, nb=NB,
+                    kmin=kmin, kmax=kmax, fmin=batch.grids[i].fmin, df=batch.grids[i].df,
+                    nf=batch.grids[i].nf) for i in idx]
+        t0 = time.perf_counter()
+        oracle.bls_many(cur, nthreads=cores, topk=1)
+        return time.perf_counter() - t0, sum(len(batch.curves[i].t) * batch.grids[i].nf
+                                             for i in idx)
+
+    # calibrate on one curve per core, then size the sample to ~seconds_hint
+    n0 = min(len(batch), max(1, cores))
+    dt0, u0 = run(list(range(n0)))
+    rate = u0 / dt0
+    per_curve = u0 / n0
+    ncur = int(min(max_curves, len(batch), max(n0, seconds_hint * rate / per_curve)))
+    dt, u = run(list(range(ncur)))
+    return {"value": u / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{ncur} of {len(batch)} curves x full {batch.grids[0].nf}-frequency grid, "
+                      f"FP64 C oracle on {cores} host threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle timed on the host cores, same metric and workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    batch = synth.config2(args.ncurves, nf=args.nf)
+    cores = os.cpu_count() or 1
+    kmin, kmax = oracle.kminmax(NB, batch.qmin, batch.qmax)
+    per_step = max(1, min(len(batch), args.ref_curves or cores))
+    times, units = [], []
+    for s in range(args.warmup + args.steps):
+        idx = [(s * per_step + i) % len(batch) for i in range(per_step)]
+        cur = [dict(t=batch.curves[i].t, y=batch.curves[i].y, dy=batch.curves[i].dy, nb=NB,
+                    kmin=kmin, kmax=kmax, fmin=batch.grids[i].fmin, df=batch.grids[i].df,
+                    nf=batch.grids[i].nf) for i in idx]
+        t0 = time.perf_counter()
+        oracle.bls_many(cur, nthreads=cores, topk=1)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            units.append(sum(len(batch.curves[i].t) * batch.grids[i].nf for i in idx))
+    value = sum(units) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(batch, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} curves x full grid per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(batch, args):
+    return {"workload": f"batched BLS: {len(batch)} curves, N log-uniform 500-5000 over 60 "
+                        f"nights, {batch.grids[0].nf} freqs uniform in [0.1, 5]/d, nb={NB}, "
+                        f"q {QMIN}-{QMAX}",
+            "ncurves": len(batch), "nf": batch.grids[0].nf, "nb": NB,
+            "points": int(sum(len(c.t) for c in batch.curves)),
+            "l2": "flushed (256 MiB write) before every step, inside the timed region",
+            "inputs": "device-resident for value; pinned host for e2e",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ncurves", type=int, default=1024)
+    ap.add_argument("--nf", type=int, default=50000)
+    ap.add_argument("--ref-curves", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--plain-curves", type=int, default=8,
+                    help="curves of the plain FP64 baseline timing (0 = skip)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1112_1701_b300 import bls
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    batch = synth.config2(args.ncurves, nf=args.nf, first=rank * args.ncurves)
+    units = batch.point_freqs()
+    evals = box_evals(batch)
+    dev = bls.curves_from_batch(batch, device="cuda")
+    stream = torch.cuda.current_stream()
+    plan = bls.Plan(nb=NB, qmin=QMIN, qmax=QMAX, topk=1, stream=stream.cuda_stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        plan.search(dev)
+    plan.profile(reset=True)
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        plan.search(dev)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = plan.profile(reset=True)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = units * world / (ms_step / 1000.0)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        ts = torch.from_numpy(np.concatenate([c.t for c in batch.curves])).pin_memory()
+        ys = torch.from_numpy(np.concatenate([c.y for c in batch.curves])).pin_memory()
+        dys = torch.from_numpy(np.concatenate([c.dy for c in batch.curves])).pin_memory()
+        hostc, o = [], 0
+        for c, g in zip(batch.curves, batch.grids):
+            n = len(c.t)
+            hostc.append(bls.CurveInput(ts[o:o + n], ys[o:o + n], dys[o:o + n], nf=g.nf,
+                                        fmin=g.fmin, df=g.df, nb=NB, qmin=QMIN, qmax=QMAX))
+            o += n
+        for _ in range(max(1, args.warmup)):
+            plan.search(hostc)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.search(hostc)
+        barrier()
+        wall = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([wall], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        npts = int(ts.numel())
+        e2e = {"value": units * world * args.steps / wall, "unit": UNIT,
+               "h2d_bytes_per_step": npts * (8 + 4 + 4),
+               "d2h_bytes_per_step": len(batch) * bls.C.sizeof(bls.PeakStruct)}
+
+    # roofline of the fold-bin-sweep kernel, from CUDA events around its launches
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    fold_ms = prof["fold_ms"] / max(1, prof["fold_launches"])
+    launches_per_step = prof["fold_launches"] / max(1, args.steps)
+    eq_ops = (16.0 * units + 7.0 * evals) / max(1.0, launches_per_step)
+    achieved = eq_ops / (fold_ms / 1000.0) / 1e12
+    clk_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak = sms * 128 * clk_max * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "T FP32 lane-op/s (shared-memory RMW and FP32-issue model)",
+            "frac": achieved / peak,
+            "traffic": (NCU_TRAFFIC["bytes_per_launch"]
+                        if NCU_TRAFFIC["kernel_sha256"] == kernel_sha() else None),
+            "kernel": "fold_sweep_kernel", "peak_source": f"{peak_src}: {sms} SMs x 128 lanes x "
+                                                          f"{clk_max:.0f} MHz",
+            "fold_ms_per_launch": fold_ms,
+            "loop_a_units": units, "loop_b_units": evals}
+    if clk.get("sm_mhz"):
+        roof["frac_at_run_clock"] = achieved / (sms * 128 * clk["sm_mhz"] * 1e6 / 1e12)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(batch, args),
+            "roofline": roof, "clocks": clk,
+            "gpu_launches": int(prof["kernel_launches"]),
+            "box_evals_per_s": evals * world / (ms_step / 1000.0),
+            "kernel_ms": {"prep": prof["prep_ms"] / args.steps,
+                          "fold_sweep": prof["fold_ms"] / args.steps,
+                          "reduce": prof["reduce_ms"] / args.steps}}
+    if e2e:
+        line["e2e"] = e2e
+
+    # the plain FP64 one-curve-per-launch GPU kernel on a sample of the same curves
+    if args.plain_curves > 0 and rank == 0:
+        sub = batch.subset(range(min(args.plain_curves, len(batch))))
+        pdev = bls.curves_from_batch(sub, device="cuda")
+        with bls.Plan(nb=NB, qmin=QMIN, qmax=QMAX, algo="plain_f64",
+                      stream=stream.cuda_stream) as pp:
+            pp.search(pdev[:1])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pp.search(pdev)
+            torch.cuda.synchronize()
+            dtp = time.perf_counter() - t0
+        line["plain_f64_gpu"] = {"value": sub.point_freqs() / dtp, "unit": UNIT,
+                                 "sample": f"{len(sub)} curves x full grid, one launch per curve",
+                                 "speedup_of_value": value / world / (sub.point_freqs() / dtp)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(batch)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

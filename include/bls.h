@@ -1,0 +1,209 @@
+/*
+ * bls.h -- C ABI of the B300 box-least-squares (BLS) transit search.
+ *
+ * The method is the GPU eclipse search of Sec. 2.2.2 of the paper: a standard BLS
+ * (Kovacs, Zucker & Mazeh 2002; Tingley 2003, cited there) that phases every light
+ * curve at every trial period, tests a range of box durations and phases, and keeps
+ * the best.  The paper prints no formula; the statistic computed here is
+ *
+ *   w_i = dy_i^-2 / W, W = sum dy_i^-2;  x_i = y_i - sum w y;
+ *   for a box B of phase bins: r = sum_B w, s = sum_B w x,
+ *   P = s^2 / (r (1 - r)),  SR = sqrt(P),  depth = -s / (r (1 - r)),  SNR = SR sqrt(W).
+ *
+ * Phases are cut into nb equal bins; B runs over cyclic runs of k consecutive bins,
+ * kmin <= k <= kmax.  The peak of each curve is the frequency with the largest P
+ * (ties to the smallest frequency index, then the smallest start bin, then the
+ * smallest width).
+ *
+ * Conventions for every entry point:
+ *   - Status codes are returned; nothing is thrown, nothing aborts.  On failure
+ *     bls_last_error() returns a message for the calling thread.
+ *   - Input arrays may be host memory (pageable or pinned) or device memory of the
+ *     plan's device; the library tells them apart by cudaPointerGetAttributes.  The
+ *     caller keeps ownership.  The library never writes to inputs and does not keep
+ *     pointers to them after the call returns (bls_submit copies its input).
+ *   - Output arrays are caller-owned: `out` peaks are host memory; a spectrum may be
+ *     host or device memory.
+ *   - A plan is not thread-safe for concurrent bls_search calls (they serialise on an
+ *     internal lock); bls_submit/bls_poll may be called from any thread.
+ */
+#ifndef BLS_H
+#define BLS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BLS_API_VERSION 1
+
+typedef enum {
+    BLS_OK = 0,
+    BLS_PENDING = 1,          /* bls_poll: the request is not finished yet */
+    BLS_ERR_INVALID = -1,     /* bad argument or input value (NaN, dy <= 0, n < 2, ...) */
+    BLS_ERR_NOMEM = -2,       /* device or host allocation failed, or over budget */
+    BLS_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    BLS_ERR_TIMEOUT = -4,     /* bls_poll waited timeout_ms without completion */
+    BLS_ERR_INTERNAL = -5,    /* a device-side consistency check failed */
+    BLS_ERR_CANCELLED = -6    /* the request was cancelled */
+} bls_status;
+
+/* Phase step (fold) precision. */
+enum {
+    BLS_PHASE_DF32 = 0,  /* default: double-FP32 product with an error bound; points whose
+                            bin is not certain are re-folded in FP64 (bins identical to FP64) */
+    BLS_PHASE_F64 = 1,   /* every point folded in FP64 */
+    BLS_PHASE_F32 = 2    /* FP32 product, no fallback (precision study only: bins can differ) */
+};
+
+/* Accumulation of the phase histograms and box sums. */
+enum {
+    BLS_SUM_F32 = 0,     /* default: FP32 */
+    BLS_SUM_KAHAN = 1    /* FP32 with Kahan compensation (bins and box sums) */
+};
+
+/* Which boxes count. */
+enum {
+    BLS_SIGN_DIPS = 0,   /* default: only boxes below the mean (s < 0): eclipses and transits */
+    BLS_SIGN_BOTH = 1    /* dips and bumps */
+};
+
+/* Kernel family. */
+enum {
+    BLS_ALGO_TILED = 0,     /* default: batched persistent fold-bin-sweep kernels */
+    BLS_ALGO_PLAIN_F64 = 1  /* baseline: one launch per curve, one thread per frequency, FP64 */
+};
+
+typedef struct {
+    int nb;                     /* phase bins (>= 2); a curve may override */
+    double qmin, qmax;          /* fractional box duration range, 0 < qmin <= qmax < 1 */
+    int kmin, kmax;             /* box widths in bins; 0 = derive from q (bls_kminmax) */
+    int topk;                   /* peaks returned per curve, 1..16 */
+    int phase;                  /* BLS_PHASE_* */
+    int sum;                    /* BLS_SUM_* */
+    int sign;                   /* BLS_SIGN_* */
+    int algo;                   /* BLS_ALGO_* */
+    size_t max_device_bytes;    /* device memory budget of the plan; 0 = half the free memory */
+    int max_curves_per_launch;  /* 0 = as many as the budget allows */
+    int freqs_per_block;        /* frequencies per thread block; 0 = tuned */
+    int point_chunk;            /* points staged in shared memory at a time; 0 = tuned */
+    int max_active_requests;    /* serving: requests resident on the device at once; 0 = 64 */
+    long long step_point_freqs; /* serving: point x frequency work per step; 0 = tuned */
+} bls_plan_desc;
+
+/* One light curve and its trial-frequency grid. */
+typedef struct {
+    const double* t;      /* n times [d], any order; FP64 (host or device) */
+    const float* y;       /* n fluxes */
+    const float* dy;      /* n 1-sigma errors (> 0), or NULL for unit weights */
+    int n;                /* number of points, >= 2 */
+    const double* freqs;  /* nf trial frequencies [1/d] (> 0), or NULL for a uniform grid */
+    int nf;               /* number of trial frequencies, >= 1 */
+    double fmin, df;      /* uniform grid: f_j = fmin + j*df, each op rounded (freqs == NULL) */
+    int nb;               /* phase bins for this curve; 0 = plan default */
+    double qmin, qmax;    /* duration range for this curve; 0 = plan default */
+} bls_curve;
+
+/* One peak of one curve.  Reported values are recomputed in FP64 for the chosen box. */
+typedef struct {
+    int best_j;           /* frequency index of the peak, -1 for an empty slot */
+    int i1, k;            /* first bin and width (bins) of the best box at that frequency */
+    int pad_;
+    double freq;          /* f [1/d] */
+    double period;        /* 1/f [d] */
+    double epoch;         /* mid-box time of the first eclipse after min(t) [d] */
+    double duration;      /* k/(nb f) [d] */
+    double depth;         /* -s/(r(1-r)): positive for a dip, in flux units */
+    double snr;           /* depth / sigma_depth = SR sqrt(W) */
+    double sr;            /* signal residue sqrt(P) */
+    double power;         /* P = s^2/(r(1-r)) */
+} bls_peak;
+
+typedef struct bls_plan bls_plan;
+
+/* Create a plan on the current CUDA device.  cuda_stream (a cudaStream_t, may be NULL)
+ * is the stream all work is ordered on; NULL makes the plan create its own.
+ * Errors: BLS_ERR_INVALID (bad descriptor), BLS_ERR_CUDA (no device). */
+bls_status bls_plan_create(const bls_plan_desc* desc, void* cuda_stream, bls_plan** out);
+
+/* Release the plan, its device memory and its serving thread.  Pending requests are
+ * cancelled.  NULL is ignored. */
+void bls_plan_destroy(bls_plan* plan);
+
+/* Batched search (Sec. 2.2.2): the periodogram of every curve, all frequencies, all box
+ * starts and widths; out[c*topk + q] receives peak q of curve c (host memory).
+ * spectrum (optional, host or device) receives SR(f_j) of every curve back to back
+ * (sum of nf floats).  Blocks until the results are written.
+ * Errors: BLS_ERR_INVALID, BLS_ERR_NOMEM, BLS_ERR_CUDA, BLS_ERR_INTERNAL. */
+bls_status bls_search(bls_plan* plan, const bls_curve* curves, int ncurves,
+                      bls_peak* out, float* spectrum);
+
+/* Serving: queue one curve.  The input is copied before the call returns; the call
+ * never waits for the GPU.  Requests are admitted to the device as memory and slots
+ * free up and share the GPU with requests already running (continuous batching).
+ * *ticket identifies the request.  Errors: BLS_ERR_INVALID, BLS_ERR_NOMEM. */
+bls_status bls_submit(bls_plan* plan, const bls_curve* curve, uint64_t* ticket);
+
+/* Serving: wait up to timeout_ms (0 = just look, < 0 = forever) for a request.
+ * BLS_OK: out[0..topk) holds its peaks and the ticket is retired.
+ * BLS_PENDING (timeout_ms == 0) or BLS_ERR_TIMEOUT: not finished yet.
+ * BLS_ERR_INVALID: unknown or retired ticket.  Other errors: the request failed. */
+bls_status bls_poll(bls_plan* plan, uint64_t ticket, bls_peak* out, int timeout_ms);
+
+/* Serving: cancel a queued or running request; a later poll returns BLS_ERR_CANCELLED. */
+bls_status bls_cancel(bls_plan* plan, uint64_t ticket);
+
+typedef struct {
+    uint64_t submitted, completed, cancelled, failed;
+    uint64_t steps;             /* scheduler steps run */
+    uint64_t active;            /* requests resident on the device now */
+    uint64_t queued;            /* requests waiting for admission */
+    size_t device_bytes_in_use; /* request state on the device now */
+    size_t device_bytes_peak;   /* highest value of the above */
+    double p50_ms, p99_ms;      /* submit -> result latency over completed requests */
+} bls_server_stats;
+
+/* Serving statistics.  Errors: BLS_ERR_INVALID. */
+bls_status bls_server_stats_get(bls_plan* plan, bls_server_stats* out);
+
+/* Box widths from the fractional duration range (reading of the paper's "range of
+ * durations"): kmin = max(1, floor(qmin nb + 1e-9)), kmax = min(nb-1, ceil(qmax nb - 1e-9)).
+ * Errors: BLS_ERR_INVALID. */
+bls_status bls_kminmax(int nb, double qmin, double qmax, int* kmin, int* kmax);
+
+/* Diagnostic: the phase bin of every point of one curve at frequencies js[0..nj), as
+ * the search kernels compute them (plan's phase mode); bins_out[q*n + i] (host).
+ * Errors: BLS_ERR_INVALID, BLS_ERR_CUDA. */
+bls_status bls_debug_fold(bls_plan* plan, const bls_curve* curve, const int* js, int nj,
+                          int* bins_out);
+
+/* Diagnostic: the per-frequency best box of one curve as the search kernels leave it
+ * before the peak reduction: power_out[j] (FP32 P), i1_out[j], k_out[j] (host).
+ * Errors: as bls_search. */
+bls_status bls_debug_powers(bls_plan* plan, const bls_curve* curve, float* power_out,
+                            int* i1_out, int* k_out);
+
+typedef struct {
+    uint64_t searches;          /* launch groups run by bls_search since the last reset */
+    uint64_t kernel_launches;   /* kernels those groups launched */
+    uint64_t fold_launches;     /* of which fold-bin-sweep (or baseline) kernels */
+    double prep_ms;             /* CUDA-event time of the prep kernels */
+    double fold_ms;             /* CUDA-event time of the fold-bin-sweep kernels */
+    double reduce_ms;           /* CUDA-event time of the peak reductions */
+} bls_profile;
+
+/* Diagnostic: kernel timings of bls_search, measured with CUDA events recorded on the
+ * plan's stream around each kernel phase; reset != 0 clears the counters after reading.
+ * Errors: BLS_ERR_INVALID. */
+bls_status bls_profile_get(bls_plan* plan, bls_profile* out, int reset);
+
+/* Thread-local message of the last failure on the calling thread ("" if none). */
+const char* bls_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLS_H */

@@ -4,5 +4,5 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline le
 import this package. It shares no code with the CUDA library and never imports it.
 """
 from .oracle import (  # noqa: F401
-    OraclePeak, build, kminmax, freq, fold, prep, bins, power, bls, bls_many, lib_path,
+    OraclePeak, build, kminmax, freq, fold, prep, bins, power, box, bls, bls_many, lib_path,
 )

@@ -187,6 +187,24 @@ int oracle_power(int n, const double* dt, const double* w, const double* x, doub
     return 0;
 }
 
+/* Power of one given box (i1, k) at frequency f: P = s^2/(r(1-r)) with the sums taken bin
+ * by bin as in the sweep; 0 when the box does not count (r outside (0,1), or s >= 0 with
+ * dips only).  Also returns r and s. */
+int oracle_box(int n, const double* dt, const double* w, const double* x, double f, int nb,
+               int i1, int k, int sign, double* P, double* r, double* s)
+{
+    if (n < 1 || nb < 2 || i1 < 0 || i1 >= nb || k < 1 || k > nb) return -1;
+    double* H = (double*)malloc(sizeof(double) * 2 * (size_t)nb);
+    if (!H) return -2;
+    histogram(n, dt, w, x, f, nb, H, H + nb);
+    box_sums(nb, H, H + nb, i1, k, r, s);
+    free(H);
+    double rr = *r, ss = *s;
+    *P = 0.0;
+    if (rr > 0.0 && rr < 1.0 && (sign == 1 || ss < 0.0)) *P = (ss * ss) / (rr * (1.0 - rr));
+    return 0;
+}
+
 /* Reported quantities of one (frequency, box).  Reading: period = 1/f,
  * duration = k/(nb f), epoch = mid-box time t_ref + frac((i1 + k/2)/nb)/f,
  * depth = -s/(r(1-r)), SR = sqrt(P), SNR = depth/sigma_depth = SR*sqrt(W). */

@@ -80,6 +80,8 @@ def _load():
             lib.oracle_power.argtypes = [I, P, P, P, D, I, I, I, I, C.POINTER(D),
                                          C.POINTER(I), C.POINTER(I), C.POINTER(D),
                                          C.POINTER(D)]
+            lib.oracle_box.argtypes = [I, P, P, P, D, I, I, I, I, C.POINTER(D), C.POINTER(D),
+                                       C.POINTER(D)]
             lib.oracle_bls.argtypes = [C.POINTER(_Curve), I, P, P, P, I, P]
             lib.oracle_bls_many.argtypes = [I, C.POINTER(_Curve), I, I, P, I, P]
             _lib = lib
@@ -145,6 +147,18 @@ def power(dt, w, x, f: float, nb: int, kmin: int, kmax: int, sign: int = 0):
     if rc != 0:
         raise ValueError("invalid input")
     return P.value, i1.value, k.value, r.value, s.value
+
+
+def box(dt, w, x, f: float, nb: int, i1: int, k: int, sign: int = 0):
+    """Power of the given box at one frequency: (P, r, s)."""
+    dt = np.ascontiguousarray(dt, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    P, r, s = C.c_double(), C.c_double(), C.c_double()
+    if _load().oracle_box(len(dt), _p(dt), _p(w), _p(x), float(f), nb, int(i1), int(k), sign,
+                          C.byref(P), C.byref(r), C.byref(s)) != 0:
+        raise ValueError("invalid input")
+    return P.value, r.value, s.value
 
 
 def _curve_struct(t, y, dy, nb, kmin, kmax, freqs=None, fmin=0.0, df=0.0, nf=None):

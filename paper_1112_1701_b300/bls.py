@@ -1,0 +1,283 @@
+"""Python binding of ``libbls.so`` (argument marshalling only).
+
+Every computation happens in the library's CUDA kernels; this module only builds the C
+structs of ``include/bls.h`` from numpy arrays or torch tensors and converts results.
+There is no CPU fallback: if the library is missing, loading it raises.
+
+Inputs may be numpy arrays (host) or CUDA torch tensors (device); device tensors are
+passed by ``data_ptr()`` and the plan can be bound to ``torch.cuda.current_stream()``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libbls.so")
+
+OK, PENDING = 0, 1
+ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL, ERR_CANCELLED = -1, -2, -3, -4, -5, -6
+PHASE = {"df32": 0, "f64": 1, "f32": 2}
+SUM = {"f32": 0, "kahan": 1}
+SIGN = {"dips": 0, "both": 1}
+ALGO = {"tiled": 0, "plain_f64": 1}
+
+
+class BLSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"BLS status {status}: {msg}")
+        self.status = status
+
+
+class PlanDesc(C.Structure):
+    _fields_ = [("nb", C.c_int), ("qmin", C.c_double), ("qmax", C.c_double),
+                ("kmin", C.c_int), ("kmax", C.c_int), ("topk", C.c_int), ("phase", C.c_int),
+                ("sum", C.c_int), ("sign", C.c_int), ("algo", C.c_int),
+                ("max_device_bytes", C.c_size_t), ("max_curves_per_launch", C.c_int),
+                ("freqs_per_block", C.c_int), ("point_chunk", C.c_int),
+                ("max_active_requests", C.c_int), ("step_point_freqs", C.c_longlong)]
+
+
+class CurveStruct(C.Structure):
+    _fields_ = [("t", C.c_void_p), ("y", C.c_void_p), ("dy", C.c_void_p), ("n", C.c_int),
+                ("freqs", C.c_void_p), ("nf", C.c_int), ("fmin", C.c_double),
+                ("df", C.c_double), ("nb", C.c_int), ("qmin", C.c_double),
+                ("qmax", C.c_double)]
+
+
+class PeakStruct(C.Structure):
+    _fields_ = [("best_j", C.c_int), ("i1", C.c_int), ("k", C.c_int), ("pad_", C.c_int),
+                ("freq", C.c_double), ("period", C.c_double), ("epoch", C.c_double),
+                ("duration", C.c_double), ("depth", C.c_double), ("snr", C.c_double),
+                ("sr", C.c_double), ("power", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64),
+                ("cancelled", C.c_uint64), ("failed", C.c_uint64), ("steps", C.c_uint64),
+                ("active", C.c_uint64), ("queued", C.c_uint64),
+                ("device_bytes_in_use", C.c_size_t), ("device_bytes_peak", C.c_size_t),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("searches", C.c_uint64), ("kernel_launches", C.c_uint64),
+                ("fold_launches", C.c_uint64), ("prep_ms", C.c_double),
+                ("fold_ms", C.c_double), ("reduce_ms", C.c_double)]
+
+
+PEAK_DTYPE = np.dtype([("j", np.int32), ("i1", np.int32), ("k", np.int32), ("pad_", np.int32),
+                       ("freq", np.float64), ("period", np.float64), ("epoch", np.float64),
+                       ("duration", np.float64), ("depth", np.float64), ("snr", np.float64),
+                       ("sr", np.float64), ("power", np.float64)])
+assert PEAK_DTYPE.itemsize == C.sizeof(PeakStruct)
+
+_lib = None
+_lock = threading.Lock()
+
+EXPORTS = ["bls_plan_create", "bls_plan_destroy", "bls_search", "bls_submit", "bls_poll",
+           "bls_cancel", "bls_server_stats_get", "bls_kminmax", "bls_debug_fold",
+           "bls_debug_powers", "bls_profile_get", "bls_last_error"]
+
+
+def lib():
+    """Load ``libbls.so`` (built in-tree); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run `python -m "
+                                   "paper_1112_1701_b300.build` (there is no CPU fallback)")
+            L = C.CDLL(LIB_PATH)
+            P, I, D = C.c_void_p, C.c_int, C.c_double
+            L.bls_plan_create.argtypes = [C.POINTER(PlanDesc), P, C.POINTER(P)]
+            L.bls_plan_destroy.argtypes = [P]
+            L.bls_plan_destroy.restype = None
+            L.bls_search.argtypes = [P, C.POINTER(CurveStruct), I, P, P]
+            L.bls_submit.argtypes = [P, C.POINTER(CurveStruct), C.POINTER(C.c_uint64)]
+            L.bls_poll.argtypes = [P, C.c_uint64, P, I]
+            L.bls_cancel.argtypes = [P, C.c_uint64]
+            L.bls_server_stats_get.argtypes = [P, C.POINTER(ServerStats)]
+            L.bls_kminmax.argtypes = [I, D, D, C.POINTER(I), C.POINTER(I)]
+            L.bls_debug_fold.argtypes = [P, C.POINTER(CurveStruct), P, I, P]
+            L.bls_debug_powers.argtypes = [P, C.POINTER(CurveStruct), P, P, P]
+            L.bls_profile_get.argtypes = [P, C.POINTER(Profile), I]
+            L.bls_last_error.argtypes = []
+            L.bls_last_error.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st not in (OK,):
+        raise BLSError(st, lib().bls_last_error().decode())
+    return st
+
+
+def kminmax(nb: int, qmin: float, qmax: float):
+    a, b = C.c_int(), C.c_int()
+    _check(lib().bls_kminmax(nb, qmin, qmax, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor (keeps no reference)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _host(a, dtype):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+@dataclass
+class CurveInput:
+    """One light curve and its grid.  Arrays: numpy (host) or CUDA torch tensors."""
+    t: object
+    y: object
+    dy: object = None
+    nf: int = 0
+    fmin: float = 0.0
+    df: float = 0.0
+    freqs: object = None
+    nb: int = 0
+    qmin: float = 0.0
+    qmax: float = 0.0
+
+
+def _struct(c: CurveInput, keep: list) -> CurveStruct:
+    t = _host(c.t, np.float64)
+    y = _host(c.y, np.float32)
+    dy = _host(c.dy, np.float32)
+    fr = _host(c.freqs, np.float64)
+    keep += [t, y, dy, fr]
+    n = int(t.shape[0])
+    nf = int(fr.shape[0]) if fr is not None else int(c.nf)
+    return CurveStruct(_ptr(t), _ptr(y), _ptr(dy), n, _ptr(fr), nf, float(c.fmin),
+                       float(c.df), int(c.nb), float(c.qmin), float(c.qmax))
+
+
+def curves_from_batch(batch, device=None) -> List[CurveInput]:
+    """CurveInputs of a synth.Batch, packed into contiguous arrays (one copy per array
+    for the whole batch).  With ``device`` (e.g. "cuda") the arrays are torch tensors
+    resident there."""
+    ts = np.concatenate([c.t for c in batch.curves])
+    ys = np.concatenate([c.y for c in batch.curves])
+    dys = np.concatenate([c.dy for c in batch.curves])
+    if device is not None:
+        import torch
+        ts = torch.from_numpy(ts).to(device)
+        ys = torch.from_numpy(ys).to(device)
+        dys = torch.from_numpy(dys).to(device)
+    out, o = [], 0
+    for c, g, nb in zip(batch.curves, batch.grids, batch.nb):
+        n = len(c.t)
+        out.append(CurveInput(ts[o:o + n], ys[o:o + n], dys[o:o + n], nf=g.nf, fmin=g.fmin,
+                              df=g.df, nb=nb, qmin=batch.qmin, qmax=batch.qmax))
+        o += n
+    return out
+
+
+class Plan:
+    """A search plan on the current CUDA device (``bls_plan_create``)."""
+
+    def __init__(self, nb=200, qmin=0.005, qmax=0.15, kmin=0, kmax=0, topk=1, phase="df32",
+                 sum="f32", sign="dips", algo="tiled", max_device_bytes=0,
+                 max_curves_per_launch=0, freqs_per_block=0, point_chunk=0,
+                 max_active_requests=0, step_point_freqs=0, stream=None):
+        self.desc = PlanDesc(nb, qmin, qmax, kmin, kmax, topk, PHASE[phase], SUM[sum],
+                             SIGN[sign], ALGO[algo], max_device_bytes, max_curves_per_launch,
+                             freqs_per_block, point_chunk, max_active_requests,
+                             step_point_freqs)
+        self.topk = topk
+        h = C.c_void_p()
+        _check(lib().bls_plan_create(C.byref(self.desc), stream, C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bls_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def search(self, curves: Sequence[CurveInput], spectrum=None) -> np.ndarray:
+        """Peaks of every curve: structured array of shape (ncurves, topk)."""
+        keep: list = []
+        arr = (CurveStruct * len(curves))(*[_struct(c, keep) for c in curves])
+        out = np.zeros((len(curves), self.topk), dtype=PEAK_DTYPE)
+        _check(lib().bls_search(self._h, arr, len(curves), out.ctypes.data, _ptr(spectrum)))
+        return out
+
+    def submit(self, curve: CurveInput) -> int:
+        keep: list = []
+        cs = _struct(curve, keep)
+        tk = C.c_uint64()
+        _check(lib().bls_submit(self._h, C.byref(cs), C.byref(tk)))
+        return tk.value
+
+    def poll(self, ticket: int, timeout_ms: int = 0):
+        """(status, peaks or None); status is OK, PENDING or ERR_TIMEOUT; raises on
+        other errors."""
+        out = np.zeros(self.topk, dtype=PEAK_DTYPE)
+        st = lib().bls_poll(self._h, ticket, out.ctypes.data, int(timeout_ms))
+        if st in (PENDING, ERR_TIMEOUT):
+            return st, None
+        _check(st)
+        return st, out
+
+    def cancel(self, ticket: int):
+        _check(lib().bls_cancel(self._h, ticket))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().bls_server_stats_get(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def profile(self, reset: bool = False) -> dict:
+        """CUDA-event kernel timings of the searches run so far (bls_profile_get)."""
+        s = Profile()
+        _check(lib().bls_profile_get(self._h, C.byref(s), int(reset)))
+        return {k: getattr(s, k) for k, _ in Profile._fields_}
+
+    def debug_fold(self, curve: CurveInput, js: Iterable[int]) -> np.ndarray:
+        keep: list = []
+        cs = _struct(curve, keep)
+        js = np.ascontiguousarray(list(js), dtype=np.int32)
+        n = cs.n
+        out = np.empty((len(js), n), dtype=np.int32)
+        _check(lib().bls_debug_fold(self._h, C.byref(cs), js.ctypes.data, len(js),
+                                    out.ctypes.data))
+        return out
+
+    def debug_powers(self, curve: CurveInput):
+        keep: list = []
+        cs = _struct(curve, keep)
+        P = np.empty(cs.nf, dtype=np.float32)
+        i1 = np.empty(cs.nf, dtype=np.int32)
+        k = np.empty(cs.nf, dtype=np.int32)
+        _check(lib().bls_debug_powers(self._h, C.byref(cs), P.ctypes.data, i1.ctypes.data,
+                                      k.ctypes.data))
+        return P, i1, k

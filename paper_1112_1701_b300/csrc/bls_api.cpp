@@ -1,0 +1,687 @@
+// bls_api.cpp -- C ABI of the BLS library: plans, argument checks, input staging,
+// batching of curves into launches, and the batched search (Sec. 2.2.2 of the paper:
+// many light curves, every trial period, every box duration and phase, best kept).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "bls_plan.h"
+
+using namespace blsgpu;
+
+namespace blsgpu {
+
+static thread_local std::string g_last_error;
+
+bls_status set_error(bls_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+bls_status cuda_fail(cudaError_t e, const char* what)
+{
+    return set_error(e == cudaErrorMemoryAllocation ? BLS_ERR_NOMEM : BLS_ERR_CUDA,
+                     "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaError_t DevBuf::ensure(size_t need)
+{
+    if (need <= bytes && p) return cudaSuccess;
+    release();
+    size_t sz = need + need / 4 + 256;
+    cudaError_t e = cudaMalloc(&p, sz);
+    if (e != cudaSuccess) { p = nullptr; bytes = 0; return e; }
+    bytes = sz;
+    return cudaSuccess;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+cudaError_t HostBuf::ensure(size_t need)
+{
+    if (need <= bytes && p) return cudaSuccess;
+    release();
+    size_t sz = need + need / 4 + 256;
+    cudaError_t e = cudaMallocHost(&p, sz);
+    if (e != cudaSuccess) { p = nullptr; bytes = 0; return e; }
+    bytes = sz;
+    return cudaSuccess;
+}
+
+void HostBuf::release()
+{
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+static bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static bls_status kminmax_impl(int nb, double qmin, double qmax, int* kmin, int* kmax)
+{
+    if (nb < 2 || !(qmin > 0.0) || !(qmax >= qmin) || !(qmax < 1.0))
+        return set_error(BLS_ERR_INVALID, "need nb >= 2 and 0 < qmin <= qmax < 1 (nb=%d qmin=%g qmax=%g)",
+                         nb, qmin, qmax);
+    int lo = (int)std::floor(qmin * nb + 1e-9);
+    int hi = (int)std::ceil(qmax * nb - 1e-9);
+    lo = std::max(lo, 1);
+    hi = std::min(hi, nb - 1);
+    hi = std::max(hi, lo);
+    *kmin = lo;
+    *kmax = hi;
+    return BLS_OK;
+}
+
+bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* o)
+{
+    if (!c) return set_error(BLS_ERR_INVALID, "curve %d: NULL descriptor", index);
+    if (c->n < 2) return set_error(BLS_ERR_INVALID, "curve %d: n = %d, need n >= 2", index, c->n);
+    if (c->nf < 1) return set_error(BLS_ERR_INVALID, "curve %d: nf = %d, need nf >= 1", index, c->nf);
+    if (!c->t || !c->y) return set_error(BLS_ERR_INVALID, "curve %d: NULL t or y", index);
+    o->t = c->t; o->y = c->y; o->dy = c->dy; o->freqs = c->freqs;
+    o->n = c->n; o->nf = c->nf;
+    o->fmin = c->fmin; o->df = c->df;
+    if (!c->freqs) {
+        if (!(c->fmin > 0.0) || !std::isfinite(c->fmin) || !(c->df >= 0.0) || !std::isfinite(c->df))
+            return set_error(BLS_ERR_INVALID, "curve %d: uniform grid needs fmin > 0 and df >= 0 (fmin=%g df=%g)",
+                             index, c->fmin, c->df);
+        double fmax = c->fmin + (double)(c->nf - 1) * c->df;
+        if (!std::isfinite(fmax)) return set_error(BLS_ERR_INVALID, "curve %d: grid overflows", index);
+    }
+    o->nb = c->nb > 0 ? c->nb : P->d.nb;
+    double qmin = c->qmin > 0.0 ? c->qmin : P->d.qmin;
+    double qmax = c->qmax > 0.0 ? c->qmax : P->d.qmax;
+    if (o->nb < 2) return set_error(BLS_ERR_INVALID, "curve %d: nb = %d, need nb >= 2", index, o->nb);
+    if (c->nb <= 0 && c->qmin <= 0.0 && c->qmax <= 0.0 && P->d.kmin > 0) {
+        o->kmin = P->d.kmin;
+        o->kmax = P->d.kmax;
+        if (o->kmin < 1 || o->kmax < o->kmin || o->kmax > o->nb)
+            return set_error(BLS_ERR_INVALID, "kmin/kmax %d/%d invalid for nb = %d", o->kmin, o->kmax, o->nb);
+    } else {
+        bls_status s = kminmax_impl(o->nb, qmin, qmax, &o->kmin, &o->kmax);
+        if (s != BLS_OK) return set_error(s, "curve %d: %s", index, bls_last_error());
+    }
+    if (o->nb > 65535) return set_error(BLS_ERR_INVALID, "curve %d: nb = %d exceeds 65535", index, o->nb);
+    o->t_dev = is_device_ptr(c->t);
+    o->y_dev = is_device_ptr(c->y);
+    o->dy_dev = c->dy ? is_device_ptr(c->dy) : false;
+    o->f_dev = c->freqs ? is_device_ptr(c->freqs) : false;
+    // host values are checked here; device values by the prep kernel
+    if (!o->t_dev)
+        for (int i = 0; i < c->n; ++i)
+            if (!std::isfinite(c->t[i])) return set_error(BLS_ERR_INVALID, "curve %d: t[%d] is not finite", index, i);
+    if (!o->y_dev)
+        for (int i = 0; i < c->n; ++i)
+            if (!std::isfinite(c->y[i])) return set_error(BLS_ERR_INVALID, "curve %d: y[%d] is not finite", index, i);
+    if (c->dy && !o->dy_dev)
+        for (int i = 0; i < c->n; ++i)
+            if (!(c->dy[i] > 0.0f) || !std::isfinite(c->dy[i]))
+                return set_error(BLS_ERR_INVALID, "curve %d: dy[%d] = %g, need finite dy > 0", index, i, (double)c->dy[i]);
+    if (c->freqs && !o->f_dev)
+        for (int j = 0; j < c->nf; ++j)
+            if (!(c->freqs[j] > 0.0) || !std::isfinite(c->freqs[j]))
+                return set_error(BLS_ERR_INVALID, "curve %d: freqs[%d] = %g, need finite f > 0", index, j, c->freqs[j]);
+    return BLS_OK;
+}
+
+bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g)
+{
+    const int kahan = P->d.sum == BLS_SUM_KAHAN;
+    const size_t esz = kahan ? 16 : 8;
+    const int maxT = fold_sweep_max_threads();
+    g->chunk = P->d.point_chunk > 0 ? ((P->d.point_chunk + 1) & ~1) : 256;
+    const size_t stage = (size_t)2 * g->chunk * 24;
+    const size_t avail = P->smem_optin > stage + 64 ? P->smem_optin - stage - 64 : 0;
+    int T;
+    if (P->d.freqs_per_block > 0) {
+        T = P->d.freqs_per_block;
+    } else {
+        size_t cap = avail / ((size_t)nb * esz);
+        T = (int)std::min<size_t>(cap, (size_t)256);
+        T &= ~15;
+    }
+    if (T < 16) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", nb);
+    if (T > maxT) T = maxT;
+    g->T = T;
+    g->stride = (T + 15) & ~15;
+    g->smem = fold_smem_bytes(T, g->stride, nb, g->chunk, kahan);
+    if (g->smem > P->smem_optin)
+        return set_error(BLS_ERR_INVALID, "nb = %d with %d frequencies per block needs %zu B of shared memory (> %zu)",
+                         nb, T, g->smem, P->smem_optin);
+    return BLS_OK;
+}
+
+void order_by_cost(const std::vector<CurveSpec>& cs, const std::vector<int>& idx,
+                   std::vector<int>* out)
+{
+    *out = idx;
+    std::stable_sort(out->begin(), out->end(), [&](int a, int b) {
+        double ca = (double)cs[a].n * cs[a].nf, cb = (double)cs[b].n * cs[b].nf;
+        return ca > cb;
+    });
+}
+
+}  // namespace blsgpu
+
+// ------------------------------------------------------------------------------ search
+
+namespace {
+
+struct Copy {
+    void* dst;
+    const void* src;
+    size_t bytes;
+};
+
+// Merge copies whose sources and destinations both continue the previous copy.
+void push_copy(std::vector<Copy>& v, void* dst, const void* src, size_t bytes)
+{
+    if (!v.empty()) {
+        Copy& b = v.back();
+        if ((const char*)b.src + b.bytes == (const char*)src && (char*)b.dst + b.bytes == (char*)dst) {
+            b.bytes += bytes;
+            return;
+        }
+    }
+    v.push_back({dst, src, bytes});
+}
+
+size_t curve_bytes(const bls_plan_impl* P, const CurveSpec& c, bool host_spec)
+{
+    size_t n2 = (size_t)((c.n + 1) & ~1);
+    size_t b = n2 * (16 + 8) + (size_t)c.nf * 8 + sizeof(CurveDesc) + 64;
+    if (!c.t_dev) b += (size_t)c.n * 8;
+    if (!c.y_dev) b += (size_t)c.n * 4;
+    if (c.dy && !c.dy_dev) b += (size_t)c.n * 4;
+    if (c.freqs && !c.f_dev) b += (size_t)c.nf * 8;
+    if (host_spec) b += (size_t)c.nf * 4;
+    if (P->d.algo == BLS_ALGO_PLAIN_F64) b += n2 * 16;
+    return b;
+}
+
+void to_peak(const DevPeak& s, bls_peak* d)
+{
+    d->best_j = s.j;
+    d->i1 = s.i1;
+    d->k = s.k;
+    d->pad_ = 0;
+    d->freq = s.freq;
+    d->period = s.period;
+    d->epoch = s.epoch;
+    d->duration = s.duration;
+    d->depth = s.depth;
+    d->snr = s.snr;
+    d->sr = s.sr;
+    d->power = s.power;
+}
+
+// One launch group: curves [g0, g1) of `specs`.  Writes peaks to out (host) and optionally
+// SR spectra (per-frequency result dump for diagnostics into res_dump).
+bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int g0, int g1,
+                     const std::vector<long long>& spec_off, bls_peak* out, float* spectrum,
+                     bool spectrum_dev, FreqResult* res_dump)
+{
+    const int nc = g1 - g0;
+    const int topk = P->d.topk;
+    cudaStream_t st = P->stream;
+    cudaError_t e;
+
+    // ---- layout
+    std::vector<long long> pt_off(nc), res_off(nc), raw_off(nc), f_off(nc);
+    long long npts = 0, nres = 0, nraw = 0, nfr = 0;
+    bool any_dy = false;
+    for (int c = 0; c < nc; ++c) {
+        const CurveSpec& s = specs[g0 + c];
+        pt_off[c] = npts;
+        npts += (s.n + 1) & ~1;
+        res_off[c] = nres;
+        nres += s.nf;
+        raw_off[c] = nraw;
+        nraw += s.n;
+        f_off[c] = nfr;
+        if (s.freqs && !s.f_dev) nfr += s.nf;
+        any_dy = any_dy || s.dy;
+    }
+    npts += 2;  // slack so a staged chunk never reads past the pool
+
+    // ---- buffers
+    if ((e = P->pts.ensure((size_t)npts * sizeof(float4))) != cudaSuccess) return cuda_fail(e, "allocating points");
+    if ((e = P->dt64.ensure((size_t)npts * sizeof(double))) != cudaSuccess) return cuda_fail(e, "allocating dt");
+    if ((e = P->res.ensure((size_t)nres * sizeof(FreqResult))) != cudaSuccess) return cuda_fail(e, "allocating results");
+    if ((e = P->raw_t.ensure((size_t)nraw * 8)) != cudaSuccess) return cuda_fail(e, "allocating staging");
+    if ((e = P->raw_y.ensure((size_t)nraw * 4)) != cudaSuccess) return cuda_fail(e, "allocating staging");
+    if (any_dy && (e = P->raw_dy.ensure((size_t)nraw * 4)) != cudaSuccess) return cuda_fail(e, "allocating staging");
+    if (nfr && (e = P->raw_f.ensure((size_t)nfr * 8)) != cudaSuccess) return cuda_fail(e, "allocating staging");
+    if ((e = P->cdesc.ensure((size_t)nc * sizeof(CurveDesc))) != cudaSuccess) return cuda_fail(e, "allocating descriptors");
+    if ((e = P->peaks.ensure((size_t)nc * topk * sizeof(DevPeak))) != cudaSuccess) return cuda_fail(e, "allocating peaks");
+    if ((e = P->err.ensure(64)) != cudaSuccess) return cuda_fail(e, "allocating error word");
+    if (spectrum && !spectrum_dev && (e = P->spec.ensure((size_t)nres * 4)) != cudaSuccess)
+        return cuda_fail(e, "allocating spectrum");
+    if ((e = P->h_cdesc.ensure((size_t)nc * sizeof(CurveDesc))) != cudaSuccess) return cuda_fail(e, "pinned descriptors");
+    if ((e = P->h_peaks.ensure((size_t)nc * topk * sizeof(DevPeak))) != cudaSuccess) return cuda_fail(e, "pinned peaks");
+    if ((e = P->h_err.ensure(64)) != cudaSuccess) return cuda_fail(e, "pinned error word");
+    if (P->d.algo == BLS_ALGO_PLAIN_F64) {
+        if ((e = P->w64.ensure((size_t)npts * 8)) != cudaSuccess) return cuda_fail(e, "allocating w64");
+        if ((e = P->wx64.ensure((size_t)npts * 8)) != cudaSuccess) return cuda_fail(e, "allocating wx64");
+    }
+
+    // ---- inputs: copy host arrays into staging (merged when contiguous), point at device ones
+    std::vector<Copy> copies, cy, cdy, cf;   // one list per array so contiguous runs merge
+    CurveDesc* hd = P->h_cdesc.as<CurveDesc>();
+    for (int c = 0; c < nc; ++c) {
+        const CurveSpec& s = specs[g0 + c];
+        CurveDesc d;
+        memset(&d, 0, sizeof(d));
+        if (s.t_dev) d.t = s.t;
+        else { d.t = P->raw_t.as<double>() + raw_off[c]; push_copy(copies, (void*)d.t, s.t, (size_t)s.n * 8); }
+        if (s.y_dev) d.y = s.y;
+        else { d.y = P->raw_y.as<float>() + raw_off[c]; push_copy(cy, (void*)d.y, s.y, (size_t)s.n * 4); }
+        if (!s.dy) d.dy = nullptr;
+        else if (s.dy_dev) d.dy = s.dy;
+        else { d.dy = P->raw_dy.as<float>() + raw_off[c]; push_copy(cdy, (void*)d.dy, s.dy, (size_t)s.n * 4); }
+        if (!s.freqs) d.freqs = nullptr;
+        else if (s.f_dev) d.freqs = s.freqs;
+        else { d.freqs = P->raw_f.as<double>() + f_off[c]; push_copy(cf, (void*)d.freqs, s.freqs, (size_t)s.nf * 8); }
+        d.pts = P->pts.as<float4>() + pt_off[c];
+        d.dt64 = P->dt64.as<double>() + pt_off[c];
+        d.res = P->res.as<FreqResult>() + res_off[c];
+        d.pt_off = pt_off[c];
+        d.spec_off = spectrum_dev ? spec_off[g0 + c] : res_off[c];
+        d.fmin = s.fmin;
+        d.df = s.df;
+        d.n = s.n; d.nf = s.nf; d.nb = s.nb; d.kmin = s.kmin; d.kmax = s.kmax;
+        d.T = 0;
+        hd[c] = d;
+    }
+    // fold classes (block size per nb)
+    std::vector<FoldGeom> geoms;
+    std::vector<std::vector<int>> cls;
+    if (P->d.algo == BLS_ALGO_TILED) {
+        for (int c = 0; c < nc; ++c) {
+            FoldGeom g;
+            bls_status s = fold_geometry(P, specs[g0 + c].nb, &g);
+            if (s != BLS_OK) return s;
+            int k = -1;
+            for (size_t q = 0; q < geoms.size(); ++q)
+                if (geoms[q].T == g.T && geoms[q].stride == g.stride && geoms[q].chunk == g.chunk) { k = (int)q; break; }
+            if (k < 0) { geoms.push_back(g); cls.emplace_back(); k = (int)geoms.size() - 1; }
+            else geoms[k].smem = std::max(geoms[k].smem, g.smem);
+            cls[k].push_back(c);
+            hd[c].T = g.T;
+        }
+    }
+    copies.insert(copies.end(), cy.begin(), cy.end());
+    copies.insert(copies.end(), cdy.begin(), cdy.end());
+    copies.insert(copies.end(), cf.begin(), cf.end());
+    for (const Copy& cp : copies)
+        if ((e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyDefault, st)) != cudaSuccess)
+            return cuda_fail(e, "copying inputs");
+    if ((e = cudaMemcpyAsync(P->cdesc.p, hd, (size_t)nc * sizeof(CurveDesc), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "copying descriptors");
+    if ((e = cudaMemsetAsync(P->err.p, 0, 64, st)) != cudaSuccess) return cuda_fail(e, "clearing error word");
+
+    // ---- a1 prep
+    const bool prof = P->ev[0] != nullptr;
+    uint64_t launches = 0, fold_launches = 0;
+    if (prof) cudaEventRecord(P->ev[0], st);
+    ++launches;
+    if ((e = launch_prep(P->cdesc.as<CurveDesc>(), nullptr, nc, P->err.as<int>(), st)) != cudaSuccess)
+        return cuda_fail(e, "prep launch");
+
+    // ---- a2-a6 fold, bin, sweep
+    if (prof) cudaEventRecord(P->ev[1], st);
+    if (P->d.algo == BLS_ALGO_TILED) {
+        // work lists of all classes back to back
+        size_t nr = 0;
+        for (auto& v : cls) nr += v.size();
+        if ((e = P->ranges.ensure(nr * sizeof(TileRange))) != cudaSuccess) return cuda_fail(e, "allocating work list");
+        if ((e = P->prefix.ensure((nr + cls.size()) * sizeof(long long))) != cudaSuccess) return cuda_fail(e, "allocating work list");
+        if ((e = P->counter.ensure(cls.size() * sizeof(int) + 64)) != cudaSuccess) return cuda_fail(e, "allocating counters");
+        if ((e = P->h_ranges.ensure(nr * sizeof(TileRange))) != cudaSuccess) return cuda_fail(e, "pinned work list");
+        if ((e = P->h_prefix.ensure((nr + cls.size()) * sizeof(long long))) != cudaSuccess) return cuda_fail(e, "pinned work list");
+        TileRange* hr = P->h_ranges.as<TileRange>();
+        long long* hp = P->h_prefix.as<long long>();
+        std::vector<size_t> r0(cls.size()), p0(cls.size());
+        std::vector<long long> totals(cls.size());
+        size_t rr = 0, pp = 0;
+        std::vector<CurveSpec> local(specs.begin() + g0, specs.begin() + g1);
+        for (size_t q = 0; q < cls.size(); ++q) {
+            std::vector<int> ord;
+            order_by_cost(local, cls[q], &ord);
+            r0[q] = rr;
+            p0[q] = pp;
+            long long acc = 0;
+            for (int c : ord) {
+                hr[rr++] = TileRange{c, 0};
+                hp[pp++] = acc;
+                acc += (local[c].nf + geoms[q].T - 1) / geoms[q].T;
+            }
+            hp[pp++] = acc;
+            totals[q] = acc;
+        }
+        if ((e = cudaMemcpyAsync(P->ranges.p, hr, nr * sizeof(TileRange), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "copying work list");
+        if ((e = cudaMemcpyAsync(P->prefix.p, hp, pp * sizeof(long long), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "copying work list");
+        if ((e = cudaMemsetAsync(P->counter.p, 0, cls.size() * sizeof(int), st)) != cudaSuccess)
+            return cuda_fail(e, "clearing counters");
+        for (size_t q = 0; q < cls.size(); ++q) {
+            FoldParams fp;
+            fp.curves = P->cdesc.as<CurveDesc>();
+            fp.ranges = P->ranges.as<TileRange>() + r0[q];
+            fp.prefix = P->prefix.as<long long>() + p0[q];
+            fp.nranges = (int)cls[q].size();
+            fp.total = totals[q];
+            fp.counter = P->counter.as<int>() + q;
+            fp.err = P->err.as<int>();
+            fp.chunk = geoms[q].chunk;
+            fp.stride = geoms[q].stride;
+            const int bps = fold_blocks_per_sm(geoms[q].T, geoms[q].smem, P->d.phase,
+                                               P->d.sum == BLS_SUM_KAHAN, P->d.sign);
+            long long grid = (long long)P->sm_count * bps;
+            if (grid > totals[q]) grid = totals[q];
+            if (grid < 1) grid = 1;
+            if ((e = launch_fold_sweep(fp, geoms[q].T, (int)grid, P->d.phase, P->d.sum == BLS_SUM_KAHAN,
+                                       P->d.sign, geoms[q].smem, st)) != cudaSuccess)
+                return cuda_fail(e, "fold-sweep launch");
+            ++launches;
+            ++fold_launches;
+        }
+    } else {
+        if ((e = launch_prep_f64(P->cdesc.as<CurveDesc>(), nc, P->w64.as<double>(), P->wx64.as<double>(), st)) != cudaSuccess)
+            return cuda_fail(e, "prep launch");
+        ++launches;
+        size_t hb = 0;
+        for (int c = 0; c < nc; ++c) hb = std::max(hb, (size_t)2 * specs[g0 + c].nb * specs[g0 + c].nf * 8);
+        if ((e = P->plain_hist.ensure(hb)) != cudaSuccess) return cuda_fail(e, "allocating baseline histograms");
+        for (int c = 0; c < nc; ++c) {
+            const CurveSpec& s = specs[g0 + c];
+            if ((e = launch_plain_f64(P->cdesc.as<CurveDesc>() + c, P->w64.as<double>(), P->wx64.as<double>(),
+                                      s.nf, P->plain_hist.as<double>(), P->d.sign, st)) != cudaSuccess)
+                return cuda_fail(e, "baseline launch");
+            ++launches;
+            ++fold_launches;
+        }
+    }
+
+    // ---- a7 reduce
+    ReduceParams rp;
+    rp.curves = P->cdesc.as<CurveDesc>();
+    rp.slots = nullptr;
+    rp.peaks = P->peaks.as<DevPeak>();
+    rp.topk = topk;
+    rp.sign = P->d.sign;
+    float* dev_spec = nullptr;
+    if (spectrum) dev_spec = spectrum_dev ? spectrum : P->spec.as<float>();
+    rp.spectrum = dev_spec;
+    if (prof) cudaEventRecord(P->ev[2], st);
+    if ((e = launch_reduce(rp, nc, st)) != cudaSuccess) return cuda_fail(e, "reduce launch");
+    ++launches;
+    if (prof) cudaEventRecord(P->ev[3], st);
+
+    // ---- results
+    if ((e = cudaMemcpyAsync(P->h_peaks.p, P->peaks.p, (size_t)nc * topk * sizeof(DevPeak),
+                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "copying peaks");
+    if (spectrum && !spectrum_dev)
+        if ((e = cudaMemcpyAsync(spectrum + spec_off[g0], P->spec.p, (size_t)nres * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(e, "copying spectrum");
+    if (res_dump)
+        if ((e = cudaMemcpyAsync(res_dump, P->res.p, (size_t)nres * sizeof(FreqResult), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(e, "copying per-frequency results");
+    if ((e = cudaMemcpyAsync(P->h_err.p, P->err.p, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "copying error word");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "search");
+    if (prof) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        cudaEventElapsedTime(&a, P->ev[0], P->ev[1]);
+        cudaEventElapsedTime(&b, P->ev[1], P->ev[2]);
+        cudaEventElapsedTime(&c, P->ev[2], P->ev[3]);
+        P->prof.prep_ms += a;
+        P->prof.fold_ms += b;
+        P->prof.reduce_ms += c;
+    }
+    P->prof.searches += 1;
+    P->prof.kernel_launches += launches;
+    P->prof.fold_launches += fold_launches;
+    int errw = *P->h_err.as<int>();
+    if (errw & kErrInput)
+        return set_error(BLS_ERR_INVALID, "a curve has a non-finite time or flux, a non-positive or non-finite error, "
+                                          "or a non-positive frequency (device check)");
+    if (errw) return set_error(BLS_ERR_INTERNAL, "device consistency check failed (code %d)", errw);
+    const DevPeak* hpk = P->h_peaks.as<DevPeak>();
+    for (int c = 0; c < nc; ++c)
+        for (int q = 0; q < topk; ++q) to_peak(hpk[(size_t)c * topk + q], &out[(size_t)(g0 + c) * topk + q]);
+    return BLS_OK;
+}
+
+bls_status search_impl(bls_plan_impl* P, const bls_curve* curves, int ncurves, bls_peak* out,
+                       float* spectrum, FreqResult* res_dump)
+{
+    if (ncurves < 0) return set_error(BLS_ERR_INVALID, "ncurves = %d", ncurves);
+    if (ncurves == 0) return BLS_OK;
+    if (!curves || !out) return set_error(BLS_ERR_INVALID, "NULL curves or out");
+    cudaError_t e = cudaSetDevice(P->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    std::vector<CurveSpec> specs(ncurves);
+    for (int c = 0; c < ncurves; ++c) {
+        bls_status s = resolve_curve(P, &curves[c], c, &specs[c]);
+        if (s != BLS_OK) return s;
+    }
+    const bool spec_dev = spectrum && is_device_ptr(spectrum);
+    std::vector<long long> spec_off(ncurves + 1, 0);
+    for (int c = 0; c < ncurves; ++c) spec_off[c + 1] = spec_off[c] + specs[c].nf;
+    // launch groups by memory budget and curve cap
+    const int cap = P->d.max_curves_per_launch > 0 ? P->d.max_curves_per_launch : ncurves;
+    int g0 = 0;
+    while (g0 < ncurves) {
+        size_t bytes = 0;
+        int g1 = g0;
+        while (g1 < ncurves && g1 - g0 < cap) {
+            size_t b = curve_bytes(P, specs[g1], spectrum && !spec_dev);
+            if (g1 > g0 && bytes + b > P->budget) break;
+            bytes += b;
+            ++g1;
+        }
+        if (bytes > P->budget)
+            return set_error(BLS_ERR_NOMEM, "curve %d needs %zu B, over the plan's device budget of %zu B", g0,
+                             bytes, P->budget);
+        bls_status s = run_group(P, specs, g0, g1, spec_off, out, spectrum, spec_dev, res_dump ? res_dump + spec_off[g0] : nullptr);
+        if (s != BLS_OK) return s;
+        g0 = g1;
+    }
+    return BLS_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char* bls_last_error(void) { return g_last_error.c_str(); }
+
+bls_status bls_kminmax(int nb, double qmin, double qmax, int* kmin, int* kmax)
+{
+    if (!kmin || !kmax) return set_error(BLS_ERR_INVALID, "NULL output");
+    return kminmax_impl(nb, qmin, qmax, kmin, kmax);
+}
+
+bls_status bls_plan_create(const bls_plan_desc* desc, void* cuda_stream, bls_plan** out)
+{
+    if (!desc || !out) return set_error(BLS_ERR_INVALID, "NULL descriptor or output");
+    *out = nullptr;
+    bls_plan_desc d = *desc;
+    if (d.nb < 2) return set_error(BLS_ERR_INVALID, "nb = %d, need nb >= 2", d.nb);
+    if (d.kmin > 0 || d.kmax > 0) {
+        if (d.kmin < 1 || d.kmax < d.kmin || d.kmax > d.nb)
+            return set_error(BLS_ERR_INVALID, "need 1 <= kmin <= kmax <= nb (kmin=%d kmax=%d nb=%d)", d.kmin, d.kmax, d.nb);
+    } else {
+        int a, b;
+        bls_status s = kminmax_impl(d.nb, d.qmin, d.qmax, &a, &b);
+        if (s != BLS_OK) return s;
+    }
+    if (d.topk < 1 || d.topk > kMaxTopK) return set_error(BLS_ERR_INVALID, "topk = %d, need 1..%d", d.topk, kMaxTopK);
+    if (d.phase < 0 || d.phase > 2) return set_error(BLS_ERR_INVALID, "phase = %d", d.phase);
+    if (d.sum < 0 || d.sum > 1) return set_error(BLS_ERR_INVALID, "sum = %d", d.sum);
+    if (d.sign < 0 || d.sign > 1) return set_error(BLS_ERR_INVALID, "sign = %d", d.sign);
+    if (d.algo < 0 || d.algo > 1) return set_error(BLS_ERR_INVALID, "algo = %d", d.algo);
+    if (d.freqs_per_block < 0 || d.freqs_per_block > fold_sweep_max_threads() || (d.freqs_per_block % 16) != 0)
+        return set_error(BLS_ERR_INVALID, "freqs_per_block = %d, need a multiple of 16 up to %d", d.freqs_per_block,
+                         fold_sweep_max_threads());
+    if (d.point_chunk < 0 || d.point_chunk > 4096) return set_error(BLS_ERR_INVALID, "point_chunk = %d", d.point_chunk);
+    if (d.max_curves_per_launch < 0 || d.max_active_requests < 0 || d.step_point_freqs < 0)
+        return set_error(BLS_ERR_INVALID, "negative limit");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    int sms = 0, optin = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail(e, "device attributes");
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return cuda_fail(e, "device attributes");
+    bls_plan* P = new (std::nothrow) bls_plan();
+    if (!P) return set_error(BLS_ERR_NOMEM, "plan allocation");
+    P->d = d;
+    P->device = dev;
+    P->sm_count = sms;
+    P->smem_optin = (size_t)optin - 1024;   // static shared memory of the kernels
+    if (cuda_stream) {
+        P->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+            delete P;
+            return cuda_fail(e, "stream creation");
+        }
+        P->own_stream = true;
+    }
+    if (d.max_device_bytes > 0) {
+        P->budget = d.max_device_bytes;
+    } else {
+        size_t fr = 0, tot = 0;
+        if ((e = cudaMemGetInfo(&fr, &tot)) != cudaSuccess) {
+            if (P->own_stream) cudaStreamDestroy(P->stream);
+            delete P;
+            return cuda_fail(e, "cudaMemGetInfo");
+        }
+        P->budget = fr / 2;
+    }
+    for (int q = 0; q < 4; ++q)
+        if (cudaEventCreate(&P->ev[q]) != cudaSuccess) { cudaGetLastError(); P->ev[0] = nullptr; break; }
+    if (d.algo == BLS_ALGO_TILED) {
+        FoldGeom g;
+        bls_status s = fold_geometry(P, d.nb, &g);
+        if (s != BLS_OK) {
+            if (P->own_stream) cudaStreamDestroy(P->stream);
+            delete P;
+            return s;
+        }
+    }
+    *out = P;
+    return BLS_OK;
+}
+
+void bls_plan_destroy(bls_plan* P)
+{
+    if (!P) return;
+    server_destroy(P);
+    cudaSetDevice(P->device);
+    if (P->stream) cudaStreamSynchronize(P->stream);
+    DevBuf* bufs[] = {&P->raw_t, &P->raw_y, &P->raw_dy, &P->raw_f, &P->pts, &P->dt64, &P->w64,
+                      &P->wx64, &P->cdesc, &P->ranges, &P->prefix, &P->counter, &P->err, &P->res,
+                      &P->peaks, &P->spec, &P->plain_hist, &P->jsbuf, &P->binsbuf};
+    for (DevBuf* b : bufs) b->release();
+    HostBuf* hb[] = {&P->h_cdesc, &P->h_ranges, &P->h_prefix, &P->h_peaks, &P->h_err};
+    for (HostBuf* b : hb) b->release();
+    for (int q = 0; q < 4; ++q)
+        if (P->ev[q]) cudaEventDestroy(P->ev[q]);
+    if (P->own_stream) cudaStreamDestroy(P->stream);
+    delete P;
+}
+
+bls_status bls_profile_get(bls_plan* P, bls_profile* out, int reset)
+{
+    if (!P || !out) return set_error(BLS_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lk(P->mu);
+    *out = P->prof;
+    if (reset) P->prof = bls_profile{};
+    return BLS_OK;
+}
+
+bls_status bls_search(bls_plan* P, const bls_curve* curves, int ncurves, bls_peak* out, float* spectrum)
+{
+    if (!P) return set_error(BLS_ERR_INVALID, "NULL plan");
+    std::lock_guard<std::mutex> lk(P->mu);
+    return search_impl(P, curves, ncurves, out, spectrum, nullptr);
+}
+
+bls_status bls_debug_powers(bls_plan* P, const bls_curve* curve, float* power_out, int* i1_out, int* k_out)
+{
+    if (!P || !curve || !power_out || !i1_out || !k_out) return set_error(BLS_ERR_INVALID, "NULL argument");
+    if (curve->nf < 1) return set_error(BLS_ERR_INVALID, "nf = %d", curve->nf);
+    std::lock_guard<std::mutex> lk(P->mu);
+    std::vector<FreqResult> res((size_t)curve->nf);
+    std::vector<bls_peak> pk((size_t)P->d.topk);
+    bls_status s = search_impl(P, curve, 1, pk.data(), nullptr, res.data());
+    if (s != BLS_OK) return s;
+    for (int j = 0; j < curve->nf; ++j) {
+        power_out[j] = res[j].P;
+        i1_out[j] = (int)(res[j].box >> 16);
+        k_out[j] = (int)(res[j].box & 0xffffu);
+    }
+    return BLS_OK;
+}
+
+bls_status bls_debug_fold(bls_plan* P, const bls_curve* curve, const int* js, int nj, int* bins_out)
+{
+    if (!P || !curve || !js || !bins_out || nj < 1) return set_error(BLS_ERR_INVALID, "bad argument");
+    std::lock_guard<std::mutex> lk(P->mu);
+    cudaError_t e = cudaSetDevice(P->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    CurveSpec s;
+    bls_status st = resolve_curve(P, curve, 0, &s);
+    if (st != BLS_OK) return st;
+    for (int q = 0; q < nj; ++q)
+        if (js[q] < 0 || js[q] >= s.nf) return set_error(BLS_ERR_INVALID, "js[%d] = %d out of range", q, js[q]);
+    // prepare the curve exactly as a search does, then fold with the search's device code
+    std::vector<CurveSpec> specs{s};
+    std::vector<long long> off{0, s.nf};
+    std::vector<bls_peak> pk((size_t)P->d.topk);
+    bls_plan_desc saved = P->d;
+    st = run_group(P, specs, 0, 1, off, pk.data(), nullptr, false, nullptr);
+    P->d = saved;
+    if (st != BLS_OK) return st;
+    if ((e = P->jsbuf.ensure((size_t)nj * 4)) != cudaSuccess) return cuda_fail(e, "allocating");
+    if ((e = P->binsbuf.ensure((size_t)nj * s.n * 4)) != cudaSuccess) return cuda_fail(e, "allocating");
+    if ((e = cudaMemcpyAsync(P->jsbuf.p, js, (size_t)nj * 4, cudaMemcpyHostToDevice, P->stream)) != cudaSuccess)
+        return cuda_fail(e, "copy");
+    if ((e = launch_debug_fold(P->cdesc.as<CurveDesc>(), P->jsbuf.as<int>(), nj, P->d.phase,
+                               P->binsbuf.as<int>(), P->stream)) != cudaSuccess)
+        return cuda_fail(e, "debug fold launch");
+    if ((e = cudaMemcpyAsync(bins_out, P->binsbuf.p, (size_t)nj * s.n * 4, cudaMemcpyDeviceToHost, P->stream)) != cudaSuccess)
+        return cuda_fail(e, "copy");
+    if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "debug fold");
+    return BLS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// bls_internal.h -- device data layout and kernel launchers of the B300 BLS library.
+//
+// HBM layout (one search launch):
+//   CurveDesc[ncurves]          per-curve scalars and pointers (inputs, prepared points,
+//                               per-frequency results)
+//   float4 pts[n]               prepared points (dt_hi, dt_lo, w, w*x), 16 B per point
+//   double dt64[n]              exact FP64 time offsets, read only by the exact re-fold
+//   FreqResult res[nf]          per-frequency best box (P as FP32, packed i1/k)
+//   DevPeak peaks[ncurves*topk] reduced peaks (FP64)
+// The batched search packs all curves of a launch into shared pools (curves start on even
+// point offsets, so every per-curve slice is 16-byte aligned); the server gives each
+// request its own allocation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace blsgpu {
+
+constexpr int kMaxTopK = 16;
+constexpr int kPhaseDF32 = 0, kPhaseF64 = 1, kPhaseF32 = 2;
+
+struct FreqResult {
+    float P;        // best box power at this frequency (FP32)
+    uint32_t box;   // i1 << 16 | k
+};
+
+struct CurveDesc {
+    const double* t;       // raw times (device)
+    const float* y;        // raw fluxes (device)
+    const float* dy;       // raw errors (device) or nullptr: unit weights
+    const double* freqs;   // explicit grid (device) or nullptr: uniform grid
+    float4* pts;           // prepared points of this curve
+    double* dt64;          // exact time offsets of this curve
+    FreqResult* res;       // per-frequency results of this curve
+    long long pt_off;      // first point in the pooled arrays (baseline path)
+    long long spec_off;    // first slot of this curve in a spectrum output
+    double fmin, df;       // uniform grid
+    double t_ref, W, ybar, sumwx2, dtmax;  // written by the prep kernel
+    int n, nf, nb, kmin, kmax;
+    int T;                 // frequencies per tile of this curve (block size of its class)
+};
+
+// A run of frequency tiles of one curve processed by one fold-sweep launch.
+struct TileRange {
+    int curve;
+    int tile_lo;
+};
+
+struct DevPeak {
+    int j, i1, k, pad;
+    double freq, period, epoch, duration, depth, snr, sr, power;
+};
+
+// Error bits written by device code into the plan's error word.
+enum : int {
+    kErrInput = 1,      // non-finite time/flux, non-positive error, bad frequency
+    kErrBounds = 2,     // a device-side index check failed
+};
+
+struct FoldParams {
+    const CurveDesc* curves;
+    const TileRange* ranges;
+    const long long* prefix;   // prefix[r] = tiles before range r; prefix[nranges] = total
+    int nranges;
+    long long total;
+    int* counter;              // work counter (zeroed before the launch)
+    int* err;
+    int chunk;                 // points per staged chunk (even)
+    int stride;                // histogram stride in entries (multiple of 16, >= blockDim.x)
+};
+
+struct ReduceParams {
+    const CurveDesc* curves;
+    const int* slots;          // curve of block b = slots[b] (nullptr: b)
+    DevPeak* peaks;            // peaks of block b at [b*topk, (b+1)*topk)
+    float* spectrum;           // optional (device): SR per frequency, at spec_off
+    int topk;
+    int sign;
+};
+
+// Shared memory a fold-sweep block needs.
+size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int kahan);
+
+cudaError_t launch_prep(CurveDesc* d_curves, const int* slots, int ncurves, int* err,
+                        cudaStream_t s);
+cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan,
+                              int sign, size_t smem, cudaStream_t s);
+cudaError_t launch_reduce(const ReduceParams& p, int ncurves, cudaStream_t s);
+cudaError_t launch_debug_fold(const CurveDesc* d_curve, const int* js, int nj, int phase,
+                              int* bins, cudaStream_t s);
+// Baseline: one curve, one thread per frequency, FP64 histograms in global scratch.
+cudaError_t launch_plain_f64(const CurveDesc* d_curve, const double* w64, const double* wx64,
+                             int nf, double* hist, int sign, cudaStream_t s);
+cudaError_t launch_prep_f64(const CurveDesc* d_curves, int ncurves, double* w64, double* wx64,
+                            cudaStream_t s);
+int fold_sweep_max_threads();
+int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign);
+
+}  // namespace blsgpu

@@ -1,0 +1,101 @@
+// bls_plan.h -- host-side plan object shared by the search path and the server.
+#pragma once
+
+#include <condition_variable>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdint>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bls.h"
+#include "bls_internal.h"
+
+namespace blsgpu {
+
+bls_status set_error(bls_status s, const char* fmt, ...);
+bls_status cuda_fail(cudaError_t e, const char* what);
+
+// Growable device allocation.  Growth frees the old block first.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t need);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Growable pinned host allocation.
+struct HostBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t need);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// A curve after argument resolution (host side).
+struct CurveSpec {
+    const double* t;
+    const float* y;
+    const float* dy;
+    const double* freqs;
+    int n, nf, nb, kmin, kmax;
+    double fmin, df;
+    bool t_dev, y_dev, dy_dev, f_dev;   // pointer lives on the device
+};
+
+// Launch geometry of one fold-sweep class (curves sharing a block size).
+struct FoldGeom {
+    int T;          // threads = frequencies per tile
+    int stride;     // histogram stride (multiple of 16, >= T)
+    int chunk;      // staged points per chunk
+    size_t smem;    // dynamic shared memory
+    int grid;       // persistent blocks
+};
+
+struct Server;
+
+struct bls_plan_impl {
+    bls_plan_desc d{};
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;
+
+    // search buffers (device)
+    DevBuf raw_t, raw_y, raw_dy, raw_f;   // staging of host inputs
+    DevBuf pts, dt64, w64, wx64;          // prepared points
+    DevBuf cdesc, ranges, prefix, counter, err;
+    DevBuf res, peaks, spec, plain_hist, jsbuf, binsbuf;
+    // host staging (pinned)
+    HostBuf h_cdesc, h_ranges, h_prefix, h_peaks, h_err;
+
+    // profiling (CUDA events around the kernel phases of a search)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bls_profile prof{};
+
+    std::mutex mu;                         // serialises search calls on this plan
+    Server* server = nullptr;            // created by the first bls_submit
+    std::mutex server_mu;
+};
+
+// Resolve and validate one curve against the plan (host checks only).
+bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* out);
+// Block size / stride / chunk / shared memory for a curve with nb bins.
+bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g);
+// Work-list order: curves by decreasing cost (n * nf), ties by index.
+void order_by_cost(const std::vector<CurveSpec>& cs, const std::vector<int>& idx,
+                   std::vector<int>* out);
+
+void server_destroy(bls_plan_impl* P);
+
+}  // namespace blsgpu
+
+struct bls_plan : blsgpu::bls_plan_impl {};

@@ -1,0 +1,84 @@
+"""The C-ABI library builds, loads and exports every symbol include/bls.h declares; the
+ctypes structs match the C layout; argument checks that need no GPU behave."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1112_1701_b300 import bls, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bls.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return bls.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bls_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("bls_plan_create", "bls_search", "bls_submit", "bls_poll",
+                     "bls_plan_destroy", "bls_last_error"):
+        assert required in names
+    assert set(names) == set(bls.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    out = subprocess.run(["nm", "-D", "--defined-only", bls.LIB_PATH], check=True,
+                         capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (bls_[a-z_]+)", out))
+    for name in declared_functions():
+        assert name in exported, name
+        assert hasattr(L, name)
+
+
+def test_struct_layout_matches_c(tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "bls.h"\n'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(bls_plan_desc),'
+        ' sizeof(bls_curve), sizeof(bls_peak), sizeof(bls_server_stats),'
+        ' offsetof(bls_peak, freq), offsetof(bls_curve, nb)); return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
+                   check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                           check=True).stdout.split()]
+    assert vals == [C.sizeof(bls.PlanDesc), C.sizeof(bls.CurveStruct),
+                    C.sizeof(bls.PeakStruct), C.sizeof(bls.ServerStats),
+                    bls.PeakStruct.freq.offset, bls.CurveStruct.nb.offset]
+
+
+def test_kminmax_matches_reading(L):
+    assert bls.kminmax(100, 0.01, 0.10) == (1, 10)
+    assert bls.kminmax(200, 0.005, 0.15) == (1, 30)
+    assert bls.kminmax(256, 0.005, 0.15) == (1, 39)
+    with pytest.raises(bls.BLSError) as ei:
+        bls.kminmax(1, 0.1, 0.2)
+    assert ei.value.status == bls.ERR_INVALID
+
+
+def test_kminmax_agrees_with_oracle(L):
+    import oracle
+    for nb in (2, 3, 10, 57, 100, 200, 256, 400, 1000):
+        for q0, q1 in ((0.001, 0.01), (0.005, 0.15), (0.01, 0.1), (0.3, 0.9), (0.05, 0.05)):
+            assert bls.kminmax(nb, q0, q1) == oracle.kminmax(nb, q0, q1)
+
+
+def test_plan_rejects_bad_descriptors_before_touching_cuda(L):
+    for kw in (dict(nb=1), dict(topk=0), dict(topk=99), dict(qmin=0.2, qmax=0.1),
+               dict(freqs_per_block=17), dict(kmin=5, kmax=2)):
+        with pytest.raises(bls.BLSError) as ei:
+            bls.Plan(**kw)
+        assert ei.value.status == bls.ERR_INVALID
+        assert bls.lib().bls_last_error()

@@ -116,6 +116,32 @@ def test_bruteforce_chi2(seed):
             assert (I1[q], K[q]) == arg
 
 
+def test_box_power_matches_bruteforce_for_every_box():
+    rng = np.random.default_rng(77)
+    n, nb = 10, 6
+    t = T0 + np.sort(rng.uniform(0, 3.0, n))
+    y = (1.0 + rng.normal(0, 0.1, n)).astype(np.float32)
+    dy = rng.uniform(0.5, 2.0, n).astype(np.float32)
+    dt, w, x, scal = oracle.prep(t, y, dy)
+    f = 1.37
+    b = oracle.bins(t, [f], nb)[0]
+    yy = y.astype(np.float64)
+    for i1 in range(nb):
+        for k in range(1, nb):
+            P, r, s = oracle.box(dt, w, x, f, nb, i1, k, sign=1)
+            inb = np.isin(b, [(i1 + m) % nb for m in range(k)])
+            assert r == pytest.approx(w[inb].sum(), abs=1e-15)
+            if 0 < r < 1:
+                A = np.stack([inb, ~inb], axis=1).astype(np.float64)
+                sq = np.sqrt(w)
+                coef, *_ = np.linalg.lstsq(A * sq[:, None], yy * sq, rcond=None)
+                chi2 = (w * (yy - A @ coef) ** 2).sum()
+                assert P == pytest.approx(scal[3] - chi2, abs=1e-12)
+    # the sweep's best box has the sweep's power
+    Pbest, i1b, kb, _, _ = oracle.power(dt, w, x, f, nb, 1, nb - 1, sign=1)
+    assert oracle.box(dt, w, x, f, nb, i1b, kb, sign=1)[0] == Pbest
+
+
 # ----------------------------------------------------------------------------- closed forms
 
 def test_constant_flux_zero_power():
