@@ -124,36 +124,42 @@ int oracle_bins(int n, const double* t, int nq, const double* f, int nb, int* bi
     return 0;
 }
 
-/* Phase histograms of one frequency: Hw[b] = sum w_i, Hx[b] = sum w_i x_i, point order. */
+/* Phase histograms of one frequency: Hw[b] = sum w_i, Hx[b] = sum w_i x_i, point order,
+ * and Hn[b] = number of points in bin b. */
 static void histogram(int n, const double* dt, const double* w, const double* x,
-                      double f, int nb, double* Hw, double* Hx)
+                      double f, int nb, double* Hw, double* Hx, int* Hn)
 {
-    for (int b = 0; b < nb; b++) { Hw[b] = 0.0; Hx[b] = 0.0; }
+    for (int b = 0; b < nb; b++) { Hw[b] = 0.0; Hx[b] = 0.0; Hn[b] = 0; }
     for (int i = 0; i < n; i++) {
         int b = oracle_fold(dt[i], f, nb);
         Hw[b] += w[i];
         Hx[b] += w[i] * x[i];
+        Hn[b] += 1;
     }
 }
 
 /* Box sweep of one histogram: every start i1 and width k, cyclic, sums taken bin by
- * bin from the start.  Reading: boxes with r <= 0 or r >= 1 are skipped; with
+ * bin from the start.  Reading: a box counts only when both levels of the step model
+ * are defined, i.e. it holds at least one point and leaves at least one out (0 < r < 1
+ * exactly); this is decided on point counts, not on the rounded weight sums.  With
  * sign = 0 only dips (s < 0) count; with sign = 1 both signs count.  The best box is
  * kept with a strict '>' while i1 and then k ascend, so equal powers resolve to the
  * smallest (i1, k); if no box has positive power the result is P = 0, (0, kmin). */
-static double sweep(int nb, int kmin, int kmax, int sign, const double* Hw,
-                    const double* Hx, int* bi1, int* bk)
+static double sweep(int n, int nb, int kmin, int kmax, int sign, const double* Hw,
+                    const double* Hx, const int* Hn, int* bi1, int* bk)
 {
     double best = 0.0;
     int b1 = 0, bkk = kmin;
     for (int i1 = 0; i1 < nb; i1++) {
         double r = 0.0, s = 0.0;
+        int cnt = 0;
         for (int k = 1; k <= kmax; k++) {
             int m = (i1 + k - 1) % nb;
             r += Hw[m];
             s += Hx[m];
+            cnt += Hn[m];
             if (k < kmin) continue;
-            if (!(r > 0.0) || !(r < 1.0)) continue;
+            if (cnt == 0 || cnt == n) continue;
             if (sign == 0 && !(s < 0.0)) continue;
             double P = (s * s) / (r * (1.0 - r));
             if (P > best) { best = P; b1 = i1; bkk = k; }
@@ -179,11 +185,13 @@ int oracle_power(int n, const double* dt, const double* w, const double* x, doub
 {
     if (n < 1 || nb < 2 || kmin < 1 || kmax < kmin || kmax > nb) return -1;
     double* H = (double*)malloc(sizeof(double) * 2 * (size_t)nb);
-    if (!H) return -2;
-    histogram(n, dt, w, x, f, nb, H, H + nb);
-    *P = sweep(nb, kmin, kmax, sign, H, H + nb, i1, k);
+    int* Hn = (int*)malloc(sizeof(int) * (size_t)nb);
+    if (!H || !Hn) { free(H); free(Hn); return -2; }
+    histogram(n, dt, w, x, f, nb, H, H + nb, Hn);
+    *P = sweep(n, nb, kmin, kmax, sign, H, H + nb, Hn, i1, k);
     box_sums(nb, H, H + nb, *i1, *k, r, s);
     free(H);
+    free(Hn);
     return 0;
 }
 
@@ -195,13 +203,17 @@ int oracle_box(int n, const double* dt, const double* w, const double* x, double
 {
     if (n < 1 || nb < 2 || i1 < 0 || i1 >= nb || k < 1 || k > nb) return -1;
     double* H = (double*)malloc(sizeof(double) * 2 * (size_t)nb);
-    if (!H) return -2;
-    histogram(n, dt, w, x, f, nb, H, H + nb);
+    int* Hn = (int*)malloc(sizeof(int) * (size_t)nb);
+    if (!H || !Hn) { free(H); free(Hn); return -2; }
+    histogram(n, dt, w, x, f, nb, H, H + nb, Hn);
     box_sums(nb, H, H + nb, i1, k, r, s);
+    int cnt = 0;
+    for (int m = 0; m < k; m++) cnt += Hn[(i1 + m) % nb];
     free(H);
+    free(Hn);
     double rr = *r, ss = *s;
     *P = 0.0;
-    if (rr > 0.0 && rr < 1.0 && (sign == 1 || ss < 0.0)) *P = (ss * ss) / (rr * (1.0 - rr));
+    if (cnt > 0 && cnt < n && (sign == 1 || ss < 0.0)) *P = (ss * ss) / (rr * (1.0 - rr));
     return 0;
 }
 
@@ -278,13 +290,14 @@ int oracle_bls(const oracle_curve* c, int sign, double* P, int* i1, int* k,
     if (rc) { free(p.dt); return rc; }
     int nb = c->nb, nf = c->nf;
     double* H = (double*)malloc(sizeof(double) * 2 * (size_t)nb);
+    int* Hn = (int*)malloc(sizeof(int) * (size_t)nb);
     double* Pl = P ? P : (double*)malloc(sizeof(double) * (size_t)nf);
     int* I1 = i1 ? i1 : (int*)malloc(sizeof(int) * (size_t)nf);
     int* K = k ? k : (int*)malloc(sizeof(int) * (size_t)nf);
     for (int j = 0; j < nf; j++) {
         double f = grid_freq(c, j);
-        histogram(p.n, p.dt, p.w, p.x, f, nb, H, H + nb);
-        Pl[j] = sweep(nb, c->kmin, c->kmax, sign, H, H + nb, &I1[j], &K[j]);
+        histogram(p.n, p.dt, p.w, p.x, f, nb, H, H + nb, Hn);
+        Pl[j] = sweep(p.n, nb, c->kmin, c->kmax, sign, H, H + nb, Hn, &I1[j], &K[j]);
     }
     if (topk > 0 && peaks) {
         int js[64];
@@ -294,7 +307,7 @@ int oracle_bls(const oracle_curve* c, int sign, double* P, int* i1, int* k,
             if (js[q] < 0) { memset(&peaks[q], 0, sizeof(oracle_peak)); peaks[q].j = -1; continue; }
             int j = js[q];
             double f = grid_freq(c, j), r, s;
-            histogram(p.n, p.dt, p.w, p.x, f, nb, H, H + nb);
+            histogram(p.n, p.dt, p.w, p.x, f, nb, H, H + nb, Hn);
             box_sums(nb, H, H + nb, I1[j], K[j], &r, &s);
             derive(&peaks[q], j, f, nb, I1[j], K[j], Pl[j], r, s, p.scal[0], p.scal[1]);
         }
@@ -303,6 +316,7 @@ int oracle_bls(const oracle_curve* c, int sign, double* P, int* i1, int* k,
     if (!i1) free(I1);
     if (!k) free(K);
     free(H);
+    free(Hn);
     free(p.dt);
     return 0;
 }
@@ -322,7 +336,8 @@ static void* many_worker(void* arg)
     int nbmax = 2;
     for (int c = 0; c < m->nc; c++) if (m->cv[c].nb > nbmax) nbmax = m->cv[c].nb;
     double* H = (double*)malloc(sizeof(double) * 2 * (size_t)nbmax);
-    if (!H) { atomic_store(&m->err, -2); return NULL; }
+    int* Hn = (int*)malloc(sizeof(int) * (size_t)nbmax);
+    if (!H || !Hn) { free(H); free(Hn); atomic_store(&m->err, -2); return NULL; }
     for (;;) {
         int it = atomic_fetch_add(&m->next, 1);
         if (it >= m->nitems) break;
@@ -332,12 +347,13 @@ static void* many_worker(void* arg)
         int j1 = j0 + m->chunk; if (j1 > cv->nf) j1 = cv->nf;
         for (int j = j0; j < j1; j++) {
             double f = grid_freq(cv, j);
-            histogram(p->n, p->dt, p->w, p->x, f, cv->nb, H, H + cv->nb);
-            m->Pc[c][j] = sweep(cv->nb, cv->kmin, cv->kmax, m->sign, H, H + cv->nb,
+            histogram(p->n, p->dt, p->w, p->x, f, cv->nb, H, H + cv->nb, Hn);
+            m->Pc[c][j] = sweep(p->n, cv->nb, cv->kmin, cv->kmax, m->sign, H, H + cv->nb, Hn,
                                 &m->I1c[c][j], &m->Kc[c][j]);
         }
     }
     free(H);
+    free(Hn);
     return NULL;
 }
 
@@ -392,18 +408,20 @@ int oracle_bls_many(int nc, const oracle_curve* cv, int sign, int nthreads,
         for (int c = 0; c < nc; c++) {
             const oracle_curve* q = &cv[c];
             double* H = (double*)malloc(sizeof(double) * 2 * (size_t)q->nb);
+            int* Hn = (int*)malloc(sizeof(int) * (size_t)q->nb);
             top_peaks(q->nf, m.Pc[c], kk, js);
             for (int e = 0; e < kk; e++) {
                 oracle_peak* pk = &peaks[(size_t)c * topk + e];
                 if (js[e] < 0) { memset(pk, 0, sizeof(*pk)); pk->j = -1; continue; }
                 int j = js[e];
                 double f = grid_freq(q, j), r, s;
-                histogram(m.pp[c].n, m.pp[c].dt, m.pp[c].w, m.pp[c].x, f, q->nb, H, H + q->nb);
+                histogram(m.pp[c].n, m.pp[c].dt, m.pp[c].w, m.pp[c].x, f, q->nb, H, H + q->nb, Hn);
                 box_sums(q->nb, H, H + q->nb, m.I1c[c][j], m.Kc[c][j], &r, &s);
                 derive(pk, j, f, q->nb, m.I1c[c][j], m.Kc[c][j], m.Pc[c][j], r, s,
                        m.pp[c].scal[0], m.pp[c].scal[1]);
             }
             free(H);
+            free(Hn);
         }
     }
     for (int c = 0; c < nc; c++) {

@@ -25,6 +25,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["bls_kernels.cu"]
 CPP_SOURCES = ["bls_api.cpp", "bls_server.cpp"]
+PROBES_SRC = "probes.cu"
+PROBES = os.path.join(PKG, "bls_probes")
 
 
 def _headers():
@@ -71,6 +73,12 @@ def build(force: bool = False) -> str:
         cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
+    src = os.path.join(CSRC, PROBES_SRC)
+    if force or _stale(PROBES, [src]):
+        tmp = PROBES + f".tmp{os.getpid()}"
+        subprocess.run([NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-o", tmp, src],
+                       check=True)
+        os.replace(tmp, PROBES)
     return LIB
 
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 
@@ -121,7 +122,7 @@ bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, 
         bls_status s = kminmax_impl(o->nb, qmin, qmax, &o->kmin, &o->kmax);
         if (s != BLS_OK) return set_error(s, "curve %d: %s", index, bls_last_error());
     }
-    if (o->nb > 65535) return set_error(BLS_ERR_INVALID, "curve %d: nb = %d exceeds 65535", index, o->nb);
+    if (o->nb > 4096) return set_error(BLS_ERR_INVALID, "curve %d: nb = %d exceeds 4096", index, o->nb);
     o->t_dev = is_device_ptr(c->t);
     o->y_dev = is_device_ptr(c->y);
     o->dy_dev = c->dy ? is_device_ptr(c->dy) : false;
@@ -149,17 +150,17 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g)
     const int kahan = P->d.sum == BLS_SUM_KAHAN;
     const size_t esz = kahan ? 16 : 8;
     const int maxT = fold_sweep_max_threads();
-    g->chunk = P->d.point_chunk > 0 ? ((P->d.point_chunk + 1) & ~1) : 256;
-    const size_t stage = (size_t)2 * g->chunk * 24;
-    const size_t avail = P->smem_optin > stage + 64 ? P->smem_optin - stage - 64 : 0;
-    int T;
-    if (P->d.freqs_per_block > 0) {
-        T = P->d.freqs_per_block;
-    } else {
+    // chunk: a multiple of 16 points; by default the larger of 512/256 that leaves the
+    // block size (frequencies per block) as large as 256 allows
+    auto tmax = [&](int chunk) {
+        const size_t stage = (size_t)2 * chunk * 24;
+        const size_t avail = P->smem_optin > stage + 64 ? P->smem_optin - stage - 64 : 0;
         size_t cap = avail / ((size_t)nb * esz);
-        T = (int)std::min<size_t>(cap, (size_t)256);
-        T &= ~15;
-    }
+        return (int)std::min<size_t>(cap, (size_t)maxT) & ~15;
+    };
+    if (P->d.point_chunk > 0) g->chunk = (P->d.point_chunk + 15) & ~15;
+    else g->chunk = tmax(512) >= tmax(256) ? 512 : 256;
+    int T = P->d.freqs_per_block > 0 ? P->d.freqs_per_block : tmax(g->chunk);
     if (T < 16) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", nb);
     if (T > maxT) T = maxT;
     g->T = T;
@@ -239,7 +240,7 @@ void to_peak(const DevPeak& s, bls_peak* d)
 // SR spectra (per-frequency result dump for diagnostics into res_dump).
 bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int g0, int g1,
                      const std::vector<long long>& spec_off, bls_peak* out, float* spectrum,
-                     bool spectrum_dev, FreqResult* res_dump)
+                     bool spectrum_dev, float* res_dump)
 {
     const int nc = g1 - g0;
     const int topk = P->d.topk;
@@ -267,7 +268,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     // ---- buffers
     if ((e = P->pts.ensure((size_t)npts * sizeof(float4))) != cudaSuccess) return cuda_fail(e, "allocating points");
     if ((e = P->dt64.ensure((size_t)npts * sizeof(double))) != cudaSuccess) return cuda_fail(e, "allocating dt");
-    if ((e = P->res.ensure((size_t)nres * sizeof(FreqResult))) != cudaSuccess) return cuda_fail(e, "allocating results");
+    if ((e = P->res.ensure((size_t)nres * sizeof(float))) != cudaSuccess) return cuda_fail(e, "allocating results");
     if ((e = P->raw_t.ensure((size_t)nraw * 8)) != cudaSuccess) return cuda_fail(e, "allocating staging");
     if ((e = P->raw_y.ensure((size_t)nraw * 4)) != cudaSuccess) return cuda_fail(e, "allocating staging");
     if (any_dy && (e = P->raw_dy.ensure((size_t)nraw * 4)) != cudaSuccess) return cuda_fail(e, "allocating staging");
@@ -304,7 +305,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         else { d.freqs = P->raw_f.as<double>() + f_off[c]; push_copy(cf, (void*)d.freqs, s.freqs, (size_t)s.nf * 8); }
         d.pts = P->pts.as<float4>() + pt_off[c];
         d.dt64 = P->dt64.as<double>() + pt_off[c];
-        d.res = P->res.as<FreqResult>() + res_off[c];
+        d.res = P->res.as<float>() + res_off[c];
         d.pt_off = pt_off[c];
         d.spec_off = spectrum_dev ? spec_off[g0 + c] : res_off[c];
         d.fmin = s.fmin;
@@ -431,6 +432,13 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     rp.peaks = P->peaks.as<DevPeak>();
     rp.topk = topk;
     rp.sign = P->d.sign;
+    rp.phase = P->d.phase;
+    rp.kahan = P->d.sum == BLS_SUM_KAHAN;
+    {
+        int nbmax = 2;
+        for (int c = 0; c < nc; ++c) nbmax = std::max(nbmax, specs[g0 + c].nb);
+        rp.smem_bytes = reduce_smem_bytes(nbmax, topk, rp.kahan);
+    }
     float* dev_spec = nullptr;
     if (spectrum) dev_spec = spectrum_dev ? spectrum : P->spec.as<float>();
     rp.spectrum = dev_spec;
@@ -447,7 +455,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         if ((e = cudaMemcpyAsync(spectrum + spec_off[g0], P->spec.p, (size_t)nres * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
             return cuda_fail(e, "copying spectrum");
     if (res_dump)
-        if ((e = cudaMemcpyAsync(res_dump, P->res.p, (size_t)nres * sizeof(FreqResult), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        if ((e = cudaMemcpyAsync(res_dump, P->res.p, (size_t)nres * sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
             return cuda_fail(e, "copying per-frequency results");
     if ((e = cudaMemcpyAsync(P->h_err.p, P->err.p, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(e, "copying error word");
@@ -476,7 +484,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
 }
 
 bls_status search_impl(bls_plan_impl* P, const bls_curve* curves, int ncurves, bls_peak* out,
-                       float* spectrum, FreqResult* res_dump)
+                       float* spectrum, float* res_dump)
 {
     if (ncurves < 0) return set_error(BLS_ERR_INVALID, "ncurves = %d", ncurves);
     if (ncurves == 0) return BLS_OK;
@@ -640,15 +648,25 @@ bls_status bls_debug_powers(bls_plan* P, const bls_curve* curve, float* power_ou
     if (!P || !curve || !power_out || !i1_out || !k_out) return set_error(BLS_ERR_INVALID, "NULL argument");
     if (curve->nf < 1) return set_error(BLS_ERR_INVALID, "nf = %d", curve->nf);
     std::lock_guard<std::mutex> lk(P->mu);
-    std::vector<FreqResult> res((size_t)curve->nf);
     std::vector<bls_peak> pk((size_t)P->d.topk);
-    bls_status s = search_impl(P, curve, 1, pk.data(), nullptr, res.data());
+    bls_status s = search_impl(P, curve, 1, pk.data(), nullptr, power_out);
     if (s != BLS_OK) return s;
-    for (int j = 0; j < curve->nf; ++j) {
-        power_out[j] = res[j].P;
-        i1_out[j] = (int)(res[j].box >> 16);
-        k_out[j] = (int)(res[j].box & 0xffffu);
-    }
+    // the best box of every frequency, recomputed with the exact tie-break on the curve the
+    // search just prepared (its descriptor is still the first one on the device)
+    const int nf = curve->nf;
+    int nb = curve->nb > 0 ? curve->nb : P->d.nb;
+    cudaError_t e;
+    if ((e = P->jsbuf.ensure((size_t)nf * 12)) != cudaSuccess) return cuda_fail(e, "allocating");
+    float* dP = P->jsbuf.as<float>();
+    int* di1 = reinterpret_cast<int*>(dP + nf);
+    int* dk = di1 + nf;
+    if ((e = launch_argmax(P->cdesc.as<CurveDesc>(), nb, nf, P->d.phase, P->d.sum == BLS_SUM_KAHAN,
+                           P->d.sign, dP, di1, dk, P->stream)) != cudaSuccess)
+        return cuda_fail(e, "best-box launch");
+    if ((e = cudaMemcpyAsync(i1_out, di1, (size_t)nf * 4, cudaMemcpyDeviceToHost, P->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(k_out, dk, (size_t)nf * 4, cudaMemcpyDeviceToHost, P->stream)) != cudaSuccess)
+        return cuda_fail(e, "copy");
+    if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "best box");
     return BLS_OK;
 }
 

@@ -5,7 +5,7 @@
 //                               per-frequency results)
 //   float4 pts[n]               prepared points (dt_hi, dt_lo, w, w*x), 16 B per point
 //   double dt64[n]              exact FP64 time offsets, read only by the exact re-fold
-//   FreqResult res[nf]          per-frequency best box (P as FP32, packed i1/k)
+//   float res[nf]               per-frequency largest box power P (FP32)
 //   DevPeak peaks[ncurves*topk] reduced peaks (FP64)
 // The batched search packs all curves of a launch into shared pools (curves start on even
 // point offsets, so every per-curve slice is 16-byte aligned); the server gives each
@@ -20,11 +20,6 @@ namespace blsgpu {
 constexpr int kMaxTopK = 16;
 constexpr int kPhaseDF32 = 0, kPhaseF64 = 1, kPhaseF32 = 2;
 
-struct FreqResult {
-    float P;        // best box power at this frequency (FP32)
-    uint32_t box;   // i1 << 16 | k
-};
-
 struct CurveDesc {
     const double* t;       // raw times (device)
     const float* y;        // raw fluxes (device)
@@ -32,7 +27,7 @@ struct CurveDesc {
     const double* freqs;   // explicit grid (device) or nullptr: uniform grid
     float4* pts;           // prepared points of this curve
     double* dt64;          // exact time offsets of this curve
-    FreqResult* res;       // per-frequency results of this curve
+    float* res;            // per-frequency largest power of this curve
     long long pt_off;      // first point in the pooled arrays (baseline path)
     long long spec_off;    // first slot of this curve in a spectrum output
     double fmin, df;       // uniform grid
@@ -66,7 +61,7 @@ struct FoldParams {
     long long total;
     int* counter;              // work counter (zeroed before the launch)
     int* err;
-    int chunk;                 // points per staged chunk (even)
+    int chunk;                 // points per staged chunk (a multiple of 16)
     int stride;                // histogram stride in entries (multiple of 16, >= blockDim.x)
 };
 
@@ -77,6 +72,9 @@ struct ReduceParams {
     float* spectrum;           // optional (device): SR per frequency, at spec_off
     int topk;
     int sign;
+    int phase;                 // fold mode of the search (for the best-box recomputation)
+    int kahan;                 // Kahan histograms
+    size_t smem_bytes;         // dynamic shared memory of the launch (reduce_smem_bytes)
 };
 
 // Shared memory a fold-sweep block needs.
@@ -87,6 +85,10 @@ cudaError_t launch_prep(CurveDesc* d_curves, const int* slots, int ncurves, int*
 cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan,
                               int sign, size_t smem, cudaStream_t s);
 cudaError_t launch_reduce(const ReduceParams& p, int ncurves, cudaStream_t s);
+size_t reduce_smem_bytes(int nb_max, int topk, int kahan);
+// Diagnostics: (P, i1, k) of the best box at every frequency of one prepared curve.
+cudaError_t launch_argmax(const CurveDesc* d_curve, int nb, int nf, int phase, int kahan,
+                          int sign, float* P, int* i1, int* k, cudaStream_t s);
 cudaError_t launch_debug_fold(const CurveDesc* d_curve, const int* js, int nj, int phase,
                               int* bins, cudaStream_t s);
 // Baseline: one curve, one thread per frequency, FP64 histograms in global scratch.

@@ -4,15 +4,17 @@
 //                     time offsets (FP64), stored as 16-byte points for the hot loop.
 //  fold_sweep_kernel  persistent; one work item = (curve, tile of T frequencies); one
 //                     thread per frequency with a private phase histogram in shared
-//                     memory.  Loop A folds and bins every point, loop B sweeps every
-//                     cyclic box and keeps the best per frequency.
-//  reduce_kernel      one block per curve: top-k peaks over frequencies, FP64 refit of
-//                     the chosen boxes, reported quantities.
+//                     memory.  Loop A folds and bins every point; loop B sweeps every
+//                     cyclic box and keeps the largest power P of the frequency.
+//  reduce_kernel      one block per curve: top-k peaks of P over frequencies, the best box
+//                     (i1, k) of each peak frequency with the exact tie-break, FP64 refit of
+//                     that box, reported quantities.
+//  argmax_kernel      the best box of listed frequencies (diagnostics).
 //  plain_f64_kernel   baseline, one curve per launch, one thread per frequency, FP64
 //                     histograms in global memory (the paper's decomposition).
 //
 // Fold semantics (identical to the FP64 definition): p = RN(dt*f), phase = p - floor(p),
-// bin = floor(RN(phase*nb)) clamped to nb-1.  The default fast path evaluates dt*f as a
+// bin = floor(RN(phase*nb)) clamped to nb-1.  The fast path evaluates dt*f as a
 // double-FP32 product with a proven error bound and re-folds in FP64 only the points that
 // lie within that bound of a bin edge, so every bin equals the FP64 one.
 #include <cuda_runtime.h>
@@ -23,7 +25,7 @@
 
 namespace blsgpu {
 
-// ------------------------------------------------------------------------- helpers
+// ------------------------------------------------------------------------- fold
 
 __device__ __forceinline__ double grid_freq(const CurveDesc& cd, int j)
 {
@@ -32,22 +34,21 @@ __device__ __forceinline__ double grid_freq(const CurveDesc& cd, int j)
 }
 
 // Exact fold in FP64, every operation rounded once (no contraction).
-__device__ __forceinline__ int fold_exact(double dt, double f, int nb)
+__device__ __forceinline__ unsigned fold_exact(double dt, double f, int nb)
 {
     double p = __dmul_rn(dt, f);
     double ph = __dsub_rn(p, floor(p));
     double u = __dmul_rn(ph, (double)nb);
     int b = (int)floor(u);
     b = b >= nb ? nb - 1 : b;
-    return b < 0 ? 0 : b;
+    return (unsigned)(b < 0 ? 0 : b);
 }
 
-// Constants of the double-FP32 fold of one thread's frequency.
+// Constants of the fold of one thread's frequency.
 struct FoldConst {
     float fh, fl;     // f = fh + fl (+ |err| <= 2^-48 f)
     float nbf;        // nb as float
     float lim;        // 0.5 - tol: |d| beyond this means "near a bin edge"
-    float f32;        // f rounded to FP32 (FP32 phase mode)
     double f;         // exact frequency
     int nb;
     bool fast;        // the double-FP32 path is valid for this (curve, frequency)
@@ -68,7 +69,6 @@ __device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dt
     fc.nb = nb;
     fc.fh = __double2float_rn(f);
     fc.fl = __double2float_rn(__dsub_rn(f, (double)fc.fh));
-    fc.f32 = fc.fh;
     fc.nbf = (float)nb;
     double DF = dtmax * f;
     fc.fast = DF < 1048576.0;
@@ -82,49 +82,143 @@ __device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dt
     return fc;
 }
 
-// Double-FP32 fold.  Returns the bin and sets `edge` when the bin is not certain.
-__device__ __forceinline__ int fold_df32(float dh, float dl, const FoldConst& fc, bool& edge)
-{
-    const float M = 12582912.0f;                 // 1.5 * 2^23: RN(x + M) - M = rint(x)
-    float ph = __fmul_rn(dh, fc.fh);
-    float e = __fmaf_rn(dh, fc.fh, -ph);         // exact product error
-    float t1 = __fmaf_rn(dh, fc.fl, e);
-    float c = __fmaf_rn(dl, fc.fh, t1);          // dt*f ~= ph + c
-    float m = __fadd_rn(ph, M);
-    float rp = __fsub_rn(m, M);
-    float fr = __fsub_rn(ph, rp);                // exact, in [-1/2, 1/2]
-    float cn = __fmaf_rn(c, fc.nbf, -0.5f);
-    float x = __fmaf_rn(fr, fc.nbf, cn);         // nb * (phase mod 1, centred) - 1/2
-    float m2 = __fadd_rn(x, M);
-    float rx = __fsub_rn(m2, M);
-    float d = __fsub_rn(x, rx);                  // exact, in [-1/2, 1/2]
-    int ri = __float_as_int(m2) - __float_as_int(M);   // rint(x) = floor(x + 1/2)
-    unsigned b0 = (unsigned)ri, b1 = (unsigned)(ri + fc.nb);
-    edge = !(fabsf(d) <= fc.lim);                // NaN (bad input) also takes the exact path
-    return (int)min(min(b0, b1), (unsigned)(fc.nb - 1));
-}
-
 // FP32 fold (precision study): no error bound, no fallback.
-__device__ __forceinline__ int fold_f32(float dt32, const FoldConst& fc)
+__device__ __forceinline__ unsigned fold_f32(float dt32, const FoldConst& fc)
 {
-    float p = __fmul_rn(dt32, fc.f32);
+    float p = __fmul_rn(dt32, fc.fh);
     float ph = __fsub_rn(p, floorf(p));
     int b = (int)floorf(__fmul_rn(ph, fc.nbf));
     b = b >= fc.nb ? fc.nb - 1 : b;
-    return b < 0 ? 0 : b;
+    return (unsigned)(b < 0 ? 0 : b);
 }
 
-template <int PHASE>
-__device__ __forceinline__ int fold_point(const float4& q, const double* dtp,
-                                          const FoldConst& fc)
+// ---- packed FP32 pairs (f32x2: one instruction, two lanes of FP32 arithmetic)
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk(float lo, float hi)
 {
-    if (PHASE == kPhaseF64 || !fc.fast) return fold_exact(*dtp, fc.f, fc.nb);
-    if (PHASE == kPhaseF32) return fold_f32(__fadd_rn(q.x, q.y), fc);
-    bool edge;
-    int b = fold_df32(q.x, q.y, fc, edge);
-    if (edge) b = fold_exact(*dtp, fc.f, fc.nb);
-    return b;
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
 }
+__device__ __forceinline__ void upk(u64 v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b)
+{
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b)
+{
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b)
+{
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c)
+{
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Constants of the double-FP32 fold as broadcast pairs.
+struct FoldPacked {
+    u64 FH, NFH, FL, M, NB, NNB, MHALF;
+    float lim;
+    int nb;
+};
+
+__device__ __forceinline__ FoldPacked make_fold_packed(const FoldConst& fc)
+{
+    FoldPacked q;
+    const float M = 12582912.0f;
+    q.FH = pk(fc.fh, fc.fh);
+    q.NFH = pk(-fc.fh, -fc.fh);
+    q.FL = pk(fc.fl, fc.fl);
+    q.M = pk(M, M);
+    q.NB = pk(fc.nbf, fc.nbf);
+    q.NNB = pk(-fc.nbf, -fc.nbf);
+    q.MHALF = pk(-0.5f, -0.5f);
+    q.lim = fc.lim;
+    q.nb = fc.nb;
+    return q;
+}
+
+// Double-FP32 fold of two points at once.  With dt = dh + dl and f = fh + fl:
+//   ph = RN(dh fh) and e = dh fh - ph (exact, by FMA) give the product's high part,
+//   c = dl fh + dh fl + e its low part, so dt f ~= ph + c (error <= 2^-44 dt f);
+//   fr = ph - rint(ph) (exact, in [-1/2, 1/2]) is the phase mod 1, centred;
+//   x = fr nb + c nb - 1/2, and rint(x) = floor(nb phase) up to a multiple of nb;
+//   d = x - rint(x): when |d| <= lim the bin is certain, otherwise (edge) it is re-folded
+//   in FP64.  rint uses RN(v + 1.5 2^23) - 1.5 2^23, valid for |v| < 2^22.
+// Packed instructions have no negation modifier, so ph and fr are carried negated.
+__device__ __forceinline__ void fold_df32_pair(const float4& A, const FoldPacked& q,
+                                               unsigned& b0, unsigned& b1, bool& e0, bool& e1)
+{
+    const u64 DH = pk(A.x, A.y), DL = pk(A.z, A.w);
+    const u64 NPH = mul2(DH, q.NFH);
+    const u64 E = fma2(DH, q.FH, NPH);
+    const u64 T1 = fma2(DH, q.FL, E);
+    const u64 C = fma2(DL, q.FH, T1);
+    const u64 MM = add2(NPH, q.M);
+    const u64 NRP = sub2(MM, q.M);
+    const u64 NFR = sub2(NPH, NRP);
+    const u64 CN = fma2(C, q.NB, q.MHALF);
+    const u64 X = fma2(NFR, q.NNB, CN);
+    const u64 M2 = add2(X, q.M);
+    const u64 RX = sub2(M2, q.M);
+    const u64 D = sub2(X, RX);
+    float d0, d1, m0, m1;
+    upk(D, d0, d1);
+    upk(M2, m0, m1);
+    const int Mb = __float_as_int(12582912.0f);
+    const unsigned r0 = (unsigned)(__float_as_int(m0) - Mb), r1 = (unsigned)(__float_as_int(m1) - Mb);
+    b0 = min(r0, r0 + (unsigned)q.nb);
+    b1 = min(r1, r1 + (unsigned)q.nb);
+    e0 = !(fabsf(d0) <= q.lim);   // NaN (bad input) also takes the exact path
+    e1 = !(fabsf(d1) <= q.lim);
+}
+
+// Fold of the point pair (2p, 2p+1) in a given phase mode; A = (dh0, dh1, dl0, dl1).
+template <int PHASE>
+__device__ __forceinline__ void fold_pair(const float4& A, const double* dtp, const FoldConst& fc,
+                                          const FoldPacked& q, unsigned& b0, unsigned& b1)
+{
+    if (PHASE == kPhaseF64 || !fc.fast) {
+        b0 = fold_exact(dtp[0], fc.f, fc.nb);
+        b1 = fold_exact(dtp[1], fc.f, fc.nb);
+    } else if (PHASE == kPhaseF32) {
+        b0 = fold_f32(__fadd_rn(A.x, A.z), fc);
+        b1 = fold_f32(__fadd_rn(A.y, A.w), fc);
+    } else {
+        bool e0, e1;
+        fold_df32_pair(A, q, b0, b1, e0, e1);
+        if (e0 | e1) {
+            if (e0) b0 = fold_exact(dtp[0], fc.f, fc.nb);
+            if (e1) b1 = fold_exact(dtp[1], fc.f, fc.nb);
+        }
+    }
+}
+
+__device__ __forceinline__ void fold_pair_rt(int phase, const float4& A, const double* dtp,
+                                             const FoldConst& fc, const FoldPacked& q,
+                                             unsigned& b0, unsigned& b1)
+{
+    if (phase == kPhaseF64) fold_pair<kPhaseF64>(A, dtp, fc, q, b0, b1);
+    else if (phase == kPhaseF32) fold_pair<kPhaseF32>(A, dtp, fc, q, b0, b1);
+    else fold_pair<kPhaseDF32>(A, dtp, fc, q, b0, b1);
+}
+
+// ------------------------------------------------------------------------- misc helpers
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src)
 {
@@ -138,6 +232,15 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float negabs(float x) { return __int_as_float(__float_as_int(x) | 0x80000000); }
 
 // Deterministic block sum of FP64 (fixed tree, blockDim.x a power of two <= 1024).
 __device__ double block_sum(double v, double* red)
@@ -184,8 +287,10 @@ __device__ double block_max(double v, double* red)
 constexpr int kPrepThreads = 256;
 
 // Weights w = dy^-2/W, mean ybar = y0 + sum w (y - y0) (constant flux gives exact zeros),
-// x = y - ybar, dt = t - min t; points stored as (dt_hi, dt_lo, w, w x) in FP32 and dt
-// in FP64.  Validates the inputs (finite t and y, finite dy > 0, frequencies > 0).
+// x = y - ybar, dt = t - min t.  Points are stored in pairs (2p, 2p+1) as two float4:
+// (dt_hi0, dt_hi1, dt_lo0, dt_lo1) and (w0, wx0, w1, wx1), dt in FP64 beside them; an odd
+// curve gets a pad point of zero weight.  Validates the inputs (finite t and y, finite
+// dy > 0, frequencies > 0).
 __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, const int* slots,
                                                              int* err)
 {
@@ -244,9 +349,20 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, c
         double wx = __dmul_rn(w, x);
         float dh = __double2float_rn(dt);
         float dl = __double2float_rn(__dsub_rn(dt, (double)dh));
-        pts[i] = make_float4(dh, dl, __double2float_rn(w), __double2float_rn(wx));
+        float* A = reinterpret_cast<float*>(&pts[(i >> 1) * 2]);
+        float* B = A + 4;
+        const int l = i & 1;
+        A[l] = dh;
+        A[2 + l] = dl;
+        B[2 * l] = __double2float_rn(w);
+        B[2 * l + 1] = __double2float_rn(wx);
         dt64[i] = dt;
         swx2 = __dadd_rn(swx2, __dmul_rn(wx, x));
+    }
+    if ((n & 1) && threadIdx.x == 0) {   // pad point of an odd curve: weight 0 at dt = 0
+        float* A = reinterpret_cast<float*>(&pts[(n >> 1) * 2]);
+        A[1] = 0.0f; A[3] = 0.0f; A[6] = 0.0f; A[7] = 0.0f;
+        dt64[n] = 0.0;
     }
     swx2 = block_sum(swx2, red);
     if (threadIdx.x == 0) {
@@ -288,9 +404,355 @@ cudaError_t launch_prep_f64(const CurveDesc* d_curves, int ncurves, double* w64,
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------- a4: binning
+
+// Histogram entry of one thread: (sum w, sum w x) as an FP32 pair, 8 bytes; the Kahan
+// variant adds the two compensation terms, 16 bytes.  Thread t's bin b lives at entry
+// b * stride + t, so the 32 lanes of a warp touch 32 consecutive entries whatever their
+// bins are (no bank conflicts).
+
+__device__ __forceinline__ void kahan_add(float4* hp, float w, float wx)
+{
+    float4 v = *hp;
+    const float yw = __fsub_rn(w, v.z), tw = __fadd_rn(v.x, yw);
+    v.z = __fsub_rn(__fsub_rn(tw, v.x), yw);
+    v.x = tw;
+    const float yx = __fsub_rn(wx, v.w), tx = __fadd_rn(v.y, yx);
+    v.w = __fsub_rn(__fsub_rn(tx, v.y), yx);
+    v.y = tx;
+    *hp = v;
+}
+
+__device__ __forceinline__ u64 lds64(unsigned addr)
+{
+    u64 v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void sts64(unsigned addr, u64 v)
+{
+    asm volatile("st.shared.b64 [%0], %1;" ::"r"(addr), "l"(v));
+}
+
+// Bins of the 8 point pairs of a 16-point sub-chunk, with their weight pairs; returns
+// whether any bin is not certain (then fix_sub must run before the bins are used).
+__device__ __forceinline__ bool fold_sub(const float4* cp, const FoldPacked& fq, unsigned* b,
+                                         float4* Bw)
+{
+    bool edge = false;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 A = cp[2 * q];
+        Bw[q] = cp[2 * q + 1];
+        bool e0, e1;
+        fold_df32_pair(A, fq, b[2 * q], b[2 * q + 1], e0, e1);
+        edge = edge | e0 | e1;
+    }
+    return edge;
+}
+
+// Rare path: re-fold in FP64 the points of a sub-chunk whose bin is not certain.
+__device__ __forceinline__ void fix_sub(const float4* cp, const double* cd, const FoldConst& fc,
+                                     const FoldPacked& fq, unsigned* b)
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        unsigned b0, b1;
+        bool e0, e1;
+        fold_df32_pair(cp[2 * q], fq, b0, b1, e0, e1);
+        if (e0) b[2 * q] = fold_exact(cd[2 * q], fc.f, fc.nb);
+        if (e1) b[2 * q + 1] = fold_exact(cd[2 * q + 1], fc.f, fc.nb);
+    }
+}
+
+// Read-modify-write of the 16 points of a sub-chunk, pair by pair: both bins of a pair are
+// read before either is written, and the second point adds onto the first one's new value
+// when they share a bin, so the result equals adding the points one by one in order.
+__device__ __forceinline__ void rmw_sub(unsigned hbase, unsigned rowb, const unsigned* b,
+                                        const float4* Bw)
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const unsigned a0 = hbase + b[2 * q] * rowb, a1 = hbase + b[2 * q + 1] * rowb;
+        const u64 h0 = lds64(a0), h1 = lds64(a1);
+        const u64 v0 = add2(h0, pk(Bw[q].x, Bw[q].y));
+        const u64 v1 = add2(b[2 * q + 1] == b[2 * q] ? v0 : h1, pk(Bw[q].z, Bw[q].w));
+        sts64(a0, v0);
+        sts64(a1, v1);
+    }
+}
+
+// Bins nsub staged 16-point sub-chunks into this thread's histogram (FP32 sums, point
+// order).  Software pipeline: the next sub-chunk's points are loaded and folded (8
+// independent pairs) in the same basic block as the current sub-chunk's read-modify-write
+// chain, so the fold arithmetic fills the shared-memory latency of the chain; the rare
+// FP64 re-fold runs after the stores.  hbase is the shared-memory address of this
+// thread's bin 0, rowb the byte stride between bins.
+__device__ __forceinline__ void bin_df32(const float4* cp, const double* cd, int nsub,
+                                         unsigned hbase, unsigned rowb, const FoldConst& fc,
+                                         const FoldPacked& fq)
+{
+    unsigned b[16];
+    float4 Bw[8];
+    if (fold_sub(cp, fq, b, Bw)) fix_sub(cp, cd, fc, fq, b);
+    for (int sc = 0; sc + 1 < nsub; ++sc) {
+        unsigned bn[16];
+        float4 Bn[8];
+        const float4* np = cp + 16 * (sc + 1);
+        const bool edge = fold_sub(np, fq, bn, Bn);
+        rmw_sub(hbase, rowb, b, Bw);
+        if (edge) fix_sub(np, cd + 16 * (sc + 1), fc, fq, bn);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) b[i] = bn[i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Bw[q] = Bn[q];
+    }
+    rmw_sub(hbase, rowb, b, Bw);
+}
+
+// Generic binning (FP64 or FP32 phase modes, precision studies): pair by pair.
+template <int PHASE>
+__device__ __forceinline__ void bin_generic(const float4* cp, const double* cd, int npairs,
+                                            unsigned hbase, unsigned rowb, const FoldConst& fc,
+                                            const FoldPacked& fq)
+{
+    for (int pi = 0; pi < npairs; ++pi) {
+        const float4 A = cp[2 * pi], B = cp[2 * pi + 1];
+        unsigned b0, b1;
+        fold_pair<PHASE>(A, &cd[2 * pi], fc, fq, b0, b1);
+        const unsigned a0 = hbase + b0 * rowb, a1 = hbase + b1 * rowb;
+        sts64(a0, add2(lds64(a0), pk(B.x, B.y)));
+        sts64(a1, add2(lds64(a1), pk(B.z, B.w)));
+    }
+}
+
+// ------------------------------------------------------------------------- a5/a6: sweep
+
+__device__ __forceinline__ float bin_w(const unsigned char* hist, size_t S, int kahan, int b)
+{
+    if (kahan) {
+        const float4 v = reinterpret_cast<const float4*>(hist)[(size_t)b * S];
+        return __fsub_rn(v.x, v.z);
+    }
+    return reinterpret_cast<const float2*>(hist)[(size_t)b * S].x;
+}
+
+__device__ __forceinline__ float bin_x(const unsigned char* hist, size_t S, int kahan, int b)
+{
+    if (kahan) {
+        const float4 v = reinterpret_cast<const float4*>(hist)[(size_t)b * S];
+        return __fsub_rn(v.y, v.w);
+    }
+    return reinterpret_cast<const float2*>(hist)[(size_t)b * S].y;
+}
+
+// Fast sweep: the largest power P of any box, without its position.
+//
+// SB consecutive starts share every bin load; their sums are carried as SB/2 packed pairs
+// (one f32x2 instruction updates two starts).  P = num * rcp(den) with num = s^2 (dips:
+// -s|s|, negative for bumps) and den = r(1-r); the approximate reciprocal is within one
+// FP32 ulp, far inside the tolerance of the spectrum.  Empty boxes give 0 * inf = NaN and
+// bumps (dips only) a negative P: max() ignores both.  Conditions: kmin = 1, kmax >=
+// SB - 1, and no box can hold more than 0.9 of the weight (checked by the caller), so
+// den > 0.09 r and FP32 keeps 1 - r accurate.  The starts of the last block may pass nb;
+// they repeat earlier starts and cannot change the maximum.
+template <int SIGN>
+__device__ __forceinline__ void eval_pair(u64& R, u64& X, const u64& HW2, const u64& HX2,
+                                          const u64& ONE2, bool init, bool use0, bool use1,
+                                          float& b0, float& b1)
+{
+    if (init) {
+        float hw, hw1, hx, hx1;
+        upk(HW2, hw, hw1);
+        upk(HX2, hx, hx1);
+        R = pk(hw, 0.0f);   // the second start of the pair begins at the next bin
+        X = pk(hx, 0.0f);
+    } else {
+        R = add2(R, HW2);
+        X = add2(X, HX2);
+    }
+    const u64 DEN = mul2(R, sub2(ONE2, R));
+    u64 NUM;
+    if (SIGN) {
+        NUM = mul2(X, X);
+    } else {
+        float s0, s1;
+        upk(X, s0, s1);
+        NUM = mul2(X, pk(negabs(s0), negabs(s1)));
+    }
+    float d0, d1;
+    upk(DEN, d0, d1);
+    const u64 P = mul2(NUM, pk(rcp_approx(d0), rcp_approx(d1)));
+    float p0, p1;
+    upk(P, p0, p1);
+    if (use0) b0 = fmaxf(b0, p0);
+    if (use1) b1 = fmaxf(b1, p1);
+}
+
+template <int SB, int SIGN>
+__device__ __noinline__ float sweep_fast(const u64* __restrict__ H, int stride, int nb, int kmax)
+{
+    constexpr int NP = SB / 2;
+    const size_t S = (size_t)stride;
+    const u64 ONE2 = pk(1.0f, 1.0f);
+    float best0[NP], best1[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) { best0[q] = 0.0f; best1[q] = 0.0f; }
+    for (int i0 = 0; i0 < nb; i0 += SB) {
+        u64 R[NP], X[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) { R[q] = 0ull; X[q] = 0ull; }
+        int m = i0;
+        // ramp-up: bin mm of the block starts accumulator mm and feeds those before it
+#pragma unroll
+        for (int mm = 0; mm < SB - 1; ++mm) {
+            float hw, hx;
+            upk(H[(size_t)m * S], hw, hx);
+            m = (m + 1 == nb) ? 0 : m + 1;
+            const u64 HW2 = pk(hw, hw), HX2 = pk(hx, hx);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                if (2 * q > mm) continue;
+                eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, 2 * q == mm, true, 2 * q < mm,
+                                best0[q], best1[q]);
+            }
+        }
+        // steady: every start takes the bin
+        for (int mm = SB - 1; mm < kmax; ++mm) {
+            float hw, hx;
+            upk(H[(size_t)m * S], hw, hx);
+            m = (m + 1 == nb) ? 0 : m + 1;
+            const u64 HW2 = pk(hw, hw), HX2 = pk(hx, hx);
+#pragma unroll
+            for (int q = 0; q < NP; ++q)
+                eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, false, true, true, best0[q], best1[q]);
+        }
+        // ramp-down: accumulator a keeps going while its width stays <= kmax (a > e)
+#pragma unroll
+        for (int e = 0; e < SB - 1; ++e) {
+            float hw, hx;
+            upk(H[(size_t)m * S], hw, hx);
+            m = (m + 1 == nb) ? 0 : m + 1;
+            const u64 HW2 = pk(hw, hw), HX2 = pk(hx, hx);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                if (2 * q + 1 < e + 1) continue;
+                eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, false, 2 * q >= e + 1, true,
+                                best0[q], best1[q]);
+            }
+        }
+    }
+    float best = 0.0f;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) best = fmaxf(best, fmaxf(best0[q], best1[q]));
+    return best;
+}
+
+struct Best {
+    float num, den;   // P = num / den
+    int i1, k;
+};
+
+__device__ __forceinline__ bool box_full(int i1, int k, int nb, int arc_a, int arc_len)
+{
+    int rel = arc_a - i1;
+    if (rel < 0) rel += nb;
+    return rel + arc_len <= k;
+}
+
+// Exact sweep: the best box with the definition's tie-break.
+//
+// Every start i1 and width k (cyclic), sums accumulated bin by bin from the start: r in
+// double-FP32 (so 1 - r stays accurate when the box holds most of the weight), s with
+// Kahan compensation.  A box counts when it holds at least one point and leaves one out:
+// an empty box has r = 0 exactly, and a box holding every point contains the shortest
+// cyclic arc of occupied bins, so neither depends on rounding.  Dips only: s < 0.
+// Candidates are compared as exact (num, den) pairs, num * den_best > num_best * den, so a
+// box with bit-identical sums never replaces an earlier one and equal powers resolve to
+// the smallest (i1, k).
+template <int SIGN>
+__device__ Best sweep_exact(const unsigned char* hist, int stride, int kahan, int nb, int kmin,
+                            int kmax)
+{
+    const size_t S = (size_t)stride;
+    int first = -1, last = -1, run = 0, gap = 0, gap_end = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (bin_w(hist, S, kahan, b) != 0.0f) {
+            if (first < 0) first = b;
+            else if (run > gap) { gap = run; gap_end = b; }
+            last = b;
+            run = 0;
+        } else if (first >= 0) {
+            ++run;
+        }
+    }
+    int arc_a = 0, arc_len = 0;
+    if (first >= 0) {
+        const int wrap = (nb - 1 - last) + first;
+        if (wrap >= gap) { arc_a = first; arc_len = last - first + 1; }
+        else { arc_a = gap_end; arc_len = nb - gap; }
+    }
+    Best g;
+    g.num = 0.0f; g.den = 1.0f; g.i1 = 0; g.k = kmin;
+    for (int i1 = 0; i1 < nb; ++i1) {
+        float rh = 0.0f, rl = 0.0f, s = 0.0f, cs = 0.0f;
+        int m = i1;
+        for (int k = 1; k <= kmax; ++k) {
+            const float hw = bin_w(hist, S, kahan, m), hx = bin_x(hist, S, kahan, m);
+            m = (m + 1 == nb) ? 0 : m + 1;
+            const float t = __fadd_rn(rh, hw);                      // two-sum rh + hw
+            const float bp = __fsub_rn(t, rh);
+            const float e = __fadd_rn(__fsub_rn(rh, __fsub_rn(t, bp)), __fsub_rn(hw, bp));
+            rh = t;
+            rl = __fadd_rn(rl, e);
+            const float y = __fsub_rn(hx, cs), ts = __fadd_rn(s, y);  // Kahan s + hx
+            cs = __fsub_rn(__fsub_rn(ts, s), y);
+            s = ts;
+            if (k < kmin || rh == 0.0f) continue;
+            if (box_full(i1, k, nb, arc_a, arc_len)) continue;
+            const float q = __fsub_rn(__fsub_rn(1.0f, rh), rl);     // 1 - r
+            const float den = __fmaf_rn(rh, q, __fmul_rn(rl, q));    // r (1 - r)
+            if (!(den > 0.0f)) continue;
+            const float num = SIGN ? __fmul_rn(s, s) : __fmul_rn(-s, fabsf(s));
+            if (__fmul_rn(num, g.den) > __fmul_rn(g.num, den)) {
+                g.num = num; g.den = den; g.i1 = i1; g.k = k;
+            }
+        }
+    }
+    return g;
+}
+
+__device__ __forceinline__ Best sweep_exact_rt(int sign, const unsigned char* hist, int stride,
+                                               int kahan, int nb, int kmin, int kmax)
+{
+    return sign ? sweep_exact<1>(hist, stride, kahan, nb, kmin, kmax)
+                : sweep_exact<0>(hist, stride, kahan, nb, kmin, kmax);
+}
+
+// Largest power of one private histogram: fast sweep when its conditions hold, else the
+// exact sweep.  No box can hold more than 0.9 of the weight when kmax times the heaviest
+// bin stays below 0.89 (the margin covers FP32 rounding of the sums).
+template <int KAHAN, int SIGN>
+__device__ __forceinline__ float sweep_max(const unsigned char* hist, int stride, int nb,
+                                           int kmin, int kmax)
+{
+    if (!KAHAN && kmin == 1 && kmax >= 3) {
+        float wmax = 0.0f;
+        const float2* H2 = reinterpret_cast<const float2*>(hist);
+        for (int b = 0; b < nb; ++b) wmax = fmaxf(wmax, H2[(size_t)b * stride].x);
+        if ((float)kmax * wmax < 0.89f) {
+            const u64* H = reinterpret_cast<const u64*>(hist);
+            return kmax >= 15 ? sweep_fast<8, SIGN>(H, stride, nb, kmax)
+                              : sweep_fast<4, SIGN>(H, stride, nb, kmax);
+        }
+    }
+    const Best g = sweep_exact<SIGN>(hist, stride, KAHAN, nb, kmin, kmax);
+    return g.num > 0.0f ? __fdiv_rn(g.num, g.den) : 0.0f;
+}
+
 // ------------------------------------------------------------------------- a2-a6: hot kernel
 
-constexpr int kFoldMaxThreads = 512;
+constexpr int kFoldMaxThreads = 256;
 
 size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int kahan)
 {
@@ -302,54 +764,6 @@ size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int kahan)
 
 int fold_sweep_max_threads() { return kFoldMaxThreads; }
 
-// Box sweep of one private histogram (a5, a6): every start i1 and width k, cyclic, sums
-// accumulated bin by bin from the start; a box counts when 0 < r < 1 (and s < 0 for
-// dips); the best is kept with a strict '>' in (i1, k) order, compared without a divide
-// as num > best * den.
-template <int KAHAN, int SIGN>
-__device__ __forceinline__ void sweep_private(const unsigned char* hist, int stride, int nb,
-                                              int kmin, int kmax, float& bestP, int& bi1,
-                                              int& bk)
-{
-    float best = 0.0f;
-    int b1 = 0, bw = kmin;
-    for (int i1 = 0; i1 < nb; ++i1) {
-        float r = 0.0f, s = 0.0f, cr = 0.0f, cs = 0.0f;
-        int m = i1;
-        for (int k = 1; k <= kmax; ++k) {
-            float hw, hx;
-            if (KAHAN) {
-                float4 v = reinterpret_cast<const float4*>(hist)[(size_t)m * stride];
-                hw = __fsub_rn(v.x, v.z);
-                hx = __fsub_rn(v.y, v.w);
-                float yw = __fsub_rn(hw, cr), tw = __fadd_rn(r, yw);
-                cr = __fsub_rn(__fsub_rn(tw, r), yw);
-                r = tw;
-                float yx = __fsub_rn(hx, cs), tx = __fadd_rn(s, yx);
-                cs = __fsub_rn(__fsub_rn(tx, s), yx);
-                s = tx;
-            } else {
-                float2 v = reinterpret_cast<const float2*>(hist)[(size_t)m * stride];
-                r = __fadd_rn(r, v.x);
-                s = __fadd_rn(s, v.y);
-            }
-            m = (m + 1 == nb) ? 0 : m + 1;
-            if (k >= kmin) {
-                float den = __fmaf_rn(-r, r, r);              // r (1 - r)
-                float num = SIGN ? __fmul_rn(s, s) : __fmul_rn(-s, fabsf(s));
-                if (num > __fmul_rn(best, den) && den > 0.0f) {
-                    best = __fdiv_rn(num, den);
-                    b1 = i1;
-                    bw = k;
-                }
-            }
-        }
-    }
-    bestP = best;
-    bi1 = b1;
-    bk = bw;
-}
-
 template <int PHASE, int KAHAN, int SIGN>
 __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldParams p)
 {
@@ -358,11 +772,12 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
     const int T = blockDim.x;
     const int tid = threadIdx.x;
     const int CH = p.chunk;
-    float4* cpts = reinterpret_cast<float4*>(smem);             // [2][CH]
-    double* cdt = reinterpret_cast<double*>(cpts + 2 * CH);     // [2][CH]
+    float4* cpts = reinterpret_cast<float4*>(smem);             // [2][CH]: point pairs
+    double* cdt = reinterpret_cast<double*>(cpts + 2 * CH);     // [2][CH]: FP64 offsets
     unsigned char* hist_all = reinterpret_cast<unsigned char*>(cdt + 2 * CH);
     const size_t esz = KAHAN ? sizeof(float4) : sizeof(float2);
     unsigned char* hist = hist_all + (size_t)tid * esz;         // column of this thread
+    const size_t S = (size_t)p.stride;
 
     for (;;) {
         __syncthreads();
@@ -385,70 +800,65 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
         const bool active = j < nf;
         const double f = grid_freq(cdr, active ? j : nf - 1);
         const FoldConst fc = make_fold_const(f, nb, cdr.dtmax);
+        const FoldPacked fq = make_fold_packed(fc);
 
         for (int b = 0; b < nb; ++b) {
             if (KAHAN)
-                reinterpret_cast<float4*>(hist)[(size_t)b * p.stride] = make_float4(0.f, 0.f, 0.f, 0.f);
+                reinterpret_cast<float4*>(hist)[(size_t)b * S] = make_float4(0.f, 0.f, 0.f, 0.f);
             else
-                reinterpret_cast<float2*>(hist)[(size_t)b * p.stride] = make_float2(0.f, 0.f);
+                reinterpret_cast<u64*>(hist)[(size_t)b * S] = 0ull;
         }
 
+        // a2: stage the curve through shared memory in chunks of CH points (CH a multiple
+        // of 16), double-buffered with cp.async; the last chunk is padded with zero-weight
+        // points at dt = 0 up to a whole 16-point sub-chunk (they add +0 to bin 0)
         const int nchunks = (n + CH - 1) / CH;
         auto stage = [&](int ci) {
             const int c0 = ci * CH;
-            const int cn = min(CH, n - c0);
+            const int cn = (min(CH, n - c0) + 1) & ~1;          // whole pairs exist in memory
+            const int cpad = (cn + 15) & ~15;
             float4* dp = cpts + (ci & 1) * CH;
             double* dd = cdt + (ci & 1) * CH;
             for (int i = tid; i < cn; i += T) {
                 cp_async16(&dp[i], &gpts[c0 + i]);
                 cp_async8(&dd[i], &gdt[c0 + i]);
             }
+            for (int i = cn + tid; i < cpad; i += T) {
+                dp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                dd[i] = 0.0;
+            }
             cp_async_commit();
         };
+        const unsigned hbase = (unsigned)__cvta_generic_to_shared(hist);
+        const unsigned rowb = (unsigned)(S * esz);
         stage(0);
         for (int ci = 0; ci < nchunks; ++ci) {
             if (ci + 1 < nchunks) stage(ci + 1); else cp_async_commit();
             cp_async_wait1();
             __syncthreads();
-            const int cn = min(CH, n - ci * CH);
+            const int cnum = min(CH, n - ci * CH);
             const float4* cp = cpts + (ci & 1) * CH;
             const double* cd = cdt + (ci & 1) * CH;
-            if (active) {
-#pragma unroll 4
-                for (int i = 0; i < cn; ++i) {
-                    const float4 q = cp[i];
-                    const int b = fold_point<PHASE>(q, &cd[i], fc);
-                    if (KAHAN) {
-                        float4* hp = reinterpret_cast<float4*>(hist) + (size_t)b * p.stride;
-                        float4 v = *hp;
-                        float yw = __fsub_rn(q.z, v.z), tw = __fadd_rn(v.x, yw);
-                        v.z = __fsub_rn(__fsub_rn(tw, v.x), yw);
-                        v.x = tw;
-                        float yx = __fsub_rn(q.w, v.w), tx = __fadd_rn(v.y, yx);
-                        v.w = __fsub_rn(__fsub_rn(tx, v.y), yx);
-                        v.y = tx;
-                        *hp = v;
-                    } else {
-                        float2* hp = reinterpret_cast<float2*>(hist) + (size_t)b * p.stride;
-                        float2 v = *hp;
-                        v.x = __fadd_rn(v.x, q.z);
-                        v.y = __fadd_rn(v.y, q.w);
-                        *hp = v;
+            if (active) {   // a3 + a4: fold and bin
+                if (KAHAN) {
+                    const int npairs = (cnum + 1) >> 1;
+                    for (int pi = 0; pi < npairs; ++pi) {
+                        const float4 A = cp[2 * pi], B = cp[2 * pi + 1];
+                        unsigned b0, b1;
+                        fold_pair<PHASE>(A, &cd[2 * pi], fc, fq, b0, b1);
+                        kahan_add(reinterpret_cast<float4*>(hist) + b0 * S, B.x, B.y);
+                        kahan_add(reinterpret_cast<float4*>(hist) + b1 * S, B.z, B.w);
                     }
+                } else if (PHASE == kPhaseDF32 && fc.fast) {
+                    bin_df32(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                } else {
+                    bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
                 }
             }
             __syncthreads();
         }
 
-        if (active) {
-            float bestP;
-            int bi1, bk;
-            sweep_private<KAHAN, SIGN>(hist, p.stride, nb, kmin, kmax, bestP, bi1, bk);
-            FreqResult r;
-            r.P = bestP;
-            r.box = ((uint32_t)bi1 << 16) | (uint32_t)bk;
-            cdr.res[j] = r;
-        }
+        if (active) cdr.res[j] = sweep_max<KAHAN, SIGN>(hist, p.stride, nb, kmin, kmax);
     }
 }
 
@@ -511,6 +921,71 @@ cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, i
     return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------------------- best box
+
+// The best box (exact tie-break) of one frequency: bins the curve point by point into a
+// private histogram column with the same arithmetic and order as the hot kernel, then
+// runs the exact sweep.
+__device__ Best best_box_at(const CurveDesc& cd, double f, unsigned char* hist, int stride,
+                            int phase, int kahan, int sign)
+{
+    const size_t S = (size_t)stride;
+    const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax);
+    const FoldPacked fq = make_fold_packed(fc);
+    for (int b = 0; b < cd.nb; ++b) {
+        if (kahan) reinterpret_cast<float4*>(hist)[(size_t)b * S] = make_float4(0.f, 0.f, 0.f, 0.f);
+        else reinterpret_cast<u64*>(hist)[(size_t)b * S] = 0ull;
+    }
+    for (int pi = 0; 2 * pi < cd.n; ++pi) {
+        const float4 A = cd.pts[2 * pi], B = cd.pts[2 * pi + 1];
+        unsigned b0, b1;
+        fold_pair_rt(phase, A, &cd.dt64[2 * pi], fc, fq, b0, b1);
+        if (kahan) {
+            kahan_add(reinterpret_cast<float4*>(hist) + b0 * S, B.x, B.y);
+            kahan_add(reinterpret_cast<float4*>(hist) + b1 * S, B.z, B.w);
+        } else {
+            u64* H = reinterpret_cast<u64*>(hist);
+            H[b0 * S] = add2(H[b0 * S], pk(B.x, B.y));
+            H[b1 * S] = add2(H[b1 * S], pk(B.z, B.w));
+        }
+    }
+    return sweep_exact_rt(sign, hist, stride, kahan, cd.nb, cd.kmin, cd.kmax);
+}
+
+// Diagnostics: (P, i1, k) of the best box at frequencies j0 .. j0 + count of one curve.
+__global__ void argmax_kernel(const CurveDesc* curve, int j0, int count, int phase, int kahan,
+                              int sign, float* P, int* i1, int* k)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CurveDesc cd = *curve;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    unsigned char* hist = smem + (size_t)threadIdx.x * (kahan ? 16 : 8);
+    const Best g = best_box_at(cd, grid_freq(cd, j0 + q), hist, blockDim.x, phase, kahan, sign);
+    P[q] = g.num > 0.0f ? __fdiv_rn(g.num, g.den) : 0.0f;
+    i1[q] = g.i1;
+    k[q] = g.k;
+}
+
+cudaError_t launch_argmax(const CurveDesc* d_curve, int nb, int nf, int phase, int kahan,
+                          int sign, float* P, int* i1, int* k, cudaStream_t s)
+{
+    const int esz = kahan ? 16 : 8;
+    int T = 64;
+    while (T > 1 && (size_t)T * nb * esz > 200 * 1024) T >>= 1;
+    const size_t smem = (size_t)T * nb * esz;
+    cudaError_t e = cudaFuncSetAttribute(argmax_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    for (int j0 = 0; j0 < nf; j0 += 65536) {
+        const int cnt = min(65536, nf - j0);
+        argmax_kernel<<<(cnt + T - 1) / T, T, smem, s>>>(d_curve, j0, cnt, phase, kahan, sign,
+                                                         P + j0, i1 + j0, k + j0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // ------------------------------------------------------------------------- a7: reduce
 
 constexpr int kReduceThreads = 256;
@@ -522,26 +997,29 @@ __device__ __forceinline__ bool better(float Pa, int ja, float Pb, int jb)
     return Pa > Pb || (Pa == Pb && ja < jb);
 }
 
-// Per curve: rank the local maxima of P(f_j) by (P desc, j asc) and keep topk; refit each
-// chosen box in FP64 from the raw inputs (exact FP64 fold, FP64 weights) and derive
-// period, epoch, duration, depth, SNR, SR.
+// Per curve: rank the local maxima of P(f_j) by (P desc, j asc) and keep topk; find the
+// best box of each kept frequency with the exact tie-break; refit that box in FP64 from
+// the raw inputs (exact FP64 fold, FP64 weights) and derive period, epoch, duration,
+// depth, SNR and SR.  Dynamic shared memory: one histogram column per kept frequency.
 __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
 {
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float sP[kReduceThreads / 32];
     __shared__ int sJ[kReduceThreads / 32];
     __shared__ int sT[kReduceThreads / 32];
     __shared__ int sel[kMaxTopK];
+    __shared__ int sel_i1[kMaxTopK], sel_k[kMaxTopK];
     __shared__ double red[kReduceThreads];
     const CurveDesc cd = p.curves[p.slots ? p.slots[blockIdx.x] : (int)blockIdx.x];
-    const FreqResult* res = cd.res;
+    const float* res = cd.res;
     const int K = p.topk;
     const int nf = cd.nf;
     Cand lst[kMaxTopK];
     int cnt = 0;
     for (int j = threadIdx.x; j < nf; j += blockDim.x) {
-        const float P = res[j].P;
+        const float P = res[j];
         if (p.spectrum) p.spectrum[cd.spec_off + j] = sqrtf(P);
-        const bool lm = (j == 0 || P > res[j - 1].P) && (j == nf - 1 || P >= res[j + 1].P);
+        const bool lm = (j == 0 || P > res[j - 1]) && (j == nf - 1 || P >= res[j + 1]);
         if (!lm) continue;
         int pos = cnt < K ? cnt : K;
         for (int q = 0; q < cnt; ++q) {
@@ -579,6 +1057,27 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
         if (sT[0] == (int)threadIdx.x) ++head;
         __syncthreads();
     }
+    // best box of each kept frequency, one thread per frequency, in rounds that fit
+    {
+        const int esz = p.kahan ? 16 : 8;
+        int R = (int)(p.smem_bytes / ((size_t)cd.nb * esz));
+        R = R < 1 ? 1 : (R > K ? K : R);
+        for (int q0 = 0; q0 < K; q0 += R) {
+            const int q = q0 + (int)threadIdx.x;
+            if ((int)threadIdx.x < R && q < K) {
+                if (sel[q] >= 0) {
+                    const Best g = best_box_at(cd, grid_freq(cd, sel[q]), smem + (size_t)threadIdx.x * esz,
+                                               R, p.phase, p.kahan, p.sign);
+                    sel_i1[q] = g.i1;
+                    sel_k[q] = g.k;
+                } else {
+                    sel_i1[q] = 0;
+                    sel_k[q] = cd.kmin;
+                }
+            }
+            __syncthreads();
+        }
+    }
     for (int q = 0; q < K; ++q) {
         const int j = sel[q];
         DevPeak* out = &p.peaks[(size_t)blockIdx.x * K + q];
@@ -590,13 +1089,12 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
             }
             continue;
         }
-        const FreqResult fr = res[j];
-        const int i1 = (int)(fr.box >> 16), k = (int)(fr.box & 0xffffu);
+        const int i1 = sel_i1[q], k = sel_k[q];
         const double f = grid_freq(cd, j);
         double r = 0.0, s = 0.0;
         for (int i = threadIdx.x; i < cd.n; i += blockDim.x) {
             const double dt = __dsub_rn(cd.t[i], cd.t_ref);
-            const int b = fold_exact(dt, f, cd.nb);
+            const int b = (int)fold_exact(dt, f, cd.nb);
             int rel = b - i1;
             if (rel < 0) rel += cd.nb;
             if (rel < k) {
@@ -619,7 +1117,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
             ph = ph - floor(ph);
             pk.epoch = cd.t_ref + ph / f;
             const double den = r * (1.0 - r);
-            const bool ok = fr.P > 0.0f && r > 0.0 && r < 1.0 && (p.sign || s < 0.0);
+            const bool ok = res[j] > 0.0f && r > 0.0 && r < 1.0 && (p.sign || s < 0.0);
             if (ok) {
                 pk.power = s * s / den;
                 pk.depth = -s / den;
@@ -634,10 +1132,20 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
     }
 }
 
+size_t reduce_smem_bytes(int nb_max, int topk, int kahan)
+{
+    size_t need = (size_t)nb_max * topk * (kahan ? 16 : 8);
+    const size_t cap = 160 * 1024;
+    return need < cap ? need : cap;
+}
+
 cudaError_t launch_reduce(const ReduceParams& p, int ncurves, cudaStream_t s)
 {
     if (ncurves <= 0) return cudaSuccess;
-    reduce_kernel<<<ncurves, kReduceThreads, 0, s>>>(p);
+    cudaError_t e = cudaFuncSetAttribute(reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)p.smem_bytes);
+    if (e != cudaSuccess) return e;
+    reduce_kernel<<<ncurves, kReduceThreads, p.smem_bytes, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -650,9 +1158,12 @@ __global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bi
     const int q = blockIdx.x;
     const double f = grid_freq(cd, js[q]);
     const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax);
-    for (int i = threadIdx.x; i < cd.n; i += blockDim.x) {
-        const float4 pt = cd.pts[i];
-        bins[(size_t)q * cd.n + i] = fold_point<PHASE>(pt, &cd.dt64[i], fc);
+    const FoldPacked fq = make_fold_packed(fc);
+    for (int pi = threadIdx.x; 2 * pi < cd.n; pi += blockDim.x) {
+        unsigned b0, b1;
+        fold_pair<PHASE>(cd.pts[2 * pi], &cd.dt64[2 * pi], fc, fq, b0, b1);
+        bins[(size_t)q * cd.n + 2 * pi] = (int)b0;
+        if (2 * pi + 1 < cd.n) bins[(size_t)q * cd.n + 2 * pi + 1] = (int)b1;
     }
 }
 
@@ -702,15 +1213,32 @@ __global__ void __launch_bounds__(kPlainThreads) plain_f64_kernel(
         __syncthreads();
         if (active) {
             for (int i = 0; i < cn; ++i) {
-                const int b = fold_exact(s_dt[i], f, nb);
+                const int b = (int)fold_exact(s_dt[i], f, nb);
                 hw[(size_t)b * nf] = __dadd_rn(hw[(size_t)b * nf], s_w[i]);
                 hx[(size_t)b * nf] = __dadd_rn(hx[(size_t)b * nf], s_wx[i]);
             }
         }
     }
     if (!active) return;
+    // occupied arc of bins (a box holding all of it holds every point)
+    int first = -1, last = -1, run = 0, gap = 0, gap_end = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (hw[(size_t)b * nf] != 0.0) {
+            if (first < 0) first = b;
+            else if (run > gap) { gap = run; gap_end = b; }
+            last = b;
+            run = 0;
+        } else if (first >= 0) {
+            ++run;
+        }
+    }
+    int arc_a = 0, arc_len = 0;
+    if (first >= 0) {
+        const int wrap = (nb - 1 - last) + first;
+        if (wrap >= gap) { arc_a = first; arc_len = last - first + 1; }
+        else { arc_a = gap_end; arc_len = nb - gap; }
+    }
     double best = 0.0;
-    int b1 = 0, bw = cd.kmin;
     for (int i1 = 0; i1 < nb; ++i1) {
         double r = 0.0, s = 0.0;
         int m = i1;
@@ -719,16 +1247,13 @@ __global__ void __launch_bounds__(kPlainThreads) plain_f64_kernel(
             s = __dadd_rn(s, hx[(size_t)m * nf]);
             m = (m + 1 == nb) ? 0 : m + 1;
             if (k < cd.kmin) continue;
-            if (!(r > 0.0) || !(r < 1.0)) continue;
+            if (r == 0.0 || box_full(i1, k, nb, arc_a, arc_len)) continue;
             if (!sign && !(s < 0.0)) continue;
             const double P = __ddiv_rn(__dmul_rn(s, s), __dmul_rn(r, __dsub_rn(1.0, r)));
-            if (P > best) { best = P; b1 = i1; bw = k; }
+            if (P > best) best = P;
         }
     }
-    FreqResult out;
-    out.P = __double2float_rn(best);
-    out.box = ((uint32_t)b1 << 16) | (uint32_t)bw;
-    cd.res[j] = out;
+    cd.res[j] = __double2float_rn(best);
 }
 
 cudaError_t launch_plain_f64(const CurveDesc* d_curve, const double* w64, const double* wx64,

@@ -12,7 +12,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/bls.h"
+#include "bls.h"
 #include "bls_internal.h"
 
 namespace blsgpu {

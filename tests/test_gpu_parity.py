@@ -227,6 +227,20 @@ def test_all_points_in_few_bins_degenerate_boxes():
     _edge(t, y, None, 20, 0.05, 0.5, freqs=np.array([1.0, 2.0, 0.5, 1.37]))
 
 
+def test_boxes_holding_most_of_the_weight():
+    """Points crowded into 5% of the phase at f = 1/d: with q up to 0.3 many boxes hold
+    almost all the weight (r close to 1), where FP32 loses 1 - r; those frequencies take
+    the precise sweep and must still meet the tolerance."""
+    rng = np.random.default_rng(12)
+    n = 600
+    t = synth.T0 + np.sort(rng.integers(0, 40, n) + rng.uniform(0, 0.05, n))
+    y = (1 + rng.normal(0, 0.01, n)).astype(np.float32)
+    y[np.abs(np.mod(t - synth.T0, 1.0) - 0.02) < 0.004] -= 0.02
+    freqs = np.concatenate([[1.0, 2.0, 0.5], np.linspace(0.98, 1.02, 41)])
+    _edge(t, y, None, 100, 0.01, 0.3, freqs=freqs)
+    _edge(t, y, None, 100, 0.01, 0.3, sign="both", freqs=freqs)
+
+
 def test_long_curve_many_chunks():
     rng = np.random.default_rng(6)
     n = 20000

@@ -189,6 +189,23 @@ def test_noise_free_box_on_bin_edges(nb, i1, k):
     assert P[0] == pytest.approx(scal[3], rel=1e-12)   # perfect fit: chi2 = 0
 
 
+def test_boxes_holding_every_point_or_none_do_not_count():
+    """Integer-day sampling: at f = 1 every point has phase 0, so no box has points on
+    both sides and the power is 0.  At f = 1/2 the points split into bins 0 and 5 (nb = 10);
+    with the odd days 0.02 low, equal weights give r = 1/2, s = -1/2 * 0.01, P = 1e-4.  For
+    dips, of the boxes holding only bin 5 the smallest (i1, k) with k <= 4 is (2, 4); with
+    both signs the bump box (0, 1) over bin 0 has the same power and comes first."""
+    t = T0 + np.arange(50.0)
+    y = np.where(np.arange(50) % 2 == 1, 0.98, 1.0).astype(np.float32)
+    for sign in (0, 1):
+        P, I1, K, _ = oracle.bls(t, y, None, 10, 1, 4, freqs=[1.0, 0.5], sign=sign)
+        assert P[0] == 0.0
+        yy = y.astype(np.float64)
+        d = yy[0] - yy[1]                    # 0.02 after FP32 rounding
+        assert P[1] == pytest.approx((0.5 * d / 2) ** 2 / 0.25, rel=1e-12)
+        assert (I1[1], K[1]) == ((2, 4) if sign == 0 else (0, 1))
+
+
 def test_box_across_phase_zero_wraps():
     nb, fstar = 50, 1.25
     rng = np.random.default_rng(3)
