@@ -465,20 +465,35 @@ __device__ __forceinline__ void fix_sub(const float4* cp, const double* cd, cons
     }
 }
 
-// Read-modify-write of the 16 points of a sub-chunk, pair by pair: both bins of a pair are
-// read before either is written, and the second point adds onto the first one's new value
-// when they share a bin, so the result equals adding the points one by one in order.
+// Read-modify-write of the 16 points of a sub-chunk in groups of 4: all four bins of a
+// group are read before any is written, and a point that lands in the bin of an earlier
+// point of the group adds onto that point's new value (the later store carries the
+// total), so the result equals adding the points one by one in order.
 __device__ __forceinline__ void rmw_sub(unsigned hbase, unsigned rowb, const unsigned* b,
                                         const float4* Bw)
 {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const unsigned a0 = hbase + b[2 * q] * rowb, a1 = hbase + b[2 * q + 1] * rowb;
-        const u64 h0 = lds64(a0), h1 = lds64(a1);
-        const u64 v0 = add2(h0, pk(Bw[q].x, Bw[q].y));
-        const u64 v1 = add2(b[2 * q + 1] == b[2 * q] ? v0 : h1, pk(Bw[q].z, Bw[q].w));
-        sts64(a0, v0);
-        sts64(a1, v1);
+    for (int g = 0; g < 4; ++g) {
+        unsigned a[4];
+        u64 h[4], v[4], q[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            a[i] = hbase + b[4 * g + i] * rowb;
+            h[i] = lds64(a[i]);
+        }
+        q[0] = pk(Bw[2 * g].x, Bw[2 * g].y);
+        q[1] = pk(Bw[2 * g].z, Bw[2 * g].w);
+        q[2] = pk(Bw[2 * g + 1].x, Bw[2 * g + 1].y);
+        q[3] = pk(Bw[2 * g + 1].z, Bw[2 * g + 1].w);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            u64 base = h[i];
+#pragma unroll
+            for (int j = 0; j < i; ++j) base = b[4 * g + i] == b[4 * g + j] ? v[j] : base;
+            v[i] = add2(base, q[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sts64(a[i], v[i]);
     }
 }
 

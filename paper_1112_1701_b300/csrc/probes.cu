@@ -12,6 +12,7 @@
 //   smem_red     private-column update with two shared-memory float atomic adds
 //   lds64        private-column 8-byte loads only
 //   mufu_rcp     approximate reciprocals (8 chains per thread)
+//   lds*/sts*_bw shared-memory bytes per SM per clock for 4, 8 and 16 bytes per lane
 // The histogram probes run one block per SM (like the search kernel, whose shared
 // histograms fill the SM) with 64, 128 or 192 threads.
 #include <cstdio>
@@ -125,7 +126,7 @@ __global__ void mufu_rcp(int iters, float* out, Stamp* st)
         for (int q = 0; q < 8; ++q) {
             float r;
             asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a[q]));
-            a[q] = r;
+            a[q] = __fadd_rn(r, 1.0f);
         }
     }
     float s = 0.f;
@@ -133,6 +134,43 @@ __global__ void mufu_rcp(int iters, float* out, Stamp* st)
     for (int q = 0; q < 8; ++q) s += a[q];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
     if (threadIdx.x == 0) st[blockIdx.x] = Stamp{c0, clock64(), t0, gtimer()};
+}
+
+// Shared-memory bandwidth: every lane reads (or writes) W bytes per access at conflict-free
+// consecutive addresses, 8 independent accesses per iteration.
+template <int W, int STORE>
+__global__ void smem_bw(int iters, float* out, Stamp* st)
+{
+    extern __shared__ __align__(16) float4 S4[];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int span = 8 * T;   // elements of W bytes
+    for (int i = t; i < span; i += T) S4[i] = make_float4(1.f, 2.f, 3.f, 4.f);
+    __syncthreads();
+    long long c0 = clock64();
+    unsigned long long t0 = gtimer();
+    float acc = 0.f;
+    const unsigned base = (unsigned)__cvta_generic_to_shared(S4);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const unsigned a = base + (unsigned)((q * T + t) * W);
+            if (STORE) {
+                if (W == 4) asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(acc));
+                if (W == 8) asm volatile("st.shared.v2.f32 [%0], {%1, %1};" ::"r"(a), "f"(acc));
+                if (W == 16) asm volatile("st.shared.v4.f32 [%0], {%1, %1, %1, %1};" ::"r"(a), "f"(acc));
+            } else {
+                float x, y, z, w;
+                if (W == 4) { asm volatile("ld.shared.f32 %0, [%1];" : "=f"(x) : "r"(a)); acc += x; }
+                if (W == 8) { asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a)); acc += x; }
+                if (W == 16) { asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a)); acc += x; }
+            }
+        }
+        acc *= 0.5f;
+    }
+    long long c1 = clock64();
+    unsigned long long t1 = gtimer();
+    out[blockIdx.x * blockDim.x + t] = acc;
+    if (t == 0) st[blockIdx.x] = Stamp{c0, c1, t0, t1};
 }
 
 // Private-column histogram of 128 bins (float2 entries, stride = blockDim.x).
@@ -260,6 +298,23 @@ int main(int argc, char** argv)
         const int blocks = sms * 8, T = 256, it = (int)(4000 * scale);
         Result r = run([&] { mufu_rcp<<<blocks, T>>>(it, out, st); }, blocks, (double)blocks * T * it * 8, st, sms);
         printf("{\"probe\": \"mufu_rcp\", \"ms\": %.3f, \"clk_mhz\": %.0f, \"rcp_per_sm_clk\": %.2f}\n", r.ms, r.clk_mhz, r.per_sm_clk);
+    }
+    {   // shared-memory bandwidth, 8 warps per SM (two 128-thread blocks)
+        const int T = 128, blocks = sms * 2, it = (int)(20000 * scale);
+        const size_t smem = (size_t)8 * T * 16;
+        auto runbw = [&](const char* nm, int W, auto k) {
+            CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            Result r = run([&] { k<<<blocks, T, smem>>>(it, out, st); }, blocks,
+                           (double)blocks * T * it * 8 * W, st, sms);
+            printf("{\"probe\": \"%s\", \"ms\": %.3f, \"clk_mhz\": %.0f, \"bytes_per_sm_clk\": %.1f}\n", nm, r.ms,
+                   r.clk_mhz, r.per_sm_clk);
+        };
+        runbw("lds32_bw", 4, smem_bw<4, 0>);
+        runbw("lds64_bw", 8, smem_bw<8, 0>);
+        runbw("lds128_bw", 16, smem_bw<16, 0>);
+        runbw("sts32_bw", 4, smem_bw<4, 1>);
+        runbw("sts64_bw", 8, smem_bw<8, 1>);
+        runbw("sts128_bw", 16, smem_bw<16, 1>);
     }
     const char* names[4] = {"smem_rmw", "smem_rmw2", "smem_red", "lds64"};
     const int Ts[3] = {64, 128, 192};
