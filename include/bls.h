@@ -199,6 +199,28 @@ typedef struct {
  * Errors: BLS_ERR_INVALID. */
 bls_status bls_profile_get(bls_plan* plan, bls_profile* out, int reset);
 
+/* Search of one curve that allocates nothing.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc (a plug-in whose host application
+ * owns and budgets all device memory, a latency-critical loop that cannot take
+ * cudaMalloc's implicit device synchronisation, a process under a memory cap).
+ *   curve      t, y, dy (optional), freqs (optional) in device memory; nb >= 2 and
+ *              0 < qmin <= qmax < 1 must be given (there is no plan to default from).
+ *   topk, sign as in bls_plan_desc (dips only or both signs; FP32 sums, double-FP32 fold).
+ *   cuda_stream stream the work is ordered on (NULL: the legacy default stream).
+ *   peaks_dev  device memory for topk bls_peak records, filled as bls_search fills `out`.
+ *   spectrum_dev optional device memory for nf floats, SR(f_j) as bls_search writes it.
+ * All intermediate data lives in one static device array of 32 MiB per device, which every
+ * GPU that loads this library holds until the process exits; curves needing more
+ * (about 24 bytes per point plus 4 per frequency) are rejected with BLS_ERR_INVALID.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture.  Every call shares the
+ * array and leaves its contents behind, so calls that overlap on the GPU (other threads,
+ * other streams) race: serialise them.  Blocks until the results are written.
+ * Errors: BLS_ERR_INVALID (bad argument, host memory given, too large, bad input values),
+ * BLS_ERR_CUDA. */
+bls_status bls_search_static(const bls_curve* curve, int topk, int sign, void* cuda_stream,
+                             bls_peak* peaks_dev, float* spectrum_dev);
+
 /* Thread-local message of the last failure on the calling thread ("" if none). */
 const char* bls_last_error(void);
 

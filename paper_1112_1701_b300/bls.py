@@ -82,7 +82,7 @@ _lock = threading.Lock()
 
 EXPORTS = ["bls_plan_create", "bls_plan_destroy", "bls_search", "bls_submit", "bls_poll",
            "bls_cancel", "bls_server_stats_get", "bls_kminmax", "bls_debug_fold",
-           "bls_debug_powers", "bls_profile_get", "bls_last_error"]
+           "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_last_error"]
 
 
 def lib():
@@ -107,6 +107,7 @@ def lib():
             L.bls_debug_fold.argtypes = [P, C.POINTER(CurveStruct), P, I, P]
             L.bls_debug_powers.argtypes = [P, C.POINTER(CurveStruct), P, P, P]
             L.bls_profile_get.argtypes = [P, C.POINTER(Profile), I]
+            L.bls_search_static.argtypes = [C.POINTER(CurveStruct), I, I, P, P, P]
             L.bls_last_error.argtypes = []
             L.bls_last_error.restype = C.c_char_p
             _lib = L
@@ -188,6 +189,24 @@ def curves_from_batch(batch, device=None) -> List[CurveInput]:
                               df=g.df, nb=nb, qmin=batch.qmin, qmax=batch.qmax))
         o += n
     return out
+
+
+def search_static(curve: CurveInput, topk: int = 1, sign: str = "dips", stream=None,
+                  peaks=None, spectrum=None):
+    """``bls_search_static``: one curve, device inputs and outputs, no allocation inside.
+
+    ``peaks`` is a CUDA uint8 tensor of at least topk * sizeof(bls_peak) bytes; it receives
+    the peak records (read them back with ``peaks_to_numpy``)."""
+    keep: list = []
+    cs = _struct(curve, keep)
+    _check(lib().bls_search_static(C.byref(cs), int(topk), SIGN[sign], stream, _ptr(peaks),
+                                   _ptr(spectrum)))
+
+
+def peaks_to_numpy(buf, topk: int) -> np.ndarray:
+    """Peak records written to a device byte buffer, as a structured numpy array."""
+    raw = buf.detach().cpu().numpy().view(np.uint8)[:topk * PEAK_DTYPE.itemsize]
+    return raw.view(PEAK_DTYPE).copy()
 
 
 class Plan:
