@@ -105,6 +105,38 @@ __device__ __forceinline__ void upk(u64 v, float& lo, float& hi)
 {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
+#ifdef BLS_SCALAR_PAIRS
+// Pair arithmetic spelled as two scalar FP32 instructions (same rounding, per lane).
+__device__ __forceinline__ u64 add2(u64 a, u64 b)
+{
+    float a0, a1, b0, b1;
+    upk(a, a0, a1);
+    upk(b, b0, b1);
+    return pk(__fadd_rn(a0, b0), __fadd_rn(a1, b1));
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b)
+{
+    float a0, a1, b0, b1;
+    upk(a, a0, a1);
+    upk(b, b0, b1);
+    return pk(__fsub_rn(a0, b0), __fsub_rn(a1, b1));
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b)
+{
+    float a0, a1, b0, b1;
+    upk(a, a0, a1);
+    upk(b, b0, b1);
+    return pk(__fmul_rn(a0, b0), __fmul_rn(a1, b1));
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c)
+{
+    float a0, a1, b0, b1, c0, c1;
+    upk(a, a0, a1);
+    upk(b, b0, b1);
+    upk(c, c0, c1);
+    return pk(__fmaf_rn(a0, b0, c0), __fmaf_rn(a1, b1, c1));
+}
+#else
 __device__ __forceinline__ u64 add2(u64 a, u64 b)
 {
     u64 d;
@@ -129,6 +161,8 @@ __device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+
+#endif
 
 // Constants of the double-FP32 fold as broadcast pairs.
 struct FoldPacked {
@@ -604,62 +638,78 @@ __device__ __forceinline__ void eval_pair(u64& R, u64& X, const u64& HW2, const 
     if (use1) b1 = fmaxf(b1, p1);
 }
 
+// One step of the fast sweep over one block: bin value (hw, hx) for the pairs [Q0, Q1),
+// with the ramp rules given by (init, use0, use1) per pair (see sweep_fast).
+template <int SIGN, int NP>
+__device__ __forceinline__ void sweep_step(float hw, float hx, u64* R, u64* X, float* b0,
+                                           float* b1, const u64& ONE2, int mm, int phase,
+                                           int e)
+{
+    const u64 HW2 = pk(hw, hw), HX2 = pk(hx, hx);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        if (phase == 0) {          // ramp-up at bin mm
+            if (2 * q > mm) continue;
+            eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, 2 * q == mm, true, 2 * q < mm, b0[q], b1[q]);
+        } else if (phase == 1) {   // steady
+            eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, false, true, true, b0[q], b1[q]);
+        } else {                   // ramp-down step e
+            if (2 * q + 1 < e + 1) continue;
+            eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, false, 2 * q >= e + 1, true, b0[q], b1[q]);
+        }
+    }
+}
+
+// Fast sweep over two independent blocks of SB starts at a time (starts i0.. and
+// i0 + half..), so that 2*SB/2 packed pairs are in flight per bin step.  Block A covers
+// starts [0, half), block B [half, 2 half) with half = SB * ceil(nb / (2 SB)); starts past
+// nb repeat earlier ones (cyclic) and cannot change the maximum.
 template <int SB, int SIGN>
-__device__ __noinline__ float sweep_fast(const u64* __restrict__ H, int stride, int nb, int kmax)
+__device__ __forceinline__ float sweep_fast(unsigned hbase, unsigned rowb, int nb, int kmax)
 {
     constexpr int NP = SB / 2;
-    const size_t S = (size_t)stride;
     const u64 ONE2 = pk(1.0f, 1.0f);
-    float best0[NP], best1[NP];
+    float a0[NP], a1[NP], c0[NP], c1[NP];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) { best0[q] = 0.0f; best1[q] = 0.0f; }
-    for (int i0 = 0; i0 < nb; i0 += SB) {
-        u64 R[NP], X[NP];
+    for (int q = 0; q < NP; ++q) { a0[q] = 0.0f; a1[q] = 0.0f; c0[q] = 0.0f; c1[q] = 0.0f; }
+    const int half = SB * ((nb + 2 * SB - 1) / (2 * SB));
+    for (int i0 = 0; i0 < half; i0 += SB) {
+        u64 RA[NP], XA[NP], RB[NP], XB[NP];
 #pragma unroll
-        for (int q = 0; q < NP; ++q) { R[q] = 0ull; X[q] = 0ull; }
-        int m = i0;
-        // ramp-up: bin mm of the block starts accumulator mm and feeds those before it
+        for (int q = 0; q < NP; ++q) { RA[q] = 0ull; XA[q] = 0ull; RB[q] = 0ull; XB[q] = 0ull; }
+        int ma = i0, mb = i0 + half;
+        while (mb >= nb) mb -= nb;
+#define BLS_LOAD2(HWA, HXA, HWB, HXB)                                   \
+        upk(lds64(hbase + (unsigned)ma * rowb), HWA, HXA);             \
+        upk(lds64(hbase + (unsigned)mb * rowb), HWB, HXB);             \
+        ma = (ma + 1 == nb) ? 0 : ma + 1;                               \
+        mb = (mb + 1 == nb) ? 0 : mb + 1;
 #pragma unroll
         for (int mm = 0; mm < SB - 1; ++mm) {
-            float hw, hx;
-            upk(H[(size_t)m * S], hw, hx);
-            m = (m + 1 == nb) ? 0 : m + 1;
-            const u64 HW2 = pk(hw, hw), HX2 = pk(hx, hx);
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                if (2 * q > mm) continue;
-                eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, 2 * q == mm, true, 2 * q < mm,
-                                best0[q], best1[q]);
-            }
+            float hwa, hxa, hwb, hxb;
+            BLS_LOAD2(hwa, hxa, hwb, hxb)
+            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, ONE2, mm, 0, 0);
+            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, ONE2, mm, 0, 0);
         }
-        // steady: every start takes the bin
+#pragma unroll 2
         for (int mm = SB - 1; mm < kmax; ++mm) {
-            float hw, hx;
-            upk(H[(size_t)m * S], hw, hx);
-            m = (m + 1 == nb) ? 0 : m + 1;
-            const u64 HW2 = pk(hw, hw), HX2 = pk(hx, hx);
-#pragma unroll
-            for (int q = 0; q < NP; ++q)
-                eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, false, true, true, best0[q], best1[q]);
+            float hwa, hxa, hwb, hxb;
+            BLS_LOAD2(hwa, hxa, hwb, hxb)
+            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, ONE2, 0, 1, 0);
+            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, ONE2, 0, 1, 0);
         }
-        // ramp-down: accumulator a keeps going while its width stays <= kmax (a > e)
 #pragma unroll
         for (int e = 0; e < SB - 1; ++e) {
-            float hw, hx;
-            upk(H[(size_t)m * S], hw, hx);
-            m = (m + 1 == nb) ? 0 : m + 1;
-            const u64 HW2 = pk(hw, hw), HX2 = pk(hx, hx);
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                if (2 * q + 1 < e + 1) continue;
-                eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, false, 2 * q >= e + 1, true,
-                                best0[q], best1[q]);
-            }
+            float hwa, hxa, hwb, hxb;
+            BLS_LOAD2(hwa, hxa, hwb, hxb)
+            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, ONE2, 0, 2, e);
+            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, ONE2, 0, 2, e);
         }
+#undef BLS_LOAD2
     }
     float best = 0.0f;
 #pragma unroll
-    for (int q = 0; q < NP; ++q) best = fmaxf(best, fmaxf(best0[q], best1[q]));
+    for (int q = 0; q < NP; ++q) best = fmaxf(fmaxf(best, fmaxf(a0[q], a1[q])), fmaxf(c0[q], c1[q]));
     return best;
 }
 
@@ -745,27 +795,55 @@ __device__ __forceinline__ Best sweep_exact_rt(int sign, const unsigned char* hi
 }
 
 // Largest power of one private histogram: fast sweep when its conditions hold, else the
-// exact sweep.  No box can hold more than 0.9 of the weight when kmax times the heaviest
-// bin stays below 0.89 (the margin covers FP32 rounding of the sums).
-template <int KAHAN, int SIGN>
+// exact sweep.  The fast sweep needs that no box holds more than 0.9 of the weight; the
+// cheap test kmax * (heaviest bin) < 0.89 settles most frequencies, and when it fails the
+// heaviest run of kmax bins is measured with a sliding sum (the 0.01 margin covers FP32
+// rounding of the sums).
+template <int KAHAN, int SIGN, int SB>
 __device__ __forceinline__ float sweep_max(const unsigned char* hist, int stride, int nb,
                                            int kmin, int kmax)
 {
-    if (!KAHAN && kmin == 1 && kmax >= 3) {
+    if (!KAHAN && kmin == 1 && kmax >= SB - 1) {
+        const unsigned hbase = (unsigned)__cvta_generic_to_shared(hist);
+        const unsigned rowb = (unsigned)stride * 8u;
         float wmax = 0.0f;
-        const float2* H2 = reinterpret_cast<const float2*>(hist);
-        for (int b = 0; b < nb; ++b) wmax = fmaxf(wmax, H2[(size_t)b * stride].x);
-        if ((float)kmax * wmax < 0.89f) {
-            const u64* H = reinterpret_cast<const u64*>(hist);
-            return kmax >= 15 ? sweep_fast<8, SIGN>(H, stride, nb, kmax)
-                              : sweep_fast<4, SIGN>(H, stride, nb, kmax);
+        for (int b = 0; b < nb; ++b) {
+            float hw, hx;
+            upk(lds64(hbase + (unsigned)b * rowb), hw, hx);
+            wmax = fmaxf(wmax, hw);
         }
+        bool fast = (float)kmax * wmax < 0.89f;
+        if (!fast && kmax < nb) {
+            float win = 0.0f, hw, hx;
+            for (int b = 0; b < kmax; ++b) {
+                upk(lds64(hbase + (unsigned)b * rowb), hw, hx);
+                win += hw;
+            }
+            float rmax = win;
+            int add = kmax;
+            for (int b = 0; b + 1 < nb; ++b) {   // window [b+1, b+kmax] (cyclic)
+                float hin, hout;
+                upk(lds64(hbase + (unsigned)add * rowb), hin, hx);
+                upk(lds64(hbase + (unsigned)b * rowb), hout, hx);
+                win = __fsub_rn(__fadd_rn(win, hin), hout);
+                rmax = fmaxf(rmax, win);
+                add = (add + 1 == nb) ? 0 : add + 1;
+            }
+            fast = rmax < 0.89f;
+        }
+        if (fast) return sweep_fast<SB, SIGN>(hbase, rowb, nb, kmax);
     }
     const Best g = sweep_exact<SIGN>(hist, stride, KAHAN, nb, kmin, kmax);
     return g.num > 0.0f ? __fdiv_rn(g.num, g.den) : 0.0f;
 }
 
 // ------------------------------------------------------------------------- a2-a6: hot kernel
+
+// Starts per block of the fast sweep for wide boxes (kmax >= 15).
+#ifndef BLS_SWEEP_WIDE
+#define BLS_SWEEP_WIDE 8
+#endif
+constexpr int kSweepWide = BLS_SWEEP_WIDE;
 
 constexpr int kFoldMaxThreads = 256;
 
@@ -873,7 +951,10 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
             __syncthreads();
         }
 
-        if (active) cdr.res[j] = sweep_max<KAHAN, SIGN>(hist, p.stride, nb, kmin, kmax);
+        if (active) {
+            cdr.res[j] = kmax >= 15 ? sweep_max<KAHAN, SIGN, kSweepWide>(hist, p.stride, nb, kmin, kmax)
+                                    : sweep_max<KAHAN, SIGN, 4>(hist, p.stride, nb, kmin, kmax);
+        }
     }
 }
 
