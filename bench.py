@@ -188,6 +188,100 @@ def run_reference(args):
     return 0
 
 
+def run_serving(args):
+    """Serving benchmark: a Poisson stream of single-curve requests, each with its own
+    grid and bin count (N log-uniform 200-20000, 10k-100k frequencies, nb 100-400), at
+    fractions of the measured saturation throughput; p50/p99 latency from submit to result.
+    The plain FP64 one-curve-per-launch kernel is timed per request on a sample and its
+    first-come-first-served queue is simulated on the same arrival times."""
+    import threading
+    import torch
+    from paper_1112_1701_b300 import bls
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    nreq = args.requests
+    b = synth.config4_requests(nreq)
+    reqs = [bls.CurveInput(c.t, c.y, c.dy, nf=g.nf, fmin=g.fmin, df=g.df, nb=nb, qmin=b.qmin,
+                           qmax=b.qmax) for c, g, nb in zip(b.curves, b.grids, b.nb)]
+    units = sum(len(c.t) * g.nf for c, g in zip(b.curves, b.grids))
+
+    def serve(arrivals):
+        with bls.Plan(nb=200, qmin=QMIN, qmax=QMAX, topk=1) as p:
+            warm = [p.submit(r) for r in reqs[:8]]
+            for tk in warm:
+                p.poll(tk, timeout_ms=600000)
+            tickets = [None] * nreq
+
+            def submitter():
+                t0 = time.perf_counter()
+                for i, r in enumerate(reqs):
+                    if arrivals is not None:
+                        delay = arrivals[i] - (time.perf_counter() - t0)
+                        if delay > 0:
+                            time.sleep(delay)
+                    tickets[i] = p.submit(r)
+
+            th = threading.Thread(target=submitter)
+            t0 = time.perf_counter()
+            th.start()
+            th.join()
+            for tk in tickets:
+                st, _ = p.poll(tk, timeout_ms=600000)
+                assert st == bls.OK
+            wall = time.perf_counter() - t0
+            stt = p.stats()
+            # latencies of this run only (the warm-up requests are the first 8)
+            return wall, stt
+
+    wall_sat, st_sat = serve(None)
+    sat_rate = nreq / wall_sat
+    loads = []
+    for frac in args.loads:
+        arr = synth.poisson_arrivals(nreq, frac * sat_rate)
+        wall, st = serve(arr)
+        loads.append({"offered_fraction": frac, "offered_req_per_s": frac * sat_rate,
+                      "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                      "throughput_req_per_s": nreq / wall,
+                      "point_freq_per_s": units / wall, "steps": st["steps"]})
+    # plain FP64 baseline: measured service times of a sample, FIFO queue simulated
+    rng = np.random.default_rng(0)
+    sample = sorted(rng.choice(nreq, size=min(args.plain_sample, nreq), replace=False))
+    svc = []
+    with bls.Plan(nb=200, qmin=QMIN, qmax=QMAX, algo="plain_f64") as pp:
+        pp.search([reqs[sample[0]]])
+        for i in sample:
+            t0 = time.perf_counter()
+            pp.search([reqs[i]])
+            svc.append(time.perf_counter() - t0)
+    svc = np.array(svc)
+    plain_units = sum(len(reqs[i].t) * reqs[i].nf for i in sample)
+    plain_rate = plain_units / svc.sum()
+    sim = []
+    for ld in loads:
+        arr = synth.poisson_arrivals(nreq, ld["offered_req_per_s"])
+        draw = rng.choice(svc, size=nreq, replace=True)
+        done, lat = 0.0, []
+        for a, s_ in zip(arr, draw):
+            start = max(a, done)
+            done = start + s_
+            lat.append(1000 * (done - a))
+        sim.append({"offered_fraction": ld["offered_fraction"],
+                    "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99))})
+    line = {"metric": "BLS serving latency and throughput", "value": units / wall_sat,
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"serving: {nreq} requests, N log-uniform 200-20000, "
+                                   f"nf 10k-100k, nb 100-400, Poisson arrivals",
+                       "requests": nreq},
+            "saturation": {"req_per_s": sat_rate, "point_freq_per_s": units / wall_sat},
+            "loads": loads,
+            "plain_f64_baseline": {"point_freq_per_s": plain_rate,
+                                   "sample_requests": len(sample),
+                                   "mean_service_ms": 1000 * float(svc.mean()),
+                                   "simulated_fifo_at_same_offered_rate": sim}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def workload_config(batch, args):
     return {"workload": f"batched BLS: {len(batch)} curves, N log-uniform 500-5000 over 60 "
                         f"nights, {batch.grids[0].nf} freqs uniform in [0.1, 5]/d, nb={NB}, "
@@ -212,9 +306,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--plain-curves", type=int, default=8,
                     help="curves of the plain FP64 baseline timing (0 = skip)")
+    ap.add_argument("--serving", action="store_true", help="run the serving benchmark")
+    ap.add_argument("--requests", type=int, default=4000)
+    ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.7, 0.9])
+    ap.add_argument("--plain-sample", type=int, default=60)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
 
     import torch
     from paper_1112_1701_b300 import bls
