@@ -282,6 +282,134 @@ def run_serving(args):
     return 0
 
 
+def run_precision(args):
+    """Precision study on the three-year workload (3000 points over 1095 days with seasonal
+    gaps, up to 5475 cycles at the highest frequency): every phase mode {f64, df32, f32} x
+    sum mode {f32, kahan} against the FP64 oracle on a subset of curves, full grid.
+    Reports the phase-bin mismatch rate (sampled frequencies, all points), the SR relative
+    error over the spectrum, the peak-depth error, and best-frequency disagreements."""
+    import torch
+    import oracle
+    from paper_1112_1701_b300 import bls
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    b = synth.config3(ncurves=args.prec_curves, nf=args.nf_prec)
+    nb = b.nb[0]
+    kmin, kmax = oracle.kminmax(nb, b.qmin, b.qmax)
+    cis = bls.curves_from_batch(b)
+    nf = b.grids[0].nf
+    cores = os.cpu_count() or 1
+    cur = [dict(t=c.t, y=c.y, dy=c.dy, nb=nb, kmin=kmin, kmax=kmax, fmin=g.fmin, df=g.df,
+                nf=g.nf) for c, g in zip(b.curves, b.grids)]
+    t0 = time.perf_counter()
+    opk, oP = oracle.bls_many(cur, nthreads=cores, topk=1, want_power=True)
+    t_oracle = time.perf_counter() - t0
+    osr = np.sqrt(oP).reshape(len(b), nf)
+    sumwx2 = np.array([oracle.prep(c.t, c.y, c.dy)[3][3] for c in b.curves])
+    # frequencies for the bin comparison: spread over the grid, the top 1% dense
+    js = sorted(set(np.linspace(0, nf - 1, args.prec_bin_freqs // 2).astype(int).tolist()
+                    + np.linspace(int(0.99 * nf), nf - 1,
+                                  args.prec_bin_freqs // 2).astype(int).tolist()))
+    freqs = [oracle.freq(j, b.grids[0].fmin, b.grids[0].df) for j in js]
+    obins = [oracle.bins(c.t, freqs, nb) for c in b.curves[:args.prec_bin_curves]]
+    rows = []
+    for phase in ("f64", "df32", "f32"):
+        for sm in ("f32", "kahan"):
+            with bls.Plan(nb=nb, qmin=b.qmin, qmax=b.qmax, topk=1, phase=phase, sum=sm) as p:
+                spec = np.zeros(len(b) * nf, np.float32)
+                pk = p.search(cis, spectrum=spec)
+                mism = 0
+                tot = 0
+                for q in range(len(obins)):
+                    bg = p.debug_fold(cis[q], js)
+                    mism += int((bg != obins[q]).sum())
+                    tot += bg.size
+            gsr = spec.reshape(len(b), nf).astype(np.float64)
+            rel = np.abs(gsr - osr) / np.maximum(osr, 1e-300)
+            tol = 1e-5 * osr + 1e-6 * np.sqrt(sumwx2)[:, None]
+            sig = osr > 1e-3 * osr.max(axis=1, keepdims=True)
+            dj, dj_sep, ddepth = 0, 0, []
+            for q in range(len(b)):
+                jo = opk[q][0].j
+                jg = int(pk[q, 0]["j"])
+                srt = np.sort(osr[q])
+                separated = (srt[-1] - srt[-2]) > 1e-5 * srt[-1]
+                if jg != jo:
+                    dj += 1
+                    dj_sep += int(separated)
+                else:
+                    ddepth.append(abs(float(pk[q, 0]["depth"]) - opk[q][0].depth))
+            rows.append({"phase": phase, "sum": sm,
+                         "bin_mismatch_rate": mism / max(tot, 1),
+                         "sr_rel_err_median": float(np.median(rel[sig])),
+                         "sr_rel_err_p99": float(np.percentile(rel[sig], 99)),
+                         "sr_rel_err_max": float(rel[sig].max()),
+                         "frac_outside_parity_tol": float((np.abs(gsr - osr) > tol).mean()),
+                         "depth_abs_err_max_same_j": max(ddepth) if ddepth else None,
+                         "best_j_disagree": dj, "best_j_disagree_separated": dj_sep})
+    line = {"metric": "BLS precision study", "data": "synthetic", "n_gpus": 1,
+            "config": {"workload": f"three-year baseline: {len(b)} curves x 3000 points over "
+                                   f"1095 d, seasonal gaps, {nf} freqs uniform in [0.05, 5]/d, "
+                                   f"nb={nb}, q {b.qmin}-{b.qmax}",
+                       "bin_check": f"{len(obins)} curves x {len(js)} frequencies x all points",
+                       "oracle_s": round(t_oracle, 1), "oracle_threads": cores},
+            "sr_rel_err_over": "frequencies with oracle SR > 1e-3 of the curve's maximum",
+            "modes": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_survey(args):
+    """Survey-scale subset: the 100k-curve sweep shape (2000 points over 90 nights, 200k
+    frequencies in [0.1, 5]/d, nb = 256, top-5 peaks per curve), timed on a contiguous
+    subset of curves; the full run's time is extrapolated linearly in curves."""
+    import torch
+    from paper_1112_1701_b300 import bls
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    b = synth.config5(ncurves=args.survey_curves)
+    nb = b.nb[0]
+    dev = bls.curves_from_batch(b, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    units = b.point_freqs()
+    evals = box_evals(b)
+    with bls.Plan(nb=nb, qmin=b.qmin, qmax=b.qmax, topk=5, stream=stream.cuda_stream) as p:
+        for _ in range(max(1, args.warmup)):
+            flush.zero_()
+            pk = p.search(dev)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            pk = p.search(dev)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    inj = [i for i, c in enumerate(b.curves) if c.truth is not None]
+    rec = 0
+    for i in inj:
+        P = b.curves[i].truth["period"]
+        got = [float(x["period"]) for x in pk[i]]
+        rec += any(abs(g - P) / P < 0.01 or abs(2 * g - P) / P < 0.01 or abs(g - 2 * P) / P < 0.01
+                   for g in got)
+    line = {"metric": METRIC, "value": units / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": f"survey sweep subset: {len(b)} of 100000 curves x 2000 "
+                                   f"points, {b.grids[0].nf} freqs in [0.1, 5]/d, nb={nb}, "
+                                   f"q {b.qmin}-{b.qmax}, top-5 peaks",
+                       "ncurves": len(b), "nb": nb, "topk": 5,
+                       "l2": "flushed (256 MiB write) before every step"},
+            "box_evals_per_s": evals / (ms / 1000.0),
+            "full_100k_curves_s_extrapolated": ms / 1000.0 * 100000 / len(b),
+            "injected": len(inj), "injected_recovered_top5": rec}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def workload_config(batch, args):
     return {"workload": f"batched BLS: {len(batch)} curves, N log-uniform 500-5000 over 60 "
                         f"nights, {batch.grids[0].nf} freqs uniform in [0.1, 5]/d, nb={NB}, "
@@ -310,14 +438,25 @@ def main():
     ap.add_argument("--requests", type=int, default=4000)
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.7, 0.9])
     ap.add_argument("--plain-sample", type=int, default=60)
+    ap.add_argument("--precision", action="store_true", help="run the precision study")
+    ap.add_argument("--prec-curves", type=int, default=16)
+    ap.add_argument("--nf-prec", type=int, default=200000)
+    ap.add_argument("--prec-bin-curves", type=int, default=4)
+    ap.add_argument("--prec-bin-freqs", type=int, default=400)
+    ap.add_argument("--survey", action="store_true", help="run the survey-scale subset")
+    ap.add_argument("--survey-curves", type=int, default=2048)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.serving:
         return run_serving(args)
+    if args.precision:
+        return run_precision(args)
+    if args.survey:
+        return run_survey(args)
 
     import torch
-    from paper_1112_1701_b300 import bls
+    from paper_1112_1701_b300 import bls, shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -333,7 +472,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    batch = synth.config2(args.ncurves, nf=args.nf, first=rank * args.ncurves)
+    # weak scaling: every rank searches its own args.ncurves curves of a world*ncurves batch
+    lo, hi = shard.curve_range(world * args.ncurves, world, rank)
+    batch = synth.config2(hi - lo, nf=args.nf, first=lo)
     units = batch.point_freqs()
     evals = box_evals(batch)
     dev = bls.curves_from_batch(batch, device="cuda")
@@ -428,6 +569,12 @@ def main():
                           "reduce": prof["reduce_ms"] / args.steps}}
     if e2e:
         line["e2e"] = e2e
+
+    # the per-curve records of all ranks, gathered on rank 0 (outside the timed region)
+    last = plan.search(dev)
+    gathered = shard.search_curve_shards(world * args.ncurves, lambda a, b: last)
+    if rank == 0:
+        line["gathered_peaks"] = int(gathered.shape[0])
 
     # the plain FP64 one-curve-per-launch GPU kernel on a sample of the same curves
     if args.plain_curves > 0 and rank == 0:

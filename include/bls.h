@@ -136,6 +136,11 @@ void bls_plan_destroy(bls_plan* plan);
  * starts and widths; out[c*topk + q] receives peak q of curve c (host memory).
  * spectrum (optional, host or device) receives SR(f_j) of every curve back to back
  * (sum of nf floats).  Blocks until the results are written.
+ * When every input array and the spectrum are device or pinned host memory, a launch
+ * group's stream work (copies, kernels, result copies) is captured into a CUDA graph,
+ * and a later call whose group has the same layout (same pointers, sizes, options)
+ * replays it with one launch; the arrays' contents may change between calls.  The
+ * environment variable BLS_NO_GRAPHS=1, read at plan creation, turns this off.
  * Errors: BLS_ERR_INVALID, BLS_ERR_NOMEM, BLS_ERR_CUDA, BLS_ERR_INTERNAL. */
 bls_status bls_search(bls_plan* plan, const bls_curve* curves, int ncurves,
                       bls_peak* out, float* spectrum);
@@ -192,6 +197,8 @@ typedef struct {
     double prep_ms;             /* CUDA-event time of the prep kernels */
     double fold_ms;             /* CUDA-event time of the fold-bin-sweep kernels */
     double reduce_ms;           /* CUDA-event time of the peak reductions */
+    uint64_t graph_captures;    /* groups captured into a CUDA graph (then launched) */
+    uint64_t graph_replays;     /* groups run by replaying the previous group's graph */
 } bls_profile;
 
 /* Diagnostic: kernel timings of bls_search, measured with CUDA events recorded on the

@@ -68,7 +68,8 @@ class ServerStats(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("searches", C.c_uint64), ("kernel_launches", C.c_uint64),
                 ("fold_launches", C.c_uint64), ("prep_ms", C.c_double),
-                ("fold_ms", C.c_double), ("reduce_ms", C.c_double)]
+                ("fold_ms", C.c_double), ("reduce_ms", C.c_double),
+                ("graph_captures", C.c_uint64), ("graph_replays", C.c_uint64)]
 
 
 PEAK_DTYPE = np.dtype([("j", np.int32), ("i1", np.int32), ("k", np.int32), ("pad_", np.int32),
@@ -170,18 +171,18 @@ def _struct(c: CurveInput, keep: list) -> CurveStruct:
                        float(c.df), int(c.nb), float(c.qmin), float(c.qmax))
 
 
-def curves_from_batch(batch, device=None) -> List[CurveInput]:
+def curves_from_batch(batch, device=None, pinned: bool = False) -> List[CurveInput]:
     """CurveInputs of a synth.Batch, packed into contiguous arrays (one copy per array
     for the whole batch).  With ``device`` (e.g. "cuda") the arrays are torch tensors
-    resident there."""
+    resident there; with ``pinned`` they are page-locked host torch tensors."""
     ts = np.concatenate([c.t for c in batch.curves])
     ys = np.concatenate([c.y for c in batch.curves])
     dys = np.concatenate([c.dy for c in batch.curves])
-    if device is not None:
+    if device is not None or pinned:
         import torch
-        ts = torch.from_numpy(ts).to(device)
-        ys = torch.from_numpy(ys).to(device)
-        dys = torch.from_numpy(dys).to(device)
+        conv = (lambda a: torch.from_numpy(a).to(device)) if device is not None else \
+            (lambda a: torch.from_numpy(a).pin_memory())
+        ts, ys, dys = conv(ts), conv(ys), conv(dys)
     out, o = [], 0
     for c, g, nb in zip(batch.curves, batch.grids, batch.nb):
         n = len(c.t)

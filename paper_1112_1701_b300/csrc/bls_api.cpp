@@ -69,14 +69,18 @@ void HostBuf::release()
     bytes = 0;
 }
 
-static bool is_device_ptr(const void* p)
+// Where an input lives: 0 pageable host, 1 pinned host, 2 device (or managed).
+int ptr_kind(const void* p)
 {
-    if (!p) return false;
+    if (!p) return 0;
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
-    if (e != cudaSuccess) { cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 2;
+    return a.type == cudaMemoryTypeHost ? 1 : 0;
 }
+
+static bool is_device_ptr(const void* p) { return ptr_kind(p) == 2; }
 
 static bls_status kminmax_impl(int nb, double qmin, double qmax, int* kmin, int* kmax)
 {
@@ -93,7 +97,8 @@ static bls_status kminmax_impl(int nb, double qmin, double qmax, int* kmin, int*
     return BLS_OK;
 }
 
-bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* o)
+bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* o,
+                         const int* kinds)
 {
     if (!c) return set_error(BLS_ERR_INVALID, "curve %d: NULL descriptor", index);
     if (c->n < 2) return set_error(BLS_ERR_INVALID, "curve %d: n = %d, need n >= 2", index, c->n);
@@ -123,10 +128,15 @@ bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, 
         if (s != BLS_OK) return set_error(s, "curve %d: %s", index, bls_last_error());
     }
     if (o->nb > 4096) return set_error(BLS_ERR_INVALID, "curve %d: nb = %d exceeds 4096", index, o->nb);
-    o->t_dev = is_device_ptr(c->t);
-    o->y_dev = is_device_ptr(c->y);
-    o->dy_dev = c->dy ? is_device_ptr(c->dy) : false;
-    o->f_dev = c->freqs ? is_device_ptr(c->freqs) : false;
+    const int kt = kinds ? kinds[0] : ptr_kind(c->t);
+    const int ky = kinds ? kinds[1] : ptr_kind(c->y);
+    const int kd = c->dy ? (kinds ? kinds[2] : ptr_kind(c->dy)) : 2;
+    const int kf = c->freqs ? (kinds ? kinds[3] : ptr_kind(c->freqs)) : 2;
+    o->t_dev = kt == 2;
+    o->y_dev = ky == 2;
+    o->dy_dev = c->dy ? kd == 2 : false;
+    o->f_dev = c->freqs ? kf == 2 : false;
+    o->capturable = kt != 0 && ky != 0 && kd != 0 && kf != 0;   // no pageable host copies
     // host values are checked here; device values by the prep kernel
     if (!o->t_dev)
         for (int i = 0; i < c->n; ++i)
@@ -236,8 +246,14 @@ void to_peak(const DevPeak& s, bls_peak* d)
     d->power = s.power;
 }
 
-// One launch group: curves [g0, g1) of `specs`.  Writes peaks to out (host) and optionally
-// SR spectra (per-frequency result dump for diagnostics into res_dump).
+// One launch group: curves [g0, g1) of `specs`.  Writes peaks to out (host), optionally the
+// SR spectra, and (diagnostics) the per-frequency powers into res_dump.
+//
+// All buffers are sized first; then every stream operation of the group (input copies,
+// descriptor and work-list copies, prep, fold-sweep, reduce, result copies) is issued by
+// one routine.  When every input is device or pinned host memory, that routine is captured
+// into a CUDA graph; while the group's signature (curve descriptors, buffers, options)
+// repeats, the graph is replayed with a single launch.
 bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int g0, int g1,
                      const std::vector<long long>& spec_off, bls_peak* out, float* spectrum,
                      bool spectrum_dev, float* res_dump)
@@ -246,11 +262,13 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     const int topk = P->d.topk;
     cudaStream_t st = P->stream;
     cudaError_t e;
+    const bool tiled = P->d.algo == BLS_ALGO_TILED;
 
     // ---- layout
     std::vector<long long> pt_off(nc), res_off(nc), raw_off(nc), f_off(nc);
     long long npts = 0, nres = 0, nraw = 0, nfr = 0;
-    bool any_dy = false;
+    bool any_dy = false, capturable = true;
+    size_t plain_hist = 0;
     for (int c = 0; c < nc; ++c) {
         const CurveSpec& s = specs[g0 + c];
         pt_off[c] = npts;
@@ -262,31 +280,62 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         f_off[c] = nfr;
         if (s.freqs && !s.f_dev) nfr += s.nf;
         any_dy = any_dy || s.dy;
+        capturable = capturable && s.capturable;
+        plain_hist = std::max(plain_hist, (size_t)2 * s.nb * s.nf * 8);
     }
     npts += 2;  // slack so a staged chunk never reads past the pool
 
-    // ---- buffers
-    if ((e = P->pts.ensure((size_t)npts * sizeof(float4))) != cudaSuccess) return cuda_fail(e, "allocating points");
-    if ((e = P->dt64.ensure((size_t)npts * sizeof(double))) != cudaSuccess) return cuda_fail(e, "allocating dt");
-    if ((e = P->res.ensure((size_t)nres * sizeof(float))) != cudaSuccess) return cuda_fail(e, "allocating results");
-    if ((e = P->raw_t.ensure((size_t)nraw * 8)) != cudaSuccess) return cuda_fail(e, "allocating staging");
-    if ((e = P->raw_y.ensure((size_t)nraw * 4)) != cudaSuccess) return cuda_fail(e, "allocating staging");
-    if (any_dy && (e = P->raw_dy.ensure((size_t)nraw * 4)) != cudaSuccess) return cuda_fail(e, "allocating staging");
-    if (nfr && (e = P->raw_f.ensure((size_t)nfr * 8)) != cudaSuccess) return cuda_fail(e, "allocating staging");
-    if ((e = P->cdesc.ensure((size_t)nc * sizeof(CurveDesc))) != cudaSuccess) return cuda_fail(e, "allocating descriptors");
-    if ((e = P->peaks.ensure((size_t)nc * topk * sizeof(DevPeak))) != cudaSuccess) return cuda_fail(e, "allocating peaks");
-    if ((e = P->err.ensure(64)) != cudaSuccess) return cuda_fail(e, "allocating error word");
-    if (spectrum && !spectrum_dev && (e = P->spec.ensure((size_t)nres * 4)) != cudaSuccess)
-        return cuda_fail(e, "allocating spectrum");
-    if ((e = P->h_cdesc.ensure((size_t)nc * sizeof(CurveDesc))) != cudaSuccess) return cuda_fail(e, "pinned descriptors");
-    if ((e = P->h_peaks.ensure((size_t)nc * topk * sizeof(DevPeak))) != cudaSuccess) return cuda_fail(e, "pinned peaks");
-    if ((e = P->h_err.ensure(64)) != cudaSuccess) return cuda_fail(e, "pinned error word");
-    if (P->d.algo == BLS_ALGO_PLAIN_F64) {
-        if ((e = P->w64.ensure((size_t)npts * 8)) != cudaSuccess) return cuda_fail(e, "allocating w64");
-        if ((e = P->wx64.ensure((size_t)npts * 8)) != cudaSuccess) return cuda_fail(e, "allocating wx64");
+    // fold classes (block size per nb)
+    std::vector<FoldGeom> geoms;
+    std::vector<std::vector<int>> cls;
+    std::vector<int> cls_of(nc, 0);
+    if (tiled) {
+        for (int c = 0; c < nc; ++c) {
+            FoldGeom g;
+            bls_status s = fold_geometry(P, specs[g0 + c].nb, &g);
+            if (s != BLS_OK) return s;
+            int k = -1;
+            for (size_t q = 0; q < geoms.size(); ++q)
+                if (geoms[q].T == g.T && geoms[q].stride == g.stride && geoms[q].chunk == g.chunk) { k = (int)q; break; }
+            if (k < 0) { geoms.push_back(g); cls.emplace_back(); k = (int)geoms.size() - 1; }
+            else geoms[k].smem = std::max(geoms[k].smem, g.smem);
+            cls[k].push_back(c);
+            cls_of[c] = k;
+        }
     }
+    const size_t nr = (size_t)nc;
 
-    // ---- inputs: copy host arrays into staging (merged when contiguous), point at device ones
+    // ---- buffers (all before any capture)
+#define BLS_ENSURE(buf, bytes, what) \
+    if ((e = (buf).ensure(bytes)) != cudaSuccess) return cuda_fail(e, what);
+    BLS_ENSURE(P->pts, (size_t)npts * sizeof(float4), "allocating points")
+    BLS_ENSURE(P->dt64, (size_t)npts * sizeof(double), "allocating dt")
+    BLS_ENSURE(P->res, (size_t)nres * sizeof(float), "allocating results")
+    BLS_ENSURE(P->raw_t, (size_t)nraw * 8, "allocating staging")
+    BLS_ENSURE(P->raw_y, (size_t)nraw * 4, "allocating staging")
+    if (any_dy) BLS_ENSURE(P->raw_dy, (size_t)nraw * 4, "allocating staging")
+    if (nfr) BLS_ENSURE(P->raw_f, (size_t)nfr * 8, "allocating staging")
+    BLS_ENSURE(P->cdesc, (size_t)nc * sizeof(CurveDesc), "allocating descriptors")
+    BLS_ENSURE(P->peaks, (size_t)nc * topk * sizeof(DevPeak), "allocating peaks")
+    BLS_ENSURE(P->err, 64, "allocating error word")
+    if (spectrum && !spectrum_dev) BLS_ENSURE(P->spec, (size_t)nres * 4, "allocating spectrum")
+    BLS_ENSURE(P->h_cdesc, (size_t)nc * sizeof(CurveDesc), "pinned descriptors")
+    BLS_ENSURE(P->h_peaks, (size_t)nc * topk * sizeof(DevPeak), "pinned peaks")
+    BLS_ENSURE(P->h_err, 64, "pinned error word")
+    if (tiled) {
+        BLS_ENSURE(P->ranges, nr * sizeof(TileRange), "allocating work list")
+        BLS_ENSURE(P->prefix, (nr + cls.size()) * sizeof(long long), "allocating work list")
+        BLS_ENSURE(P->counter, cls.size() * sizeof(int) + 64, "allocating counters")
+        BLS_ENSURE(P->h_ranges, nr * sizeof(TileRange), "pinned work list")
+        BLS_ENSURE(P->h_prefix, (nr + cls.size()) * sizeof(long long), "pinned work list")
+    } else {
+        BLS_ENSURE(P->w64, (size_t)npts * 8, "allocating w64")
+        BLS_ENSURE(P->wx64, (size_t)npts * 8, "allocating wx64")
+        BLS_ENSURE(P->plain_hist, plain_hist, "allocating baseline histograms")
+    }
+#undef BLS_ENSURE
+
+    // ---- host side: descriptors, input copies (merged when contiguous), work lists
     std::vector<Copy> copies, cy, cdy, cf;   // one list per array so contiguous runs merge
     CurveDesc* hd = P->h_cdesc.as<CurveDesc>();
     for (int c = 0; c < nc; ++c) {
@@ -311,60 +360,20 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         d.fmin = s.fmin;
         d.df = s.df;
         d.n = s.n; d.nf = s.nf; d.nb = s.nb; d.kmin = s.kmin; d.kmax = s.kmax;
-        d.T = 0;
+        d.T = tiled ? geoms[cls_of[c]].T : 0;
         hd[c] = d;
-    }
-    // fold classes (block size per nb)
-    std::vector<FoldGeom> geoms;
-    std::vector<std::vector<int>> cls;
-    if (P->d.algo == BLS_ALGO_TILED) {
-        for (int c = 0; c < nc; ++c) {
-            FoldGeom g;
-            bls_status s = fold_geometry(P, specs[g0 + c].nb, &g);
-            if (s != BLS_OK) return s;
-            int k = -1;
-            for (size_t q = 0; q < geoms.size(); ++q)
-                if (geoms[q].T == g.T && geoms[q].stride == g.stride && geoms[q].chunk == g.chunk) { k = (int)q; break; }
-            if (k < 0) { geoms.push_back(g); cls.emplace_back(); k = (int)geoms.size() - 1; }
-            else geoms[k].smem = std::max(geoms[k].smem, g.smem);
-            cls[k].push_back(c);
-            hd[c].T = g.T;
-        }
     }
     copies.insert(copies.end(), cy.begin(), cy.end());
     copies.insert(copies.end(), cdy.begin(), cdy.end());
     copies.insert(copies.end(), cf.begin(), cf.end());
-    for (const Copy& cp : copies)
-        if ((e = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyDefault, st)) != cudaSuccess)
-            return cuda_fail(e, "copying inputs");
-    if ((e = cudaMemcpyAsync(P->cdesc.p, hd, (size_t)nc * sizeof(CurveDesc), cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_fail(e, "copying descriptors");
-    if ((e = cudaMemsetAsync(P->err.p, 0, 64, st)) != cudaSuccess) return cuda_fail(e, "clearing error word");
 
-    // ---- a1 prep
-    const bool prof = P->ev[0] != nullptr;
-    uint64_t launches = 0, fold_launches = 0;
-    if (prof) cudaEventRecord(P->ev[0], st);
-    ++launches;
-    if ((e = launch_prep(P->cdesc.as<CurveDesc>(), nullptr, nc, P->err.as<int>(), st)) != cudaSuccess)
-        return cuda_fail(e, "prep launch");
-
-    // ---- a2-a6 fold, bin, sweep
-    if (prof) cudaEventRecord(P->ev[1], st);
-    if (P->d.algo == BLS_ALGO_TILED) {
-        // work lists of all classes back to back
-        size_t nr = 0;
-        for (auto& v : cls) nr += v.size();
-        if ((e = P->ranges.ensure(nr * sizeof(TileRange))) != cudaSuccess) return cuda_fail(e, "allocating work list");
-        if ((e = P->prefix.ensure((nr + cls.size()) * sizeof(long long))) != cudaSuccess) return cuda_fail(e, "allocating work list");
-        if ((e = P->counter.ensure(cls.size() * sizeof(int) + 64)) != cudaSuccess) return cuda_fail(e, "allocating counters");
-        if ((e = P->h_ranges.ensure(nr * sizeof(TileRange))) != cudaSuccess) return cuda_fail(e, "pinned work list");
-        if ((e = P->h_prefix.ensure((nr + cls.size()) * sizeof(long long))) != cudaSuccess) return cuda_fail(e, "pinned work list");
+    std::vector<size_t> r0(cls.size()), p0(cls.size());
+    std::vector<long long> totals(cls.size());
+    size_t pp = 0;
+    if (tiled) {
         TileRange* hr = P->h_ranges.as<TileRange>();
         long long* hp = P->h_prefix.as<long long>();
-        std::vector<size_t> r0(cls.size()), p0(cls.size());
-        std::vector<long long> totals(cls.size());
-        size_t rr = 0, pp = 0;
+        size_t rr = 0;
         std::vector<CurveSpec> local(specs.begin() + g0, specs.begin() + g1);
         for (size_t q = 0; q < cls.size(); ++q) {
             std::vector<int> ord;
@@ -380,52 +389,14 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
             hp[pp++] = acc;
             totals[q] = acc;
         }
-        if ((e = cudaMemcpyAsync(P->ranges.p, hr, nr * sizeof(TileRange), cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return cuda_fail(e, "copying work list");
-        if ((e = cudaMemcpyAsync(P->prefix.p, hp, pp * sizeof(long long), cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return cuda_fail(e, "copying work list");
-        if ((e = cudaMemsetAsync(P->counter.p, 0, cls.size() * sizeof(int), st)) != cudaSuccess)
-            return cuda_fail(e, "clearing counters");
-        for (size_t q = 0; q < cls.size(); ++q) {
-            FoldParams fp;
-            fp.curves = P->cdesc.as<CurveDesc>();
-            fp.ranges = P->ranges.as<TileRange>() + r0[q];
-            fp.prefix = P->prefix.as<long long>() + p0[q];
-            fp.nranges = (int)cls[q].size();
-            fp.total = totals[q];
-            fp.counter = P->counter.as<int>() + q;
-            fp.err = P->err.as<int>();
-            fp.chunk = geoms[q].chunk;
-            fp.stride = geoms[q].stride;
-            const int bps = fold_blocks_per_sm(geoms[q].T, geoms[q].smem, P->d.phase,
-                                               P->d.sum == BLS_SUM_KAHAN, P->d.sign);
-            long long grid = (long long)P->sm_count * bps;
-            if (grid > totals[q]) grid = totals[q];
-            if (grid < 1) grid = 1;
-            if ((e = launch_fold_sweep(fp, geoms[q].T, (int)grid, P->d.phase, P->d.sum == BLS_SUM_KAHAN,
-                                       P->d.sign, geoms[q].smem, st)) != cudaSuccess)
-                return cuda_fail(e, "fold-sweep launch");
-            ++launches;
-            ++fold_launches;
-        }
-    } else {
-        if ((e = launch_prep_f64(P->cdesc.as<CurveDesc>(), nc, P->w64.as<double>(), P->wx64.as<double>(), st)) != cudaSuccess)
-            return cuda_fail(e, "prep launch");
-        ++launches;
-        size_t hb = 0;
-        for (int c = 0; c < nc; ++c) hb = std::max(hb, (size_t)2 * specs[g0 + c].nb * specs[g0 + c].nf * 8);
-        if ((e = P->plain_hist.ensure(hb)) != cudaSuccess) return cuda_fail(e, "allocating baseline histograms");
-        for (int c = 0; c < nc; ++c) {
-            const CurveSpec& s = specs[g0 + c];
-            if ((e = launch_plain_f64(P->cdesc.as<CurveDesc>() + c, P->w64.as<double>(), P->wx64.as<double>(),
-                                      s.nf, P->plain_hist.as<double>(), P->d.sign, st)) != cudaSuccess)
-                return cuda_fail(e, "baseline launch");
-            ++launches;
-            ++fold_launches;
-        }
     }
-
-    // ---- a7 reduce
+    std::vector<int> grids(cls.size());
+    for (size_t q = 0; q < cls.size(); ++q) {
+        const int bps = fold_blocks_per_sm(geoms[q].T, geoms[q].smem, P->d.phase,
+                                           P->d.sum == BLS_SUM_KAHAN, P->d.sign);
+        long long grid = std::min<long long>((long long)P->sm_count * bps, totals[q]);
+        grids[q] = (int)std::max<long long>(grid, 1);
+    }
     ReduceParams rp;
     rp.curves = P->cdesc.as<CurveDesc>();
     rp.slots = nullptr;
@@ -439,32 +410,143 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         for (int c = 0; c < nc; ++c) nbmax = std::max(nbmax, specs[g0 + c].nb);
         rp.smem_bytes = reduce_smem_bytes(nbmax, topk, rp.kahan);
     }
-    float* dev_spec = nullptr;
-    if (spectrum) dev_spec = spectrum_dev ? spectrum : P->spec.as<float>();
-    rp.spectrum = dev_spec;
-    if (prof) cudaEventRecord(P->ev[2], st);
-    if ((e = launch_reduce(rp, nc, st)) != cudaSuccess) return cuda_fail(e, "reduce launch");
-    ++launches;
-    if (prof) cudaEventRecord(P->ev[3], st);
+    rp.spectrum = spectrum ? (spectrum_dev ? spectrum : P->spec.as<float>()) : nullptr;
+    const bool prof = P->ev[0] != nullptr;
+    uint64_t launches = 0, fold_launches = 0;
+
+    // ---- every stream operation of the group
+    // inside a capture, an event record becomes a graph node only with the external flag
+    // (which is rejected outside a capture)
+    bool capturing = false;
+    auto record = [&](cudaEvent_t ev) {
+        if (capturing) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+        else cudaEventRecord(ev, st);
+    };
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t x;
+        launches = 0;
+        fold_launches = 0;
+        for (const Copy& cp : copies)
+            if ((x = cudaMemcpyAsync(cp.dst, cp.src, cp.bytes, cudaMemcpyDefault, st)) != cudaSuccess) return x;
+        if ((x = cudaMemcpyAsync(P->cdesc.p, hd, (size_t)nc * sizeof(CurveDesc), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return x;
+        if ((x = cudaMemsetAsync(P->err.p, 0, 64, st)) != cudaSuccess) return x;
+        if (prof) record(P->ev[0]);
+        if ((x = launch_prep(P->cdesc.as<CurveDesc>(), nullptr, nc, P->err.as<int>(), st)) != cudaSuccess) return x;
+        ++launches;
+        if (prof) record(P->ev[1]);
+        if (tiled) {
+            if ((x = cudaMemcpyAsync(P->ranges.p, P->h_ranges.p, nr * sizeof(TileRange), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (x = cudaMemcpyAsync(P->prefix.p, P->h_prefix.p, pp * sizeof(long long), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+                (x = cudaMemsetAsync(P->counter.p, 0, cls.size() * sizeof(int), st)) != cudaSuccess)
+                return x;
+            for (size_t q = 0; q < cls.size(); ++q) {
+                FoldParams fp;
+                fp.curves = P->cdesc.as<CurveDesc>();
+                fp.ranges = P->ranges.as<TileRange>() + r0[q];
+                fp.prefix = P->prefix.as<long long>() + p0[q];
+                fp.nranges = (int)cls[q].size();
+                fp.total = totals[q];
+                fp.counter = P->counter.as<int>() + q;
+                fp.err = P->err.as<int>();
+                fp.chunk = geoms[q].chunk;
+                fp.stride = geoms[q].stride;
+                if ((x = launch_fold_sweep(fp, geoms[q].T, grids[q], P->d.phase, P->d.sum == BLS_SUM_KAHAN,
+                                           P->d.sign, geoms[q].smem, st)) != cudaSuccess)
+                    return x;
+                ++launches;
+                ++fold_launches;
+            }
+        } else {
+            if ((x = launch_prep_f64(P->cdesc.as<CurveDesc>(), nc, P->w64.as<double>(), P->wx64.as<double>(), st)) != cudaSuccess)
+                return x;
+            ++launches;
+            for (int c = 0; c < nc; ++c) {
+                if ((x = launch_plain_f64(P->cdesc.as<CurveDesc>() + c, P->w64.as<double>(), P->wx64.as<double>(),
+                                          specs[g0 + c].nf, P->plain_hist.as<double>(), P->d.sign, st)) != cudaSuccess)
+                    return x;
+                ++launches;
+                ++fold_launches;
+            }
+        }
+        if (prof) record(P->ev[2]);
+        if ((x = launch_reduce(rp, nc, st)) != cudaSuccess) return x;
+        ++launches;
+        if (prof) record(P->ev[3]);
+        if ((x = cudaMemcpyAsync(P->h_peaks.p, P->peaks.p, (size_t)nc * topk * sizeof(DevPeak),
+                                 cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return x;
+        if (spectrum && !spectrum_dev)
+            if ((x = cudaMemcpyAsync(spectrum + spec_off[g0], P->spec.p, (size_t)nres * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return x;
+        if (res_dump)
+            if ((x = cudaMemcpyAsync(res_dump, P->res.p, (size_t)nres * sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return x;
+        return cudaMemcpyAsync(P->h_err.p, P->err.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    };
+
+    // ---- graph replay / capture, or direct launch
+    bool launched = false;
+    const bool graphable = P->graphs && capturable && !res_dump && (!spectrum || spectrum_dev ||
+                                                                   ptr_kind(spectrum) == 1);
+    if (graphable) {
+        std::string sig;
+        auto put = [&](const void* p, size_t n) { sig.append(static_cast<const char*>(p), n); };
+        put(&nc, sizeof(nc));
+        put(hd, (size_t)nc * sizeof(CurveDesc));
+        for (const Copy& cp : copies) put(&cp, sizeof(cp));
+        put(&spectrum, sizeof(spectrum));
+        put(&P->d, sizeof(P->d));
+        put(&pp, sizeof(pp));
+        if (tiled) {
+            put(P->h_ranges.p, nr * sizeof(TileRange));
+            put(P->h_prefix.p, pp * sizeof(long long));
+        }
+        void* bufs[] = {P->pts.p, P->res.p, P->peaks.p, P->spec.p, P->err.p, P->h_peaks.p, P->h_err.p, P->ranges.p};
+        put(bufs, sizeof(bufs));
+        if (P->graph && sig == P->graph_sig) {
+            if ((e = cudaGraphLaunch(P->graph, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+            launches = P->graph_launches;
+            fold_launches = P->graph_fold_launches;
+            P->prof.graph_replays += 1;
+            launched = true;
+        } else {
+            if (P->graph) { cudaGraphExecDestroy(P->graph); P->graph = nullptr; P->graph_sig.clear(); }
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                capturing = true;
+                cudaError_t x = enqueue();
+                capturing = false;
+                cudaError_t y = cudaStreamEndCapture(st, &g);
+                if (x == cudaSuccess && y == cudaSuccess && g &&
+                    cudaGraphInstantiate(&P->graph, g, 0) == cudaSuccess) {
+                    P->graph_sig = sig;
+                    P->graph_launches = launches;
+                    P->graph_fold_launches = fold_launches;
+                    P->prof.graph_captures += 1;
+                    if ((e = cudaGraphLaunch(P->graph, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
+                    launched = true;
+                } else {
+                    P->graph = nullptr;
+                    P->graphs = false;   // not capturable here: launch directly from now on
+                }
+                if (g) cudaGraphDestroy(g);
+            } else {
+                P->graphs = false;
+            }
+            cudaGetLastError();   // a failed capture leaves no sticky error; launch directly
+        }
+    }
+    if (!launched && (e = enqueue()) != cudaSuccess) return cuda_fail(e, "search launch");
 
     // ---- results
-    if ((e = cudaMemcpyAsync(P->h_peaks.p, P->peaks.p, (size_t)nc * topk * sizeof(DevPeak),
-                             cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        return cuda_fail(e, "copying peaks");
-    if (spectrum && !spectrum_dev)
-        if ((e = cudaMemcpyAsync(spectrum + spec_off[g0], P->spec.p, (size_t)nres * 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-            return cuda_fail(e, "copying spectrum");
-    if (res_dump)
-        if ((e = cudaMemcpyAsync(res_dump, P->res.p, (size_t)nres * sizeof(float), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-            return cuda_fail(e, "copying per-frequency results");
-    if ((e = cudaMemcpyAsync(P->h_err.p, P->err.p, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        return cuda_fail(e, "copying error word");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "search");
     if (prof) {
         float a = 0.f, b = 0.f, c = 0.f;
         cudaEventElapsedTime(&a, P->ev[0], P->ev[1]);
         cudaEventElapsedTime(&b, P->ev[1], P->ev[2]);
         cudaEventElapsedTime(&c, P->ev[2], P->ev[3]);
+        cudaGetLastError();
         P->prof.prep_ms += a;
         P->prof.fold_ms += b;
         P->prof.reduce_ms += c;
@@ -491,9 +573,23 @@ bls_status search_impl(bls_plan_impl* P, const bls_curve* curves, int ncurves, b
     if (!curves || !out) return set_error(BLS_ERR_INVALID, "NULL curves or out");
     cudaError_t e = cudaSetDevice(P->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    // memory kind of every input array, queried once per contiguous run of curves
     std::vector<CurveSpec> specs(ncurves);
+    const void* run_end[4] = {nullptr, nullptr, nullptr, nullptr};
+    int run_kind[4] = {0, 0, 0, 0};
     for (int c = 0; c < ncurves; ++c) {
-        bls_status s = resolve_curve(P, &curves[c], c, &specs[c]);
+        const bls_curve& cv = curves[c];
+        const void* ptrs[4] = {cv.t, cv.y, cv.dy, cv.freqs};
+        const size_t sz[4] = {8, 4, 4, 8};
+        const long long cnt[4] = {cv.n, cv.n, cv.n, cv.nf};
+        int kinds[4];
+        for (int a = 0; a < 4; ++a) {
+            if (!ptrs[a]) { kinds[a] = 2; continue; }
+            if (ptrs[a] != run_end[a]) run_kind[a] = ptr_kind(ptrs[a]);
+            kinds[a] = run_kind[a];
+            run_end[a] = static_cast<const char*>(ptrs[a]) + (cnt[a] > 0 ? cnt[a] : 0) * sz[a];
+        }
+        bls_status s = resolve_curve(P, &cv, c, &specs[c], kinds);
         if (s != BLS_OK) return s;
     }
     const bool spec_dev = spectrum && is_device_ptr(spectrum);
@@ -574,6 +670,7 @@ bls_status bls_plan_create(const bls_plan_desc* desc, void* cuda_stream, bls_pla
     P->device = dev;
     P->sm_count = sms;
     P->smem_optin = (size_t)optin - 1024;   // static shared memory of the kernels
+    if (const char* g = getenv("BLS_NO_GRAPHS")) P->graphs = atoi(g) == 0;
     if (cuda_stream) {
         P->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -623,6 +720,7 @@ void bls_plan_destroy(bls_plan* P)
     for (HostBuf* b : hb) b->release();
     for (int q = 0; q < 4; ++q)
         if (P->ev[q]) cudaEventDestroy(P->ev[q]);
+    if (P->graph) cudaGraphExecDestroy(P->graph);
     if (P->own_stream) cudaStreamDestroy(P->stream);
     delete P;
 }

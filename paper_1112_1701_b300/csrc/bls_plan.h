@@ -47,6 +47,7 @@ struct CurveSpec {
     int n, nf, nb, kmin, kmax;
     double fmin, df;
     bool t_dev, y_dev, dy_dev, f_dev;   // pointer lives on the device
+    bool capturable;                     // no input is pageable host memory
 };
 
 // Launch geometry of one fold-sweep class (curves sharing a block size).
@@ -77,6 +78,12 @@ struct bls_plan_impl {
     // host staging (pinned)
     HostBuf h_cdesc, h_ranges, h_prefix, h_peaks, h_err;
 
+    // CUDA graph of the last launch group, replayed while its signature repeats
+    cudaGraphExec_t graph = nullptr;
+    std::string graph_sig;
+    bool graphs = true;
+    uint64_t graph_launches = 0, graph_fold_launches = 0;
+
     // profiling (CUDA events around the kernel phases of a search)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     bls_profile prof{};
@@ -86,8 +93,11 @@ struct bls_plan_impl {
     std::mutex server_mu;
 };
 
-// Resolve and validate one curve against the plan (host checks only).
-bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* out);
+// Resolve and validate one curve against the plan (host checks only).  kinds (optional):
+// the memory kind of t, y, dy, freqs (0 pageable, 1 pinned, 2 device) when already known.
+bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* out,
+                         const int* kinds = nullptr);
+int ptr_kind(const void* p);
 // Block size / stride / chunk / shared memory for a curve with nb bins.
 bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g);
 // Work-list order: curves by decreasing cost (n * nf), ties by index.

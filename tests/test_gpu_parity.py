@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_1112_1701_b300 import bls, build, synth
-from tests.parity import check_peak, check_powers, oracle_run, prep_of, separated_best
+from tests.parity import check_peak, check_powers, oracle_run, prep_of, separated_best, sr_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -353,3 +353,47 @@ def test_batched_workload_full_size_sampled():
         assert abs(pk[c, 0]["power"] - Pb) <= 1e-9 * Pb
         # no sampled frequency beats the reported peak beyond the tolerance
         assert spec[c].max() == pytest.approx(np.sqrt(pk[c, 0]["power"]), rel=2e-5)
+
+
+# ------------------------------------------------------------------------------ CUDA graphs
+
+def test_graph_replay_reads_new_contents_and_matches_direct_launch():
+    """Pinned host inputs: the first search captures the group into a graph, the next ones
+    replay it.  New contents in the same buffers must give that data's results (the
+    graph reads the arrays at replay), identical to a plan that launches directly."""
+    torch = pytest.importorskip("torch")
+    import os
+    b1 = synth.config2(ncurves=5, nf=1200, seed=11)
+    rng = np.random.default_rng(12)
+    new = [(c.t, rng.permutation(c.y), rng.permutation(c.dy)) for c in b1.curves]
+    old = [(c.t, c.y, c.dy) for c in b1.curves]
+    cis = bls.curves_from_batch(b1, pinned=True)
+    nb = 200
+    kmin, kmax = oracle.kminmax(nb, b1.qmin, b1.qmax)
+    spec = torch.zeros(5 * 1200, dtype=torch.float32).pin_memory()
+    os.environ["BLS_NO_GRAPHS"] = "1"
+    try:
+        direct = _plan(nb, b1.qmin, b1.qmax, topk=2)
+    finally:
+        del os.environ["BLS_NO_GRAPHS"]
+    with _plan(nb, b1.qmin, b1.qmax, topk=2) as p, direct:
+        for it, data in enumerate((old, old, new, old)):
+            for q, (t, y, dy) in enumerate(data):   # same shapes: overwrite in place
+                cis[q].t.copy_(torch.from_numpy(t))
+                cis[q].y.copy_(torch.from_numpy(y))
+                cis[q].dy.copy_(torch.from_numpy(dy))
+            pk = p.search(cis, spectrum=spec.numpy())
+            s_g = spec.numpy().copy()
+            s_d = np.zeros(5 * 1200, np.float32)
+            pk_d = direct.search(cis, spectrum=s_d)
+            assert np.array_equal(pk, pk_d), it
+            assert np.array_equal(s_g, s_d), it
+            if it == 2:
+                for q in range(5):
+                    Po = oracle_run(cis[q], nb, kmin, kmax)[0]
+                    scal = prep_of(cis[q])[3]
+                    sro = np.sqrt(Po)
+                    assert np.all(np.abs(s_g[q * 1200:(q + 1) * 1200] - sro) <= sr_tol(sro, scal[3]))
+        prof = p.profile()
+        assert prof["graph_captures"] == 1 and prof["graph_replays"] == 3, prof
+        assert direct.profile()["graph_replays"] == 0
