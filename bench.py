@@ -48,9 +48,11 @@ METRIC = "BLS point x freq evals/s"
 UNIT = "point*freq/s"
 NB, QMIN, QMAX = 200, 0.005, 0.15
 
-# DRAM traffic of one fold-bin-sweep launch on this workload, from one ncu capture of the
-# kernel source with the given SHA-256 (reported as null once the source changes).
-NCU_TRAFFIC = {"kernel_sha256": None, "bytes_per_launch": None}
+# DRAM traffic of one fold-bin-sweep launch on this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum, one ncu capture of the timed launch after an L2 flush), for the
+# kernel source with the given SHA-256; reported as null once the source changes.
+NCU_TRAFFIC = {"kernel_sha256": "93e5fc4ce7ab248473286d409e1ae28a803692d8889998f2e3e16f6dc5cb4517",
+               "bytes_per_launch": 58689792 + 151370752}
 
 
 def kernel_sha():
@@ -312,7 +314,7 @@ def run_precision(args):
     freqs = [oracle.freq(j, b.grids[0].fmin, b.grids[0].df) for j in js]
     obins = [oracle.bins(c.t, freqs, nb) for c in b.curves[:args.prec_bin_curves]]
     rows = []
-    for phase in ("f64", "df32", "f32"):
+    for phase in ("f64", "df32", "fx64", "f32"):
         for sm in ("f32", "kahan"):
             with bls.Plan(nb=nb, qmin=b.qmin, qmax=b.qmax, topk=1, phase=phase, sum=sm) as p:
                 spec = np.zeros(len(b) * nf, np.float32)

@@ -52,10 +52,13 @@ typedef enum {
 
 /* Phase step (fold) precision. */
 enum {
-    BLS_PHASE_DF32 = 0,  /* default: double-FP32 product with an error bound; points whose
-                            bin is not certain are re-folded in FP64 (bins identical to FP64) */
+    BLS_PHASE_FX64 = 0,  /* default: 64-bit fixed-point product (integer multiply-adds) with
+                            an error bound; points whose bin is not certain are re-folded in
+                            FP64 (bins identical to FP64) */
     BLS_PHASE_F64 = 1,   /* every point folded in FP64 */
-    BLS_PHASE_F32 = 2    /* FP32 product, no fallback (precision study only: bins can differ) */
+    BLS_PHASE_F32 = 2,   /* FP32 product, no fallback (precision study only: bins can differ) */
+    BLS_PHASE_DF32 = 3   /* double-FP32 product with an error bound and the same FP64
+                            re-fold (bins identical to FP64) */
 };
 
 /* Accumulation of the phase histograms and box sums. */
@@ -88,7 +91,8 @@ typedef struct {
     size_t max_device_bytes;    /* device memory budget of the plan; 0 = half the free memory */
     int max_curves_per_launch;  /* 0 = as many as the budget allows */
     int freqs_per_block;        /* frequencies per thread block; 0 = tuned */
-    int point_chunk;            /* points staged in shared memory at a time; 0 = tuned */
+    int point_chunk;            /* points staged in shared memory at a time (rounded up to a
+                                   multiple of 16, at least 32); 0 = tuned */
     int max_active_requests;    /* serving: requests resident on the device at once; 0 = 64 */
     long long step_point_freqs; /* serving: point x frequency work per step; 0 = tuned */
 } bls_plan_desc;
@@ -212,7 +216,7 @@ bls_status bls_profile_get(bls_plan* plan, bls_profile* out, int reset);
  * cudaMalloc's implicit device synchronisation, a process under a memory cap).
  *   curve      t, y, dy (optional), freqs (optional) in device memory; nb >= 2 and
  *              0 < qmin <= qmax < 1 must be given (there is no plan to default from).
- *   topk, sign as in bls_plan_desc (dips only or both signs; FP32 sums, double-FP32 fold).
+ *   topk, sign as in bls_plan_desc (dips only or both signs; FP32 sums, fixed-point fold).
  *   cuda_stream stream the work is ordered on (NULL: the legacy default stream).
  *   peaks_dev  device memory for topk bls_peak records, filled as bls_search fills `out`.
  *   spectrum_dev optional device memory for nf floats, SR(f_j) as bls_search writes it.

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_PKG, "libbls.so")
 
 OK, PENDING = 0, 1
 ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL, ERR_CANCELLED = -1, -2, -3, -4, -5, -6
-PHASE = {"df32": 0, "f64": 1, "f32": 2}
+PHASE = {"fx64": 0, "f64": 1, "f32": 2, "df32": 3}
 SUM = {"f32": 0, "kahan": 1}
 SIGN = {"dips": 0, "both": 1}
 ALGO = {"tiled": 0, "plain_f64": 1}
@@ -213,7 +213,7 @@ def peaks_to_numpy(buf, topk: int) -> np.ndarray:
 class Plan:
     """A search plan on the current CUDA device (``bls_plan_create``)."""
 
-    def __init__(self, nb=200, qmin=0.005, qmax=0.15, kmin=0, kmax=0, topk=1, phase="df32",
+    def __init__(self, nb=200, qmin=0.005, qmax=0.15, kmin=0, kmax=0, topk=1, phase="fx64",
                  sum="f32", sign="dips", algo="tiled", max_device_bytes=0,
                  max_curves_per_launch=0, freqs_per_block=0, point_chunk=0,
                  max_active_requests=0, step_point_freqs=0, stream=None):

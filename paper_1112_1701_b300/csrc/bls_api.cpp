@@ -161,14 +161,18 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g)
     const size_t esz = kahan ? 16 : 8;
     const int maxT = fold_sweep_max_threads();
     // chunk: a multiple of 16 points; by default the larger of 512/256 that leaves the
-    // block size (frequencies per block) as large as 256 allows
+    // block size (frequencies per block) as large as 256 allows.  tmax: the most columns
+    // (a multiple of 16) whose block fits in shared memory.
     auto tmax = [&](int chunk) {
         const size_t stage = (size_t)2 * chunk * 24;
         const size_t avail = P->smem_optin > stage + 64 ? P->smem_optin - stage - 64 : 0;
-        size_t cap = avail / ((size_t)nb * esz);
-        return (int)std::min<size_t>(cap, (size_t)maxT) & ~15;
+        int T = (int)std::min<size_t>(avail / ((size_t)nb * esz), (size_t)maxT) & ~15;
+        while (T >= 16 && fold_smem_bytes(T, (T + 15) & ~15, nb, chunk, kahan) > P->smem_optin) T -= 16;
+        return T;
     };
-    if (P->d.point_chunk > 0) g->chunk = (P->d.point_chunk + 15) & ~15;
+    // (at least 32 points: the staging buffers then also hold the sweep's 2 x 256 partial
+    // maxima at the end of a tile)
+    if (P->d.point_chunk > 0) g->chunk = std::max(32, (P->d.point_chunk + 15) & ~15);
     else g->chunk = tmax(512) >= tmax(256) ? 512 : 256;
     int T = P->d.freqs_per_block > 0 ? P->d.freqs_per_block : tmax(g->chunk);
     if (T < 16) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", nb);
@@ -432,7 +436,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
             return x;
         if ((x = cudaMemsetAsync(P->err.p, 0, 64, st)) != cudaSuccess) return x;
         if (prof) record(P->ev[0]);
-        if ((x = launch_prep(P->cdesc.as<CurveDesc>(), nullptr, nc, P->err.as<int>(), st)) != cudaSuccess) return x;
+        if ((x = launch_prep(P->cdesc.as<CurveDesc>(), nullptr, nc, P->err.as<int>(), P->d.phase, st)) != cudaSuccess) return x;
         ++launches;
         if (prof) record(P->ev[1]);
         if (tiled) {
@@ -646,7 +650,7 @@ bls_status bls_plan_create(const bls_plan_desc* desc, void* cuda_stream, bls_pla
         if (s != BLS_OK) return s;
     }
     if (d.topk < 1 || d.topk > kMaxTopK) return set_error(BLS_ERR_INVALID, "topk = %d, need 1..%d", d.topk, kMaxTopK);
-    if (d.phase < 0 || d.phase > 2) return set_error(BLS_ERR_INVALID, "phase = %d", d.phase);
+    if (d.phase < 0 || d.phase > 3) return set_error(BLS_ERR_INVALID, "phase = %d", d.phase);
     if (d.sum < 0 || d.sum > 1) return set_error(BLS_ERR_INVALID, "sum = %d", d.sum);
     if (d.sign < 0 || d.sign > 1) return set_error(BLS_ERR_INVALID, "sign = %d", d.sign);
     if (d.algo < 0 || d.algo > 1) return set_error(BLS_ERR_INVALID, "algo = %d", d.algo);

@@ -18,7 +18,7 @@
 namespace blsgpu {
 
 constexpr int kMaxTopK = 16;
-constexpr int kPhaseDF32 = 0, kPhaseF64 = 1, kPhaseF32 = 2;
+constexpr int kPhaseFX64 = 0, kPhaseF64 = 1, kPhaseF32 = 2, kPhaseDF32 = 3;
 
 struct CurveDesc {
     const double* t;       // raw times (device)
@@ -34,6 +34,7 @@ struct CurveDesc {
     double t_ref, W, ybar, sumwx2, dtmax;  // written by the prep kernel
     int n, nf, nb, kmin, kmax;
     int T;                 // frequencies per tile of this curve (block size of its class)
+    int fxs;               // fixed-point scale of the FX64 fold: DT = dt 2^fxs (prep kernel)
 };
 
 // A run of frequency tiles of one curve processed by one fold-sweep launch.
@@ -62,7 +63,8 @@ struct FoldParams {
     int* counter;              // work counter (zeroed before the launch)
     int* err;
     int chunk;                 // points per staged chunk (a multiple of 16)
-    int stride;                // histogram stride in entries (multiple of 16, >= blockDim.x)
+    int stride;                // histogram stride in entries (multiple of 16, >= cols)
+    int cols;                  // frequencies per tile (set by launch_fold_sweep)
 };
 
 struct ReduceParams {
@@ -80,7 +82,7 @@ struct ReduceParams {
 // Shared memory a fold-sweep block needs.
 size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int kahan);
 
-cudaError_t launch_prep(CurveDesc* d_curves, const int* slots, int ncurves, int* err,
+cudaError_t launch_prep(CurveDesc* d_curves, const int* slots, int ncurves, int* err, int phase,
                         cudaStream_t s);
 cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan,
                               int sign, size_t smem, cudaStream_t s);
@@ -98,5 +100,6 @@ cudaError_t launch_prep_f64(const CurveDesc* d_curves, int ncurves, double* w64,
                             cudaStream_t s);
 int fold_sweep_max_threads();
 int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign);
+int fold_block_threads(int cols);   // threads of a fold-sweep block with `cols` columns
 
 }  // namespace blsgpu

@@ -52,7 +52,25 @@ struct FoldConst {
     double f;         // exact frequency
     int nb;
     bool fast;        // the double-FP32 path is valid for this (curve, frequency)
+    // fixed-point fold (FX64)
+    unsigned Flo, Fhi;   // F = RN_int(f 2^(64 - fxs))
+    unsigned ftol;       // edge window: bin certain iff ftol <= r < 2^32 - ftol - nb
+    unsigned fspan;      // 2^32 - 2 ftol - nb
+    bool fxok;           // the fixed-point path is valid for this (curve, frequency)
 };
+
+// Fixed-point scale of a curve's offsets: DT = RN_int(dt 2^s) with dt < 2^L.  The fold
+// error f 2^-(s+1) + dtmax 2^(s-65) (see make_fold_const) is smallest near
+// s = 32 + (log2 f - L) / 2; s = 34 - (L+1)/2 suits frequencies up to ~16 cycles per unit
+// of time, and DT < 2^62 leaves headroom.
+__host__ __device__ __forceinline__ int fx_shift(double dtmax)
+{
+    int L = 0;
+    if (dtmax > 0.0) L = ilogb(dtmax) + 1;
+    int s = 34 - (L + 1) / 2;
+    if (s > 62 - L) s = 62 - L;
+    return s < 1 ? 1 : s;
+}
 
 // Error bound of the double-FP32 fold, in bins.  With D = dt, F = f, DF = D*F and
 // u = 2^-24 (FP32 unit roundoff):
@@ -62,9 +80,32 @@ struct FoldConst {
 //   cn = RN(c nb - 1/2) and x = RN(fr nb + cn) add u|cn| + u|x|;
 //   the FP64 definition itself is within nb 2^-53 (DF + 1) bins of nb*frac(DF).
 // tol doubles the sum.  Valid while DF < 2^20 (then |c| < 3u DF < 0.19 cycles).
-__device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dtmax)
+//
+// Fixed-point fold (FX64), with s = fxs: the prep kernel stores DT = RN_int(dt 2^s) and
+// F = RN_int(f 2^(64-s)), so |DT F 2^-64 - dt f| <= f 2^-(s+1) + dt 2^(s-65) + 2^-66 =: E
+// cycles, and the low 64 bits of DT*F are the phase frac(dt f) in units of 2^-64 up to E.
+// Only the high word q of that fraction is formed; b = floor(q nb 2^-32), r = q nb mod
+// 2^32, and the dropped low word adds less than nb to r.  The FP64 definition lies within
+// 2^-52 (DF + 1) nb bins of nb*frac(dt f), so b is the definition's bin whenever r is at
+// least tol = (E + 2^-52 (DF + 1)) nb 2^32 (with margin) from both ends of the bin:
+// tol <= r < 2^32 - tol - nb.
+__device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dtmax, int fxs)
 {
     FoldConst fc;
+    {
+        const double Fd = ldexp(f, 64 - fxs);
+        fc.fxok = Fd < 18446744073709551616.0;   // F < 2^64
+        const unsigned long long F = fc.fxok ? __double2ull_rn(Fd) : 0ull;
+        fc.Flo = (unsigned)F;
+        fc.Fhi = (unsigned)(F >> 32);
+        const double E = f * ldexp(1.0, -(fxs + 1)) + dtmax * ldexp(1.0, fxs - 65) + ldexp(1.0, -66)
+                       + ldexp(1.0, -52) * (dtmax * f + 1.0);
+        const double tolu = E * nb * 4294967296.0 * 1.01 + 4.0;
+        fc.fxok = fc.fxok && tolu < 1.0e9;
+        const unsigned tol = fc.fxok ? (unsigned)ceil(tolu) : 0u;
+        fc.ftol = tol;
+        fc.fspan = fc.fxok ? (unsigned)(4294967296.0 - 2.0 * tol - nb) : 0u;
+    }
     fc.f = f;
     fc.nb = nb;
     fc.fh = __double2float_rn(f);
@@ -222,12 +263,35 @@ __device__ __forceinline__ void fold_df32_pair(const float4& A, const FoldPacked
     e1 = !(fabsf(d1) <= q.lim);
 }
 
-// Fold of the point pair (2p, 2p+1) in a given phase mode; A = (dh0, dh1, dl0, dl1).
+// Fixed-point fold of two points at once; A = (DT0 lo, DT1 lo, DT0 hi, DT1 hi) as bit
+// patterns.  The high word of the low 64 bits of DT*F is lo*Fhi + hi*Flo + the carry word
+// of lo*Flo (mod 2^32): three integer multiply-adds per point, then one for the bin.
+__device__ __forceinline__ void fold_fx_pair(const float4& A, const FoldConst& fc,
+                                             unsigned& b0, unsigned& b1, bool& e0, bool& e1)
+{
+    const unsigned lo0 = __float_as_uint(A.x), lo1 = __float_as_uint(A.y);
+    const unsigned hi0 = __float_as_uint(A.z), hi1 = __float_as_uint(A.w);
+    const unsigned q0 = __umulhi(lo0, fc.Flo) + lo0 * fc.Fhi + hi0 * fc.Flo;
+    const unsigned q1 = __umulhi(lo1, fc.Flo) + lo1 * fc.Fhi + hi1 * fc.Flo;
+    const unsigned nbu = (unsigned)fc.nb;
+    b0 = __umulhi(q0, nbu);
+    b1 = __umulhi(q1, nbu);
+    e0 = q0 * nbu - fc.ftol >= fc.fspan;
+    e1 = q1 * nbu - fc.ftol >= fc.fspan;
+}
+
+// Fold of the point pair (2p, 2p+1) in a given phase mode; A = (dh0, dh1, dl0, dl1), or
+// the fixed-point offsets in FX64 mode.
 template <int PHASE>
 __device__ __forceinline__ void fold_pair(const float4& A, const double* dtp, const FoldConst& fc,
                                           const FoldPacked& q, unsigned& b0, unsigned& b1)
 {
-    if (PHASE == kPhaseF64 || !fc.fast) {
+    if (PHASE == kPhaseFX64) {
+        bool e0 = true, e1 = true;
+        if (fc.fxok) fold_fx_pair(A, fc, b0, b1, e0, e1);
+        if (e0) b0 = fold_exact(dtp[0], fc.f, fc.nb);
+        if (e1) b1 = fold_exact(dtp[1], fc.f, fc.nb);
+    } else if (PHASE == kPhaseF64 || !fc.fast) {
         b0 = fold_exact(dtp[0], fc.f, fc.nb);
         b1 = fold_exact(dtp[1], fc.f, fc.nb);
     } else if (PHASE == kPhaseF32) {
@@ -249,7 +313,8 @@ __device__ __forceinline__ void fold_pair_rt(int phase, const float4& A, const d
 {
     if (phase == kPhaseF64) fold_pair<kPhaseF64>(A, dtp, fc, q, b0, b1);
     else if (phase == kPhaseF32) fold_pair<kPhaseF32>(A, dtp, fc, q, b0, b1);
-    else fold_pair<kPhaseDF32>(A, dtp, fc, q, b0, b1);
+    else if (phase == kPhaseDF32) fold_pair<kPhaseDF32>(A, dtp, fc, q, b0, b1);
+    else fold_pair<kPhaseFX64>(A, dtp, fc, q, b0, b1);
 }
 
 // ------------------------------------------------------------------------- misc helpers
@@ -274,7 +339,13 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
-__device__ __forceinline__ float negabs(float x) { return __int_as_float(__float_as_int(x) | 0x80000000); }
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 
 // Deterministic block sum of FP64 (fixed tree, blockDim.x a power of two <= 1024).
 __device__ double block_sum(double v, double* red)
@@ -323,10 +394,11 @@ constexpr int kPrepThreads = 256;
 // Weights w = dy^-2/W, mean ybar = y0 + sum w (y - y0) (constant flux gives exact zeros),
 // x = y - ybar, dt = t - min t.  Points are stored in pairs (2p, 2p+1) as two float4:
 // (dt_hi0, dt_hi1, dt_lo0, dt_lo1) and (w0, wx0, w1, wx1), dt in FP64 beside them; an odd
-// curve gets a pad point of zero weight.  Validates the inputs (finite t and y, finite
+// curve gets a pad point of zero weight.  In the FX64 phase mode the first float4 holds
+// the bit patterns of DT = RN_int(dt 2^fxs) instead: (lo0, lo1, hi0, hi1).  Validates the inputs (finite t and y, finite
 // dy > 0, frequencies > 0).
 __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, const int* slots,
-                                                             int* err)
+                                                             int* err, int phase)
 {
     __shared__ double red[kPrepThreads];
     CurveDesc* cd = &curves[slots ? slots[blockIdx.x] : (int)blockIdx.x];
@@ -373,6 +445,8 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, c
     }
     acc = block_sum(acc, red);
     const double ybar = __dadd_rn(y0, acc);
+    const int fxs = fx_shift(__dsub_rn(tmax, tmin));
+    const bool fx = phase == kPhaseFX64;
     double swx2 = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double inv = 1.0;
@@ -381,13 +455,18 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, c
         double dt = __dsub_rn(t[i], tmin);
         double x = __dsub_rn((double)y[i], ybar);
         double wx = __dmul_rn(w, x);
-        float dh = __double2float_rn(dt);
-        float dl = __double2float_rn(__dsub_rn(dt, (double)dh));
         float* A = reinterpret_cast<float*>(&pts[(i >> 1) * 2]);
         float* B = A + 4;
         const int l = i & 1;
-        A[l] = dh;
-        A[2 + l] = dl;
+        if (fx) {
+            const unsigned long long DT = __double2ull_rn(ldexp(dt, fxs));
+            A[l] = __uint_as_float((unsigned)DT);
+            A[2 + l] = __uint_as_float((unsigned)(DT >> 32));
+        } else {
+            const float dh = __double2float_rn(dt);
+            A[l] = dh;
+            A[2 + l] = __double2float_rn(__dsub_rn(dt, (double)dh));
+        }
         B[2 * l] = __double2float_rn(w);
         B[2 * l + 1] = __double2float_rn(wx);
         dt64[i] = dt;
@@ -405,14 +484,15 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, c
         cd->ybar = ybar;
         cd->sumwx2 = swx2;
         cd->dtmax = __dsub_rn(tmax, tmin);
+        cd->fxs = fxs;
     }
 }
 
-cudaError_t launch_prep(CurveDesc* d_curves, const int* slots, int ncurves, int* err,
+cudaError_t launch_prep(CurveDesc* d_curves, const int* slots, int ncurves, int* err, int phase,
                         cudaStream_t s)
 {
     if (ncurves <= 0) return cudaSuccess;
-    prep_kernel<<<ncurves, kPrepThreads, 0, s>>>(d_curves, slots, err);
+    prep_kernel<<<ncurves, kPrepThreads, 0, s>>>(d_curves, slots, err, phase);
     return cudaGetLastError();
 }
 
@@ -470,8 +550,9 @@ __device__ __forceinline__ void sts64(unsigned addr, u64 v)
 
 // Bins of the 8 point pairs of a 16-point sub-chunk, with their weight pairs; returns
 // whether any bin is not certain (then fix_sub must run before the bins are used).
-__device__ __forceinline__ bool fold_sub(const float4* cp, const FoldPacked& fq, unsigned* b,
-                                         float4* Bw)
+template <int PHASE>
+__device__ __forceinline__ bool fold_sub(const float4* cp, const FoldConst& fc, const FoldPacked& fq,
+                                         unsigned* b, float4* Bw)
 {
     bool edge = false;
 #pragma unroll
@@ -479,13 +560,15 @@ __device__ __forceinline__ bool fold_sub(const float4* cp, const FoldPacked& fq,
         const float4 A = cp[2 * q];
         Bw[q] = cp[2 * q + 1];
         bool e0, e1;
-        fold_df32_pair(A, fq, b[2 * q], b[2 * q + 1], e0, e1);
+        if (PHASE == kPhaseFX64) fold_fx_pair(A, fc, b[2 * q], b[2 * q + 1], e0, e1);
+        else fold_df32_pair(A, fq, b[2 * q], b[2 * q + 1], e0, e1);
         edge = edge | e0 | e1;
     }
     return edge;
 }
 
 // Rare path: re-fold in FP64 the points of a sub-chunk whose bin is not certain.
+template <int PHASE>
 __device__ __forceinline__ void fix_sub(const float4* cp, const double* cd, const FoldConst& fc,
                                      const FoldPacked& fq, unsigned* b)
 {
@@ -493,7 +576,8 @@ __device__ __forceinline__ void fix_sub(const float4* cp, const double* cd, cons
     for (int q = 0; q < 8; ++q) {
         unsigned b0, b1;
         bool e0, e1;
-        fold_df32_pair(cp[2 * q], fq, b0, b1, e0, e1);
+        if (PHASE == kPhaseFX64) fold_fx_pair(cp[2 * q], fc, b0, b1, e0, e1);
+        else fold_df32_pair(cp[2 * q], fq, b0, b1, e0, e1);
         if (e0) b[2 * q] = fold_exact(cd[2 * q], fc.f, fc.nb);
         if (e1) b[2 * q + 1] = fold_exact(cd[2 * q + 1], fc.f, fc.nb);
     }
@@ -537,20 +621,21 @@ __device__ __forceinline__ void rmw_sub(unsigned hbase, unsigned rowb, const uns
 // chain, so the fold arithmetic fills the shared-memory latency of the chain; the rare
 // FP64 re-fold runs after the stores.  hbase is the shared-memory address of this
 // thread's bin 0, rowb the byte stride between bins.
-__device__ __forceinline__ void bin_df32(const float4* cp, const double* cd, int nsub,
+template <int PHASE>
+__device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int nsub,
                                          unsigned hbase, unsigned rowb, const FoldConst& fc,
                                          const FoldPacked& fq)
 {
     unsigned b[16];
     float4 Bw[8];
-    if (fold_sub(cp, fq, b, Bw)) fix_sub(cp, cd, fc, fq, b);
+    if (fold_sub<PHASE>(cp, fc, fq, b, Bw)) fix_sub<PHASE>(cp, cd, fc, fq, b);
     for (int sc = 0; sc + 1 < nsub; ++sc) {
         unsigned bn[16];
         float4 Bn[8];
         const float4* np = cp + 16 * (sc + 1);
-        const bool edge = fold_sub(np, fq, bn, Bn);
+        const bool edge = fold_sub<PHASE>(np, fc, fq, bn, Bn);
         rmw_sub(hbase, rowb, b, Bw);
-        if (edge) fix_sub(np, cd + 16 * (sc + 1), fc, fq, bn);
+        if (edge) fix_sub<PHASE>(np, cd + 16 * (sc + 1), fc, fq, bn);
 #pragma unroll
         for (int i = 0; i < 16; ++i) b[i] = bn[i];
 #pragma unroll
@@ -598,51 +683,53 @@ __device__ __forceinline__ float bin_x(const unsigned char* hist, size_t S, int 
 // Fast sweep: the largest power P of any box, without its position.
 //
 // SB consecutive starts share every bin load; their sums are carried as SB/2 packed pairs
-// (one f32x2 instruction updates two starts).  P = num * rcp(den) with num = s^2 (dips:
-// -s|s|, negative for bumps) and den = r(1-r); the approximate reciprocal is within one
-// FP32 ulp, far inside the tolerance of the spectrum.  Empty boxes give 0 * inf = NaN and
-// bumps (dips only) a negative P: max() ignores both.  Conditions: kmin = 1, kmax >=
-// SB - 1, and no box can hold more than 0.9 of the weight (checked by the caller), so
-// den > 0.09 r and FP32 keeps 1 - r accurate.  The starts of the last block may pass nb;
-// they repeat earlier starts and cannot change the maximum.
+// (one f32x2 instruction updates two starts).  Conditions: kmin = 1, kmax >= SB - 1, and
+// no box can hold more than 0.89 of the weight (checked by the caller).  The starts of the
+// last block may pass nb; they repeat earlier starts and cannot change the maximum.
+//
+// Fast-sweep evaluation of two boxes (starts 2q and 2q+1 of a block) that grow by one bin.
+//
+// R holds -r of the two boxes and X their s.  The sweep ranks boxes by the signed residue
+// z = s / sqrt(d), d = r(1-r), since P = s^2/d = z^2: one fused rounding gives -d = r^2 - r,
+// one approximate reciprocal square root and one product give z (relative error about
+// 2^-22, far inside the tolerance of the spectrum), and no division or squaring is needed.
+// Dips (SIGN = 0) are the boxes with s < 0, so the most negative z wins; with both signs
+// the largest |z| does.  An empty box (r = 0, s = 0 exactly) gives 0 * inf = NaN, which
+// min/max ignore.  The fast sweep only runs where every box has r < 0.89, so d > 0.
 template <int SIGN>
 __device__ __forceinline__ void eval_pair(u64& R, u64& X, const u64& HW2, const u64& HX2,
-                                          const u64& ONE2, bool init, bool use0, bool use1,
-                                          float& b0, float& b1)
+                                          bool init, bool use0, bool use1, float& b0, float& b1)
 {
     if (init) {
         float hw, hw1, hx, hx1;
         upk(HW2, hw, hw1);
         upk(HX2, hx, hx1);
-        R = pk(hw, 0.0f);   // the second start of the pair begins at the next bin
+        R = pk(-hw, 0.0f);   // the second start of the pair begins at the next bin
         X = pk(hx, 0.0f);
     } else {
-        R = add2(R, HW2);
+        R = sub2(R, HW2);
         X = add2(X, HX2);
     }
-    const u64 DEN = mul2(R, sub2(ONE2, R));
-    u64 NUM;
+    const u64 ND = fma2(R, R, R);   // (r0^2 - r0, r1^2 - r1) = (-d0, -d1)
+    float nd0, nd1;
+    upk(ND, nd0, nd1);
+    const u64 Z = mul2(X, pk(rsqrt_approx(-nd0), rsqrt_approx(-nd1)));
+    float z0, z1;
+    upk(Z, z0, z1);
     if (SIGN) {
-        NUM = mul2(X, X);
+        if (use0) b0 = fmaxf(b0, fabsf(z0));
+        if (use1) b1 = fmaxf(b1, fabsf(z1));
     } else {
-        float s0, s1;
-        upk(X, s0, s1);
-        NUM = mul2(X, pk(negabs(s0), negabs(s1)));
+        if (use0) b0 = fminf(b0, z0);
+        if (use1) b1 = fminf(b1, z1);
     }
-    float d0, d1;
-    upk(DEN, d0, d1);
-    const u64 P = mul2(NUM, pk(rcp_approx(d0), rcp_approx(d1)));
-    float p0, p1;
-    upk(P, p0, p1);
-    if (use0) b0 = fmaxf(b0, p0);
-    if (use1) b1 = fmaxf(b1, p1);
 }
 
 // One step of the fast sweep over one block: bin value (hw, hx) for the pairs [Q0, Q1),
 // with the ramp rules given by (init, use0, use1) per pair (see sweep_fast).
 template <int SIGN, int NP>
 __device__ __forceinline__ void sweep_step(float hw, float hx, u64* R, u64* X, float* b0,
-                                           float* b1, const u64& ONE2, int mm, int phase,
+                                           float* b1, int mm, int phase,
                                            int e)
 {
     const u64 HW2 = pk(hw, hw), HX2 = pk(hx, hx);
@@ -650,12 +737,12 @@ __device__ __forceinline__ void sweep_step(float hw, float hx, u64* R, u64* X, f
     for (int q = 0; q < NP; ++q) {
         if (phase == 0) {          // ramp-up at bin mm
             if (2 * q > mm) continue;
-            eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, 2 * q == mm, true, 2 * q < mm, b0[q], b1[q]);
+            eval_pair<SIGN>(R[q], X[q], HW2, HX2, 2 * q == mm, true, 2 * q < mm, b0[q], b1[q]);
         } else if (phase == 1) {   // steady
-            eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, false, true, true, b0[q], b1[q]);
+            eval_pair<SIGN>(R[q], X[q], HW2, HX2, false, true, true, b0[q], b1[q]);
         } else {                   // ramp-down step e
             if (2 * q + 1 < e + 1) continue;
-            eval_pair<SIGN>(R[q], X[q], HW2, HX2, ONE2, false, 2 * q >= e + 1, true, b0[q], b1[q]);
+            eval_pair<SIGN>(R[q], X[q], HW2, HX2, false, 2 * q >= e + 1, true, b0[q], b1[q]);
         }
     }
 }
@@ -663,17 +750,18 @@ __device__ __forceinline__ void sweep_step(float hw, float hx, u64* R, u64* X, f
 // Fast sweep over two independent blocks of SB starts at a time (starts i0.. and
 // i0 + half..), so that 2*SB/2 packed pairs are in flight per bin step.  Block A covers
 // starts [0, half), block B [half, 2 half) with half = SB * ceil(nb / (2 SB)); starts past
-// nb repeat earlier ones (cyclic) and cannot change the maximum.
+// nb repeat earlier ones (cyclic) and cannot change the maximum.  The outer steps i0 are
+// dealt round-robin to `nparts` threads sharing the histogram; `part` is this thread's.
 template <int SB, int SIGN>
-__device__ __forceinline__ float sweep_fast(unsigned hbase, unsigned rowb, int nb, int kmax)
+__device__ __forceinline__ float sweep_fast(unsigned hbase, unsigned rowb, int nb, int kmax,
+                                            int part, int nparts)
 {
     constexpr int NP = SB / 2;
-    const u64 ONE2 = pk(1.0f, 1.0f);
     float a0[NP], a1[NP], c0[NP], c1[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) { a0[q] = 0.0f; a1[q] = 0.0f; c0[q] = 0.0f; c1[q] = 0.0f; }
     const int half = SB * ((nb + 2 * SB - 1) / (2 * SB));
-    for (int i0 = 0; i0 < half; i0 += SB) {
+    for (int i0 = part * SB; i0 < half; i0 += nparts * SB) {
         u64 RA[NP], XA[NP], RB[NP], XB[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) { RA[q] = 0ull; XA[q] = 0ull; RB[q] = 0ull; XB[q] = 0ull; }
@@ -688,29 +776,33 @@ __device__ __forceinline__ float sweep_fast(unsigned hbase, unsigned rowb, int n
         for (int mm = 0; mm < SB - 1; ++mm) {
             float hwa, hxa, hwb, hxb;
             BLS_LOAD2(hwa, hxa, hwb, hxb)
-            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, ONE2, mm, 0, 0);
-            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, ONE2, mm, 0, 0);
+            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, mm, 0, 0);
+            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, mm, 0, 0);
         }
 #pragma unroll 2
         for (int mm = SB - 1; mm < kmax; ++mm) {
             float hwa, hxa, hwb, hxb;
             BLS_LOAD2(hwa, hxa, hwb, hxb)
-            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, ONE2, 0, 1, 0);
-            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, ONE2, 0, 1, 0);
+            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, 0, 1, 0);
+            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, 0, 1, 0);
         }
 #pragma unroll
         for (int e = 0; e < SB - 1; ++e) {
             float hwa, hxa, hwb, hxb;
             BLS_LOAD2(hwa, hxa, hwb, hxb)
-            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, ONE2, 0, 2, e);
-            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, ONE2, 0, 2, e);
+            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, 0, 2, e);
+            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, 0, 2, e);
         }
 #undef BLS_LOAD2
     }
+    // best signed residue -> power P = z^2
     float best = 0.0f;
 #pragma unroll
-    for (int q = 0; q < NP; ++q) best = fmaxf(fmaxf(best, fmaxf(a0[q], a1[q])), fmaxf(c0[q], c1[q]));
-    return best;
+    for (int q = 0; q < NP; ++q) {
+        if (SIGN) best = fmaxf(fmaxf(best, fmaxf(a0[q], a1[q])), fmaxf(c0[q], c1[q]));
+        else best = fminf(fminf(best, fminf(a0[q], a1[q])), fminf(c0[q], c1[q]));
+    }
+    return best * best;
 }
 
 struct Best {
@@ -799,9 +891,12 @@ __device__ __forceinline__ Best sweep_exact_rt(int sign, const unsigned char* hi
 // cheap test kmax * (heaviest bin) < 0.89 settles most frequencies, and when it fails the
 // heaviest run of kmax bins is measured with a sliding sum (the 0.01 margin covers FP32
 // rounding of the sums).
+// The largest power of one frequency's histogram, or (nparts > 1) of this thread's share
+// of the box starts: the fast sweep is split over the threads, the exact sweep runs on
+// part 0 alone (the others return 0, below any power a box can reach).
 template <int KAHAN, int SIGN, int SB>
 __device__ __forceinline__ float sweep_max(const unsigned char* hist, int stride, int nb,
-                                           int kmin, int kmax)
+                                           int kmin, int kmax, int part, int nparts)
 {
     if (!KAHAN && kmin == 1 && kmax >= SB - 1) {
         const unsigned hbase = (unsigned)__cvta_generic_to_shared(hist);
@@ -831,22 +926,28 @@ __device__ __forceinline__ float sweep_max(const unsigned char* hist, int stride
             }
             fast = rmax < 0.89f;
         }
-        if (fast) return sweep_fast<SB, SIGN>(hbase, rowb, nb, kmax);
+        if (fast) return sweep_fast<SB, SIGN>(hbase, rowb, nb, kmax, part, nparts);
     }
+    if (part != 0) return 0.0f;
     const Best g = sweep_exact<SIGN>(hist, stride, KAHAN, nb, kmin, kmax);
     return g.num > 0.0f ? __fdiv_rn(g.num, g.den) : 0.0f;
 }
 
 // ------------------------------------------------------------------------- a2-a6: hot kernel
 
-// Starts per block of the fast sweep for wide boxes (kmax >= 15).
-#ifndef BLS_SWEEP_WIDE
-#define BLS_SWEEP_WIDE 8
-#endif
-constexpr int kSweepWide = BLS_SWEEP_WIDE;
+// Starts per block of the fast sweep for wide boxes (kmax >= 15): 8 or 10, whichever
+// wastes fewer starts once the nb starts are dealt to nparts threads in steps of two
+// blocks (nb = 200 over 2 threads: 10 gives 5 + 5 steps with none wasted, 8 gives 7 + 6).
+__device__ __forceinline__ bool wide_sweep_10(int nb, int nparts)
+{
+    const int s8 = 16 * nparts, s10 = 20 * nparts;
+    return ((nb + s10 - 1) / s10) * s10 < ((nb + s8 - 1) / s8) * s8;
+}
 
 constexpr int kFoldMaxThreads = 256;
 
+// Shared memory of a fold-sweep block: [staging: 2 x chunk point pairs + FP64 offsets]
+// [histograms: nb_max rows x stride entries].
 size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int kahan)
 {
     (void)T;
@@ -857,19 +958,37 @@ size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int kahan)
 
 int fold_sweep_max_threads() { return kFoldMaxThreads; }
 
+// Threads per block for `cols` frequencies per tile: two per column when they fit (the
+// second one halves the sweep's share of each thread), else one.
+#ifndef BLS_SWEEP_SPLIT
+#define BLS_SWEEP_SPLIT 2
+#endif
+int fold_block_threads(int cols)
+{
+    return (BLS_SWEEP_SPLIT == 2 && 2 * cols <= kFoldMaxThreads) ? 2 * cols : cols;
+}
+
 template <int PHASE, int KAHAN, int SIGN>
 __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
-    const int T = blockDim.x;
+    // p.cols frequencies per tile, one histogram column each; blockDim.x is cols or
+    // 2 cols: threads [cols, 2 cols) help stage the points and sweep the boxes of column
+    // tid - cols (the binning needs one private histogram per thread and shared memory
+    // holds only cols of them; the sweep only reads them)
+    const int T = p.cols;
+    const int NT = blockDim.x;
     const int tid = threadIdx.x;
+    const int part = tid < T ? 0 : 1;
+    const int col = tid - part * T;
+    const int nparts = NT / T;
     const int CH = p.chunk;
     float4* cpts = reinterpret_cast<float4*>(smem);             // [2][CH]: point pairs
     double* cdt = reinterpret_cast<double*>(cpts + 2 * CH);     // [2][CH]: FP64 offsets
     unsigned char* hist_all = reinterpret_cast<unsigned char*>(cdt + 2 * CH);
     const size_t esz = KAHAN ? sizeof(float4) : sizeof(float2);
-    unsigned char* hist = hist_all + (size_t)tid * esz;         // column of this thread
+    unsigned char* hist = hist_all + (size_t)col * esz;         // column of this thread
     const size_t S = (size_t)p.stride;
 
     for (;;) {
@@ -889,13 +1008,13 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
         const float4* gpts = cdr.pts;
         const double* gdt = cdr.dt64;
         const int tile = tr.tile_lo + (int)(it - p.prefix[lo]);
-        const int j = tile * T + tid;
+        const int j = tile * T + col;
         const bool active = j < nf;
         const double f = grid_freq(cdr, active ? j : nf - 1);
-        const FoldConst fc = make_fold_const(f, nb, cdr.dtmax);
+        const FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs);
         const FoldPacked fq = make_fold_packed(fc);
 
-        for (int b = 0; b < nb; ++b) {
+        for (int b = 0; b < nb && part == 0; ++b) {
             if (KAHAN)
                 reinterpret_cast<float4*>(hist)[(size_t)b * S] = make_float4(0.f, 0.f, 0.f, 0.f);
             else
@@ -912,11 +1031,11 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
             const int cpad = (cn + 15) & ~15;
             float4* dp = cpts + (ci & 1) * CH;
             double* dd = cdt + (ci & 1) * CH;
-            for (int i = tid; i < cn; i += T) {
+            for (int i = tid; i < cn; i += NT) {
                 cp_async16(&dp[i], &gpts[c0 + i]);
                 cp_async8(&dd[i], &gdt[c0 + i]);
             }
-            for (int i = cn + tid; i < cpad; i += T) {
+            for (int i = cn + tid; i < cpad; i += NT) {
                 dp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
                 dd[i] = 0.0;
             }
@@ -932,7 +1051,7 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
             const int cnum = min(CH, n - ci * CH);
             const float4* cp = cpts + (ci & 1) * CH;
             const double* cd = cdt + (ci & 1) * CH;
-            if (active) {   // a3 + a4: fold and bin
+            if (active && part == 0) {   // a3 + a4: fold and bin
                 if (KAHAN) {
                     const int npairs = (cnum + 1) >> 1;
                     for (int pi = 0; pi < npairs; ++pi) {
@@ -942,8 +1061,8 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
                         kahan_add(reinterpret_cast<float4*>(hist) + b0 * S, B.x, B.y);
                         kahan_add(reinterpret_cast<float4*>(hist) + b1 * S, B.z, B.w);
                     }
-                } else if (PHASE == kPhaseDF32 && fc.fast) {
-                    bin_df32(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                } else if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
+                    bin_fast<PHASE>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
                 } else {
                     bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
                 }
@@ -951,9 +1070,22 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
             __syncthreads();
         }
 
-        if (active) {
-            cdr.res[j] = kmax >= 15 ? sweep_max<KAHAN, SIGN, kSweepWide>(hist, p.stride, nb, kmin, kmax)
-                                    : sweep_max<KAHAN, SIGN, 4>(hist, p.stride, nb, kmin, kmax);
+        // a5 + a6: box sweep; the partial maxima of a column meet in the staging buffer,
+        // idle once the last chunk is binned (2 CH x 24 B >= 1536 B since CH >= 32, more
+        // than the 4 B x blockDim.x <= 1024 B needed)
+        float v = 0.0f;
+        if (active)
+            v = kmax < 15 ? sweep_max<KAHAN, SIGN, 4>(hist, p.stride, nb, kmin, kmax, part, nparts)
+                : wide_sweep_10(nb, nparts)
+                    ? sweep_max<KAHAN, SIGN, 10>(hist, p.stride, nb, kmin, kmax, part, nparts)
+                    : sweep_max<KAHAN, SIGN, 8>(hist, p.stride, nb, kmin, kmax, part, nparts);
+        if (nparts == 1) {
+            if (active) cdr.res[j] = v;
+        } else {
+            float* red = reinterpret_cast<float*>(cpts);
+            red[tid] = v;
+            __syncthreads();
+            if (active && part == 0) cdr.res[j] = fmaxf(v, red[T + col]);
         }
     }
 }
@@ -966,7 +1098,9 @@ static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t sm
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, T, smem, s>>>(p);
+    FoldParams q = p;
+    q.cols = T;
+    k<<<grid, fold_block_threads(T), smem, s>>>(q);
     return cudaGetLastError();
 }
 
@@ -979,7 +1113,7 @@ static int blocks_t(int T, size_t smem)
         return 1;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, T, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, fold_block_threads(T), smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -996,6 +1130,7 @@ int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign)
     BLS_OCC(kPhaseDF32)
     BLS_OCC(kPhaseF64)
     BLS_OCC(kPhaseF32)
+    BLS_OCC(kPhaseFX64)
 #undef BLS_OCC
     return 1;
 }
@@ -1013,6 +1148,7 @@ cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, i
     BLS_DISPATCH(kPhaseDF32)
     BLS_DISPATCH(kPhaseF64)
     BLS_DISPATCH(kPhaseF32)
+    BLS_DISPATCH(kPhaseFX64)
 #undef BLS_DISPATCH
     return cudaErrorInvalidValue;
 }
@@ -1026,7 +1162,7 @@ __device__ Best best_box_at(const CurveDesc& cd, double f, unsigned char* hist, 
                             int phase, int kahan, int sign)
 {
     const size_t S = (size_t)stride;
-    const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax);
+    const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax, cd.fxs);
     const FoldPacked fq = make_fold_packed(fc);
     for (int b = 0; b < cd.nb; ++b) {
         if (kahan) reinterpret_cast<float4*>(hist)[(size_t)b * S] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1253,7 +1389,7 @@ __global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bi
     const CurveDesc cd = *curve;
     const int q = blockIdx.x;
     const double f = grid_freq(cd, js[q]);
-    const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax);
+    const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax, cd.fxs);
     const FoldPacked fq = make_fold_packed(fc);
     for (int pi = threadIdx.x; 2 * pi < cd.n; pi += blockDim.x) {
         unsigned b0, b1;
@@ -1271,8 +1407,10 @@ cudaError_t launch_debug_fold(const CurveDesc* d_curve, const int* js, int nj, i
         debug_fold_kernel<kPhaseF64><<<nj, 256, 0, s>>>(d_curve, js, bins);
     else if (phase == kPhaseF32)
         debug_fold_kernel<kPhaseF32><<<nj, 256, 0, s>>>(d_curve, js, bins);
-    else
+    else if (phase == kPhaseDF32)
         debug_fold_kernel<kPhaseDF32><<<nj, 256, 0, s>>>(d_curve, js, bins);
+    else
+        debug_fold_kernel<kPhaseFX64><<<nj, 256, 0, s>>>(d_curve, js, bins);
     return cudaGetLastError();
 }
 

@@ -220,7 +220,7 @@ bool Server::step()
     if (nadm > 0) {
         cudaMemcpyAsync(dsl, hs, sizeof(int) * nadm, cudaMemcpyHostToDevice, stream);
         cudaMemsetAsync(err.p, 0, sizeof(int), stream);
-        if ((e = launch_prep(cdesc.as<CurveDesc>(), dsl, nadm, err.as<int>(), stream)) != cudaSuccess) {
+        if ((e = launch_prep(cdesc.as<CurveDesc>(), dsl, nadm, err.as<int>(), P->d.phase, stream)) != cudaSuccess) {
             fail_all(std::string("prep launch: ") + cudaGetErrorString(e));
             return false;
         }

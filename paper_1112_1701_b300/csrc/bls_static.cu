@@ -119,7 +119,9 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
         const size_t stage = (size_t)2 * chunk * 24;
         const size_t avail = avail_all > stage + 64 ? avail_all - stage - 64 : 0;
         const size_t cap = avail / ((size_t)c->nb * 8);
-        return (int)std::min<size_t>(cap, (size_t)fold_sweep_max_threads()) & ~15;
+        int T = (int)std::min<size_t>(cap, (size_t)fold_sweep_max_threads()) & ~15;
+        while (T >= 16 && fold_smem_bytes(T, T, c->nb, chunk, 0) > avail_all) T -= 16;
+        return T;
     };
     const int chunk = tmax(512) >= tmax(256) ? 512 : 256;
     const int T = tmax(chunk);
@@ -145,7 +147,7 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
 
     static_init_kernel<<<1, 1, 0, s>>>(d, cdesc, range, prefix, ntiles, counter, err);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "static init launch");
-    if ((e = launch_prep(cdesc, nullptr, 1, err, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
+    if ((e = launch_prep(cdesc, nullptr, 1, err, kPhaseFX64, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
     FoldParams fp;
     fp.curves = cdesc;
     fp.ranges = range;
@@ -156,9 +158,9 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
     fp.err = err;
     fp.chunk = chunk;
     fp.stride = T;
-    long long grid = (long long)sms * fold_blocks_per_sm(T, smem, kPhaseDF32, 0, sign);
+    long long grid = (long long)sms * fold_blocks_per_sm(T, smem, kPhaseFX64, 0, sign);
     if (grid > ntiles) grid = ntiles;
-    if ((e = launch_fold_sweep(fp, T, (int)grid, kPhaseDF32, 0, sign, smem, s)) != cudaSuccess)
+    if ((e = launch_fold_sweep(fp, T, (int)grid, kPhaseFX64, 0, sign, smem, s)) != cudaSuccess)
         return cuda_fail(e, "fold-sweep launch");
     ReduceParams rp;
     rp.curves = cdesc;
@@ -167,7 +169,7 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
     rp.spectrum = spectrum_dev;
     rp.topk = topk;
     rp.sign = sign;
-    rp.phase = kPhaseDF32;
+    rp.phase = kPhaseFX64;
     rp.kahan = 0;
     rp.smem_bytes = reduce_smem_bytes(c->nb, topk, 0);
     if ((e = launch_reduce(rp, 1, s)) != cudaSuccess) return cuda_fail(e, "reduce launch");

@@ -58,7 +58,7 @@ def _bins_check(ci, nb, js, phase="df32"):
     return bg, bo
 
 
-@pytest.mark.parametrize("phase", ["df32", "f64"])
+@pytest.mark.parametrize("phase", ["df32", "f64", "fx64"])
 def test_bins_bit_exact_plain_and_long_baseline(phase):
     b1 = synth.config1()
     ci1 = _ci(b1.curves[0], b1.grids[0], 100, 0.01, 0.1)
@@ -73,7 +73,8 @@ def test_bins_bit_exact_plain_and_long_baseline(phase):
     assert np.array_equal(bg, bo), f"{int((bg != bo).sum())} of {bg.size} bins differ"
 
 
-def test_bins_bit_exact_on_exact_edges():
+@pytest.mark.parametrize("phase", ["df32", "fx64"])
+def test_bins_bit_exact_on_exact_edges(phase):
     """Points placed exactly on bin edges (and on integer cycles) at grid frequencies:
     every one lands within the error bound and takes the exact FP64 re-fold."""
     nb, f0, df = 64, 0.5, 0.25
@@ -89,10 +90,25 @@ def test_bins_bit_exact_on_exact_edges():
     t = synth.T0 + dt
     y = np.ones(len(t), np.float32)
     ci = bls.CurveInput(t, y, None, nf=11, fmin=f0, df=df, nb=nb, qmin=0.02, qmax=0.2)
-    with _plan(nb, 0.02, 0.2) as p:
+    with _plan(nb, 0.02, 0.2, phase=phase) as p:
         bg = p.debug_fold(ci, js)
     bo = oracle.bins(t, [oracle.freq(j, f0, df) for j in js], nb)
     assert np.array_equal(bg, bo)
+
+
+def test_fast_phase_modes_give_identical_searches():
+    """The double-FP32 and fixed-point folds both reproduce the FP64 bins exactly, and the
+    binning order is the same, so spectra and peaks must agree bit for bit."""
+    b = synth.config2(ncurves=12, nf=2000, seed=31)
+    cis = bls.curves_from_batch(b)
+    out = {}
+    for phase in ("df32", "fx64"):
+        with _plan(200, b.qmin, b.qmax, topk=3, phase=phase) as p:
+            spec = np.zeros(12 * 2000, np.float32)
+            pk = p.search(cis, spectrum=spec)
+            out[phase] = (pk, spec)
+    assert np.array_equal(out["df32"][1], out["fx64"][1])
+    assert np.array_equal(out["df32"][0], out["fx64"][0])
 
 
 def test_f32_phase_mode_runs_and_can_differ():
