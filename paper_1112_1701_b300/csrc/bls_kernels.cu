@@ -688,15 +688,26 @@ __device__ __forceinline__ float bin_x(const unsigned char* hist, size_t S, int 
 // last block may pass nb; they repeat earlier starts and cannot change the maximum.
 //
 // Fast-sweep evaluation of two boxes (starts 2q and 2q+1 of a block) that grow by one bin.
+// R holds -r of the two boxes and X their s; d = r(1-r) comes from one fused rounding,
+// -d = r^2 - r.  The fast sweep only runs where every box has r < 0.89, so d > 0.  Two
+// forms rank the boxes, with different shares of special-function and FP32 work:
 //
-// R holds -r of the two boxes and X their s.  The sweep ranks boxes by the signed residue
-// z = s / sqrt(d), d = r(1-r), since P = s^2/d = z^2: one fused rounding gives -d = r^2 - r,
-// one approximate reciprocal square root and one product give z (relative error about
-// 2^-22, far inside the tolerance of the spectrum), and no division or squaring is needed.
-// Dips (SIGN = 0) are the boxes with s < 0, so the most negative z wins; with both signs
-// the largest |z| does.  An empty box (r = 0, s = 0 exactly) gives 0 * inf = NaN, which
-// min/max ignore.  The fast sweep only runs where every box has r < 0.89, so d > 0.
-template <int SIGN>
+// FORM 0, signed residue: z = s * rsqrt(d) (P = z^2), one approximate reciprocal square
+// root per box and one product.  Dips (SIGN = 0) are the boxes with s < 0, so the most
+// negative z wins; with both signs the largest |z| does.  An empty box (r = 0, s = 0
+// exactly) gives 0 * inf = NaN, which min/max ignore.
+//
+// FORM 1, power with a shared reciprocal: 1/(d0 d1) gives 1/d0 = d1/(d0 d1) and
+// 1/d1 = d0/(d0 d1), one reciprocal for the two boxes; P = s^2/d (dips: -s|s|/d, negative
+// for bumps).  An empty box would make the shared product zero, so its -r starts at
+// -kEmptyBox instead of 0: d0 d1 >= kEmptyBox^2 stays a normal FP32 number, an empty box
+// evaluates to P = 0, and for a real box (r >= 1e-10, far below one point's weight in
+// practice) the offset is below half an ulp of r and changes nothing.
+//
+// Both approximations err by about 2^-22 relative, far inside the spectrum's tolerance.
+constexpr float kEmptyBox = 1e-18f;
+
+template <int SIGN, int FORM>
 __device__ __forceinline__ void eval_pair(u64& R, u64& X, const u64& HW2, const u64& HX2,
                                           bool init, bool use0, bool use1, float& b0, float& b1)
 {
@@ -704,7 +715,8 @@ __device__ __forceinline__ void eval_pair(u64& R, u64& X, const u64& HW2, const 
         float hw, hw1, hx, hx1;
         upk(HW2, hw, hw1);
         upk(HX2, hx, hx1);
-        R = pk(-hw, 0.0f);   // the second start of the pair begins at the next bin
+        // the second start of the pair begins at the next bin
+        R = FORM ? pk(-hw - kEmptyBox, -kEmptyBox) : pk(-hw, 0.0f);
         X = pk(hx, 0.0f);
     } else {
         R = sub2(R, HW2);
@@ -713,21 +725,33 @@ __device__ __forceinline__ void eval_pair(u64& R, u64& X, const u64& HW2, const 
     const u64 ND = fma2(R, R, R);   // (r0^2 - r0, r1^2 - r1) = (-d0, -d1)
     float nd0, nd1;
     upk(ND, nd0, nd1);
-    const u64 Z = mul2(X, pk(rsqrt_approx(-nd0), rsqrt_approx(-nd1)));
-    float z0, z1;
-    upk(Z, z0, z1);
-    if (SIGN) {
-        if (use0) b0 = fmaxf(b0, fabsf(z0));
-        if (use1) b1 = fmaxf(b1, fabsf(z1));
+    if (FORM == 0) {
+        const u64 Z = mul2(X, pk(rsqrt_approx(-nd0), rsqrt_approx(-nd1)));
+        float z0, z1;
+        upk(Z, z0, z1);
+        if (SIGN) {
+            if (use0) b0 = fmaxf(b0, fabsf(z0));
+            if (use1) b1 = fmaxf(b1, fabsf(z1));
+        } else {
+            if (use0) b0 = fminf(b0, z0);
+            if (use1) b1 = fminf(b1, z1);
+        }
     } else {
-        if (use0) b0 = fminf(b0, z0);
-        if (use1) b1 = fminf(b1, z1);
+        const float rc = rcp_approx(nd0 * nd1);
+        const u64 Q = mul2(X, pk(nd1 * rc, nd0 * rc));   // (-s0/d0, -s1/d1)
+        float q0, q1, s0, s1;
+        upk(Q, q0, q1);
+        upk(X, s0, s1);
+        const float p0 = SIGN ? q0 * -s0 : q0 * fabsf(s0);
+        const float p1 = SIGN ? q1 * -s1 : q1 * fabsf(s1);
+        if (use0) b0 = fmaxf(b0, p0);
+        if (use1) b1 = fmaxf(b1, p1);
     }
 }
 
 // One step of the fast sweep over one block: bin value (hw, hx) for the pairs [Q0, Q1),
 // with the ramp rules given by (init, use0, use1) per pair (see sweep_fast).
-template <int SIGN, int NP>
+template <int SIGN, int NP, int FORM>
 __device__ __forceinline__ void sweep_step(float hw, float hx, u64* R, u64* X, float* b0,
                                            float* b1, int mm, int phase,
                                            int e)
@@ -737,15 +761,22 @@ __device__ __forceinline__ void sweep_step(float hw, float hx, u64* R, u64* X, f
     for (int q = 0; q < NP; ++q) {
         if (phase == 0) {          // ramp-up at bin mm
             if (2 * q > mm) continue;
-            eval_pair<SIGN>(R[q], X[q], HW2, HX2, 2 * q == mm, true, 2 * q < mm, b0[q], b1[q]);
+            eval_pair<SIGN, FORM>(R[q], X[q], HW2, HX2, 2 * q == mm, true, 2 * q < mm, b0[q], b1[q]);
         } else if (phase == 1) {   // steady
-            eval_pair<SIGN>(R[q], X[q], HW2, HX2, false, true, true, b0[q], b1[q]);
+            eval_pair<SIGN, FORM>(R[q], X[q], HW2, HX2, false, true, true, b0[q], b1[q]);
         } else {                   // ramp-down step e
             if (2 * q + 1 < e + 1) continue;
-            eval_pair<SIGN>(R[q], X[q], HW2, HX2, false, 2 * q >= e + 1, true, b0[q], b1[q]);
+            eval_pair<SIGN, FORM>(R[q], X[q], HW2, HX2, false, 2 * q >= e + 1, true, b0[q], b1[q]);
         }
     }
 }
+
+#ifndef BLS_SWEEP_MIX
+#define BLS_SWEEP_MIX 1
+#endif
+// Form of block B (block A always uses the signed residue): mixing the two balances the
+// special-function unit against the FP32 pipe.
+constexpr int kFormB = BLS_SWEEP_MIX;
 
 // Fast sweep over two independent blocks of SB starts at a time (starts i0.. and
 // i0 + half..), so that 2*SB/2 packed pairs are in flight per bin step.  Block A covers
@@ -776,33 +807,34 @@ __device__ __forceinline__ float sweep_fast(unsigned hbase, unsigned rowb, int n
         for (int mm = 0; mm < SB - 1; ++mm) {
             float hwa, hxa, hwb, hxb;
             BLS_LOAD2(hwa, hxa, hwb, hxb)
-            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, mm, 0, 0);
-            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, mm, 0, 0);
+            sweep_step<SIGN, NP, 0>(hwa, hxa, RA, XA, a0, a1, mm, 0, 0);
+            sweep_step<SIGN, NP, kFormB>(hwb, hxb, RB, XB, c0, c1, mm, 0, 0);
         }
 #pragma unroll 2
         for (int mm = SB - 1; mm < kmax; ++mm) {
             float hwa, hxa, hwb, hxb;
             BLS_LOAD2(hwa, hxa, hwb, hxb)
-            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, 0, 1, 0);
-            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, 0, 1, 0);
+            sweep_step<SIGN, NP, 0>(hwa, hxa, RA, XA, a0, a1, 0, 1, 0);
+            sweep_step<SIGN, NP, kFormB>(hwb, hxb, RB, XB, c0, c1, 0, 1, 0);
         }
 #pragma unroll
         for (int e = 0; e < SB - 1; ++e) {
             float hwa, hxa, hwb, hxb;
             BLS_LOAD2(hwa, hxa, hwb, hxb)
-            sweep_step<SIGN, NP>(hwa, hxa, RA, XA, a0, a1, 0, 2, e);
-            sweep_step<SIGN, NP>(hwb, hxb, RB, XB, c0, c1, 0, 2, e);
+            sweep_step<SIGN, NP, 0>(hwa, hxa, RA, XA, a0, a1, 0, 2, e);
+            sweep_step<SIGN, NP, kFormB>(hwb, hxb, RB, XB, c0, c1, 0, 2, e);
         }
 #undef BLS_LOAD2
     }
-    // best signed residue -> power P = z^2
-    float best = 0.0f;
+    // best signed residue of block A -> power P = z^2; block B holds powers or residues
+    float za = 0.0f, zb = 0.0f, pb = 0.0f;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-        if (SIGN) best = fmaxf(fmaxf(best, fmaxf(a0[q], a1[q])), fmaxf(c0[q], c1[q]));
-        else best = fminf(fminf(best, fminf(a0[q], a1[q])), fminf(c0[q], c1[q]));
+        za = SIGN ? fmaxf(za, fmaxf(a0[q], a1[q])) : fminf(za, fminf(a0[q], a1[q]));
+        if (kFormB) pb = fmaxf(pb, fmaxf(c0[q], c1[q]));
+        else zb = SIGN ? fmaxf(zb, fmaxf(c0[q], c1[q])) : fminf(zb, fminf(c0[q], c1[q]));
     }
-    return best * best;
+    return fmaxf(fmaxf(za * za, zb * zb), pb);
 }
 
 struct Best {
