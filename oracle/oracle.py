@@ -1,4 +1,5 @@
-"""ctypes binding of ``bls_oracle.c``, the plain FP64 BLS oracle (test infrastructure).
+"""ctypes binding of ``bls_oracle.c`` and ``window_oracle.c``, the plain FP64 oracles (test
+infrastructure).
 
 Every function mirrors one C function; see that file for the definition each one
 follows (Sec. 2.2.2 of the paper and the BLS method it cites).
@@ -16,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bls_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "window_oracle.c")]
 _LIB = os.path.join(_HERE, "libbls_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -27,10 +29,11 @@ def lib_path() -> str:
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc: -O2, no FMA contraction, no fast-math."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(s)
+                                                  for s in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-Wall", "-o", tmp, _SRC, "-lm", "-lpthread"]
+               "-shared", "-Wall", "-o", tmp, *_SRCS, "-lm", "-lpthread"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -84,6 +87,8 @@ def _load():
                                        C.POINTER(D)]
             lib.oracle_bls.argtypes = [C.POINTER(_Curve), I, P, P, P, I, P]
             lib.oracle_bls_many.argtypes = [I, C.POINTER(_Curve), I, I, P, I, P]
+            lib.oracle_window_count.argtypes = [I, P, D, D, D, I]
+            lib.oracle_window.argtypes = [I, P, I, P, D, D, I, D, D, I, I, P, P]
             _lib = lib
     return _lib
 
@@ -221,3 +226,27 @@ def bls_many(curves, nthreads: int = 1, sign: int = 0, topk: int = 1,
     del keep
     out = _peaks(pk)
     return [out[i * topk:(i + 1) * topk] for i in range(len(curves))], P
+
+
+def window(t, nphi: int, *, freqs=None, fmin=0.0, df=0.0, nf: Optional[int] = None,
+           duration: float = 0.0, qfrac: float = 0.0, min_eclipses: int = 2,
+           min_points: int = 1, want_counts: bool = False):
+    """Eclipse-window detection efficiency per frequency (``oracle_window``):
+    (eff[nf], counts[nf, nphi] or None)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    if freqs is not None:
+        freqs = np.ascontiguousarray(freqs, dtype=np.float64)
+        nf = len(freqs)
+    eff = np.empty(nf)
+    counts = np.empty((nf, nphi), dtype=np.int32) if want_counts else None
+    rc = _load().oracle_window(len(t), _p(t), nf, _p(freqs), fmin, df, nphi, duration, qfrac,
+                               min_eclipses, min_points, _p(eff), _p(counts))
+    if rc != 0:
+        raise ValueError("oracle_window: bad arguments")
+    return eff, counts
+
+
+def window_count(t, f: float, phi: float, h: float, min_points: int = 1) -> int:
+    """Observed eclipses of one (frequency, phase) pair (``oracle_window_count``)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    return _load().oracle_window_count(len(t), _p(t), f, phi, h, min_points)
