@@ -210,6 +210,35 @@ typedef struct {
  * Errors: BLS_ERR_INVALID. */
 bls_status bls_profile_get(bls_plan* plan, bls_profile* out, int reset);
 
+/* Eclipse-window detection efficiency (Sec. 5 of the paper, detection-efficiency figure):
+ * for every trial frequency f, the fraction of eclipse phases phi_m = (2m+1)/(2 nphi),
+ * m < nphi, at which at least min_eclipses eclipses contain at least min_points
+ * observations each.  Eclipse n of phase phi is centred at t_0 + (phi + n)/f; a time is
+ * in it when it lies within half an eclipse duration of the centre.  Decisions are taken
+ * in FP64: u = RN(RN(RN(t_i - t_0) f) - phi), c = floor(RN(u + 1/2)), in eclipse iff
+ * |RN(u - c)| <= h with h = RN(RN(duration f) / 2), or RN(qfrac / 2) when duration == 0. */
+typedef struct {
+    const double* t;      /* observation times, sorted ascending (host or device) */
+    int n;                /* >= 1 */
+    const double* freqs;  /* explicit frequencies > 0 (host or device), or NULL: uniform grid */
+    int nf;               /* >= 1 */
+    double fmin, df;      /* uniform grid f_k = RN(fmin + RN(k df)) when freqs is NULL */
+    int nphi;             /* eclipse phases per frequency, >= 1 */
+    double duration;      /* eclipse duration in time units (> 0), or 0: use qfrac */
+    double qfrac;         /* eclipse duration as a fraction of the period, 0 < qfrac < 1 */
+    int min_eclipses;     /* observed eclipses needed for a detection (the paper: 2) */
+    int min_points;       /* observations an eclipse needs to count as observed, >= 1 */
+} bls_window_desc;
+
+/* eff[k] (nf doubles) receives the efficiency at frequency k; counts (optional, nf * nphi
+ * ints, frequency-major) the observed eclipses of every (frequency, phase).  Outputs may
+ * be host or device memory; work is ordered on cuda_stream (NULL: the legacy default
+ * stream) and the call returns when the results are written.  Allocates its scratch with
+ * cudaMallocAsync on that stream.  Errors: BLS_ERR_INVALID (bad descriptor; times not
+ * sorted or not finite, frequencies <= 0: device check), BLS_ERR_NOMEM, BLS_ERR_CUDA. */
+bls_status bls_window_efficiency(const bls_window_desc* desc, void* cuda_stream, double* eff,
+                                 int* counts);
+
 /* Search of one curve that allocates nothing.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc (a plug-in whose host application
  * owns and budgets all device memory, a latency-critical loop that cannot take

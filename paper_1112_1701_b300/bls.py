@@ -65,6 +65,13 @@ class ServerStats(C.Structure):
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
 
 
+class WindowDesc(C.Structure):
+    _fields_ = [("t", C.c_void_p), ("n", C.c_int), ("freqs", C.c_void_p), ("nf", C.c_int),
+                ("fmin", C.c_double), ("df", C.c_double), ("nphi", C.c_int),
+                ("duration", C.c_double), ("qfrac", C.c_double), ("min_eclipses", C.c_int),
+                ("min_points", C.c_int)]
+
+
 class Profile(C.Structure):
     _fields_ = [("searches", C.c_uint64), ("kernel_launches", C.c_uint64),
                 ("fold_launches", C.c_uint64), ("prep_ms", C.c_double),
@@ -83,7 +90,8 @@ _lock = threading.Lock()
 
 EXPORTS = ["bls_plan_create", "bls_plan_destroy", "bls_search", "bls_submit", "bls_poll",
            "bls_cancel", "bls_server_stats_get", "bls_kminmax", "bls_debug_fold",
-           "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_last_error"]
+           "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_window_efficiency",
+           "bls_last_error"]
 
 
 def lib():
@@ -109,6 +117,7 @@ def lib():
             L.bls_debug_powers.argtypes = [P, C.POINTER(CurveStruct), P, P, P]
             L.bls_profile_get.argtypes = [P, C.POINTER(Profile), I]
             L.bls_search_static.argtypes = [C.POINTER(CurveStruct), I, I, P, P, P]
+            L.bls_window_efficiency.argtypes = [C.POINTER(WindowDesc), P, P, P]
             L.bls_last_error.argtypes = []
             L.bls_last_error.restype = C.c_char_p
             _lib = L
@@ -190,6 +199,30 @@ def curves_from_batch(batch, device=None, pinned: bool = False) -> List[CurveInp
                               df=g.df, nb=nb, qmin=batch.qmin, qmax=batch.qmax))
         o += n
     return out
+
+
+def window_efficiency(t, nphi: int, *, freqs=None, fmin: float = 0.0, df: float = 0.0,
+                      nf: Optional[int] = None, duration: float = 0.0, qfrac: float = 0.0,
+                      min_eclipses: int = 2, min_points: int = 1, want_counts: bool = False,
+                      stream=None, eff=None, counts=None):
+    """``bls_window_efficiency``: eclipse-window detection efficiency per frequency.
+
+    ``t`` (sorted) and ``freqs`` are numpy arrays or CUDA tensors.  Returns (eff, counts):
+    numpy arrays, or the given ``eff`` / ``counts`` buffers (numpy or CUDA tensors)."""
+    t = _host(t, np.float64)
+    if freqs is not None:
+        freqs = _host(freqs, np.float64)
+        nf = len(freqs)
+    if nf is None:
+        raise ValueError("give freqs, or fmin/df/nf")
+    if eff is None:
+        eff = np.zeros(nf, np.float64)
+    if counts is None and want_counts:
+        counts = np.zeros((nf, nphi), np.int32)
+    d = WindowDesc(_ptr(t), len(t), _ptr(freqs), nf, fmin, df, nphi, duration, qfrac,
+                   min_eclipses, min_points)
+    _check(lib().bls_window_efficiency(C.byref(d), stream, _ptr(eff), _ptr(counts)))
+    return eff, counts
 
 
 def search_static(curve: CurveInput, topk: int = 1, sign: str = "dips", stream=None,

@@ -238,3 +238,50 @@ def config5(ncurves: int = 100000, seed: int = 5, nf: int = 200000, first: int =
     g = Grid.span(0.1, 5.0, nf)
     return Batch(curves, [g] * ncurves, [256] * ncurves, 0.005, 0.15, "cfg5-survey",
                  dict(topk=5))
+
+
+# ----------------------------------------------------------------------------------
+# Detection-efficiency workloads: survey cadences and injected eclipses.
+# ----------------------------------------------------------------------------------
+
+def survey_cadence(seed: int = 6, nights: int = 60, p_weather: float = 0.3,
+                   cadence_min: float = 20.0, window=(0.10, 0.30), jitter_min: float = 1.0,
+                   field: int = 0) -> np.ndarray:
+    """Exposure times of one survey field: an exposure every cadence_min minutes through
+    each night's window (about 5 h), each shifted by a uniform jitter of +-jitter_min
+    minutes, on the nights the weather leaves (each lost with probability p_weather).
+    Sorted, HJD-like."""
+    rng = curve_rng(seed, field)
+    step = cadence_min / 1440.0
+    per_night = np.arange(window[0], window[1], step)
+    keep = np.flatnonzero(rng.random(nights) >= p_weather)
+    if len(keep) == 0:
+        keep = np.array([0])
+    t = (keep[:, None].astype(np.float64) + per_night[None, :]).ravel()
+    t = t + rng.uniform(-jitter_min, jitter_min, size=t.size) / 1440.0
+    return T0 + np.sort(t)
+
+
+def eclipse_injections(t: np.ndarray, periods: Sequence[float], per_period: int,
+                       duration: float, depth: float, sigma: float, seed: int = 7,
+                       nf: int = 20000, fmin: float = 0.1, fmax: float = 5.0,
+                       nb: int = 200) -> Batch:
+    """Injection set for the recovery harness: for each period, per_period copies of the
+    cadence t with white noise N(0, sigma) and a box eclipse of the given depth and
+    duration at a random epoch (truth in Curve.truth, the epoch in [0, period))."""
+    curves, grids = [], []
+    g = Grid.span(fmin, fmax, nf)
+    c = 0
+    for P in periods:
+        for _ in range(per_period):
+            rng = curve_rng(seed, c)
+            c += 1
+            epoch = rng.uniform(0.0, P)
+            y = 1.0 + rng.normal(0.0, sigma, size=len(t))
+            y = inject_box(t, y, P, epoch, duration, depth)
+            curves.append(Curve(t.copy(), y.astype(np.float32),
+                                np.full(len(t), sigma, dtype=np.float32),
+                                dict(period=P, epoch=T0 + epoch, duration=duration,
+                                     depth=depth)))
+            grids.append(g)
+    return Batch(curves, grids, [nb] * len(curves), 0.005, 0.15, "injection-recovery")
