@@ -51,8 +51,8 @@ NB, QMIN, QMAX = 200, 0.005, 0.15
 # DRAM traffic of one fold-bin-sweep launch on this workload (dram__bytes_read.sum +
 # dram__bytes_write.sum, one ncu capture of the timed launch after an L2 flush), for the
 # kernel source with the given SHA-256; reported as null once the source changes.
-NCU_TRAFFIC = {"kernel_sha256": "93e5fc4ce7ab248473286d409e1ae28a803692d8889998f2e3e16f6dc5cb4517",
-               "bytes_per_launch": 58689792 + 151370752}
+NCU_TRAFFIC = {"kernel_sha256": "a99556a07ee24a97b05d798f6dbfa6eef40488ff25fb36c862d4f787f40f14fd",
+               "bytes_per_launch": 57669120 + 151185408}
 
 
 def kernel_sha():
@@ -133,12 +133,12 @@ def cpu_baseline(batch, seconds_hint=15.0, max_curves=1024):
     cores = os.cpu_count() or 1
     kmin, kmax = oracle.kminmax(NB, batch.qmin, batch.qmax)
 
-    def run(idx):
+    def run(idx, threads=cores):
         cur = [dict(t=batch.curves[i].t, y=batch.curves[i].y, dy=batch.curves[i].dy, nb=NB,
                     kmin=kmin, kmax=kmax, fmin=batch.grids[i].fmin, df=batch.grids[i].df,
                     nf=batch.grids[i].nf) for i in idx]
         t0 = time.perf_counter()
-        oracle.bls_many(cur, nthreads=cores, topk=1)
+        oracle.bls_many(cur, nthreads=threads, topk=1)
         return time.perf_counter() - t0, sum(len(batch.curves[i].t) * batch.grids[i].nf
                                              for i in idx)
 
@@ -149,9 +149,22 @@ def cpu_baseline(batch, seconds_hint=15.0, max_curves=1024):
     per_curve = u0 / n0
     ncur = int(min(max_curves, len(batch), max(n0, seconds_hint * rate / per_curve)))
     dt, u = run(list(range(ncur)))
+    dt1, u1 = run([0], threads=1)   # one thread, one curve
     return {"value": u / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{ncur} of {len(batch)} curves x full {batch.grids[0].nf}-frequency grid, "
-                      f"FP64 C oracle on {cores} host threads, {dt:.1f} s"}
+                      f"FP64 C oracle on {cores} host threads, {dt:.1f} s",
+            "single_thread": {"value": u1 / dt1, "sample": "curve 0, one thread"},
+            "cpu_model": cpu_model()}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
 
 
 def run_reference(args):
@@ -284,6 +297,27 @@ def run_serving(args):
     return 0
 
 
+def plain_f64_sample(batch, ncurves, value):
+    """The plain FP64 one-curve-per-launch GPU kernel (the paper's decomposition without
+    redesign) on the first ncurves curves of a batch, full grid each."""
+    import torch
+    from paper_1112_1701_b300 import bls
+    sub = batch.subset(range(min(ncurves, len(batch))))
+    pdev = bls.curves_from_batch(sub, device="cuda")
+    with bls.Plan(nb=sub.nb[0], qmin=sub.qmin, qmax=sub.qmax, algo="plain_f64",
+                  stream=torch.cuda.current_stream().cuda_stream) as pp:
+        pp.search(pdev[:1])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pp.search(pdev)
+        torch.cuda.synchronize()
+        dtp = time.perf_counter() - t0
+    rate = sub.point_freqs() / dtp
+    return {"value": rate, "unit": UNIT,
+            "sample": f"{len(sub)} curves x full grid, one launch per curve",
+            "speedup_of_value": value / rate}
+
+
 def run_precision(args):
     """Precision study on the three-year workload (3000 points over 1095 days with seasonal
     gaps, up to 5475 cycles at the highest frequency): every phase mode {f64, df32, f32} x
@@ -407,7 +441,8 @@ def run_survey(args):
                        "l2": "flushed (256 MiB write) before every step"},
             "box_evals_per_s": evals / (ms / 1000.0),
             "full_100k_curves_s_extrapolated": ms / 1000.0 * 100000 / len(b),
-            "injected": len(inj), "injected_recovered_top5": rec}
+            "injected": len(inj), "injected_recovered_top5": rec,
+            "plain_f64_gpu": plain_f64_sample(b, 4, units / (ms / 1000.0))}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -662,19 +697,7 @@ def main():
 
     # the plain FP64 one-curve-per-launch GPU kernel on a sample of the same curves
     if args.plain_curves > 0 and rank == 0:
-        sub = batch.subset(range(min(args.plain_curves, len(batch))))
-        pdev = bls.curves_from_batch(sub, device="cuda")
-        with bls.Plan(nb=NB, qmin=QMIN, qmax=QMAX, algo="plain_f64",
-                      stream=stream.cuda_stream) as pp:
-            pp.search(pdev[:1])
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            pp.search(pdev)
-            torch.cuda.synchronize()
-            dtp = time.perf_counter() - t0
-        line["plain_f64_gpu"] = {"value": sub.point_freqs() / dtp, "unit": UNIT,
-                                 "sample": f"{len(sub)} curves x full grid, one launch per curve",
-                                 "speedup_of_value": value / world / (sub.point_freqs() / dtp)}
+        line["plain_f64_gpu"] = plain_f64_sample(batch, args.plain_curves, value / world)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch)
