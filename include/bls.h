@@ -123,6 +123,8 @@ typedef struct {
     double snr;           /* depth / sigma_depth = SR sqrt(W) */
     double sr;            /* signal residue sqrt(P) */
     double power;         /* P = s^2/(r(1-r)) */
+    double sde;           /* signal detection efficiency (SR - mean SR) / sd SR over the
+                             curve's spectrum (Kovacs et al. 2002); 0 if the spectrum is flat */
 } bls_peak;
 
 typedef struct bls_plan bls_plan;
@@ -148,6 +150,19 @@ void bls_plan_destroy(bls_plan* plan);
  * Errors: BLS_ERR_INVALID, BLS_ERR_NOMEM, BLS_ERR_CUDA, BLS_ERR_INTERNAL. */
 bls_status bls_search(bls_plan* plan, const bls_curve* curves, int ncurves,
                       bls_peak* out, float* spectrum);
+
+/* Peak refinement (the search's follow-up step): for every peak q of every curve c in
+ * coarse[c*topk + q] (as bls_search returned them for the same curves; best_j < 0 marks
+ * an empty slot), searches the fine grid f_q + (i - half*oversample) * step,
+ * i = 0 .. 2*half*oversample (each RN(f_q + RN(i' * step)), non-positive frequencies
+ * dropped), step = RN(df / oversample) for a uniform grid, or for an explicit grid the
+ * mean spacing of best_j's neighbours divided by oversample; out[c*topk + q] receives the
+ * best peak of that fine grid (best_j indexes the fine grid, sde is over the fine grid;
+ * empty slots get best_j = -1).  All arrays host memory except the curves' data, which
+ * follow bls_search's rules.  Errors: as bls_search; BLS_ERR_INVALID for oversample < 1,
+ * half < 1, or best_j outside a curve's grid. */
+bls_status bls_refine(bls_plan* plan, const bls_curve* curves, int ncurves,
+                      const bls_peak* coarse, int oversample, int half, bls_peak* out);
 
 /* Serving: queue one curve.  The input is copied before the call returns; the call
  * never waits for the GPU.  Requests are admitted to the device as memory and slots

@@ -37,6 +37,7 @@ typedef struct {
     int j;              /* frequency index, -1 if the slot is empty */
     double freq, period, epoch, duration, depth, snr, sr, power;
     int i1, k;          /* first bin and width (bins) of the best box */
+    double sde;         /* signal detection efficiency of the peak */
 } oracle_peak;
 
 typedef struct {
@@ -300,6 +301,17 @@ int oracle_bls(const oracle_curve* c, int sign, double* P, int* i1, int* k,
         Pl[j] = sweep(p.n, nb, c->kmin, c->kmax, sign, H, H + nb, Hn, &I1[j], &K[j]);
     }
     if (topk > 0 && peaks) {
+        /* signal detection efficiency (Kovacs, Zucker & Mazeh 2002, the BLS paper cited in
+         * Sec. 2.2.2): SDE = (SR_peak - <SR>) / sd(SR) over the curve's whole spectrum,
+         * sd the population standard deviation; 0 for a flat spectrum */
+        double mean = 0.0, var = 0.0;
+        for (int j = 0; j < nf; j++) mean += sqrt(Pl[j]);
+        mean /= (double)nf;
+        for (int j = 0; j < nf; j++) {
+            double d = sqrt(Pl[j]) - mean;
+            var += d * d;
+        }
+        double sd = sqrt(var / (double)nf);
         int js[64];
         int kk = topk > 64 ? 64 : topk;
         top_peaks(nf, Pl, kk, js);
@@ -310,6 +322,7 @@ int oracle_bls(const oracle_curve* c, int sign, double* P, int* i1, int* k,
             histogram(p.n, p.dt, p.w, p.x, f, nb, H, H + nb, Hn);
             box_sums(nb, H, H + nb, I1[j], K[j], &r, &s);
             derive(&peaks[q], j, f, nb, I1[j], K[j], Pl[j], r, s, p.scal[0], p.scal[1]);
+            peaks[q].sde = sd > 0.0 ? (peaks[q].sr - mean) / sd : 0.0;
         }
     }
     if (!P) free(Pl);

@@ -43,7 +43,7 @@ class _Peak(C.Structure):
     _fields_ = [("j", C.c_int), ("freq", C.c_double), ("period", C.c_double),
                 ("epoch", C.c_double), ("duration", C.c_double), ("depth", C.c_double),
                 ("snr", C.c_double), ("sr", C.c_double), ("power", C.c_double),
-                ("i1", C.c_int), ("k", C.c_int)]
+                ("i1", C.c_int), ("k", C.c_int), ("sde", C.c_double)]
 
 
 class _Curve(C.Structure):
@@ -65,6 +65,7 @@ class OraclePeak:
     power: float
     i1: int
     k: int
+    sde: float
 
 
 def _load():
@@ -176,7 +177,7 @@ def _curve_struct(t, y, dy, nb, kmin, kmax, freqs=None, fmin=0.0, df=0.0, nf=Non
 
 def _peaks(arr) -> List[OraclePeak]:
     return [OraclePeak(p.j, p.freq, p.period, p.epoch, p.duration, p.depth, p.snr, p.sr,
-                       p.power, p.i1, p.k) for p in arr]
+                       p.power, p.i1, p.k, p.sde) for p in arr]
 
 
 def bls(t, y, dy, nb: int, kmin: int, kmax: int, *, freqs=None, fmin=0.0, df=0.0,

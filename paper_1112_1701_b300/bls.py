@@ -54,7 +54,7 @@ class PeakStruct(C.Structure):
     _fields_ = [("best_j", C.c_int), ("i1", C.c_int), ("k", C.c_int), ("pad_", C.c_int),
                 ("freq", C.c_double), ("period", C.c_double), ("epoch", C.c_double),
                 ("duration", C.c_double), ("depth", C.c_double), ("snr", C.c_double),
-                ("sr", C.c_double), ("power", C.c_double)]
+                ("sr", C.c_double), ("power", C.c_double), ("sde", C.c_double)]
 
 
 class ServerStats(C.Structure):
@@ -82,7 +82,7 @@ class Profile(C.Structure):
 PEAK_DTYPE = np.dtype([("j", np.int32), ("i1", np.int32), ("k", np.int32), ("pad_", np.int32),
                        ("freq", np.float64), ("period", np.float64), ("epoch", np.float64),
                        ("duration", np.float64), ("depth", np.float64), ("snr", np.float64),
-                       ("sr", np.float64), ("power", np.float64)])
+                       ("sr", np.float64), ("power", np.float64), ("sde", np.float64)])
 assert PEAK_DTYPE.itemsize == C.sizeof(PeakStruct)
 
 _lib = None
@@ -90,7 +90,7 @@ _lock = threading.Lock()
 
 EXPORTS = ["bls_plan_create", "bls_plan_destroy", "bls_search", "bls_submit", "bls_poll",
            "bls_cancel", "bls_server_stats_get", "bls_kminmax", "bls_debug_fold",
-           "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_window_efficiency",
+           "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_window_efficiency", "bls_refine",
            "bls_last_error"]
 
 
@@ -118,6 +118,7 @@ def lib():
             L.bls_profile_get.argtypes = [P, C.POINTER(Profile), I]
             L.bls_search_static.argtypes = [C.POINTER(CurveStruct), I, I, P, P, P]
             L.bls_window_efficiency.argtypes = [C.POINTER(WindowDesc), P, P, P]
+            L.bls_refine.argtypes = [P, C.POINTER(CurveStruct), I, P, I, I, P]
             L.bls_last_error.argtypes = []
             L.bls_last_error.restype = C.c_char_p
             _lib = L
@@ -282,6 +283,18 @@ class Plan:
         arr = (CurveStruct * len(curves))(*[_struct(c, keep) for c in curves])
         out = np.zeros((len(curves), self.topk), dtype=PEAK_DTYPE)
         _check(lib().bls_search(self._h, arr, len(curves), out.ctypes.data, _ptr(spectrum)))
+        return out
+
+    def refine(self, curves: Sequence[CurveInput], peaks: np.ndarray, oversample: int = 10,
+               half: int = 2) -> np.ndarray:
+        """``bls_refine``: fine-grid re-search around each peak of ``peaks`` (as returned by
+        ``search`` for the same curves)."""
+        keep: list = []
+        arr = (CurveStruct * len(curves))(*[_struct(c, keep) for c in curves])
+        coarse = np.ascontiguousarray(peaks, dtype=PEAK_DTYPE).reshape(len(curves), self.topk)
+        out = np.zeros((len(curves), self.topk), dtype=PEAK_DTYPE)
+        _check(lib().bls_refine(self._h, arr, len(curves), coarse.ctypes.data, oversample, half,
+                                out.ctypes.data))
         return out
 
     def submit(self, curve: CurveInput) -> int:

@@ -51,7 +51,8 @@ def _compile(src):
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                "-I", INCLUDE, "-c", path, "-o", obj]
     else:
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function",
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall",
+               "-Wno-unused-function",
                "-I", INCLUDE, "-I", os.path.join(CUDA_HOME, "include"), "-c", path, "-o", obj]
     subprocess.run(cmd, check=True)
     return obj

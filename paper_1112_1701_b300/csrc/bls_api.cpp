@@ -196,6 +196,23 @@ void order_by_cost(const std::vector<CurveSpec>& cs, const std::vector<int>& idx
     });
 }
 
+void to_peak(const DevPeak& s, bls_peak* d)
+{
+    d->best_j = s.j;
+    d->i1 = s.i1;
+    d->k = s.k;
+    d->pad_ = 0;
+    d->freq = s.freq;
+    d->period = s.period;
+    d->epoch = s.epoch;
+    d->duration = s.duration;
+    d->depth = s.depth;
+    d->snr = s.snr;
+    d->sr = s.sr;
+    d->power = s.power;
+    d->sde = s.sde;
+}
+
 }  // namespace blsgpu
 
 // ------------------------------------------------------------------------------ search
@@ -234,21 +251,6 @@ size_t curve_bytes(const bls_plan_impl* P, const CurveSpec& c, bool host_spec)
     return b;
 }
 
-void to_peak(const DevPeak& s, bls_peak* d)
-{
-    d->best_j = s.j;
-    d->i1 = s.i1;
-    d->k = s.k;
-    d->pad_ = 0;
-    d->freq = s.freq;
-    d->period = s.period;
-    d->epoch = s.epoch;
-    d->duration = s.duration;
-    d->depth = s.depth;
-    d->snr = s.snr;
-    d->sr = s.sr;
-    d->power = s.power;
-}
 
 // One launch group: curves [g0, g1) of `specs`.  Writes peaks to out (host), optionally the
 // SR spectra, and (diagnostics) the per-frequency powers into res_dump.
@@ -743,6 +745,65 @@ bls_status bls_search(bls_plan* P, const bls_curve* curves, int ncurves, bls_pea
     if (!P) return set_error(BLS_ERR_INVALID, "NULL plan");
     std::lock_guard<std::mutex> lk(P->mu);
     return search_impl(P, curves, ncurves, out, spectrum, nullptr);
+}
+
+// Fine-grid re-search around every peak: the frequencies of peak q of curve c are
+// f_q + (i - half*oversample) * step, i = 0 .. 2*half*oversample (FP64, one rounded product
+// and one rounded sum each, non-positive ones dropped), step = the curve's grid spacing
+// divided by oversample (explicit grids: half the distance between best_j's neighbours).
+bls_status bls_refine(bls_plan* P, const bls_curve* curves, int ncurves, const bls_peak* coarse,
+                      int oversample, int half, bls_peak* out)
+{
+    if (!P || !curves || !coarse || !out) return set_error(BLS_ERR_INVALID, "NULL argument");
+    if (ncurves < 0) return set_error(BLS_ERR_INVALID, "ncurves = %d", ncurves);
+    if (oversample < 1 || half < 1 || (long long)2 * half * oversample + 1 > (1 << 24))
+        return set_error(BLS_ERR_INVALID, "oversample = %d, half = %d", oversample, half);
+    std::lock_guard<std::mutex> lk(P->mu);
+    const int K = P->d.topk;
+    const int nfine = 2 * half * oversample + 1;
+    std::vector<bls_curve> fc;
+    std::vector<int> slot;                 // output slot of every fine search
+    std::vector<std::vector<double>> grids;
+    for (int c = 0; c < ncurves; ++c) {
+        const bls_curve& cv = curves[c];
+        for (int q = 0; q < K; ++q) {
+            const bls_peak& pk = coarse[(size_t)c * K + q];
+            bls_peak& o = out[(size_t)c * K + q];
+            memset(&o, 0, sizeof(o));
+            o.best_j = -1;
+            if (pk.best_j < 0) continue;
+            if (pk.best_j >= cv.nf || cv.nf < 1)
+                return set_error(BLS_ERR_INVALID, "curve %d peak %d: best_j = %d outside the grid", c, q, pk.best_j);
+            double step;
+            if (!cv.freqs) {
+                step = cv.df / (double)oversample;
+            } else {
+                const int a = pk.best_j > 0 ? pk.best_j - 1 : pk.best_j;
+                const int b = pk.best_j + 1 < cv.nf ? pk.best_j + 1 : pk.best_j;
+                const double span = b > a ? (cv.freqs[b] - cv.freqs[a]) / (double)(b - a) : 0.0;
+                step = span / (double)oversample;
+            }
+            std::vector<double> g;
+            g.reserve(nfine);
+            for (int i = 0; i < nfine; ++i) {
+                const double f = pk.freq + (double)(i - half * oversample) * step;
+                if (f > 0.0) g.push_back(f);
+            }
+            if (g.empty() || !(step > 0.0)) g.assign(1, pk.freq);
+            grids.push_back(std::move(g));
+            bls_curve f2 = cv;
+            f2.nf = (int)grids.back().size();
+            slot.push_back(c * K + q);
+            fc.push_back(f2);
+        }
+    }
+    for (size_t i = 0; i < fc.size(); ++i) fc[i].freqs = grids[i].data();
+    if (fc.empty()) return BLS_OK;
+    std::vector<bls_peak> tmp(fc.size() * (size_t)K);
+    bls_status s = search_impl(P, fc.data(), (int)fc.size(), tmp.data(), nullptr, nullptr);
+    if (s != BLS_OK) return s;
+    for (size_t i = 0; i < fc.size(); ++i) out[slot[i]] = tmp[i * (size_t)K];
+    return BLS_OK;
 }
 
 bls_status bls_debug_powers(bls_plan* P, const bls_curve* curve, float* power_out, int* i1_out, int* k_out)

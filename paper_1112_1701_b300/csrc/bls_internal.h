@@ -45,7 +45,7 @@ struct TileRange {
 
 struct DevPeak {
     int j, i1, k, pad;
-    double freq, period, epoch, duration, depth, snr, sr, power;
+    double freq, period, epoch, duration, depth, snr, sr, power, sde;
 };
 
 // Error bits written by device code into the plan's error word.

@@ -1280,9 +1280,12 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
     const int nf = cd.nf;
     Cand lst[kMaxTopK];
     int cnt = 0;
+    double srsum = 0.0;
     for (int j = threadIdx.x; j < nf; j += blockDim.x) {
         const float P = res[j];
-        if (p.spectrum) p.spectrum[cd.spec_off + j] = sqrtf(P);
+        const float sr = sqrtf(P);
+        if (p.spectrum) p.spectrum[cd.spec_off + j] = sr;
+        srsum = __dadd_rn(srsum, (double)sr);
         const bool lm = (j == 0 || P > res[j - 1]) && (j == nf - 1 || P >= res[j + 1]);
         if (!lm) continue;
         int pos = cnt < K ? cnt : K;
@@ -1296,6 +1299,15 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
         lst[pos].j = j;
         if (cnt < K) ++cnt;
     }
+    // signal detection efficiency: mean and population standard deviation of SR over the
+    // spectrum (two passes, FP64 sums in a fixed tree)
+    const double srmean = __ddiv_rn(block_sum(srsum, red), (double)nf);
+    double srvar = 0.0;
+    for (int j = threadIdx.x; j < nf; j += blockDim.x) {
+        const double d = __dsub_rn((double)sqrtf(res[j]), srmean);
+        srvar = __dadd_rn(srvar, __dmul_rn(d, d));
+    }
+    const double srsd = sqrt(__ddiv_rn(block_sum(srvar, red), (double)nf));
     int head = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = 0; q < K; ++q) {
@@ -1390,6 +1402,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
             } else {
                 pk.power = 0.0; pk.depth = 0.0; pk.sr = 0.0; pk.snr = 0.0;
             }
+            pk.sde = srsd > 0.0 ? (pk.sr - srmean) / srsd : 0.0;
             *out = pk;
         }
         __syncthreads();

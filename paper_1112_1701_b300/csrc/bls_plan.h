@@ -98,6 +98,7 @@ struct bls_plan_impl {
 bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* out,
                          const int* kinds = nullptr);
 int ptr_kind(const void* p);
+void to_peak(const DevPeak& s, bls_peak* d);   // device record -> ABI record
 // Block size / stride / chunk / shared memory for a curve with nb bins.
 bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g);
 // Work-list order: curves by decreasing cost (n * nf), ties by index.

@@ -334,13 +334,7 @@ bool Server::step()
             ++failed;
         } else {
             r->peaks.resize(topk);
-            for (int e2 = 0; e2 < topk; ++e2) {
-                const DevPeak& s = pk[q * topk + e2];
-                bls_peak& d = r->peaks[e2];
-                d.best_j = s.j; d.i1 = s.i1; d.k = s.k; d.pad_ = 0;
-                d.freq = s.freq; d.period = s.period; d.epoch = s.epoch; d.duration = s.duration;
-                d.depth = s.depth; d.snr = s.snr; d.sr = s.sr; d.power = s.power;
-            }
+            for (int e2 = 0; e2 < topk; ++e2) to_peak(pk[q * topk + e2], &r->peaks[e2]);
             r->state = RState::Done;
             r->status = BLS_OK;
             ++completed;

@@ -10,8 +10,10 @@ frequency ranges.  Each rank searches an explicit sub-grid whose frequencies are
 grid's, evaluated by the same formula f_j = fmin + j*df (one rounded product, one rounded
 sum), so every rank sees bit-identical trial frequencies; the best peak is then one
 argmax over ranks under the search's ordering key: power descending, then frequency
-index, box start and box width ascending.  Only the best peak (top-1) is merged this way:
-a local maximum of SR(f) at a shard boundary would need its neighbour on the other rank.
+index, box start and box width ascending, and its signal detection efficiency is
+recomputed from the merged moments of the ranks' spectra.  Only the best peak (top-1) is
+merged this way: a local maximum of SR(f) at a shard boundary would need its neighbour
+on the other rank.
 
 The collectives are torch.distributed object gathers, so any backend works (gloo on CPU
 hosts, NCCL between GPUs); a group of one rank needs no process group at all.
@@ -106,24 +108,57 @@ def merge_best(peaks: Sequence[np.void]) -> np.ndarray:
     return np.array([best], dtype=PEAK_DTYPE)
 
 
+def spectrum_moments(sr: np.ndarray) -> Tuple[int, float, float]:
+    """(count, mean, sum of squared deviations) of an SR spectrum, two-pass in FP64."""
+    sr = np.asarray(sr, np.float64)
+    if sr.size == 0:
+        return 0, 0.0, 0.0
+    m = float(sr.mean())
+    return int(sr.size), m, float(((sr - m) ** 2).sum())
+
+
+def merge_moments(parts) -> Tuple[int, float, float]:
+    """Combines (count, mean, M2) of disjoint parts (pairwise update of Chan, Golub and
+    LeVeque)."""
+    n, m, m2 = 0, 0.0, 0.0
+    for nb, mb, m2b in parts:
+        if nb == 0:
+            continue
+        d = mb - m
+        tot = n + nb
+        m = m + d * nb / tot
+        m2 = m2 + m2b + d * d * n * nb / tot
+        n = tot
+    return n, m, m2
+
+
 def search_freq_shards(nf: int, fmin: float, df: float,
-                       search: Callable[[np.ndarray, int], np.void],
+                       search: Callable[[np.ndarray, int], Tuple[np.void, np.ndarray]],
                        group=None) -> Optional[np.ndarray]:
     """Runs `search(freqs, lo)` on this rank's slice of a uniform grid of nf frequencies;
-    it returns the best PEAK_DTYPE record over that slice with `j` local to it.  Rank 0
-    returns the best record over the whole grid (j global); the other ranks None.  A rank
-    whose slice is empty contributes nothing."""
+    it returns the best PEAK_DTYPE record over that slice (`j` local to it) and the slice's
+    SR spectrum.  Rank 0 returns the best record over the whole grid with j global and its
+    signal detection efficiency recomputed over the whole spectrum (the slices' moments
+    merged); the other ranks return None.  A rank whose slice is empty contributes
+    nothing."""
     world, rank = _world(group)
     lo, hi = freq_range(nf, world, rank)
     rec = None
+    mom = (0, 0.0, 0.0)
     if hi > lo:
-        arr = np.array(search(sub_grid(fmin, df, lo, hi), lo), dtype=PEAK_DTYPE).reshape(1)
+        r, sr = search(sub_grid(fmin, df, lo, hi), lo)
+        arr = np.array(r, dtype=PEAK_DTYPE).reshape(1)
         arr["j"] += lo
         rec = arr[0]
-    parts = _gather(rec, group)
+        mom = spectrum_moments(sr)
+    parts = _gather((rec, mom), group)
     if rank != 0:
         return None
-    return merge_best([p for p in parts if p is not None])
+    best = merge_best([p[0] for p in parts if p[0] is not None])
+    n, m, m2 = merge_moments([p[1] for p in parts])
+    sd = (m2 / n) ** 0.5 if n > 0 else 0.0
+    best["sde"] = (best["sr"] - m) / sd if sd > 0.0 else 0.0
+    return best
 
 
 def world_info(group=None) -> Tuple[int, int]:
@@ -132,4 +167,5 @@ def world_info(group=None) -> Tuple[int, int]:
 
 
 __all__: List[str] = ["curve_range", "freq_range", "sub_grid", "search_curve_shards",
-                      "search_freq_shards", "merge_best", "better", "world_info"]
+                      "search_freq_shards", "merge_best", "better", "world_info",
+                      "spectrum_moments", "merge_moments"]

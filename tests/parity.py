@@ -85,6 +85,21 @@ def separated_best(P, sumwx2):
     return j, sep
 
 
+def check_sde(pg, po, P_oracle, sumwx2):
+    """SDE = (SR_peak - mean SR) / sd SR: the GPU's spectrum may differ from the oracle's
+    by T = max_j tol(SR_j) at every frequency, which moves the mean and the standard
+    deviation by at most T each; the peak SR itself is an FP64 refit (equal to 1e-9).
+    So |dSDE| <= (T + |SDE| T) / sd, doubled for the second-order terms."""
+    sr = np.sqrt(np.asarray(P_oracle, np.float64))
+    T = float(np.max(sr_tol(sr, sumwx2)))
+    sd = float(sr.std())
+    if sd == 0.0:
+        assert pg["sde"] == 0.0
+        return
+    bound = 2.0 * (1.0 + abs(po.sde)) * T / sd + 1e-9 * abs(po.sde)
+    assert abs(pg["sde"] - po.sde) <= bound, (pg["sde"], po.sde, bound)
+
+
 def check_peak(pg, po, rel=1e-9):
     """A GPU peak record against the oracle's for the same (j, i1, k)."""
     assert pg["j"] == po.j and pg["i1"] == po.i1 and pg["k"] == po.k, (pg, po)

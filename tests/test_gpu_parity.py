@@ -8,7 +8,8 @@ import pytest
 
 import oracle
 from paper_1112_1701_b300 import bls, build, synth
-from tests.parity import check_peak, check_powers, oracle_run, prep_of, separated_best, sr_tol
+from tests.parity import (check_peak, check_powers, check_sde, oracle_run, prep_of,
+                          separated_best, sr_tol)
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +45,8 @@ def test_plain_workload_spectrum_and_peak():
     jo, sep = separated_best(Po, scal[3])
     assert sep and pk["j"] == jo
     check_peak(pk, opk[0])
+    check_sde(pk, opk[0], Po, scal[3])
+    assert pk["sde"] > 5.0   # the injected box stands far above the noise peaks
     # the injected 0.40 d box is recovered
     assert abs(pk["period"] - 0.40) < 0.40 ** 2 * g.df
 
@@ -157,6 +160,7 @@ def test_batch_matches_oracle_per_curve():
             _, _, _, opk = oracle_run(ci, nb, kmin, kmax)
             if sep:
                 check_peak(pk[q, 0], opk[0])
+                check_sde(pk[q, 0], opk[0], Po, scal[3])
 
 
 def test_batch_result_equals_alone_bit_for_bit():
@@ -181,7 +185,7 @@ def test_topk_peaks_match_oracle():
         pk = p.search(cis)
         for q, ci in enumerate(cis):
             Pg, I1g, Kg = p.debug_powers(ci)
-            Po, *_ = check_powers(ci, Pg, I1g, Kg, nb, kmin, kmax, label=f"top{q}")
+            Po, _, _, scal = check_powers(ci, Pg, I1g, Kg, nb, kmin, kmax, label=f"top{q}")
             _, _, _, opk = oracle_run(ci, nb, kmin, kmax, topk=5)
             sro = np.sqrt(np.array([o.power for o in opk]))
             for e in range(5):
@@ -190,6 +194,7 @@ def test_topk_peaks_match_oracle():
                 sep_next = e == 4 or sro[e] - sro[e + 1] > 2e-5 * sro[e]
                 if sep_prev and sep_next:
                     check_peak(pk[q, e], opk[e])
+                    check_sde(pk[q, e], opk[e], Po, scal[3])
 
 
 # ------------------------------------------------------------------------------ edge cases

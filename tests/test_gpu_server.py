@@ -49,7 +49,8 @@ def test_served_results_equal_results_alone():
         assert stats["steps"] > 1
         for ci, pk in zip(reqs, served):
             alone = p.search([ci])[0]
-            assert np.array_equal(alone, pk)
+            diff = [f for f in bls.PEAK_DTYPE.names if not np.array_equal(alone[f], pk[f])]
+            assert not diff, (diff, alone[diff], pk[diff])
 
 
 def test_admission_respects_memory_budget():

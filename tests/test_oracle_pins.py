@@ -368,3 +368,46 @@ def test_many_matches_single_and_threads():
                                  nf=g.nf, topk=2)
         assert np.array_equal(P, P1[q * 700:(q + 1) * 700])
         assert [p.j for p in pk] == [p.j for p in pk1[q]]
+
+
+# ------------------------------------------------------------------------------ SDE
+
+def _sde_case(scale=1.0, offset=0.0, err_scale=1.0):
+    b = synth.config1()
+    c, g = b.curves[0], b.grids[0]
+    y = (1.0 + offset + scale * (c.y.astype(np.float64) - 1.0)).astype(np.float32)
+    dy = (c.dy * err_scale).astype(np.float32)
+    kmin, kmax = oracle.kminmax(100, b.qmin, b.qmax)
+    P, _, _, pk = oracle.bls(c.t, y, dy, 100, kmin, kmax, fmin=g.fmin, df=g.df, nf=g.nf, topk=3)
+    return P, pk
+
+
+def test_sde_is_the_spectrum_statistic():
+    """SDE = (SR_peak - mean SR) / population sd of SR over the whole spectrum."""
+    P, pk = _sde_case()
+    sr = np.sqrt(P)
+    for p in pk:
+        assert p.sde == pytest.approx((p.sr - sr.mean()) / sr.std(), rel=1e-12)
+    assert pk[0].sde > pk[1].sde > pk[2].sde
+
+
+def test_sde_invariances():
+    """SDE does not change when the flux deviations and errors scale together (SR scales,
+    the spectrum's mean and spread scale with it), when the flux is offset, or when the
+    errors alone scale (normalised weights).  A factor 2 on the deviations and on the
+    errors is exact in FP32, so those spectra agree to FP64 rounding; the offset flux is
+    re-rounded to FP32 (about 1e-7 of a 1% noise level), hence the looser bound there."""
+    _, base = _sde_case()
+    for kw, rel in ((dict(scale=2.0, err_scale=2.0), 1e-9), (dict(err_scale=3.0), 1e-9),
+                    (dict(offset=0.5), 1e-5)):
+        _, pk = _sde_case(**kw)
+        for a, b in zip(pk, base):
+            assert a.j == b.j
+            assert a.sde == pytest.approx(b.sde, rel=rel), kw
+
+
+def test_sde_flat_spectrum_is_zero():
+    t = synth.T0 + np.linspace(0, 10, 50)
+    y = np.ones(50, np.float32)
+    _, _, _, pk = oracle.bls(t, y, None, 20, 1, 4, fmin=0.3, df=0.1, nf=30)
+    assert pk[0].sde == 0.0

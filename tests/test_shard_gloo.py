@@ -25,7 +25,7 @@ def _records(peaks):
     """OraclePeak list -> PEAK_DTYPE array."""
     out = np.zeros(len(peaks), dtype=bls.PEAK_DTYPE)
     for q, p in enumerate(peaks):
-        for f in ("freq", "period", "epoch", "duration", "depth", "snr", "sr", "power"):
+        for f in ("freq", "period", "epoch", "duration", "depth", "snr", "sr", "power", "sde"):
             out[q][f] = getattr(p, f)
         out[q]["j"], out[q]["i1"], out[q]["k"] = p.j, p.i1, p.k
     return out
@@ -49,8 +49,8 @@ def _curve_search(b, kmin, kmax, topk):
 
 def _freq_search(c, kmin, kmax):
     def search(freqs, lo):
-        _, _, _, pk = oracle.bls(c.t, c.y, c.dy, NB, kmin, kmax, freqs=freqs)
-        return _records(pk)[0]
+        P, _, _, pk = oracle.bls(c.t, c.y, c.dy, NB, kmin, kmax, freqs=freqs)
+        return _records(pk)[0], np.sqrt(P)
     return search
 
 
@@ -98,7 +98,11 @@ def test_curve_and_frequency_shards_match_single_process():
     assert np.array_equal(allp, ref)
     c, g = b.curves[3], b.grids[3]
     _, _, _, pk = oracle.bls(c.t, c.y, c.dy, NB, kmin, kmax, fmin=g.fmin, df=g.df, nf=g.nf)
-    assert np.array_equal(best, _records(pk[:1]))
+    ref1 = _records(pk[:1])
+    others = [f for f in bls.PEAK_DTYPE.names if f != "sde"]
+    assert all(np.array_equal(best[f], ref1[f]) for f in others)
+    # SDE from merged per-rank moments vs one two-pass sum over the whole spectrum
+    assert abs(best["sde"][0] - ref1["sde"][0]) <= 1e-10 * abs(ref1["sde"][0])
 
 
 def test_ranges_cover_exactly_once():
@@ -119,6 +123,16 @@ def test_sub_grid_is_bit_identical_to_the_uniform_grid():
     full = np.array([oracle.freq(j, fmin, df) for j in range(0, 50000, 7)])
     sub = np.concatenate([shard.sub_grid(fmin, df, lo, lo + 1) for lo in range(0, 50000, 7)])
     assert np.array_equal(full, sub)
+
+
+def test_moments_merge_equals_whole():
+    rng = np.random.default_rng(5)
+    x = rng.gamma(2.0, 1.0, 1001)
+    whole = shard.spectrum_moments(x)
+    parts = [shard.spectrum_moments(x[a:b]) for a, b in ((0, 300), (300, 300), (300, 1001))]
+    n, m, m2 = shard.merge_moments(parts)
+    assert n == whole[0] and abs(m - whole[1]) < 1e-12 * whole[1]
+    assert abs(m2 - whole[2]) < 1e-10 * whole[2]
 
 
 def test_merge_order_key():

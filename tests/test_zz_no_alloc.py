@@ -49,7 +49,7 @@ def test_static_search_matches_search_on_two_calls_in_a_row():
         assert np.all(np.abs(got_spec.astype(np.float64) - ref_spec) <= tol)
         for e in range(topk):
             assert (got[e]["j"], got[e]["i1"], got[e]["k"]) == (ref[e]["j"], ref[e]["i1"], ref[e]["k"])
-            for f in ("freq", "period", "epoch", "duration", "depth", "snr", "sr", "power"):
+            for f in ("freq", "period", "epoch", "duration", "depth", "snr", "sr", "power", "sde"):
                 assert got[e][f] == pytest.approx(ref[e][f], rel=1e-9, abs=1e-12), f
 
 
