@@ -1,5 +1,5 @@
-"""ctypes binding of ``bls_oracle.c`` and ``window_oracle.c``, the plain FP64 oracles (test
-infrastructure).
+"""ctypes binding of ``bls_oracle.c``, ``window_oracle.c`` and ``shape_oracle.c``, the plain
+FP64 oracles (test infrastructure).
 
 Every function mirrors one C function; see that file for the definition each one
 follows (Sec. 2.2.2 of the paper and the BLS method it cites).
@@ -17,7 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bls_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "window_oracle.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "window_oracle.c"), os.path.join(_HERE, "shape_oracle.c")]
 _LIB = os.path.join(_HERE, "libbls_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -44,6 +44,11 @@ class _Peak(C.Structure):
                 ("epoch", C.c_double), ("duration", C.c_double), ("depth", C.c_double),
                 ("snr", C.c_double), ("sr", C.c_double), ("power", C.c_double),
                 ("i1", C.c_int), ("k", C.c_int), ("sde", C.c_double)]
+
+
+class _Shape(C.Structure):
+    _fields_ = [("index", C.c_int), ("power", C.c_double), ("centre", C.c_double),
+                ("width", C.c_double), ("ingress", C.c_double), ("depth", C.c_double)]
 
 
 class _Curve(C.Structure):
@@ -90,6 +95,10 @@ def _load():
             lib.oracle_bls_many.argtypes = [I, C.POINTER(_Curve), I, I, P, I, P]
             lib.oracle_window_count.argtypes = [I, P, D, D, D, I]
             lib.oracle_window.argtypes = [I, P, I, P, D, D, I, D, D, I, I, P, P]
+            lib.oracle_shape_point.argtypes = [I, P, P, P, D, D, D, C.POINTER(D), C.POINTER(I)]
+            lib.oracle_shape_point.restype = D
+            lib.oracle_shape.argtypes = [I, P, P, P, D, I, I, I, I, I, I, D, D, D,
+                                         C.POINTER(_Shape), P]
             _lib = lib
     return _lib
 
@@ -251,3 +260,37 @@ def window_count(t, f: float, phi: float, h: float, min_points: int = 1) -> int:
     """Observed eclipses of one (frequency, phase) pair (``oracle_window_count``)."""
     t = np.ascontiguousarray(t, dtype=np.float64)
     return _load().oracle_window_count(len(t), _p(t), f, phi, h, min_points)
+
+
+@dataclass
+class OracleShape:
+    index: int
+    power: float
+    centre: float
+    width: float
+    ingress: float
+    depth: float
+
+
+def shape(dt, w, x, f: float, nb: int, i1: int, k: int, nc: int = 17, nw: int = 13,
+          na: int = 6, wlo: float = 0.5, whi: float = 2.0, amax: float = 0.5,
+          want_grid: bool = False):
+    """Trapezoid refit of one peak (``oracle_shape``): (OracleShape, Q[grid] or None)."""
+    dt, w, x = (np.ascontiguousarray(a, dtype=np.float64) for a in (dt, w, x))
+    out = _Shape()
+    Q = np.zeros(nc * nw * na) if want_grid else None
+    rc = _load().oracle_shape(len(dt), _p(dt), _p(w), _p(x), f, nb, i1, k, nc, nw, na, wlo, whi,
+                              amax, C.byref(out), _p(Q))
+    if rc != 0:
+        raise ValueError(f"oracle_shape failed ({rc})")
+    return OracleShape(out.index, out.power, out.centre, out.width, out.ingress, out.depth), Q
+
+
+def shape_point(phi, w, x, c: float, T: float, tau: float):
+    """Q and depth of one trapezoid on folded phases (``oracle_shape_point``)."""
+    phi, w, x = (np.ascontiguousarray(a, dtype=np.float64) for a in (phi, w, x))
+    d = C.c_double()
+    ok = C.c_int()
+    Q = _load().oracle_shape_point(len(phi), _p(phi), _p(w), _p(x), c, T, tau, C.byref(d),
+                                   C.byref(ok))
+    return Q, d.value, bool(ok.value)
