@@ -545,6 +545,7 @@ def main():
     ap.add_argument("--ref-curves", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-shapes", action="store_true")
     ap.add_argument("--plain-curves", type=int, default=8,
                     help="curves of the plain FP64 baseline timing (0 = skip)")
     ap.add_argument("--serving", action="store_true", help="run the serving benchmark")
@@ -688,6 +689,27 @@ def main():
                           "reduce": prof["reduce_ms"] / args.steps}}
     if e2e:
         line["e2e"] = e2e
+
+    # trapezoid refit of the peaks: the extra time of a search that also refits them
+    if rank == 0 and not args.no_shapes:
+        def timed(fn):
+            best = None
+            for _ in range(3):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+            return best
+        t_plain = timed(lambda: plan.search(dev))
+        t_shape = timed(lambda: plan.search_shapes(dev))
+        line["shape_refit"] = {"extra_ms_per_step": t_shape - t_plain,
+                               "grid": "17 centres x 13 widths x 6 ingress fractions",
+                               "peaks": len(batch)}
 
     # the per-curve records of all ranks, gathered on rank 0 (outside the timed region)
     last = plan.search(dev)

@@ -164,6 +164,41 @@ bls_status bls_search(bls_plan* plan, const bls_curve* curves, int ncurves,
 bls_status bls_refine(bls_plan* plan, const bls_curve* curves, int ncurves,
                       const bls_peak* coarse, int oversample, int half, bls_peak* out);
 
+/* Trapezoid refit of the peaks (Sec. 5 of the paper names the eclipse duration and the
+ * flat-bottomed shape as discriminators).  At a peak's frequency f the curve is folded
+ * and a trapezoid -- centre c, total duration T, ingress tau, phase units -- is fitted to
+ * the weighted, mean-subtracted flux x by least squares: with s the trapezoid's shape
+ * (1 in the flat bottom, linear edges; tau = 0 is a box), Ss = sum w s, Sss = sum w s^2,
+ * Sxs = sum w x s, the power is Q = Sxs^2 / (Sss - Ss^2) (a box gives the BLS power) and
+ * the depth -Sxs / (Sss - Ss^2); only dips (Sxs < 0) count.  The grid is built around the
+ * peak's box (centre phi_b = frac((i1 + k/2)/nb), width q = k/nb):
+ *   c_m = phi_b + q (m/(ncentre-1) - 1/2), T_u = q (width_lo + u (width_hi - width_lo)/
+ *   (nwidth-1)), tau_v = T_u ingress_max v/(ningress-1), flat index (m nwidth + u)
+ *   ningress + v (a size of 1 takes the middle centre, the low width, no ingress). */
+typedef struct {
+    int ncentre, nwidth, ningress;   /* grid sizes >= 1; 0 = defaults 17, 13, 6 */
+    double width_lo, width_hi;       /* widths in box widths, 0 < lo <= hi; 0 = 0.5, 2.0 */
+    double ingress_max;              /* largest ingress / width, in [0, 0.5]; < 0 = 0.5 */
+} bls_shape_grid;
+
+typedef struct {
+    int index;            /* best flat grid index, -1 if no trapezoid fits as a dip */
+    int box_index;        /* best grid index among the boxes (tau = 0), -1 if none */
+    double power;         /* Q of the best trapezoid (FP64 refit) */
+    double box_power;     /* Q of the best box (FP64 refit) */
+    double epoch;         /* mid-eclipse time t_ref + c/f */
+    double duration;      /* total duration T/f */
+    double ingress;       /* ingress duration tau/f (0 for a box) */
+    double depth;         /* least-squares depth of the best trapezoid */
+} bls_shape;
+
+/* bls_search plus the trapezoid refit of every peak: shapes[c*topk + q] (host) belongs to
+ * out[c*topk + q]; empty peak slots get index = box_index = -1.  grid may be NULL (all
+ * defaults).  Errors: as bls_search; BLS_ERR_INVALID for a bad grid. */
+bls_status bls_search_shapes(bls_plan* plan, const bls_curve* curves, int ncurves,
+                             bls_peak* out, float* spectrum, const bls_shape_grid* grid,
+                             bls_shape* shapes);
+
 /* Serving: queue one curve.  The input is copied before the call returns; the call
  * never waits for the GPU.  Requests are admitted to the device as memory and slots
  * free up and share the GPU with requests already running (continuous batching).

@@ -72,6 +72,16 @@ class WindowDesc(C.Structure):
                 ("min_points", C.c_int)]
 
 
+class ShapeGrid(C.Structure):
+    _fields_ = [("ncentre", C.c_int), ("nwidth", C.c_int), ("ningress", C.c_int),
+                ("width_lo", C.c_double), ("width_hi", C.c_double), ("ingress_max", C.c_double)]
+
+
+SHAPE_DTYPE = np.dtype([("index", np.int32), ("box_index", np.int32), ("power", np.float64),
+                        ("box_power", np.float64), ("epoch", np.float64),
+                        ("duration", np.float64), ("ingress", np.float64), ("depth", np.float64)])
+
+
 class Profile(C.Structure):
     _fields_ = [("searches", C.c_uint64), ("kernel_launches", C.c_uint64),
                 ("fold_launches", C.c_uint64), ("prep_ms", C.c_double),
@@ -90,7 +100,7 @@ _lock = threading.Lock()
 
 EXPORTS = ["bls_plan_create", "bls_plan_destroy", "bls_search", "bls_submit", "bls_poll",
            "bls_cancel", "bls_server_stats_get", "bls_kminmax", "bls_debug_fold",
-           "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_window_efficiency", "bls_refine",
+           "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_window_efficiency", "bls_refine", "bls_search_shapes",
            "bls_last_error"]
 
 
@@ -119,6 +129,8 @@ def lib():
             L.bls_search_static.argtypes = [C.POINTER(CurveStruct), I, I, P, P, P]
             L.bls_window_efficiency.argtypes = [C.POINTER(WindowDesc), P, P, P]
             L.bls_refine.argtypes = [P, C.POINTER(CurveStruct), I, P, I, I, P]
+            L.bls_search_shapes.argtypes = [P, C.POINTER(CurveStruct), I, P, P,
+                                            C.POINTER(ShapeGrid), P]
             L.bls_last_error.argtypes = []
             L.bls_last_error.restype = C.c_char_p
             _lib = L
@@ -284,6 +296,19 @@ class Plan:
         out = np.zeros((len(curves), self.topk), dtype=PEAK_DTYPE)
         _check(lib().bls_search(self._h, arr, len(curves), out.ctypes.data, _ptr(spectrum)))
         return out
+
+    def search_shapes(self, curves: Sequence[CurveInput], ncentre: int = 0, nwidth: int = 0,
+                      ningress: int = 0, width_lo: float = 0.0, width_hi: float = 0.0,
+                      ingress_max: float = -1.0, spectrum=None):
+        """``bls_search_shapes``: (peaks, trapezoid refits), both (ncurves, topk)."""
+        keep: list = []
+        arr = (CurveStruct * len(curves))(*[_struct(c, keep) for c in curves])
+        out = np.zeros((len(curves), self.topk), dtype=PEAK_DTYPE)
+        shapes = np.zeros((len(curves), self.topk), dtype=SHAPE_DTYPE)
+        g = ShapeGrid(ncentre, nwidth, ningress, width_lo, width_hi, ingress_max)
+        _check(lib().bls_search_shapes(self._h, arr, len(curves), out.ctypes.data,
+                                       _ptr(spectrum), C.byref(g), shapes.ctypes.data))
+        return out, shapes
 
     def refine(self, curves: Sequence[CurveInput], peaks: np.ndarray, oversample: int = 10,
                half: int = 2) -> np.ndarray:

@@ -262,7 +262,7 @@ size_t curve_bytes(const bls_plan_impl* P, const CurveSpec& c, bool host_spec)
 // repeats, the graph is replayed with a single launch.
 bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int g0, int g1,
                      const std::vector<long long>& spec_off, bls_peak* out, float* spectrum,
-                     bool spectrum_dev, float* res_dump)
+                     bool spectrum_dev, float* res_dump, const ShapeReq* shape)
 {
     const int nc = g1 - g0;
     const int topk = P->d.topk;
@@ -328,6 +328,10 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     BLS_ENSURE(P->h_cdesc, (size_t)nc * sizeof(CurveDesc), "pinned descriptors")
     BLS_ENSURE(P->h_peaks, (size_t)nc * topk * sizeof(DevPeak), "pinned peaks")
     BLS_ENSURE(P->h_err, 64, "pinned error word")
+    if (shape) {
+        BLS_ENSURE(P->shapes, (size_t)nc * topk * sizeof(DevShape), "allocating shape fits")
+        BLS_ENSURE(P->h_shapes, (size_t)nc * topk * sizeof(DevShape), "pinned shape fits")
+    }
     if (tiled) {
         BLS_ENSURE(P->ranges, nr * sizeof(TileRange), "allocating work list")
         BLS_ENSURE(P->prefix, (nr + cls.size()) * sizeof(long long), "allocating work list")
@@ -478,6 +482,20 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         if (prof) record(P->ev[2]);
         if ((x = launch_reduce(rp, nc, st)) != cudaSuccess) return x;
         ++launches;
+        if (shape) {
+            ShapeParams sp;
+            sp.curves = P->cdesc.as<CurveDesc>();
+            sp.peaks = P->peaks.as<DevPeak>();
+            sp.out = P->shapes.as<DevShape>();
+            sp.topk = topk;
+            sp.nc = shape->nc; sp.nw = shape->nw; sp.na = shape->na;
+            sp.wlo = shape->wlo; sp.whi = shape->whi; sp.amax = shape->amax;
+            if ((x = launch_shape(sp, nc, st)) != cudaSuccess) return x;
+            ++launches;
+            if ((x = cudaMemcpyAsync(P->h_shapes.p, P->shapes.p, (size_t)nc * topk * sizeof(DevShape),
+                                     cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return x;
+        }
         if (prof) record(P->ev[3]);
         if ((x = cudaMemcpyAsync(P->h_peaks.p, P->peaks.p, (size_t)nc * topk * sizeof(DevPeak),
                                  cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -503,12 +521,17 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         for (const Copy& cp : copies) put(&cp, sizeof(cp));
         put(&spectrum, sizeof(spectrum));
         put(&P->d, sizeof(P->d));
+        const int shp[3] = {shape ? shape->nc : 0, shape ? shape->nw : 0, shape ? shape->na : 0};
+        const double shd[3] = {shape ? shape->wlo : 0.0, shape ? shape->whi : 0.0, shape ? shape->amax : 0.0};
+        put(shp, sizeof(shp));
+        put(shd, sizeof(shd));
         put(&pp, sizeof(pp));
         if (tiled) {
             put(P->h_ranges.p, nr * sizeof(TileRange));
             put(P->h_prefix.p, pp * sizeof(long long));
         }
-        void* bufs[] = {P->pts.p, P->res.p, P->peaks.p, P->spec.p, P->err.p, P->h_peaks.p, P->h_err.p, P->ranges.p};
+        void* bufs[] = {P->pts.p, P->res.p, P->peaks.p, P->spec.p, P->err.p, P->h_peaks.p, P->h_err.p, P->ranges.p,
+                        P->shapes.p, P->h_shapes.p};
         put(bufs, sizeof(bufs));
         if (P->graph && sig == P->graph_sig) {
             if ((e = cudaGraphLaunch(P->graph, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
@@ -568,11 +591,15 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     const DevPeak* hpk = P->h_peaks.as<DevPeak>();
     for (int c = 0; c < nc; ++c)
         for (int q = 0; q < topk; ++q) to_peak(hpk[(size_t)c * topk + q], &out[(size_t)(g0 + c) * topk + q]);
+    if (shape) {
+        static_assert(sizeof(DevShape) == sizeof(bls_shape), "DevShape mirrors bls_shape");
+        memcpy(shape->out + (size_t)g0 * topk, P->h_shapes.p, (size_t)nc * topk * sizeof(bls_shape));
+    }
     return BLS_OK;
 }
 
 bls_status search_impl(bls_plan_impl* P, const bls_curve* curves, int ncurves, bls_peak* out,
-                       float* spectrum, float* res_dump)
+                       float* spectrum, float* res_dump, const ShapeReq* shape = nullptr)
 {
     if (ncurves < 0) return set_error(BLS_ERR_INVALID, "ncurves = %d", ncurves);
     if (ncurves == 0) return BLS_OK;
@@ -616,7 +643,8 @@ bls_status search_impl(bls_plan_impl* P, const bls_curve* curves, int ncurves, b
         if (bytes > P->budget)
             return set_error(BLS_ERR_NOMEM, "curve %d needs %zu B, over the plan's device budget of %zu B", g0,
                              bytes, P->budget);
-        bls_status s = run_group(P, specs, g0, g1, spec_off, out, spectrum, spec_dev, res_dump ? res_dump + spec_off[g0] : nullptr);
+        bls_status s = run_group(P, specs, g0, g1, spec_off, out, spectrum, spec_dev,
+                                 res_dump ? res_dump + spec_off[g0] : nullptr, shape);
         if (s != BLS_OK) return s;
         g0 = g1;
     }
@@ -806,6 +834,26 @@ bls_status bls_refine(bls_plan* P, const bls_curve* curves, int ncurves, const b
     return BLS_OK;
 }
 
+bls_status bls_search_shapes(bls_plan* P, const bls_curve* curves, int ncurves, bls_peak* out,
+                             float* spectrum, const bls_shape_grid* grid, bls_shape* shapes)
+{
+    if (!P || !shapes) return set_error(BLS_ERR_INVALID, "NULL plan or shapes");
+    ShapeReq r;
+    r.nc = grid && grid->ncentre ? grid->ncentre : 17;
+    r.nw = grid && grid->nwidth ? grid->nwidth : 13;
+    r.na = grid && grid->ningress ? grid->ningress : 6;
+    r.wlo = grid && grid->width_lo != 0.0 ? grid->width_lo : 0.5;
+    r.whi = grid && grid->width_hi != 0.0 ? grid->width_hi : 2.0;
+    r.amax = grid && grid->ingress_max >= 0.0 ? grid->ingress_max : 0.5;
+    r.out = shapes;
+    if (r.nc < 1 || r.nw < 1 || r.na < 1 || (long long)r.nc * r.nw * r.na > (1 << 20))
+        return set_error(BLS_ERR_INVALID, "shape grid %d x %d x %d", r.nc, r.nw, r.na);
+    if (!(r.wlo > 0.0) || !(r.whi >= r.wlo) || !(r.amax >= 0.0 && r.amax <= 0.5))
+        return set_error(BLS_ERR_INVALID, "shape grid widths %g..%g, ingress %g", r.wlo, r.whi, r.amax);
+    std::lock_guard<std::mutex> lk(P->mu);
+    return search_impl(P, curves, ncurves, out, spectrum, nullptr, &r);
+}
+
 bls_status bls_debug_powers(bls_plan* P, const bls_curve* curve, float* power_out, int* i1_out, int* k_out)
 {
     if (!P || !curve || !power_out || !i1_out || !k_out) return set_error(BLS_ERR_INVALID, "NULL argument");
@@ -849,7 +897,7 @@ bls_status bls_debug_fold(bls_plan* P, const bls_curve* curve, const int* js, in
     std::vector<long long> off{0, s.nf};
     std::vector<bls_peak> pk((size_t)P->d.topk);
     bls_plan_desc saved = P->d;
-    st = run_group(P, specs, 0, 1, off, pk.data(), nullptr, false, nullptr);
+    st = run_group(P, specs, 0, 1, off, pk.data(), nullptr, false, nullptr, nullptr);
     P->d = saved;
     if (st != BLS_OK) return st;
     if ((e = P->jsbuf.ensure((size_t)nj * 4)) != cudaSuccess) return cuda_fail(e, "allocating");

@@ -67,6 +67,23 @@ struct FoldParams {
     int cols;                  // frequencies per tile (set by launch_fold_sweep)
 };
 
+// Trapezoid refit of a peak (same layout as bls_shape).
+struct DevShape {
+    int index, box_index;
+    double power, box_power, epoch, duration, ingress, depth;
+};
+
+struct ShapeParams {
+    const CurveDesc* curves;
+    const DevPeak* peaks;      // peaks of curve c at [c*topk, (c+1)*topk)
+    DevShape* out;             // same indexing
+    int topk;
+    int nc, nw, na;            // grid: centres, widths, ingress fractions
+    double wlo, whi, amax;     // widths in box widths; largest ingress / width
+};
+
+cudaError_t launch_shape(const ShapeParams& p, int ncurves, cudaStream_t s);
+
 struct ReduceParams {
     const CurveDesc* curves;
     const int* slots;          // curve of block b = slots[b] (nullptr: b)

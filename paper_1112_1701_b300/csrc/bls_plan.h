@@ -74,9 +74,9 @@ struct bls_plan_impl {
     DevBuf raw_t, raw_y, raw_dy, raw_f;   // staging of host inputs
     DevBuf pts, dt64, w64, wx64;          // prepared points
     DevBuf cdesc, ranges, prefix, counter, err;
-    DevBuf res, peaks, spec, plain_hist, jsbuf, binsbuf;
+    DevBuf res, peaks, spec, plain_hist, jsbuf, binsbuf, shapes;
     // host staging (pinned)
-    HostBuf h_cdesc, h_ranges, h_prefix, h_peaks, h_err;
+    HostBuf h_cdesc, h_ranges, h_prefix, h_peaks, h_err, h_shapes;
 
     // CUDA graph of the last launch group, replayed while its signature repeats
     cudaGraphExec_t graph = nullptr;
@@ -98,6 +98,13 @@ struct bls_plan_impl {
 bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* out,
                          const int* kinds = nullptr);
 int ptr_kind(const void* p);
+
+// A validated trapezoid-refit request of bls_search_shapes.
+struct ShapeReq {
+    int nc, nw, na;
+    double wlo, whi, amax;
+    bls_shape* out;            // host, indexed like the peaks
+};
 void to_peak(const DevPeak& s, bls_peak* d);   // device record -> ABI record
 // Block size / stride / chunk / shared memory for a curve with nb bins.
 bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g);
