@@ -1,5 +1,5 @@
-"""ctypes binding of ``bls_oracle.c``, ``window_oracle.c`` and ``shape_oracle.c``, the plain
-FP64 oracles (test infrastructure).
+"""ctypes binding of ``bls_oracle.c``, ``window_oracle.c``, ``shape_oracle.c`` and
+``variability_oracle.c``, the plain FP64 oracles (test infrastructure).
 
 Every function mirrors one C function; see that file for the definition each one
 follows (Sec. 2.2.2 of the paper and the BLS method it cites).
@@ -17,7 +17,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bls_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "window_oracle.c"), os.path.join(_HERE, "shape_oracle.c")]
+_SRCS = [_SRC] + [os.path.join(_HERE, f) for f in ("window_oracle.c", "shape_oracle.c",
+                                                  "variability_oracle.c")]
 _LIB = os.path.join(_HERE, "libbls_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -99,6 +100,9 @@ def _load():
             lib.oracle_shape_point.restype = D
             lib.oracle_shape.argtypes = [I, P, P, P, D, I, I, I, I, I, I, D, D, D,
                                          C.POINTER(_Shape), P]
+            lib.oracle_star_stats.argtypes = [I, P, C.POINTER(D), C.POINTER(D)]
+            lib.oracle_clip.argtypes = [I, P, D, I, C.POINTER(D), C.POINTER(D)]
+            lib.oracle_variability.argtypes = [I, P, P, P, I, D, I, D, I, P, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -294,3 +298,37 @@ def shape_point(phi, w, x, c: float, T: float, tau: float):
     Q = _load().oracle_shape_point(len(phi), _p(phi), _p(w), _p(x), c, T, tau, C.byref(d),
                                    C.byref(ok))
     return Q, d.value, bool(ok.value)
+
+
+def star_stats(m):
+    """Mean magnitude and population RMS of one light curve (``oracle_star_stats``)."""
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    mag, rms = C.c_double(), C.c_double()
+    _load().oracle_star_stats(len(m), _p(m), C.byref(mag), C.byref(rms))
+    return mag.value, rms.value
+
+
+def clip(vals, clip: float = 3.0, iters: int = 5):
+    """Sigma-clipped (mu, sd, kept) of a set of values (``oracle_clip``)."""
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    mu, sd = C.c_double(), C.c_double()
+    kept = _load().oracle_clip(len(vals), _p(vals), clip, iters, C.byref(mu), C.byref(sd))
+    return mu.value, sd.value, kept
+
+
+def variability(off, m, chip, nchips: int, clip: float = 3.0, iters: int = 5,
+                nsig: float = 2.0, min_stars: int = 5):
+    """High-variability flags (``oracle_variability``): dict of per-star arrays mag, rms,
+    bin, mu, sd, flag."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    chip = np.ascontiguousarray(chip, dtype=np.int32)
+    n = len(chip)
+    out = dict(mag=np.zeros(n), rms=np.zeros(n), bin=np.zeros(n, np.int32), mu=np.zeros(n),
+               sd=np.zeros(n), flag=np.zeros(n, np.uint8))
+    rc = _load().oracle_variability(n, _p(off), _p(m), _p(chip), nchips, clip, iters, nsig,
+                                    min_stars, _p(out["mag"]), _p(out["rms"]), _p(out["bin"]),
+                                    _p(out["mu"]), _p(out["sd"]), _p(out["flag"]))
+    if rc != 0:
+        raise ValueError("oracle_variability: bad arguments")
+    return out

@@ -285,3 +285,42 @@ def eclipse_injections(t: np.ndarray, periods: Sequence[float], per_period: int,
                                      depth=depth)))
             grids.append(g)
     return Batch(curves, grids, [nb] * len(curves), 0.005, 0.15, "injection-recovery")
+
+
+# ----------------------------------------------------------------------------------
+# High-variability pre-filter workload: chip catalogs of light curves in magnitudes.
+# ----------------------------------------------------------------------------------
+
+@dataclass
+class Catalog:
+    """Light curves of the stars of several chips, concatenated: star s has magnitudes
+    m[off[s]:off[s+1]] and lies on chip[s]; variable[s] marks the injected variables."""
+    off: np.ndarray
+    m: np.ndarray
+    chip: np.ndarray
+    variable: np.ndarray
+    nchips: int
+
+
+def chip_catalog(seed: int = 12, nchips: int = 11, stars_per_chip: int = 3000,
+                 npts: int = 600, var_frac: float = 0.01, mag_range=(14.0, 20.5)) -> Catalog:
+    """Stars with magnitudes rising in number towards the faint end (log N ~ 0.3 m), a
+    noise floor of 3 mmag plus photon noise growing with magnitude (about 1% at 18.5,
+    ~10% at 20.5), npts epochs each; a fraction var_frac are eclipsing-binary-like
+    variables with box dips of depth U[0.1, 0.4] mag over 10-20% of their epochs."""
+    rng = np.random.Generator(np.random.PCG64(seed * 10**6))
+    n = nchips * stars_per_chip
+    lo, hi = mag_range
+    a = 0.3 * np.log(10.0)
+    u = rng.random(n)
+    mag = lo + np.log1p(u * (np.exp(a * (hi - lo)) - 1.0)) / a
+    sigma = np.sqrt(0.003 ** 2 + (0.01 * 10 ** (0.4 * (mag - 18.5))) ** 2)
+    variable = rng.random(n) < var_frac
+    m = mag[:, None] + sigma[:, None] * rng.normal(0.0, 1.0, (n, npts))
+    for s in np.flatnonzero(variable):
+        frac = rng.uniform(0.1, 0.2)
+        dip = rng.random(npts) < frac
+        m[s, dip] += rng.uniform(0.1, 0.4)
+    off = np.arange(n + 1, dtype=np.int64) * npts
+    chip = np.repeat(np.arange(nchips, dtype=np.int32), stars_per_chip)
+    return Catalog(off, m.astype(np.float32).ravel(), chip, variable, nchips)
