@@ -289,6 +289,41 @@ typedef struct {
 bls_status bls_window_efficiency(const bls_window_desc* desc, void* cuda_stream, double* eff,
                                  int* counts);
 
+/* High-variability pre-filter (Sec. 2.2.1 of the paper): stars whose photometric
+ * variability lies more than nsig standard deviations above the expectation for their
+ * magnitude -- estimated per 0.1-mag bin from a sigma-clipped average over the stars of
+ * their chip -- are flagged.  Per star, from its light curve in magnitudes: mag = mean,
+ * rms = population RMS, bin = floor(RN(mag * 10)).  Per (chip, bin), over the rms of its
+ * stars in star order: mu and sd (population) of the kept values, keep |rms - mu| <=
+ * clip * sd, at most `iters` rounds, stop when the kept set no longer changes; a star is
+ * flagged when its bin has at least min_stars stars and rms > mu + nsig * sd.  All sums
+ * in FP64 in the order given, so the results equal the definition's exactly. */
+typedef struct {
+    const long long* off;   /* nstars + 1 offsets into m (host or device) */
+    const float* m;         /* magnitudes of all light curves, concatenated (host or device) */
+    const int* chip;        /* chip of every star, 0 .. nchips-1 (host or device) */
+    int nstars, nchips;     /* >= 1 each */
+    double clip;            /* clipping threshold, in sd (> 0; 3 is the usual choice) */
+    int iters;              /* clipping rounds (>= 0) */
+    double nsig;            /* flag threshold above the expectation, in sd (the paper: 2) */
+    int min_stars;          /* bins with fewer stars flag nothing (>= 1) */
+} bls_var_desc;
+
+typedef struct {
+    double mag, rms;        /* mean magnitude and RMS of the star's light curve */
+    double mu, sd;          /* sigma-clipped expectation of its (chip, bin) */
+    int bin;                /* floor(mag * 10) */
+    unsigned char flag;     /* 1: more variable than nsig sd above the expectation */
+    unsigned char pad_[3];
+} bls_var_star;
+
+/* out: nstars records (host or device).  Work is ordered on cuda_stream (NULL: legacy
+ * default stream); returns when the results are written; scratch from cudaMallocAsync on
+ * that stream.  Errors: BLS_ERR_INVALID (bad descriptor; empty or non-finite light curves,
+ * chip ids out of range, or one chip spanning more than 4096 bins: device check),
+ * BLS_ERR_NOMEM, BLS_ERR_CUDA. */
+bls_status bls_variability(const bls_var_desc* desc, void* cuda_stream, bls_var_star* out);
+
 /* Search of one curve that allocates nothing.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc (a plug-in whose host application
  * owns and budgets all device memory, a latency-critical loop that cannot take

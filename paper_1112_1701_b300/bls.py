@@ -82,6 +82,17 @@ SHAPE_DTYPE = np.dtype([("index", np.int32), ("box_index", np.int32), ("power", 
                         ("duration", np.float64), ("ingress", np.float64), ("depth", np.float64)])
 
 
+class VarDesc(C.Structure):
+    _fields_ = [("off", C.c_void_p), ("m", C.c_void_p), ("chip", C.c_void_p),
+                ("nstars", C.c_int), ("nchips", C.c_int), ("clip", C.c_double),
+                ("iters", C.c_int), ("nsig", C.c_double), ("min_stars", C.c_int)]
+
+
+VAR_DTYPE = np.dtype([("mag", np.float64), ("rms", np.float64), ("mu", np.float64),
+                      ("sd", np.float64), ("bin", np.int32), ("flag", np.uint8),
+                      ("pad_", np.uint8, 3)])
+
+
 class Profile(C.Structure):
     _fields_ = [("searches", C.c_uint64), ("kernel_launches", C.c_uint64),
                 ("fold_launches", C.c_uint64), ("prep_ms", C.c_double),
@@ -100,7 +111,7 @@ _lock = threading.Lock()
 
 EXPORTS = ["bls_plan_create", "bls_plan_destroy", "bls_search", "bls_submit", "bls_poll",
            "bls_cancel", "bls_server_stats_get", "bls_kminmax", "bls_debug_fold",
-           "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_window_efficiency", "bls_refine", "bls_search_shapes",
+           "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_window_efficiency", "bls_refine", "bls_search_shapes", "bls_variability",
            "bls_last_error"]
 
 
@@ -131,6 +142,7 @@ def lib():
             L.bls_refine.argtypes = [P, C.POINTER(CurveStruct), I, P, I, I, P]
             L.bls_search_shapes.argtypes = [P, C.POINTER(CurveStruct), I, P, P,
                                             C.POINTER(ShapeGrid), P]
+            L.bls_variability.argtypes = [C.POINTER(VarDesc), P, P]
             L.bls_last_error.argtypes = []
             L.bls_last_error.restype = C.c_char_p
             _lib = L
@@ -236,6 +248,21 @@ def window_efficiency(t, nphi: int, *, freqs=None, fmin: float = 0.0, df: float 
                    min_eclipses, min_points)
     _check(lib().bls_window_efficiency(C.byref(d), stream, _ptr(eff), _ptr(counts)))
     return eff, counts
+
+
+def variability(off, m, chip, nchips: int, clip: float = 3.0, iters: int = 5,
+                nsig: float = 2.0, min_stars: int = 5, stream=None, out=None):
+    """``bls_variability``: high-variability flags of every star.  Arrays: numpy or CUDA
+    tensors; returns the records (numpy structured array of VAR_DTYPE, or ``out``)."""
+    off = _host(off, np.int64)
+    m = _host(m, np.float32)
+    chip = _host(chip, np.int32)
+    n = len(chip)
+    if out is None:
+        out = np.zeros(n, dtype=VAR_DTYPE)
+    d = VarDesc(_ptr(off), _ptr(m), _ptr(chip), n, nchips, clip, iters, nsig, min_stars)
+    _check(lib().bls_variability(C.byref(d), stream, _ptr(out)))
+    return out
 
 
 def search_static(curve: CurveInput, topk: int = 1, sign: str = "dips", stream=None,

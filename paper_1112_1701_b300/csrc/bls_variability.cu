@@ -1,0 +1,321 @@
+// bls_variability.cu -- high-variability pre-filter (Sec. 2.2.1 of the paper): stars whose
+// photometric variability stands more than nsig standard deviations above the expectation
+// for their magnitude -- estimated per 0.1-mag bin from a sigma-clipped average over the
+// stars of their chip -- are flagged before the BLS search.
+//
+// Per star (light curve in magnitudes): mag = mean, rms = population RMS (two passes),
+// bin = floor(RN(mag * 10)).  Per (chip, bin): sigma clipping of the stars' rms values
+// (mu, sd of the kept; keep |rms - mu| <= clip * sd; at most `iters` rounds, stop when the
+// kept set no longer changes); flag = (bin has >= min_stars stars) && rms > mu + nsig * sd.
+//
+// Every floating-point decision here (bins, kept sets, flags) must come out as in the
+// definition, so every sum is taken in FP64 in the definition's order: one thread per
+// star runs the two passes over its points in order, and one thread per (chip, bin) runs
+// the clipping over the bin's stars in star order.  The data-parallel work around them is
+// the grouping: a chip's stars are compacted in star order (block prefix sums), counted
+// per bin and laid out bin by bin, still in star order.
+//
+// Kernels: star_kernel (one thread per star), chip_count / chip_scan (stars per chip and
+// their offsets), chip_kernel (one block per chip: compaction, bins, clipping, flags).
+#include <cstring>
+
+#include "bls_plan.h"
+
+namespace blsgpu {
+namespace {
+
+constexpr int kVarThreads = 256;
+constexpr int kMaxBinsPerChip = 4096;   // 409.6 mag of range within one chip
+
+__global__ void star_kernel(const long long* off, const float* m, int nstars, double* mag,
+                            double* rms, int* bin, int* err)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nstars) return;
+    const long long a = off[s], b = off[s + 1];
+    if (!(b > a)) { atomicOr(err, kErrInput); return; }
+    double sum = 0.0;
+    for (long long i = a; i < b; ++i) sum = __dadd_rn(sum, (double)m[i]);
+    const double n = (double)(b - a);
+    const double mu = __ddiv_rn(sum, n);
+    double v = 0.0;
+    for (long long i = a; i < b; ++i) {
+        const double d = __dsub_rn((double)m[i], mu);
+        v = __dadd_rn(v, __dmul_rn(d, d));
+    }
+    if (!isfinite(mu)) atomicOr(err, kErrInput);
+    mag[s] = mu;
+    rms[s] = sqrt(__ddiv_rn(v, n));
+    bin[s] = (int)floor(__dmul_rn(mu, 10.0));
+}
+
+__global__ void chip_count_kernel(const int* chip, int nstars, int nchips, int* count, int* err)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nstars) return;
+    const int c = chip[s];
+    if (c < 0 || c >= nchips) { atomicOr(err, kErrInput); return; }
+    atomicAdd(&count[c], 1);
+}
+
+// Exclusive prefix sum of the per-chip counts (one block; chunks of blockDim).
+__global__ void chip_scan_kernel(const int* count, int nchips, int* offs)
+{
+    __shared__ int sh[kVarThreads];
+    int carry = 0;
+    for (int c0 = 0; c0 < nchips; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        const int v = c < nchips ? count[c] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            const int t = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (c < nchips) offs[c] = carry + sh[threadIdx.x] - v;
+        carry += sh[blockDim.x - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) offs[nchips] = carry;
+}
+
+struct ChipParams {
+    const int* chip;
+    const int* offs;          // nchips + 1
+    const double* rms;
+    const int* bin;
+    int nstars;
+    double clip;
+    int iters;
+    double nsig;
+    int min_stars;
+    int* members;             // scratch: stars of each chip, in star order
+    int* sorted;              // scratch: the same, bin by bin
+    unsigned char* keep;      // scratch: kept flags, indexed like `sorted`
+    double* mu;               // outputs per star
+    double* sd;
+    unsigned char* flag;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kVarThreads) chip_kernel(ChipParams p)
+{
+    __shared__ int sh[kVarThreads];
+    __shared__ int bcount[kMaxBinsPerChip + 1];
+    __shared__ int s_lo, s_hi;
+    const int c = blockIdx.x;
+    const int base = p.offs[c], cnt = p.offs[c + 1] - base;
+    if (cnt == 0) return;
+    int* mem = p.members + base;
+    int* srt = p.sorted + base;
+    unsigned char* kp = p.keep + base;
+    // (a) stable compaction of the chip's stars
+    int pos = 0;
+    for (int s0 = 0; s0 < p.nstars; s0 += blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        const int in = s < p.nstars && p.chip[s] == c;
+        sh[threadIdx.x] = in;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            const int t = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (in) mem[pos + sh[threadIdx.x] - 1] = s;
+        pos += sh[blockDim.x - 1];
+        __syncthreads();
+    }
+    // (b) bin range of the chip
+    if (threadIdx.x == 0) { s_lo = 0x7fffffff; s_hi = -0x7fffffff; }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int b = p.bin[mem[i]];
+        atomicMin(&s_lo, b);
+        atomicMax(&s_hi, b);
+    }
+    __syncthreads();
+    const int lo = s_lo, nbins = s_hi - s_lo + 1;
+    if (nbins > kMaxBinsPerChip || nbins < 1) {
+        if (threadIdx.x == 0) atomicOr(p.err, kErrInput);
+        return;
+    }
+    // (c) stars per bin and bin offsets
+    for (int b = threadIdx.x; b <= nbins; b += blockDim.x) bcount[b] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) atomicAdd(&bcount[p.bin[mem[i]] - lo], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 0; b < nbins; ++b) { const int v = bcount[b]; bcount[b] = acc; acc += v; }
+        bcount[nbins] = acc;
+    }
+    __syncthreads();
+    // (d) bin by bin, in star order (one thread per bin appends its stars)
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        int w = bcount[b];
+        for (int i = 0; i < cnt; ++i)
+            if (p.bin[mem[i]] - lo == b) srt[w++] = mem[i];
+    }
+    __syncthreads();
+    // (e) sigma clipping per bin, sequential over the bin's stars; (f) flags
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        const int a = bcount[b], k = bcount[b + 1] - a;
+        if (k == 0) continue;
+        for (int i = 0; i < k; ++i) kp[a + i] = 1;
+        double mu = 0.0, sd = 0.0;
+        for (int it = 0; it <= p.iters; ++it) {
+            double s = 0.0;
+            int kc = 0;
+            for (int i = 0; i < k; ++i)
+                if (kp[a + i]) { s = __dadd_rn(s, p.rms[srt[a + i]]); ++kc; }
+            mu = kc > 0 ? __ddiv_rn(s, (double)kc) : 0.0;
+            double v = 0.0;
+            for (int i = 0; i < k; ++i)
+                if (kp[a + i]) {
+                    const double d = __dsub_rn(p.rms[srt[a + i]], mu);
+                    v = __dadd_rn(v, __dmul_rn(d, d));
+                }
+            sd = kc > 0 ? sqrt(__ddiv_rn(v, (double)kc)) : 0.0;
+            if (it == p.iters) break;
+            bool changed = false;
+            const double lim = __dmul_rn(p.clip, sd);
+            for (int i = 0; i < k; ++i) {
+                const unsigned char nk = fabs(__dsub_rn(p.rms[srt[a + i]], mu)) <= lim;
+                if (nk != kp[a + i]) { kp[a + i] = nk; changed = true; }
+            }
+            if (!changed) break;
+        }
+        const double thr = __dadd_rn(mu, __dmul_rn(p.nsig, sd));
+        for (int i = 0; i < k; ++i) {
+            const int s = srt[a + i];
+            p.mu[s] = mu;
+            p.sd[s] = sd;
+            p.flag[s] = (unsigned char)(k >= p.min_stars && p.rms[s] > thr);
+        }
+    }
+}
+
+// Packs the per-star outputs into the ABI records.
+__global__ void pack_kernel(int nstars, const double* mag, const double* rms, const int* bin,
+                            const double* mu, const double* sd, const unsigned char* flag,
+                            bls_var_star* out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nstars) return;
+    bls_var_star r;
+    memset(&r, 0, sizeof(r));
+    r.mag = mag[s]; r.rms = rms[s]; r.mu = mu[s]; r.sd = sd[s];
+    r.bin = bin[s]; r.flag = flag[s];
+    out[s] = r;
+}
+
+}  // namespace
+}  // namespace blsgpu
+
+using namespace blsgpu;
+
+extern "C" bls_status bls_variability(const bls_var_desc* d, void* cuda_stream, bls_var_star* out)
+{
+    if (!d || !out || !d->off || !d->m || !d->chip) return set_error(BLS_ERR_INVALID, "NULL argument");
+    if (d->nstars < 1 || d->nchips < 1)
+        return set_error(BLS_ERR_INVALID, "nstars = %d, nchips = %d", d->nstars, d->nchips);
+    if (!(d->clip > 0.0) || d->iters < 0 || !(d->nsig >= 0.0) || d->min_stars < 1)
+        return set_error(BLS_ERR_INVALID, "clip = %g, iters = %d, nsig = %g, min_stars = %d", d->clip, d->iters,
+                         d->nsig, d->min_stars);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e;
+    const int ko = ptr_kind(d->off), km = ptr_kind(d->m), kc = ptr_kind(d->chip), kout = ptr_kind(out);
+    const size_t ns = (size_t)d->nstars, nc = (size_t)d->nchips;
+    long long npts = 0;
+    if (ko == 2) {
+        if ((e = cudaMemcpyAsync(&npts, d->off + ns, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "reading the point count");
+    } else {
+        npts = d->off[ns];
+    }
+    if (npts < 1) return set_error(BLS_ERR_INVALID, "no points");
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    // one device block for everything: [err | off | m | chip | mag | rms | bin | mu | sd | flag |
+    //  count | offs | members | sorted | keep | out]
+    size_t o = 256;
+    const size_t o_off = o;   o += ko == 2 ? 0 : up((ns + 1) * 8);
+    const size_t o_m = o;     o += km == 2 ? 0 : up((size_t)npts * 4);
+    const size_t o_chip = o;  o += kc == 2 ? 0 : up(ns * 4);
+    const size_t o_mag = o;   o += up(ns * 8);
+    const size_t o_rms = o;   o += up(ns * 8);
+    const size_t o_bin = o;   o += up(ns * 4);
+    const size_t o_mu = o;    o += up(ns * 8);
+    const size_t o_sd = o;    o += up(ns * 8);
+    const size_t o_flag = o;  o += up(ns);
+    const size_t o_cnt = o;   o += up(nc * 4);
+    const size_t o_offs = o;  o += up((nc + 1) * 4);
+    const size_t o_mem = o;   o += up(ns * 4);
+    const size_t o_srt = o;   o += up(ns * 4);
+    const size_t o_keep = o;  o += up(ns);
+    const size_t o_out = o;   o += kout == 2 ? 0 : up(ns * sizeof(bls_var_star));
+    unsigned char* buf = nullptr;
+    if ((e = cudaMallocAsync(&buf, o, s)) != cudaSuccess) return cuda_fail(e, "variability buffers");
+    int* err = reinterpret_cast<int*>(buf);
+    const long long* doff = ko == 2 ? d->off : reinterpret_cast<const long long*>(buf + o_off);
+    const float* dm = km == 2 ? d->m : reinterpret_cast<const float*>(buf + o_m);
+    const int* dchip = kc == 2 ? d->chip : reinterpret_cast<const int*>(buf + o_chip);
+    bls_var_star* dout = kout == 2 ? out : reinterpret_cast<bls_var_star*>(buf + o_out);
+    double* mag = reinterpret_cast<double*>(buf + o_mag);
+    double* rms = reinterpret_cast<double*>(buf + o_rms);
+    int* bin = reinterpret_cast<int*>(buf + o_bin);
+    int herr = 0;
+    auto run = [&]() -> cudaError_t {
+        cudaError_t x;
+        if ((x = cudaMemsetAsync(err, 0, 4, s)) != cudaSuccess) return x;
+        if ((x = cudaMemsetAsync(buf + o_cnt, 0, nc * 4, s)) != cudaSuccess) return x;
+        if (ko != 2 && (x = cudaMemcpyAsync((void*)doff, d->off, (ns + 1) * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return x;
+        if (km != 2 && (x = cudaMemcpyAsync((void*)dm, d->m, (size_t)npts * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return x;
+        if (kc != 2 && (x = cudaMemcpyAsync((void*)dchip, d->chip, ns * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return x;
+        const int g = (int)((ns + kVarThreads - 1) / kVarThreads);
+        star_kernel<<<g, kVarThreads, 0, s>>>(doff, dm, d->nstars, mag, rms, bin, err);
+        chip_count_kernel<<<g, kVarThreads, 0, s>>>(dchip, d->nstars, d->nchips,
+                                                   reinterpret_cast<int*>(buf + o_cnt), err);
+        chip_scan_kernel<<<1, kVarThreads, 0, s>>>(reinterpret_cast<int*>(buf + o_cnt), d->nchips,
+                                                  reinterpret_cast<int*>(buf + o_offs));
+        ChipParams cp;
+        cp.chip = dchip;
+        cp.offs = reinterpret_cast<int*>(buf + o_offs);
+        cp.rms = rms;
+        cp.bin = bin;
+        cp.nstars = d->nstars;
+        cp.clip = d->clip;
+        cp.iters = d->iters;
+        cp.nsig = d->nsig;
+        cp.min_stars = d->min_stars;
+        cp.members = reinterpret_cast<int*>(buf + o_mem);
+        cp.sorted = reinterpret_cast<int*>(buf + o_srt);
+        cp.keep = buf + o_keep;
+        cp.mu = reinterpret_cast<double*>(buf + o_mu);
+        cp.sd = reinterpret_cast<double*>(buf + o_sd);
+        cp.flag = buf + o_flag;
+        cp.err = err;
+        chip_kernel<<<d->nchips, kVarThreads, 0, s>>>(cp);
+        pack_kernel<<<g, kVarThreads, 0, s>>>(d->nstars, mag, rms, bin, cp.mu, cp.sd, cp.flag, dout);
+        if ((x = cudaGetLastError()) != cudaSuccess) return x;
+        if (kout != 2 && (x = cudaMemcpyAsync(out, dout, ns * sizeof(bls_var_star), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return x;
+        if ((x = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return x;
+        return cudaStreamSynchronize(s);
+    };
+    e = run();
+    cudaError_t ef = cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) return cuda_fail(e, "variability");
+    if (ef != cudaSuccess) return cuda_fail(ef, "variability buffers");
+    if (herr & kErrInput)
+        return set_error(BLS_ERR_INVALID, "a star has no points or non-finite magnitudes, a chip id is out of range, "
+                                          "or one chip spans more than %d bins (device check)", kMaxBinsPerChip);
+    if (herr) return set_error(BLS_ERR_INTERNAL, "device consistency check failed (code %d)", herr);
+    return BLS_OK;
+}

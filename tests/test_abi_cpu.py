@@ -46,11 +46,11 @@ def test_struct_layout_matches_c(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "bls.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bls_plan_desc),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(bls_plan_desc),'
         ' sizeof(bls_curve), sizeof(bls_peak), sizeof(bls_server_stats),'
         ' offsetof(bls_peak, freq), offsetof(bls_curve, nb), sizeof(bls_window_desc),'
         ' offsetof(bls_window_desc, duration), sizeof(bls_profile), sizeof(bls_shape),'
-        ' sizeof(bls_shape_grid)); return 0;}\n')
+        ' sizeof(bls_shape_grid), sizeof(bls_var_desc), sizeof(bls_var_star)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
@@ -60,7 +60,8 @@ def test_struct_layout_matches_c(tmp_path):
                     C.sizeof(bls.PeakStruct), C.sizeof(bls.ServerStats),
                     bls.PeakStruct.freq.offset, bls.CurveStruct.nb.offset,
                     C.sizeof(bls.WindowDesc), bls.WindowDesc.duration.offset,
-                    C.sizeof(bls.Profile), bls.SHAPE_DTYPE.itemsize, C.sizeof(bls.ShapeGrid)]
+                    C.sizeof(bls.Profile), bls.SHAPE_DTYPE.itemsize, C.sizeof(bls.ShapeGrid),
+                    C.sizeof(bls.VarDesc), bls.VAR_DTYPE.itemsize]
 
 
 def test_kminmax_matches_reading(L):
