@@ -9,14 +9,17 @@
 // kept set no longer changes); flag = (bin has >= min_stars stars) && rms > mu + nsig * sd.
 //
 // Every floating-point decision here (bins, kept sets, flags) must come out as in the
-// definition, so every sum is taken in FP64 in the definition's order: one thread per
-// star runs the two passes over its points in order, and one thread per (chip, bin) runs
-// the clipping over the bin's stars in star order.  The data-parallel work around them is
-// the grouping: a chip's stars are compacted in star order (block prefix sums), counted
-// per bin and laid out bin by bin, still in star order.
+// definition, so every sum is taken in FP64 in the definition's order: 32 interleaved
+// partial sums (lane l adds elements l, l+32, ... in order) combined by an xor butterfly
+// over offsets 16, 8, 4, 2, 1 -- exactly what one warp computes with coalesced loads and
+// shuffles.  One warp per star takes the two passes over its light curve; one warp per
+// (chip, bin) runs the clipping over the bin's stars in star order (dropped stars add
+// zero in their places).  Around them, the grouping: a chip's stars are compacted in star
+// order (warp ballots), counted per bin and laid out bin by bin, still in star order.
 //
-// Kernels: star_kernel (one thread per star), chip_count / chip_scan (stars per chip and
-// their offsets), chip_kernel (one block per chip: compaction, bins, clipping, flags).
+// Kernels: star_kernel (one warp per star), chip_count / chip_scan (stars per chip and
+// their offsets), chip_kernel (one block per chip: compaction, bins, clipping, flags; a
+// chip's stars live in shared memory while they fit).
 #include <cstring>
 
 #include "bls_plan.h"
@@ -27,26 +30,40 @@ namespace {
 constexpr int kVarThreads = 256;
 constexpr int kMaxBinsPerChip = 4096;   // 409.6 mag of range within one chip
 
+// FP64 sum of one value per lane in the definition's order: the xor butterfly.
+__device__ __forceinline__ double butterfly(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 __global__ void star_kernel(const long long* off, const float* m, int nstars, double* mag,
                             double* rms, int* bin, int* err)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (s >= nstars) return;
     const long long a = off[s], b = off[s + 1];
-    if (!(b > a)) { atomicOr(err, kErrInput); return; }
-    double sum = 0.0;
-    for (long long i = a; i < b; ++i) sum = __dadd_rn(sum, (double)m[i]);
-    const double n = (double)(b - a);
-    const double mu = __ddiv_rn(sum, n);
-    double v = 0.0;
-    for (long long i = a; i < b; ++i) {
-        const double d = __dsub_rn((double)m[i], mu);
-        v = __dadd_rn(v, __dmul_rn(d, d));
+    if (!(b > a)) {
+        if (lane == 0) atomicOr(err, kErrInput);
+        return;
     }
-    if (!isfinite(mu)) atomicOr(err, kErrInput);
-    mag[s] = mu;
-    rms[s] = sqrt(__ddiv_rn(v, n));
-    bin[s] = (int)floor(__dmul_rn(mu, 10.0));
+    double part = 0.0;
+    for (long long i = a + lane; i < b; i += 32) part = __dadd_rn(part, (double)m[i]);
+    const double n = (double)(b - a);
+    const double mu = __ddiv_rn(butterfly(part), n);
+    part = 0.0;
+    for (long long i = a + lane; i < b; i += 32) {
+        const double d = __dsub_rn((double)m[i], mu);
+        part = __dadd_rn(part, __dmul_rn(d, d));
+    }
+    const double v = butterfly(part);
+    if (lane == 0) {
+        if (!isfinite(mu)) atomicOr(err, kErrInput);
+        mag[s] = mu;
+        rms[s] = sqrt(__ddiv_rn(v, n));
+        bin[s] = (int)floor(__dmul_rn(mu, 10.0));
+    }
 }
 
 __global__ void chip_count_kernel(const int* chip, int nstars, int nchips, int* count, int* err)
@@ -55,7 +72,9 @@ __global__ void chip_count_kernel(const int* chip, int nstars, int nchips, int* 
     if (s >= nstars) return;
     const int c = chip[s];
     if (c < 0 || c >= nchips) { atomicOr(err, kErrInput); return; }
-    atomicAdd(&count[c], 1);
+    // one atomic per distinct chip of the warp
+    const unsigned grp = __match_any_sync(__activemask(), c);
+    if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&count[c], __popc(grp));
 }
 
 // Exclusive prefix sum of the per-chip counts (one block; chunks of blockDim).
@@ -100,39 +119,52 @@ struct ChipParams {
     int* err;
 };
 
+// Stars of one chip staged in shared memory (bin offset, rms, kept flag, star index in bin
+// order); larger chips work on the global scratch arrays instead.
+constexpr int kSmemStars = 8192;
+constexpr size_t kChipSmem = (size_t)kSmemStars * (sizeof(double) + 2 * sizeof(int) + 1);
+
 __global__ void __launch_bounds__(kVarThreads) chip_kernel(ChipParams p)
 {
-    __shared__ int sh[kVarThreads];
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ int wsum[kVarThreads / 32];
     __shared__ int bcount[kMaxBinsPerChip + 1];
     __shared__ int s_lo, s_hi;
     const int c = blockIdx.x;
     const int base = p.offs[c], cnt = p.offs[c + 1] - base;
     if (cnt == 0) return;
+    const bool staged = cnt <= kSmemStars;
     int* mem = p.members + base;
-    int* srt = p.sorted + base;
-    unsigned char* kp = p.keep + base;
-    // (a) stable compaction of the chip's stars
+    // bin-ordered arrays: in shared memory when they fit
+    double* srms = staged ? reinterpret_cast<double*>(dsm) : nullptr;
+    int* sbin = staged ? reinterpret_cast<int*>(dsm + (size_t)kSmemStars * sizeof(double)) : nullptr;
+    int* srt = staged ? sbin + kSmemStars : p.sorted + base;
+    unsigned char* kp = staged ? reinterpret_cast<unsigned char*>(srt + kSmemStars) : p.keep + base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // (a) stable compaction of the chip's stars (warp ballots, then a scan of warp totals)
     int pos = 0;
     for (int s0 = 0; s0 < p.nstars; s0 += blockDim.x) {
         const int s = s0 + threadIdx.x;
-        const int in = s < p.nstars && p.chip[s] == c;
-        sh[threadIdx.x] = in;
+        const bool in = s < p.nstars && p.chip[s] == c;
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (lane == 0) wsum[warp] = __popc(bal);
         __syncthreads();
-        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-            const int t = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0;
-            __syncthreads();
-            sh[threadIdx.x] += t;
-            __syncthreads();
+        int before = pos, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < warp) before += wsum[w];
+            total += wsum[w];
         }
-        if (in) mem[pos + sh[threadIdx.x] - 1] = s;
-        pos += sh[blockDim.x - 1];
+        if (in) mem[before + __popc(bal & ((1u << lane) - 1u))] = s;
+        pos += total;
         __syncthreads();
     }
-    // (b) bin range of the chip
+    __syncthreads();
+    // (b) bin range of the chip; member bins staged
     if (threadIdx.x == 0) { s_lo = 0x7fffffff; s_hi = -0x7fffffff; }
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         const int b = p.bin[mem[i]];
+        if (staged) sbin[i] = b;
         atomicMin(&s_lo, b);
         atomicMax(&s_hi, b);
     }
@@ -145,7 +177,8 @@ __global__ void __launch_bounds__(kVarThreads) chip_kernel(ChipParams p)
     // (c) stars per bin and bin offsets
     for (int b = threadIdx.x; b <= nbins; b += blockDim.x) bcount[b] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) atomicAdd(&bcount[p.bin[mem[i]] - lo], 1);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x)
+        atomicAdd(&bcount[(staged ? sbin[i] : p.bin[mem[i]]) - lo], 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         int acc = 0;
@@ -153,47 +186,62 @@ __global__ void __launch_bounds__(kVarThreads) chip_kernel(ChipParams p)
         bcount[nbins] = acc;
     }
     __syncthreads();
-    // (d) bin by bin, in star order (one thread per bin appends its stars)
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+    // (d) bin by bin, in star order: one warp per bin appends its stars (ballots)
+    for (int b = warp; b < nbins; b += nw) {
         int w = bcount[b];
-        for (int i = 0; i < cnt; ++i)
-            if (p.bin[mem[i]] - lo == b) srt[w++] = mem[i];
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            const bool hit = i < cnt && (staged ? sbin[i] : p.bin[mem[i]]) - lo == b;
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) srt[w + __popc(bal & ((1u << lane) - 1u))] = mem[i];
+            w += __popc(bal);
+        }
     }
     __syncthreads();
-    // (e) sigma clipping per bin, sequential over the bin's stars; (f) flags
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+    if (staged)
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) srms[i] = p.rms[srt[i]];
+    __syncthreads();
+    // (e) sigma clipping, one warp per bin, sums in the definition's order; (f) flags
+    for (int b = warp; b < nbins; b += nw) {
         const int a = bcount[b], k = bcount[b + 1] - a;
         if (k == 0) continue;
-        for (int i = 0; i < k; ++i) kp[a + i] = 1;
+        auto rv = [&](int i) { return staged ? srms[a + i] : p.rms[srt[a + i]]; };
+        for (int i = lane; i < k; i += 32) kp[a + i] = 1;
+        __syncwarp();
         double mu = 0.0, sd = 0.0;
         for (int it = 0; it <= p.iters; ++it) {
-            double s = 0.0;
+            double part = 0.0;
             int kc = 0;
-            for (int i = 0; i < k; ++i)
-                if (kp[a + i]) { s = __dadd_rn(s, p.rms[srt[a + i]]); ++kc; }
+            for (int i = lane; i < k; i += 32) {
+                const bool kept = kp[a + i];
+                part = __dadd_rn(part, kept ? rv(i) : 0.0);
+                kc += kept;
+            }
+            for (int o = 16; o > 0; o >>= 1) kc += __shfl_xor_sync(0xffffffffu, kc, o);
+            const double s = butterfly(part);
             mu = kc > 0 ? __ddiv_rn(s, (double)kc) : 0.0;
-            double v = 0.0;
-            for (int i = 0; i < k; ++i)
-                if (kp[a + i]) {
-                    const double d = __dsub_rn(p.rms[srt[a + i]], mu);
-                    v = __dadd_rn(v, __dmul_rn(d, d));
-                }
+            part = 0.0;
+            for (int i = lane; i < k; i += 32) {
+                const double d = __dsub_rn(rv(i), mu);
+                part = __dadd_rn(part, kp[a + i] ? __dmul_rn(d, d) : 0.0);
+            }
+            const double v = butterfly(part);
             sd = kc > 0 ? sqrt(__ddiv_rn(v, (double)kc)) : 0.0;
             if (it == p.iters) break;
             bool changed = false;
             const double lim = __dmul_rn(p.clip, sd);
-            for (int i = 0; i < k; ++i) {
-                const unsigned char nk = fabs(__dsub_rn(p.rms[srt[a + i]], mu)) <= lim;
+            for (int i = lane; i < k; i += 32) {
+                const unsigned char nk = fabs(__dsub_rn(rv(i), mu)) <= lim;
                 if (nk != kp[a + i]) { kp[a + i] = nk; changed = true; }
             }
-            if (!changed) break;
+            if (!__any_sync(0xffffffffu, changed)) break;
         }
         const double thr = __dadd_rn(mu, __dmul_rn(p.nsig, sd));
-        for (int i = 0; i < k; ++i) {
+        for (int i = lane; i < k; i += 32) {
             const int s = srt[a + i];
             p.mu[s] = mu;
             p.sd[s] = sd;
-            p.flag[s] = (unsigned char)(k >= p.min_stars && p.rms[s] > thr);
+            p.flag[s] = (unsigned char)(k >= p.min_stars && rv(i) > thr);
         }
     }
 }
@@ -279,7 +327,8 @@ extern "C" bls_status bls_variability(const bls_var_desc* d, void* cuda_stream, 
         if (kc != 2 && (x = cudaMemcpyAsync((void*)dchip, d->chip, ns * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
             return x;
         const int g = (int)((ns + kVarThreads - 1) / kVarThreads);
-        star_kernel<<<g, kVarThreads, 0, s>>>(doff, dm, d->nstars, mag, rms, bin, err);
+        const int gw = (int)((ns * 32 + kVarThreads - 1) / kVarThreads);   // one warp per star
+        star_kernel<<<gw, kVarThreads, 0, s>>>(doff, dm, d->nstars, mag, rms, bin, err);
         chip_count_kernel<<<g, kVarThreads, 0, s>>>(dchip, d->nstars, d->nchips,
                                                    reinterpret_cast<int*>(buf + o_cnt), err);
         chip_scan_kernel<<<1, kVarThreads, 0, s>>>(reinterpret_cast<int*>(buf + o_cnt), d->nchips,
@@ -301,7 +350,10 @@ extern "C" bls_status bls_variability(const bls_var_desc* d, void* cuda_stream, 
         cp.sd = reinterpret_cast<double*>(buf + o_sd);
         cp.flag = buf + o_flag;
         cp.err = err;
-        chip_kernel<<<d->nchips, kVarThreads, 0, s>>>(cp);
+        if ((x = cudaFuncSetAttribute(chip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kChipSmem)) != cudaSuccess)
+            return x;
+        chip_kernel<<<d->nchips, kVarThreads, kChipSmem, s>>>(cp);
         pack_kernel<<<g, kVarThreads, 0, s>>>(d->nstars, mag, rms, bin, cp.mu, cp.sd, cp.flag, dout);
         if ((x = cudaGetLastError()) != cudaSuccess) return x;
         if (kout != 2 && (x = cudaMemcpyAsync(out, dout, ns * sizeof(bls_var_star), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
