@@ -1,5 +1,6 @@
-"""ctypes binding of ``bls_oracle.c``, ``window_oracle.c``, ``shape_oracle.c`` and
-``variability_oracle.c``, the plain FP64 oracles (test infrastructure).
+"""ctypes binding of ``bls_oracle.c``, ``window_oracle.c``, ``shape_oracle.c``,
+``variability_oracle.c`` and ``unbinned_oracle.c``, the plain FP64 oracles (test
+infrastructure).
 
 Every function mirrors one C function; see that file for the definition each one
 follows (Sec. 2.2.2 of the paper and the BLS method it cites).
@@ -18,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bls_oracle.c")
 _SRCS = [_SRC] + [os.path.join(_HERE, f) for f in ("window_oracle.c", "shape_oracle.c",
-                                                  "variability_oracle.c")]
+                                                  "variability_oracle.c", "unbinned_oracle.c")]
 _LIB = os.path.join(_HERE, "libbls_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -50,6 +51,13 @@ class _Peak(C.Structure):
 class _Shape(C.Structure):
     _fields_ = [("index", C.c_int), ("power", C.c_double), ("centre", C.c_double),
                 ("width", C.c_double), ("ingress", C.c_double), ("depth", C.c_double)]
+
+
+class _UPeak(C.Structure):
+    _fields_ = [("j", C.c_int), ("first", C.c_int), ("len", C.c_int), ("first_point", C.c_int),
+                ("freq", C.c_double), ("power", C.c_double), ("sr", C.c_double),
+                ("depth", C.c_double), ("epoch", C.c_double), ("duration", C.c_double),
+                ("snr", C.c_double)]
 
 
 class _Curve(C.Structure):
@@ -103,6 +111,12 @@ def _load():
             lib.oracle_star_stats.argtypes = [I, P, C.POINTER(D), C.POINTER(D)]
             lib.oracle_clip.argtypes = [I, P, D, I, C.POINTER(D), C.POINTER(D)]
             lib.oracle_variability.argtypes = [I, P, P, P, I, D, I, D, I, P, P, P, P, P, P]
+            lib.oracle_fx_shift.argtypes = [D]
+            lib.oracle_ubls_keys.argtypes = [I, P, D, D, P]
+            lib.oracle_ubls_power.argtypes = [I, P, P, P, D, D, D, D, I, C.POINTER(I), C.POINTER(I),
+                                              C.POINTER(D), C.POINTER(D), P]
+            lib.oracle_ubls_power.restype = D
+            lib.oracle_ubls.argtypes = [I, P, P, P, I, P, D, D, D, D, I, P, C.POINTER(_UPeak)]
             _lib = lib
     return _lib
 
@@ -332,3 +346,58 @@ def variability(off, m, chip, nchips: int, clip: float = 3.0, iters: int = 5,
     if rc != 0:
         raise ValueError("oracle_variability: bad arguments")
     return out
+
+
+@dataclass
+class UnbinnedPeak:
+    j: int
+    first: int
+    len: int
+    first_point: int
+    freq: float
+    power: float
+    sr: float
+    depth: float
+    epoch: float
+    duration: float
+    snr: float
+
+
+def fx_shift(dtmax: float) -> int:
+    return _load().oracle_fx_shift(float(dtmax))
+
+
+def ubls_keys(dt, dtmax: float, f: float) -> np.ndarray:
+    """32-bit fixed-point phase keys of every point (``oracle_ubls_keys``)."""
+    dt = np.ascontiguousarray(dt, dtype=np.float64)
+    key = np.zeros(len(dt), np.uint32)
+    _load().oracle_ubls_keys(len(dt), _p(dt), dtmax, f, _p(key))
+    return key
+
+
+def ubls_power(dt, w, x, dtmax: float, f: float, qmin: float, qmax: float, sign: int = 0):
+    """Best unbinned box of one frequency: (P, first, len, r, s, order)."""
+    dt, w, x = (np.ascontiguousarray(a, dtype=np.float64) for a in (dt, w, x))
+    a, l = C.c_int(), C.c_int()
+    r, s = C.c_double(), C.c_double()
+    order = np.zeros(len(dt), np.int32)
+    P = _load().oracle_ubls_power(len(dt), _p(dt), _p(w), _p(x), dtmax, f, qmin, qmax, sign,
+                                  C.byref(a), C.byref(l), C.byref(r), C.byref(s), _p(order))
+    return P, a.value, l.value, r.value, s.value, order
+
+
+def ubls(t, y, dy, qmin: float, qmax: float, *, freqs=None, fmin=0.0, df=0.0, nf=None,
+         sign: int = 0):
+    """Unbinned periodogram (``oracle_ubls``): (P[nf], UnbinnedPeak)."""
+    t, y, dy = _arrays(t, y, dy)
+    if freqs is not None:
+        freqs = np.ascontiguousarray(freqs, dtype=np.float64)
+        nf = len(freqs)
+    P = np.zeros(nf)
+    pk = _UPeak()
+    rc = _load().oracle_ubls(len(t), _p(t), _p(y), _p(dy), nf, _p(freqs), fmin, df, qmin, qmax,
+                             sign, _p(P), C.byref(pk))
+    if rc != 0:
+        raise ValueError(f"oracle_ubls failed ({rc})")
+    return P, UnbinnedPeak(pk.j, pk.first, pk.len, pk.first_point, pk.freq, pk.power, pk.sr,
+                           pk.depth, pk.epoch, pk.duration, pk.snr)

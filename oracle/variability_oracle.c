@@ -51,7 +51,7 @@ static double sum32(int k, const double* v)
 /* mean and population RMS of one light curve (two passes) */
 void oracle_star_stats(int n, const float* m, double* mag, double* rms)
 {
-    double* v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* v = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
     for (int i = 0; i < n; ++i) v[i] = (double)m[i];
     double mu = sum32(n, v) / (double)n;
     for (int i = 0; i < n; ++i) {
