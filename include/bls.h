@@ -76,7 +76,17 @@ enum {
 /* Kernel family. */
 enum {
     BLS_ALGO_TILED = 0,     /* default: batched persistent fold-bin-sweep kernels */
-    BLS_ALGO_PLAIN_F64 = 1  /* baseline: one launch per curve, one thread per frequency, FP64 */
+    BLS_ALGO_PLAIN_F64 = 1, /* baseline: one launch per curve, one thread per frequency, FP64 */
+    BLS_ALGO_UNBINNED = 2   /* unbinned (edge-to-edge) boxes: at every frequency the points are
+                               ordered by phase and every cyclic run of consecutive points whose
+                               phase extent lies in [qmin, qmax] is a box.  Phases are 64-bit
+                               fixed-point fractions: with s = 34 - (L+1)/2 (dtmax < 2^L, capped
+                               to [1, 62-L]), DT = RN_int(dt 2^s), F = RN_int(f 2^(64-s)), the key
+                               is ((DT F) mod 2^64) >> 32; order (key, point); extent
+                               (key_last - key_first) mod 2^32 in [ceil(qmin 2^32),
+                               floor(qmax 2^32)].  Peaks report i1 = the run's first position in
+                               phase order and k = its number of points.  Up to 8192 points per
+                               curve; the plan's qmin/qmax apply to every curve. */
 };
 
 typedef struct {

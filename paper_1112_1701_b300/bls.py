@@ -25,7 +25,7 @@ ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL, ERR_CANCELLED = -1,
 PHASE = {"fx64": 0, "f64": 1, "f32": 2, "df32": 3}
 SUM = {"f32": 0, "kahan": 1}
 SIGN = {"dips": 0, "both": 1}
-ALGO = {"tiled": 0, "plain_f64": 1}
+ALGO = {"tiled": 0, "plain_f64": 1, "unbinned": 2}
 
 
 class BLSError(RuntimeError):
@@ -205,6 +205,17 @@ def _struct(c: CurveInput, keep: list) -> CurveStruct:
                        float(c.df), int(c.nb), float(c.qmin), float(c.qmax))
 
 
+def _check_spectrum(spectrum, arr) -> None:
+    """The spectrum output must hold the sum of the curves' frequency counts (the library
+    writes that many floats)."""
+    if spectrum is None:
+        return
+    need = sum(int(c.nf) for c in arr)
+    have = int(spectrum.numel()) if hasattr(spectrum, "numel") else int(np.asarray(spectrum).size)
+    if have < need:
+        raise ValueError(f"spectrum holds {have} values, the curves have {need} frequencies")
+
+
 def curves_from_batch(batch, device=None, pinned: bool = False) -> List[CurveInput]:
     """CurveInputs of a synth.Batch, packed into contiguous arrays (one copy per array
     for the whole batch).  With ``device`` (e.g. "cuda") the arrays are torch tensors
@@ -320,6 +331,7 @@ class Plan:
         """Peaks of every curve: structured array of shape (ncurves, topk)."""
         keep: list = []
         arr = (CurveStruct * len(curves))(*[_struct(c, keep) for c in curves])
+        _check_spectrum(spectrum, arr)
         out = np.zeros((len(curves), self.topk), dtype=PEAK_DTYPE)
         _check(lib().bls_search(self._h, arr, len(curves), out.ctypes.data, _ptr(spectrum)))
         return out
@@ -332,6 +344,7 @@ class Plan:
         arr = (CurveStruct * len(curves))(*[_struct(c, keep) for c in curves])
         out = np.zeros((len(curves), self.topk), dtype=PEAK_DTYPE)
         shapes = np.zeros((len(curves), self.topk), dtype=SHAPE_DTYPE)
+        _check_spectrum(spectrum, arr)
         g = ShapeGrid(ncentre, nwidth, ningress, width_lo, width_hi, ingress_max)
         _check(lib().bls_search_shapes(self._h, arr, len(curves), out.ctypes.data,
                                        _ptr(spectrum), C.byref(g), shapes.ctypes.data))

@@ -24,7 +24,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["bls_kernels.cu", "bls_static.cu", "bls_window.cu", "bls_shape.cu",
-              "bls_variability.cu"]
+              "bls_variability.cu", "bls_unbinned.cu"]
 CPP_SOURCES = ["bls_api.cpp", "bls_server.cpp"]
 PROBES_SRC = "probes.cu"
 PROBES = os.path.join(PKG, "bls_probes")

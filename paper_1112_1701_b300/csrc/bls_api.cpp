@@ -248,9 +248,20 @@ size_t curve_bytes(const bls_plan_impl* P, const CurveSpec& c, bool host_spec)
     if (c.freqs && !c.f_dev) b += (size_t)c.nf * 8;
     if (host_spec) b += (size_t)c.nf * 4;
     if (P->d.algo == BLS_ALGO_PLAIN_F64) b += n2 * 16;
+    if (P->d.algo == BLS_ALGO_UNBINNED) b += (size_t)c.nf * sizeof(int2);
     return b;
 }
 
+
+// Run extents of the unbinned search in units of 2^-32 cycle: QMIN = ceil(qmin 2^32),
+// QMAX = floor(qmax 2^32), capped at 2^32 - 1.
+void ubls_extents(double qmin, double qmax, unsigned* QMIN, unsigned* QMAX)
+{
+    const double two32 = 4294967296.0;
+    const double lo = ceil(qmin * two32), hi = floor(qmax * two32);
+    *QMIN = lo >= two32 ? 0xffffffffu : (unsigned)lo;
+    *QMAX = hi >= two32 ? 0xffffffffu : (unsigned)hi;
+}
 
 // One launch group: curves [g0, g1) of `specs`.  Writes peaks to out (host), optionally the
 // SR spectra, and (diagnostics) the per-frequency powers into res_dump.
@@ -269,6 +280,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     cudaStream_t st = P->stream;
     cudaError_t e;
     const bool tiled = P->d.algo == BLS_ALGO_TILED;
+    const bool unbinned = P->d.algo == BLS_ALGO_UNBINNED;
 
     // ---- layout
     std::vector<long long> pt_off(nc), res_off(nc), raw_off(nc), f_off(nc);
@@ -290,6 +302,11 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         plain_hist = std::max(plain_hist, (size_t)2 * s.nb * s.nf * 8);
     }
     npts += 2;  // slack so a staged chunk never reads past the pool
+    int nmax = 2;
+    for (int c = 0; c < nc; ++c) nmax = std::max(nmax, specs[g0 + c].n);
+    if (unbinned && nmax > kUblsMaxPoints)
+        return set_error(BLS_ERR_INVALID, "the unbinned search takes up to %d points per curve (got %d)",
+                         kUblsMaxPoints, nmax);
 
     // fold classes (block size per nb)
     std::vector<FoldGeom> geoms;
@@ -338,6 +355,10 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         BLS_ENSURE(P->counter, cls.size() * sizeof(int) + 64, "allocating counters")
         BLS_ENSURE(P->h_ranges, nr * sizeof(TileRange), "pinned work list")
         BLS_ENSURE(P->h_prefix, (nr + cls.size()) * sizeof(long long), "pinned work list")
+    } else if (unbinned) {
+        BLS_ENSURE(P->runs, (size_t)nres * sizeof(int2), "allocating runs")
+        BLS_ENSURE(P->prefix, (nr + 1) * sizeof(long long), "allocating work list")
+        BLS_ENSURE(P->h_prefix, (nr + 1) * sizeof(long long), "pinned work list")
     } else {
         BLS_ENSURE(P->w64, (size_t)npts * 8, "allocating w64")
         BLS_ENSURE(P->wx64, (size_t)npts * 8, "allocating wx64")
@@ -400,6 +421,30 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
             totals[q] = acc;
         }
     }
+    long long utiles = 0;
+    UblsParams up = {};
+    if (unbinned) {
+        long long* hp = P->h_prefix.as<long long>();
+        for (int c = 0; c < nc; ++c) {
+            hp[c] = utiles;
+            utiles += (specs[g0 + c].nf + ubls_tile() - 1) / ubls_tile();
+        }
+        hp[nc] = utiles;
+        pp = (size_t)nc + 1;
+        up.curves = P->cdesc.as<CurveDesc>();
+        up.ncurves = nc;
+        up.tile_prefix = P->prefix.as<long long>();
+        up.res_base = P->res.as<float>();
+        up.runs = P->runs.as<int2>();
+        up.peaks = P->peaks.as<DevPeak>();
+        up.spectrum = spectrum ? (spectrum_dev ? spectrum : P->spec.as<float>()) : nullptr;
+        up.topk = topk;
+        up.sign = P->d.sign;
+        ubls_extents(P->d.qmin, P->d.qmax, &up.QMIN, &up.QMAX);
+        up.nmax = nmax;
+        up.M = 1;
+        while (up.M < nmax) up.M <<= 1;
+    }
     std::vector<int> grids(cls.size());
     for (size_t q = 0; q < cls.size(); ++q) {
         const int bps = fold_blocks_per_sm(geoms[q].T, geoms[q].smem, P->d.phase,
@@ -442,7 +487,10 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
             return x;
         if ((x = cudaMemsetAsync(P->err.p, 0, 64, st)) != cudaSuccess) return x;
         if (prof) record(P->ev[0]);
-        if ((x = launch_prep(P->cdesc.as<CurveDesc>(), nullptr, nc, P->err.as<int>(), P->d.phase, st)) != cudaSuccess) return x;
+        // (the unbinned search reads the fixed-point offsets of the FX64 layout)
+        if ((x = launch_prep(P->cdesc.as<CurveDesc>(), nullptr, nc, P->err.as<int>(),
+                             unbinned ? kPhaseFX64 : P->d.phase, st)) != cudaSuccess)
+            return x;
         ++launches;
         if (prof) record(P->ev[1]);
         if (tiled) {
@@ -467,6 +515,12 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
                 ++launches;
                 ++fold_launches;
             }
+        } else if (unbinned) {
+            if ((x = cudaMemcpyAsync(P->prefix.p, P->h_prefix.p, pp * sizeof(long long), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return x;
+            if ((x = launch_ubls(up, utiles, st)) != cudaSuccess) return x;
+            ++launches;
+            ++fold_launches;
         } else {
             if ((x = launch_prep_f64(P->cdesc.as<CurveDesc>(), nc, P->w64.as<double>(), P->wx64.as<double>(), st)) != cudaSuccess)
                 return x;
@@ -480,7 +534,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
             }
         }
         if (prof) record(P->ev[2]);
-        if ((x = launch_reduce(rp, nc, st)) != cudaSuccess) return x;
+        if ((x = unbinned ? launch_ubls_reduce(up, st) : launch_reduce(rp, nc, st)) != cudaSuccess) return x;
         ++launches;
         if (shape) {
             ShapeParams sp;
@@ -530,8 +584,9 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
             put(P->h_ranges.p, nr * sizeof(TileRange));
             put(P->h_prefix.p, pp * sizeof(long long));
         }
+        if (unbinned) put(P->h_prefix.p, pp * sizeof(long long));
         void* bufs[] = {P->pts.p, P->res.p, P->peaks.p, P->spec.p, P->err.p, P->h_peaks.p, P->h_err.p, P->ranges.p,
-                        P->shapes.p, P->h_shapes.p};
+                        P->shapes.p, P->h_shapes.p, P->runs.p, P->prefix.p};
         put(bufs, sizeof(bufs));
         if (P->graph && sig == P->graph_sig) {
             if ((e = cudaGraphLaunch(P->graph, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
@@ -683,7 +738,7 @@ bls_status bls_plan_create(const bls_plan_desc* desc, void* cuda_stream, bls_pla
     if (d.phase < 0 || d.phase > 3) return set_error(BLS_ERR_INVALID, "phase = %d", d.phase);
     if (d.sum < 0 || d.sum > 1) return set_error(BLS_ERR_INVALID, "sum = %d", d.sum);
     if (d.sign < 0 || d.sign > 1) return set_error(BLS_ERR_INVALID, "sign = %d", d.sign);
-    if (d.algo < 0 || d.algo > 1) return set_error(BLS_ERR_INVALID, "algo = %d", d.algo);
+    if (d.algo < 0 || d.algo > 2) return set_error(BLS_ERR_INVALID, "algo = %d", d.algo);
     if (d.freqs_per_block < 0 || d.freqs_per_block > fold_sweep_max_threads() || (d.freqs_per_block % 16) != 0)
         return set_error(BLS_ERR_INVALID, "freqs_per_block = %d, need a multiple of 16 up to %d", d.freqs_per_block,
                          fold_sweep_max_threads());
@@ -838,6 +893,8 @@ bls_status bls_search_shapes(bls_plan* P, const bls_curve* curves, int ncurves, 
                              float* spectrum, const bls_shape_grid* grid, bls_shape* shapes)
 {
     if (!P || !shapes) return set_error(BLS_ERR_INVALID, "NULL plan or shapes");
+    if (P->d.algo == BLS_ALGO_UNBINNED)
+        return set_error(BLS_ERR_INVALID, "the trapezoid refit starts from binned boxes (plan algo is unbinned)");
     ShapeReq r;
     r.nc = grid && grid->ncentre ? grid->ncentre : 17;
     r.nw = grid && grid->nwidth ? grid->nwidth : 13;

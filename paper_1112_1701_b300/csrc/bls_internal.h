@@ -84,6 +84,25 @@ struct ShapeParams {
 
 cudaError_t launch_shape(const ShapeParams& p, int ncurves, cudaStream_t s);
 
+// Unbinned (edge-to-edge) search of one launch group.
+struct UblsParams {
+    const CurveDesc* curves;
+    int ncurves;
+    const long long* tile_prefix;   // ncurves + 1: frequency tiles before curve c
+    const float* res_base;          // pool of the per-frequency powers
+    int2* runs;                     // per frequency (indexed like res): best run (start, len)
+    DevPeak* peaks;                 // topk per curve
+    float* spectrum;                // optional (device): SR per frequency, at spec_off
+    int topk, sign;
+    unsigned QMIN, QMAX;            // run extents in units of 2^-32 cycle
+    int nmax, M;                    // largest curve of the group and the power of two >= it
+};
+
+cudaError_t launch_ubls(const UblsParams& p, long long nitems, cudaStream_t s);
+cudaError_t launch_ubls_reduce(const UblsParams& p, cudaStream_t s);
+size_t ubls_smem_bytes(int nmax);
+int ubls_tile();
+
 struct ReduceParams {
     const CurveDesc* curves;
     const int* slots;          // curve of block b = slots[b] (nullptr: b)

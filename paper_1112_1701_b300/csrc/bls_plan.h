@@ -74,7 +74,7 @@ struct bls_plan_impl {
     DevBuf raw_t, raw_y, raw_dy, raw_f;   // staging of host inputs
     DevBuf pts, dt64, w64, wx64;          // prepared points
     DevBuf cdesc, ranges, prefix, counter, err;
-    DevBuf res, peaks, spec, plain_hist, jsbuf, binsbuf, shapes;
+    DevBuf res, peaks, spec, plain_hist, jsbuf, binsbuf, shapes, runs;
     // host staging (pinned)
     HostBuf h_cdesc, h_ranges, h_prefix, h_peaks, h_err, h_shapes;
 
@@ -98,6 +98,8 @@ struct bls_plan_impl {
 bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* out,
                          const int* kinds = nullptr);
 int ptr_kind(const void* p);
+void ubls_extents(double qmin, double qmax, unsigned* QMIN, unsigned* QMAX);
+constexpr int kUblsMaxPoints = 8192;   // the unbinned search sorts a curve in shared memory
 
 // A validated trapezoid-refit request of bls_search_shapes.
 struct ShapeReq {
