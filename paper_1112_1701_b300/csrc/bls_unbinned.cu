@@ -12,10 +12,11 @@
 //
 // Search kernel: one block per (curve, tile of kTile frequencies).  For each frequency the
 // block forms the keys (key << 32 | index) in shared memory, sorts them with a bitonic
-// network, gathers (w, w x) in phase order, and gives each thread a set of run starts: it
-// extends the run point by point in FP32 while the extent allows, keeping the largest P
-// (ties to the smaller start, then the shorter run).  A block argmax gives P(f_j) and the
-// best run of the frequency.
+// network, and builds prefix sums of (w, w x) in phase order (FP64, stored as double-float
+// pairs).  Each thread takes a range of run starts; the admissible ends of a start (extent
+// within [QMIN, QMAX]) only move right as the start does, so two pointers give them, and
+// every run's sums are independent prefix differences.  The largest P wins (ties to the
+// smaller start, then the shorter run); a block argmax gives P(f_j) and its run.
 //
 // Reduce kernel: one block per curve: the top-k local maxima of P(f_j) (as in the binned
 // search), the signal detection efficiency, and for each kept frequency the run's FP64
@@ -27,7 +28,7 @@
 namespace blsgpu {
 namespace {
 
-constexpr int kUThreads = 256;
+constexpr int kUThreads = 512;
 constexpr int kTile = 16;
 
 __host__ __device__ __forceinline__ int shift_of(double dtmax)
@@ -89,13 +90,39 @@ __device__ __forceinline__ bool run_ahead(float pa, int sa, int la, float pb, in
     return pa > pb || (pa == pb && (sa < sb || (sa == sb && la < lb)));
 }
 
+// Double-float value (hi + lo) of an FP64 number.
+__device__ __forceinline__ float2 split_df(double v)
+{
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(__dsub_rn(v, (double)hi)));
+}
+
+// Error-free sum of two floats (Knuth's two-sum): hi + lo == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& hi, float& lo)
+{
+    hi = a + b;
+    const float bb = hi - a;
+    lo = (a - (hi - bb)) + (b - bb);
+}
+
+// Score of one run with sums (r, s): P = s^2 / (r(1-r)), dips only unless sign; 0 if the
+// run does not count.  An approximate division suffices: P only ranks the runs of a
+// frequency (the kept run is refitted in FP64).
+__device__ __forceinline__ float run_score(float r, float s, int sign)
+{
+    const float d = fmaf(-r, r, r);
+    if (!(d > 0.0f) || (!sign && !(s < 0.0f))) return 0.0f;
+    return __fdividef(s * s, d);
+}
+
 __global__ void __launch_bounds__(kUThreads) ubls_kernel(UblsParams p)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ float sP[kUThreads / 32];
     __shared__ int sS[kUThreads / 32], sL[kUThreads / 32];
+    __shared__ double sred[2 * kUThreads];
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(dsm);
-    float2* sw = reinterpret_cast<float2*>(keys + p.M);
+    float4* C = reinterpret_cast<float4*>(keys + p.M);      // n + 1 prefix entries
     // work item -> (curve, tile)
     const long long it = blockIdx.x;
     int lo = 0, hi = p.ncurves;
@@ -109,32 +136,104 @@ __global__ void __launch_bounds__(kUThreads) ubls_kernel(UblsParams p)
     int M = 1;
     while (M < n) M <<= 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nt = blockDim.x;
+    const int ch = (n + nt - 1) / nt;                 // positions per thread
+    const int q0 = min(n, (int)threadIdx.x * ch), q1 = min(n, q0 + ch);
     for (int j = j0; j < min(j0 + kTile, cd.nf); ++j) {
         const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
         sorted_keys(cd, fixed_freq(f, cd.dtmax), keys, M);
-        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        // prefix sums in phase order: FP64 over each thread's positions, a scan of the
+        // thread totals, then double-float values in shared memory
+        double tw = 0.0, tx = 0.0;
+        for (int q = q0; q < q1; ++q) {
             float w, wx;
             point_weights(cd, (int)(keys[q] & 0xffffffffu), w, wx);
-            sw[q] = make_float2(w, wx);
+            tw = __dadd_rn(tw, (double)w);
+            tx = __dadd_rn(tx, (double)wx);
+        }
+        // exclusive scan of the thread totals: inclusive scans within warps (shuffles),
+        // then the warp totals in order
+        double iw = tw, ix = tx;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double uw = __shfl_up_sync(0xffffffffu, iw, o);
+            const double ux = __shfl_up_sync(0xffffffffu, ix, o);
+            if (lane >= o) { iw = __dadd_rn(iw, uw); ix = __dadd_rn(ix, ux); }
+        }
+        if (lane == 31) { sred[warp] = iw; sred[nt + warp] = ix; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double aw = 0.0, ax = 0.0;
+            for (int w = 0; w < nt / 32; ++w) {
+                const double vw = sred[w], vx = sred[nt + w];
+                sred[w] = aw;
+                sred[nt + w] = ax;
+                aw = __dadd_rn(aw, vw);
+                ax = __dadd_rn(ax, vx);
+            }
+            const float2 W = split_df(aw), X = split_df(ax);
+            C[n] = make_float4(W.x, W.y, X.x, X.y);
         }
         __syncthreads();
+        const double base_w = __dsub_rn(__dadd_rn(sred[warp], iw), tw);
+        const double base_x = __dsub_rn(__dadd_rn(sred[nt + warp], ix), tx);
+        __syncthreads();
+        {
+            double aw = base_w, ax = base_x;
+            for (int q = q0; q < q1; ++q) {
+                const float2 W = split_df(aw), X = split_df(ax);
+                C[q] = make_float4(W.x, W.y, X.x, X.y);
+                float w, wx;
+                point_weights(cd, (int)(keys[q] & 0xffffffffu), w, wx);
+                aw = __dadd_rn(aw, (double)w);
+                ax = __dadd_rn(ax, (double)wx);
+            }
+        }
+        __syncthreads();
+        const float4 T = C[n];
+        // runs: starts dealt round-robin to the threads (phases clump, so contiguous ranges
+        // would leave the threads unevenly loaded); the ends [emin, emax] of a start
+        // (unwrapped positions; extents within [QMIN, QMAX], at most n - 1 points) by
+        // binary search, extents growing with the end.  Run sums are prefix differences;
+        // runs past the end add the totals with an error-free sum, so both cases keep
+        // double-float accuracy.
         float bp = 0.0f;
         int bs = 0x7fffffff, bl = 0x7fffffff;
-        for (int a = threadIdx.x; a < n; a += blockDim.x) {
+        for (int a = threadIdx.x; a < n; a += nt) {
             const unsigned k0 = (unsigned)(keys[a] >> 32);
-            float r = 0.0f, s = 0.0f;
-            for (int l = 1; l <= n - 1; ++l) {
-                int q = a + l - 1;
-                if (q >= n) q -= n;
-                const unsigned E = (unsigned)(keys[q] >> 32) - k0;
-                if (E > p.QMAX) break;
-                const float2 v = sw[q];
-                r += v.x;
-                s += v.y;
-                if (E < p.QMIN || !(r > 0.0f && r < 1.0f)) continue;
-                if (!p.sign && !(s < 0.0f)) continue;
-                const float P = s * s / (r * (1.0f - r));
-                if (run_ahead(P, a, l, bp, bs, bl)) { bp = P; bs = a; bl = l; }
+            auto ext = [&](int e) { return (unsigned)(keys[e < n ? e : e - n] >> 32) - k0; };
+            // largest e in [a, a + n - 2] with ext(e) <= QMAX (ext(a) = 0)
+            int lo2 = a, hi2 = a + n - 1;            // ext(lo2) <= QMAX; hi2 out of range
+            while (hi2 - lo2 > 1) {
+                const int mid = (lo2 + hi2) >> 1;
+                if (ext(mid) <= p.QMAX) lo2 = mid; else hi2 = mid;
+            }
+            const int emax = lo2;
+            // smallest e in [a, emax] with ext(e) >= QMIN
+            int lo1 = a - 1, hi1 = emax + 1;          // ext(hi1) >= QMIN or hi1 past emax
+            while (hi1 - lo1 > 1) {
+                const int mid = (lo1 + hi1) >> 1;
+                if (ext(mid) >= p.QMIN) hi1 = mid; else lo1 = mid;
+            }
+            const int emin = hi1;
+            const float4 ca = C[a];
+            const int e1 = min(emax, n - 1);
+#pragma unroll 4
+            for (int e = emin; e <= e1; ++e) {            // runs inside [a, n)
+                const float4 cb = C[e + 1];
+                const float r = (cb.x - ca.x) + (cb.y - ca.y);
+                const float s = (cb.z - ca.z) + (cb.w - ca.w);
+                const float P = run_score(r, s, p.sign);
+                if (P > bp) { bp = P; bs = a; bl = e - a + 1; }
+            }
+            for (int e = max(emin, n); e <= emax; ++e) {  // runs that wrap past the end
+                const float4 c = C[e + 1 - n];
+                float wh, wl, xh, xl;
+                two_sum(T.x, c.x, wh, wl);
+                two_sum(T.z, c.z, xh, xl);
+                const float r = (wh - ca.x) + ((wl + T.y + c.y) - ca.y);
+                const float s = (xh - ca.z) + ((xl + T.w + c.w) - ca.w);
+                const float P = run_score(r, s, p.sign);
+                if (P > bp) { bp = P; bs = a; bl = e - a + 1; }
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -296,7 +395,7 @@ size_t ubls_smem_bytes(int nmax)
 {
     int M = 1;
     while (M < nmax) M <<= 1;
-    return (size_t)M * sizeof(unsigned long long) + (size_t)nmax * sizeof(float2);
+    return (size_t)M * sizeof(unsigned long long) + (size_t)(nmax + 1) * sizeof(float4);
 }
 
 int ubls_tile() { return kTile; }
