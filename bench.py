@@ -220,7 +220,8 @@ def run_serving(args):
     units = sum(len(c.t) * g.nf for c, g in zip(b.curves, b.grids))
 
     def serve(arrivals):
-        with bls.Plan(nb=200, qmin=QMIN, qmax=QMAX, topk=1) as p:
+        with bls.Plan(nb=200, qmin=QMIN, qmax=QMAX, topk=1,
+                      step_point_freqs=args.step_units) as p:
             warm = [p.submit(r) for r in reqs[:8]]
             for tk in warm:
                 p.poll(tk, timeout_ms=600000)
@@ -679,8 +680,10 @@ def main():
                     help="curves of the plain FP64 baseline timing (0 = skip)")
     ap.add_argument("--serving", action="store_true", help="run the serving benchmark")
     ap.add_argument("--requests", type=int, default=4000)
-    ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.7, 0.9])
+    ap.add_argument("--loads", type=float, nargs="*", default=[0.5, 0.7, 0.9])
     ap.add_argument("--plain-sample", type=int, default=60)
+    ap.add_argument("--step-units", type=int, default=0,
+                    help="serving: point x frequency units per scheduler step (0: default)")
     ap.add_argument("--precision", action="store_true", help="run the precision study")
     ap.add_argument("--prec-curves", type=int, default=16)
     ap.add_argument("--nf-prec", type=int, default=200000)

@@ -7,11 +7,13 @@
 //   2. gives every active request its share of a fixed amount of work (point x frequency
 //      units, box evaluations counted at their relative cost) as its next frequency tiles,
 //      and runs all of them in one persistent fold-bin-sweep launch per block-size class;
-//   3. reduces the requests whose last tile ran, copies their peaks back and frees their
-//      memory.
-// Requests that arrive while others are on the GPU join at the next step, so their work
-// overlaps on the device (iteration-level continuous batching); no kernel waits on the
-// host.  The per-frequency arithmetic is the batched search's, so a request's result is
+//   3. reduces the requests whose last tile ran and copies their peaks back.
+// Steps are pipelined two deep: after enqueueing step k the thread waits for step k-1 and
+// retires its finished requests (results, memory), so the GPU works on step k while the
+// host finishes k-1 and prepares k+1.  Admission copies run on a copy stream (the curve
+// arrays are pageable) that the compute stream waits for.  Requests that arrive while
+// others are on the GPU join at the next step, so their work overlaps on the device
+// (iteration-level continuous batching); no kernel waits on the host.  The per-frequency arithmetic is the batched search's, so a request's result is
 // the same alone and in a mix.
 #include <algorithm>
 #include <chrono>
@@ -58,6 +60,7 @@ struct Request {
     double tile_cost = 0.0;
     RState state = RState::Queued;
     bool cancel = false;
+    bool finishing = false;       // its last tiles are in the step in flight
     bls_status status = BLS_OK;
     std::string error;
     std::vector<bls_peak> peaks;
@@ -86,10 +89,27 @@ struct Server {
     std::string fatal;                       // set when the device became unusable
 
     DevBuf cdesc, ranges, prefix, counter, err, dslots, dpeaks;
-    HostBuf h_cdesc, h_ranges, h_prefix, h_slots, h_peaks, h_err;
+    HostBuf h_cdesc;
+    // host staging of a step, one set per pipeline parity
+    struct StepBufs { HostBuf h_ranges, h_prefix, h_slots, h_peaks, h_err; } sb[2];
+    cudaEvent_t ev_step[2] = {};
+    int parity = 0;
+    // the step in flight
+    bool inflight = false;
+    int fl_parity = 0;
+    std::vector<Request*> fl_finishing;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copy = nullptr;
+    // requests of different block sizes run in different fold-sweep launches; these
+    // streams let the launches of one step share the GPU instead of queueing behind each
+    // other (each forks from and joins back into `stream`)
+    static constexpr int kClassStreams = 4;
+    cudaStream_t cls_stream[kClassStreams] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kClassStreams] = {};
 
     void run();
     bool step();
+    bool retire_inflight();
     void fail_all(const std::string& why);
 };
 
@@ -113,7 +133,7 @@ void Server::run()
             std::unique_lock<std::mutex> lk(mu);
             cv_work.wait(lk, [&] {
                 if (stop) return true;
-                if (!queue.empty()) return true;
+                if (inflight || !queue.empty()) return true;
                 for (Request* r : slots) if (r) return true;
                 return false;
             });
@@ -132,7 +152,7 @@ bool Server::step()
         std::lock_guard<std::mutex> lk(mu);
         for (int s = 0; s < max_active; ++s) {
             Request* r = slots[s];
-            if (r && r->cancel) { retire_cancel.push_back(r); slots[s] = nullptr; }
+            if (r && r->cancel && !r->finishing) { retire_cancel.push_back(r); slots[s] = nullptr; }
         }
         // admission: first come, first served, while a slot is free and memory fits
         while (!queue.empty()) {
@@ -170,11 +190,14 @@ bool Server::step()
     }
 
     // ---- admit: device memory, input copies, descriptors, prep
+    const int par = parity;
+    parity ^= 1;
+    StepBufs& B = sb[par];
     CurveDesc* hd = h_cdesc.as<CurveDesc>();
-    int* hs = h_slots.as<int>();
+    int* hs = B.h_slots.as<int>();
     int nadm = 0;
     for (Request* r : admitted) {
-        e = cudaMallocAsync(&r->dmem, r->bytes, stream);
+        e = cudaMallocAsync(&r->dmem, r->bytes, copy_stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             std::lock_guard<std::mutex> lk(mu);
@@ -200,10 +223,10 @@ bool Server::step()
         float4* dpts = reinterpret_cast<float4*>(carve((size_t)(n2 + 2) * 16));
         double* ddt = reinterpret_cast<double*>(carve((size_t)(n2 + 2) * 8));
         float* dres = reinterpret_cast<float*>(carve((size_t)s.nf * 4));
-        cudaMemcpyAsync(dt_raw, r->t.data(), (size_t)s.n * 8, cudaMemcpyHostToDevice, stream);
-        cudaMemcpyAsync(dy_raw, r->y.data(), (size_t)s.n * 4, cudaMemcpyHostToDevice, stream);
-        if (ddy) cudaMemcpyAsync(ddy, r->dy.data(), (size_t)s.n * 4, cudaMemcpyHostToDevice, stream);
-        if (dfr) cudaMemcpyAsync(dfr, r->freqs.data(), (size_t)s.nf * 8, cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(dt_raw, r->t.data(), (size_t)s.n * 8, cudaMemcpyHostToDevice, copy_stream);
+        cudaMemcpyAsync(dy_raw, r->y.data(), (size_t)s.n * 4, cudaMemcpyHostToDevice, copy_stream);
+        if (ddy) cudaMemcpyAsync(ddy, r->dy.data(), (size_t)s.n * 4, cudaMemcpyHostToDevice, copy_stream);
+        if (dfr) cudaMemcpyAsync(dfr, r->freqs.data(), (size_t)s.nf * 8, cudaMemcpyHostToDevice, copy_stream);
         CurveDesc d;
         memset(&d, 0, sizeof(d));
         d.t = dt_raw; d.y = dy_raw; d.dy = ddy; d.freqs = dfr;
@@ -212,14 +235,18 @@ bool Server::step()
         d.n = s.n; d.nf = s.nf; d.nb = s.nb; d.kmin = s.kmin; d.kmax = s.kmax; d.T = r->geom.T;
         hd[r->slot] = d;
         cudaMemcpyAsync(cdesc.as<CurveDesc>() + r->slot, &hd[r->slot], sizeof(CurveDesc),
-                        cudaMemcpyHostToDevice, stream);
+                        cudaMemcpyHostToDevice, copy_stream);
         hs[nadm++] = r->slot;
         r->t_admit = now_ms();
     }
     int* dsl = dslots.as<int>();
+    bool enq = false;   // anything enqueued in this step
     if (nadm > 0) {
-        cudaMemcpyAsync(dsl, hs, sizeof(int) * nadm, cudaMemcpyHostToDevice, stream);
+        cudaEventRecord(ev_copy, copy_stream);
+        cudaStreamWaitEvent(stream, ev_copy, 0);
         cudaMemsetAsync(err.p, 0, sizeof(int), stream);
+        enq = true;
+        cudaMemcpyAsync(dsl, hs, sizeof(int) * nadm, cudaMemcpyHostToDevice, stream);
         if ((e = launch_prep(cdesc.as<CurveDesc>(), dsl, nadm, err.as<int>(), P->d.phase, stream)) != cudaSuccess) {
             fail_all(std::string("prep launch: ") + cudaGetErrorString(e));
             return false;
@@ -247,10 +274,10 @@ bool Server::step()
         if (k < 0) { geoms.push_back(r->geom); cls.emplace_back(); k = (int)geoms.size() - 1; }
         else geoms[k].smem = std::max(geoms[k].smem, r->geom.smem);
         cls[k].push_back({r, take});
-        if (r->next_tile + take == r->ntiles) finishing.push_back(r);
+        if (r->next_tile + take == r->ntiles) { finishing.push_back(r); r->finishing = true; }
     }
-    TileRange* hr = h_ranges.as<TileRange>();
-    long long* hp = h_prefix.as<long long>();
+    TileRange* hr = B.h_ranges.as<TileRange>();
+    long long* hp = B.h_prefix.as<long long>();
     size_t rr = 0, pp = 0;
     std::vector<size_t> r0(cls.size()), p0(cls.size());
     std::vector<long long> tot(cls.size());
@@ -268,9 +295,15 @@ bool Server::step()
         tot[q] = acc;
     }
     if (rr > 0) {
+        if (!enq) { cudaMemsetAsync(err.p, 0, sizeof(int), stream); enq = true; }
         cudaMemcpyAsync(ranges.p, hr, rr * sizeof(TileRange), cudaMemcpyHostToDevice, stream);
         cudaMemcpyAsync(prefix.p, hp, pp * sizeof(long long), cudaMemcpyHostToDevice, stream);
         cudaMemsetAsync(counter.p, 0, cls.size() * sizeof(int), stream);
+        const int nstr = (int)std::min<size_t>(cls.size(), (size_t)kClassStreams);
+        if (nstr > 1) {
+            cudaEventRecord(ev_fork, stream);
+            for (int q = 0; q < nstr; ++q) cudaStreamWaitEvent(cls_stream[q], ev_fork, 0);
+        }
         for (size_t q = 0; q < cls.size(); ++q) {
             FoldParams fp;
             fp.curves = cdesc.as<CurveDesc>();
@@ -285,10 +318,17 @@ bool Server::step()
             const int bps = fold_blocks_per_sm(geoms[q].T, geoms[q].smem, P->d.phase,
                                                P->d.sum == BLS_SUM_KAHAN, P->d.sign);
             long long grid = std::min<long long>((long long)P->sm_count * bps, tot[q]);
+            cudaStream_t sq = nstr > 1 ? cls_stream[q % nstr] : stream;
             if ((e = launch_fold_sweep(fp, geoms[q].T, (int)std::max<long long>(grid, 1), P->d.phase,
-                                       P->d.sum == BLS_SUM_KAHAN, P->d.sign, geoms[q].smem, stream)) != cudaSuccess) {
+                                       P->d.sum == BLS_SUM_KAHAN, P->d.sign, geoms[q].smem, sq)) != cudaSuccess) {
                 fail_all(std::string("fold-sweep launch: ") + cudaGetErrorString(e));
                 return false;
+            }
+        }
+        if (nstr > 1) {
+            for (int q = 0; q < nstr; ++q) {
+                cudaEventRecord(ev_join[q], cls_stream[q]);
+                cudaStreamWaitEvent(stream, ev_join[q], 0);
             }
         }
     }
@@ -313,21 +353,50 @@ bool Server::step()
             fail_all(std::string("reduce launch: ") + cudaGetErrorString(e));
             return false;
         }
-        cudaMemcpyAsync(h_peaks.p, dpeaks.p, sizeof(DevPeak) * (size_t)nf * topk, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(B.h_peaks.p, dpeaks.p, sizeof(DevPeak) * (size_t)nf * topk, cudaMemcpyDeviceToHost, stream);
     }
-    cudaMemcpyAsync(h_err.p, err.p, sizeof(int), cudaMemcpyDeviceToHost, stream);
-    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) {
+    if (enq) {
+        cudaMemcpyAsync(B.h_err.p, err.p, sizeof(int), cudaMemcpyDeviceToHost, stream);
+        cudaEventRecord(ev_step[par], stream);
+    }
+    // ---- retire the previous step, then hand this one over as the step in flight
+    if (!retire_inflight()) return false;
+    if (enq) {
+        inflight = true;
+        fl_parity = par;
+        fl_finishing = std::move(finishing);
+        std::lock_guard<std::mutex> lk(mu);
+        ++steps;
+    } else if (!finishing.empty()) {
+        fail_all("internal: finishing requests without a step");
+        return false;
+    }
+    return true;
+}
+
+// Waits for the step in flight and retires the requests it finished.
+bool Server::retire_inflight()
+{
+    if (!inflight) return true;
+    inflight = false;
+    cudaError_t e;
+    if ((e = cudaEventSynchronize(ev_step[fl_parity])) != cudaSuccess) {
         fail_all(std::string("serving step: ") + cudaGetErrorString(e));
         return false;
     }
-    const int errw = *h_err.as<int>();
-    // ---- retire
+    StepBufs& B = sb[fl_parity];
+    const int topk = P->d.topk;
+    const int errw = *B.h_err.as<int>();
     std::lock_guard<std::mutex> lk(mu);
-    ++steps;
-    const DevPeak* pk = h_peaks.as<DevPeak>();
-    for (size_t q = 0; q < finishing.size(); ++q) {
-        Request* r = finishing[q];
-        if (errw) {
+    const DevPeak* pk = B.h_peaks.as<DevPeak>();
+    for (size_t q = 0; q < fl_finishing.size(); ++q) {
+        Request* r = fl_finishing[q];
+        r->finishing = false;
+        if (r->cancel) {
+            r->state = RState::Cancelled;
+            r->status = BLS_ERR_CANCELLED;
+            ++cancelled;
+        } else if (errw) {
             r->state = RState::Failed;
             r->status = (errw & kErrInput) ? BLS_ERR_INVALID : BLS_ERR_INTERNAL;
             r->error = "device check failed";
@@ -350,6 +419,7 @@ bool Server::step()
         r->dy.clear(); r->dy.shrink_to_fit();
         r->freqs.clear(); r->freqs.shrink_to_fit();
     }
+    fl_finishing.clear();
     cv_done.notify_all();
     return true;
 }
@@ -378,13 +448,30 @@ static bls_status server_start(bls_plan_impl* P, Server** out)
         (e = S->dslots.ensure(sizeof(int) * 2 * M)) != cudaSuccess ||
         (e = S->dpeaks.ensure(sizeof(DevPeak) * (size_t)M * topk)) != cudaSuccess ||
         (e = S->h_cdesc.ensure(sizeof(CurveDesc) * M)) != cudaSuccess ||
-        (e = S->h_ranges.ensure(sizeof(TileRange) * M)) != cudaSuccess ||
-        (e = S->h_prefix.ensure(sizeof(long long) * 2 * M)) != cudaSuccess ||
-        (e = S->h_slots.ensure(sizeof(int) * 2 * M)) != cudaSuccess ||
-        (e = S->h_peaks.ensure(sizeof(DevPeak) * (size_t)M * topk)) != cudaSuccess ||
-        (e = S->h_err.ensure(64)) != cudaSuccess) {
+        (e = cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&S->ev_copy, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&S->ev_fork, cudaEventDisableTiming)) != cudaSuccess) {
         delete S;
         return cuda_fail(e, "server start");
+    }
+    for (int b = 0; b < 2; ++b) {
+        Server::StepBufs& B = S->sb[b];
+        if ((e = B.h_ranges.ensure(sizeof(TileRange) * M)) != cudaSuccess ||
+            (e = B.h_prefix.ensure(sizeof(long long) * 2 * M)) != cudaSuccess ||
+            (e = B.h_slots.ensure(sizeof(int) * 2 * M)) != cudaSuccess ||
+            (e = B.h_peaks.ensure(sizeof(DevPeak) * (size_t)M * topk)) != cudaSuccess ||
+            (e = B.h_err.ensure(64)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&S->ev_step[b], cudaEventDisableTiming)) != cudaSuccess) {
+            delete S;
+            return cuda_fail(e, "server start");
+        }
+    }
+    for (int q = 0; q < Server::kClassStreams; ++q) {
+        if ((e = cudaStreamCreateWithFlags(&S->cls_stream[q], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&S->ev_join[q], cudaEventDisableTiming)) != cudaSuccess) {
+            delete S;
+            return cuda_fail(e, "server start");
+        }
     }
     S->th = std::thread([S] { S->run(); });
     P->server = S;
@@ -408,14 +495,28 @@ void server_destroy(bls_plan_impl* P)
     S->cv_work.notify_all();
     if (S->th.joinable()) S->th.join();
     cudaSetDevice(P->device);
+    if (S->stream) cudaStreamSynchronize(S->stream);
+    if (S->copy_stream) cudaStreamSynchronize(S->copy_stream);
     for (Request* r : S->slots)
         if (r && r->dmem) cudaFreeAsync(r->dmem, S->stream);
     if (S->stream) cudaStreamSynchronize(S->stream);
     for (auto& kv : S->all) delete kv.second;
     DevBuf* bufs[] = {&S->cdesc, &S->ranges, &S->prefix, &S->counter, &S->err, &S->dslots, &S->dpeaks};
     for (DevBuf* b : bufs) b->release();
-    HostBuf* hb[] = {&S->h_cdesc, &S->h_ranges, &S->h_prefix, &S->h_slots, &S->h_peaks, &S->h_err};
-    for (HostBuf* b : hb) b->release();
+    S->h_cdesc.release();
+    for (int b = 0; b < 2; ++b) {
+        Server::StepBufs& B = S->sb[b];
+        HostBuf* hb[] = {&B.h_ranges, &B.h_prefix, &B.h_slots, &B.h_peaks, &B.h_err};
+        for (HostBuf* h : hb) h->release();
+        if (S->ev_step[b]) cudaEventDestroy(S->ev_step[b]);
+    }
+    if (S->ev_copy) cudaEventDestroy(S->ev_copy);
+    if (S->copy_stream) cudaStreamDestroy(S->copy_stream);
+    for (int q = 0; q < Server::kClassStreams; ++q) {
+        if (S->cls_stream[q]) cudaStreamDestroy(S->cls_stream[q]);
+        if (S->ev_join[q]) cudaEventDestroy(S->ev_join[q]);
+    }
+    if (S->ev_fork) cudaEventDestroy(S->ev_fork);
     if (S->stream) cudaStreamDestroy(S->stream);
     delete S;
 }
