@@ -165,9 +165,9 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g)
     // (a multiple of 16) whose block fits in shared memory.
     auto tmax = [&](int chunk) {
         const size_t stage = (size_t)2 * chunk * 24;
-        const size_t avail = P->smem_optin > stage + 64 ? P->smem_optin - stage - 64 : 0;
+        const size_t avail = P->smem_optin > stage + kFoldSmemReserve ? P->smem_optin - stage - kFoldSmemReserve : 0;
         int T = (int)std::min<size_t>(avail / ((size_t)nb * esz), (size_t)maxT) & ~15;
-        while (T >= 16 && fold_smem_bytes(T, (T + 15) & ~15, nb, chunk, kahan) > P->smem_optin) T -= 16;
+        while (T >= 16 && fold_smem_bytes(T, (T + 15) & ~15, nb, chunk, kahan) + kFoldSmemReserve > P->smem_optin) T -= 16;
         return T;
     };
     // (at least 32 points: the staging buffers then also hold the sweep's 2 x 256 partial
@@ -180,7 +180,7 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g)
     g->T = T;
     g->stride = (T + 15) & ~15;
     g->smem = fold_smem_bytes(T, g->stride, nb, g->chunk, kahan);
-    if (g->smem > P->smem_optin)
+    if (g->smem + kFoldSmemReserve > P->smem_optin)
         return set_error(BLS_ERR_INVALID, "nb = %d with %d frequencies per block needs %zu B of shared memory (> %zu)",
                          nb, T, g->smem, P->smem_optin);
     return BLS_OK;
@@ -642,6 +642,9 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     if (errw & kErrInput)
         return set_error(BLS_ERR_INVALID, "a curve has a non-finite time or flux, a non-positive or non-finite error, "
                                           "or a non-positive frequency (device check)");
+    if (errw & kErrTimeout)
+        return set_error(BLS_ERR_INTERNAL, "a bounded wait between the fold-sweep kernel's warp groups gave up "
+                                           "(code %d)", errw);
     if (errw) return set_error(BLS_ERR_INTERNAL, "device consistency check failed (code %d)", errw);
     const DevPeak* hpk = P->h_peaks.as<DevPeak>();
     for (int c = 0; c < nc; ++c)

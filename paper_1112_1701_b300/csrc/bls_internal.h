@@ -52,7 +52,12 @@ struct DevPeak {
 enum : int {
     kErrInput = 1,      // non-finite time/flux, non-positive error, bad frequency
     kErrBounds = 2,     // a device-side index check failed
+    kErrTimeout = 4,    // a bounded wait between a kernel's warp groups gave up
 };
+
+// Shared memory per fold-sweep block kept free for the kernels' static arrays (the
+// warp-specialised kernel's hand-over slots and partial maxima).
+constexpr size_t kFoldSmemReserve = 2048;
 
 struct FoldParams {
     const CurveDesc* curves;

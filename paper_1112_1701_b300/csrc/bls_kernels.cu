@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "bls_internal.h"
 
@@ -778,14 +779,89 @@ __device__ __forceinline__ void sweep_step(float hw, float hx, u64* R, u64* X, f
 // special-function unit against the FP32 pipe.
 constexpr int kFormB = BLS_SWEEP_MIX;
 
+// Bin sources of the fast sweep.  start(a, b) places block A at bin a and block B at bin
+// b; next() returns the next bin of each block; finish() ends a block.
+//
+// SmemBins reads the private histogram column in shared memory, cyclically.
+struct SmemBins {
+    unsigned hbase, rowb;
+    int nb, ma, mb;
+    __device__ __forceinline__ void start(int a, int b) { ma = a; mb = b; }
+    __device__ __forceinline__ void next(float& hwa, float& hxa, float& hwb, float& hxb)
+    {
+        upk(lds64(hbase + (unsigned)ma * rowb), hwa, hxa);
+        upk(lds64(hbase + (unsigned)mb * rowb), hwb, hxb);
+        ma = (ma + 1 == nb) ? 0 : ma + 1;
+        mb = (mb + 1 == nb) ? 0 : mb + 1;
+    }
+    __device__ __forceinline__ void finish() {}
+};
+
+// Tensor-memory access of this thread's own lane (shape 32x32b: lane i of the warp reads
+// or writes TMEM lane base + i, the address's column field selects 32-bit columns).  The
+// loads complete asynchronously; tmem_wait_ld4 takes the destination registers as
+// operands, so no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld2(unsigned ta, unsigned& v0, unsigned& v1)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                 : "=r"(v0), "=r"(v1) : "r"(ta));
+}
+__device__ __forceinline__ void tmem_wait_ld4(unsigned& a, unsigned& b, unsigned& c, unsigned& d)
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(a), "+r"(b), "+r"(c), "+r"(d));
+}
+__device__ __forceinline__ void tmem_st16(unsigned ta, const unsigned* v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, "
+                 "%9, %10, %11, %12, %13, %14, %15, %16};"
+                 :: "r"(ta), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+                    "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
+                    "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// TmemBins reads a copy of the histogram column in this thread's TMEM lane: bin b at
+// columns (2b, 2b + 1), laid out linearly past nb (bins nb.. repeat bins 0..), so a block
+// reads consecutive columns.  The next bin of both blocks is always in flight while the
+// current one is evaluated.
+struct TmemBins {
+    unsigned base, ta, tb;
+    unsigned pa0, pa1, pb0, pb1;
+    __device__ __forceinline__ void issue()
+    {
+        tmem_ld2(ta, pa0, pa1);
+        tmem_ld2(tb, pb0, pb1);
+        ta += 2;
+        tb += 2;
+    }
+    __device__ __forceinline__ void start(int a, int b)
+    {
+        ta = base + 2u * (unsigned)a;
+        tb = base + 2u * (unsigned)b;
+        issue();
+    }
+    __device__ __forceinline__ void next(float& hwa, float& hxa, float& hwb, float& hxb)
+    {
+        tmem_wait_ld4(pa0, pa1, pb0, pb1);
+        hwa = __uint_as_float(pa0);
+        hxa = __uint_as_float(pa1);
+        hwb = __uint_as_float(pb0);
+        hxb = __uint_as_float(pb1);
+        issue();
+    }
+    __device__ __forceinline__ void finish() { tmem_wait_ld4(pa0, pa1, pb0, pb1); }
+};
+
 // Fast sweep over two independent blocks of SB starts at a time (starts i0.. and
 // i0 + half..), so that 2*SB/2 packed pairs are in flight per bin step.  Block A covers
 // starts [0, half), block B [half, 2 half) with half = SB * ceil(nb / (2 SB)); starts past
 // nb repeat earlier ones (cyclic) and cannot change the maximum.  The outer steps i0 are
 // dealt round-robin to `nparts` threads sharing the histogram; `part` is this thread's.
-template <int SB, int SIGN>
-__device__ __forceinline__ float sweep_fast(unsigned hbase, unsigned rowb, int nb, int kmax,
-                                            int part, int nparts)
+// A block reads kmax + SB - 1 consecutive bins (cyclic) from its start.  FB is the form of
+// block B.
+template <int SB, int SIGN, class Bins, int FB = kFormB>
+__device__ __forceinline__ float sweep_fast(Bins& src, int nb, int kmax, int part, int nparts)
 {
     constexpr int NP = SB / 2;
     float a0[NP], a1[NP], c0[NP], c1[NP];
@@ -796,42 +872,38 @@ __device__ __forceinline__ float sweep_fast(unsigned hbase, unsigned rowb, int n
         u64 RA[NP], XA[NP], RB[NP], XB[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) { RA[q] = 0ull; XA[q] = 0ull; RB[q] = 0ull; XB[q] = 0ull; }
-        int ma = i0, mb = i0 + half;
+        int mb = i0 + half;
         while (mb >= nb) mb -= nb;
-#define BLS_LOAD2(HWA, HXA, HWB, HXB)                                   \
-        upk(lds64(hbase + (unsigned)ma * rowb), HWA, HXA);             \
-        upk(lds64(hbase + (unsigned)mb * rowb), HWB, HXB);             \
-        ma = (ma + 1 == nb) ? 0 : ma + 1;                               \
-        mb = (mb + 1 == nb) ? 0 : mb + 1;
+        src.start(i0, mb);
 #pragma unroll
         for (int mm = 0; mm < SB - 1; ++mm) {
             float hwa, hxa, hwb, hxb;
-            BLS_LOAD2(hwa, hxa, hwb, hxb)
+            src.next(hwa, hxa, hwb, hxb);
             sweep_step<SIGN, NP, 0>(hwa, hxa, RA, XA, a0, a1, mm, 0, 0);
-            sweep_step<SIGN, NP, kFormB>(hwb, hxb, RB, XB, c0, c1, mm, 0, 0);
+            sweep_step<SIGN, NP, FB>(hwb, hxb, RB, XB, c0, c1, mm, 0, 0);
         }
 #pragma unroll 2
         for (int mm = SB - 1; mm < kmax; ++mm) {
             float hwa, hxa, hwb, hxb;
-            BLS_LOAD2(hwa, hxa, hwb, hxb)
+            src.next(hwa, hxa, hwb, hxb);
             sweep_step<SIGN, NP, 0>(hwa, hxa, RA, XA, a0, a1, 0, 1, 0);
-            sweep_step<SIGN, NP, kFormB>(hwb, hxb, RB, XB, c0, c1, 0, 1, 0);
+            sweep_step<SIGN, NP, FB>(hwb, hxb, RB, XB, c0, c1, 0, 1, 0);
         }
 #pragma unroll
         for (int e = 0; e < SB - 1; ++e) {
             float hwa, hxa, hwb, hxb;
-            BLS_LOAD2(hwa, hxa, hwb, hxb)
+            src.next(hwa, hxa, hwb, hxb);
             sweep_step<SIGN, NP, 0>(hwa, hxa, RA, XA, a0, a1, 0, 2, e);
-            sweep_step<SIGN, NP, kFormB>(hwb, hxb, RB, XB, c0, c1, 0, 2, e);
+            sweep_step<SIGN, NP, FB>(hwb, hxb, RB, XB, c0, c1, 0, 2, e);
         }
-#undef BLS_LOAD2
+        src.finish();
     }
     // best signed residue of block A -> power P = z^2; block B holds powers or residues
     float za = 0.0f, zb = 0.0f, pb = 0.0f;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         za = SIGN ? fmaxf(za, fmaxf(a0[q], a1[q])) : fminf(za, fminf(a0[q], a1[q]));
-        if (kFormB) pb = fmaxf(pb, fmaxf(c0[q], c1[q]));
+        if (FB) pb = fmaxf(pb, fmaxf(c0[q], c1[q]));
         else zb = SIGN ? fmaxf(zb, fmaxf(c0[q], c1[q])) : fminf(zb, fminf(c0[q], c1[q]));
     }
     return fmaxf(fmaxf(za * za, zb * zb), pb);
@@ -849,6 +921,21 @@ __device__ __forceinline__ bool box_full(int i1, int k, int nb, int arc_a, int a
     return rel + arc_len <= k;
 }
 
+// Sequential bin stream over a shared-memory histogram column (cyclic).
+struct SmemStream {
+    const unsigned char* hist;
+    size_t S;
+    int kahan, nb, m;
+    __device__ __forceinline__ void start(int a) { m = a; }
+    __device__ __forceinline__ void next(float& hw, float& hx)
+    {
+        hw = bin_w(hist, S, kahan, m);
+        hx = bin_x(hist, S, kahan, m);
+        m = (m + 1 == nb) ? 0 : m + 1;
+    }
+    __device__ __forceinline__ void finish() {}
+};
+
 // Exact sweep: the best box with the definition's tie-break.
 //
 // Every start i1 and width k (cyclic), sums accumulated bin by bin from the start: r in
@@ -858,15 +945,16 @@ __device__ __forceinline__ bool box_full(int i1, int k, int nb, int arc_a, int a
 // cyclic arc of occupied bins, so neither depends on rounding.  Dips only: s < 0.
 // Candidates are compared as exact (num, den) pairs, num * den_best > num_best * den, so a
 // box with bit-identical sums never replaces an earlier one and equal powers resolve to
-// the smallest (i1, k).
-template <int SIGN>
-__device__ Best sweep_exact(const unsigned char* hist, int stride, int kahan, int nb, int kmin,
-                            int kmax)
+// the smallest (i1, k).  The bins come from a sequential stream (start, next, finish).
+template <int SIGN, class Stream>
+__device__ Best sweep_exact_src(Stream& src, int nb, int kmin, int kmax)
 {
-    const size_t S = (size_t)stride;
     int first = -1, last = -1, run = 0, gap = 0, gap_end = 0;
+    src.start(0);
     for (int b = 0; b < nb; ++b) {
-        if (bin_w(hist, S, kahan, b) != 0.0f) {
+        float hw, hx;
+        src.next(hw, hx);
+        if (hw != 0.0f) {
             if (first < 0) first = b;
             else if (run > gap) { gap = run; gap_end = b; }
             last = b;
@@ -875,6 +963,7 @@ __device__ Best sweep_exact(const unsigned char* hist, int stride, int kahan, in
             ++run;
         }
     }
+    src.finish();
     int arc_a = 0, arc_len = 0;
     if (first >= 0) {
         const int wrap = (nb - 1 - last) + first;
@@ -885,10 +974,10 @@ __device__ Best sweep_exact(const unsigned char* hist, int stride, int kahan, in
     g.num = 0.0f; g.den = 1.0f; g.i1 = 0; g.k = kmin;
     for (int i1 = 0; i1 < nb; ++i1) {
         float rh = 0.0f, rl = 0.0f, s = 0.0f, cs = 0.0f;
-        int m = i1;
+        src.start(i1);
         for (int k = 1; k <= kmax; ++k) {
-            const float hw = bin_w(hist, S, kahan, m), hx = bin_x(hist, S, kahan, m);
-            m = (m + 1 == nb) ? 0 : m + 1;
+            float hw, hx;
+            src.next(hw, hx);
             const float t = __fadd_rn(rh, hw);                      // two-sum rh + hw
             const float bp = __fsub_rn(t, rh);
             const float e = __fadd_rn(__fsub_rn(rh, __fsub_rn(t, bp)), __fsub_rn(hw, bp));
@@ -907,8 +996,21 @@ __device__ Best sweep_exact(const unsigned char* hist, int stride, int kahan, in
                 g.num = num; g.den = den; g.i1 = i1; g.k = k;
             }
         }
+        src.finish();
     }
     return g;
+}
+
+template <int SIGN>
+__device__ Best sweep_exact(const unsigned char* hist, int stride, int kahan, int nb, int kmin,
+                            int kmax)
+{
+    SmemStream src;
+    src.hist = hist;
+    src.S = (size_t)stride;
+    src.kahan = kahan;
+    src.nb = nb;
+    return sweep_exact_src<SIGN>(src, nb, kmin, kmax);
 }
 
 __device__ __forceinline__ Best sweep_exact_rt(int sign, const unsigned char* hist, int stride,
@@ -958,7 +1060,13 @@ __device__ __forceinline__ float sweep_max(const unsigned char* hist, int stride
             }
             fast = rmax < 0.89f;
         }
-        if (fast) return sweep_fast<SB, SIGN>(hbase, rowb, nb, kmax, part, nparts);
+        if (fast) {
+            SmemBins src;
+            src.hbase = hbase;
+            src.rowb = rowb;
+            src.nb = nb;
+            return sweep_fast<SB, SIGN>(src, nb, kmax, part, nparts);
+        }
     }
     if (part != 0) return 0.0f;
     const Best g = sweep_exact<SIGN>(hist, stride, KAHAN, nb, kmin, kmax);
@@ -1122,16 +1230,485 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
     }
 }
 
+// ------------------------------------------------------------------------- a2-a6: warp-specialised
+
+// Variant of the hot kernel in which binning and sweeping overlap.  The block has two warp
+// groups (T a multiple of 32, at most 128):
+//
+//   binning group (T threads, warps 0 .. T/32-1): stages the points, folds and bins tile
+//     i into the private shared-memory histograms (one column per frequency), then hands
+//     them over;
+//   sweep group (the other warps): copies column c of tile i into its TMEM lane (bins
+//     laid out linearly, the first bins repeated past nb) while zeroing the shared column,
+//     hands the histograms back, then sweeps the boxes of tile i from TMEM while the
+//     binning group already bins tile i + 1.  Its first warp also claims the work items
+//     and writes each tile's descriptor (the curve's CurveDesc and the tile index) into
+//     one of two shared slots ahead of time, so that the binning group's path from one
+//     tile to the next holds no global-memory round trip.
+//
+// The binning loop is latency-bound (one private histogram per thread, so only T threads
+// can bin) and the sweep is bound by FP32 and special-function issue, so the sweep fills
+// the issue slots that the binning chain leaves idle.  With T = 128 the sweep group has
+// two threads per column (two warps per TMEM lane quadrant), which split the copy, the
+// zeroing and the box starts.  The checks of the fast sweep's condition and the exact
+// sweep (rare) read the TMEM copy; tiles whose TMEM copy would not fit 512 columns, or that
+// the fast sweep does not cover (kmin > 1, small kmax), are swept from shared memory before
+// the hand-back.  The bins, the sums and the set of boxes are those of fold_sweep_kernel;
+// both sweep blocks rank boxes by the signed residue, so a frequency's power can differ
+// from fold_sweep_kernel's in the last bits (both are within the approximation's 2^-22).
+//
+// Hand-over: two mbarriers (count 1, arrived by a group's first thread after a group
+// barrier); each wait is bounded in time and, if it gives up, the kernel records
+// kErrTimeout and both groups stop.
+
+constexpr unsigned long long kHandoffTimeoutNs = 30ull * 1000000000ull;
+constexpr int kBarBin = 1, kBarSweep = 2;   // named barriers of the two groups
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned a)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(a)
+                 : "memory");
+}
+// One bounded test: the thread is suspended until the phase completes or about
+// kSuspendNs pass, so a waiting thread takes no issue slots from the working warps.
+constexpr unsigned kSuspendNs = 1000000;
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(a), "r"(parity), "r"(kSuspendNs) : "memory");
+    return ok != 0;
+}
+// Waits until the phase of the given parity has completed; false if it has not within
+// kHandoffTimeoutNs.
+__device__ __noinline__ bool mbar_wait(unsigned a, unsigned parity)
+{
+    if (mbar_try(a, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned it = 0; it < 0x7fffffffu; ++it) {
+        if (mbar_try(a, parity)) return true;
+        if (globaltimer_ns() - t0 > kHandoffTimeoutNs) break;
+    }
+    return false;
+}
+__device__ __forceinline__ void group_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// Group barrier that also returns whether v was non-zero on any thread of the group.
+__device__ __forceinline__ int group_or(int id, int n, int v)
+{
+    int r;
+    asm volatile("{\n\t.reg .pred q, o;\n\tsetp.ne.s32 q, %1, 0;\n\t"
+                 "bar.red.or.pred o, %2, %3, q;\n\tselp.s32 %0, 1, 0, o;\n\t}"
+                 : "=r"(r) : "r"(v), "r"(id), "r"(n) : "memory");
+    return r;
+}
+
+constexpr unsigned kTmemCols = 512;
+
+// Sequential single-bin stream over this thread's TMEM lane (linear layout), for the rare
+// checks; every access is taken by the whole warp together.
+struct TmemStream {
+    unsigned base, ta, p0, p1;
+    __device__ __forceinline__ void issue()
+    {
+        __syncwarp();
+        tmem_ld2(ta, p0, p1);
+        ta += 2;
+    }
+    __device__ __forceinline__ void start(int a)
+    {
+        ta = base + 2u * (unsigned)a;
+        issue();
+    }
+    __device__ __forceinline__ void next(float& hw, float& hx)
+    {
+        unsigned d0 = 0, d1 = 0;
+        __syncwarp();
+        tmem_wait_ld4(p0, p1, d0, d1);
+        hw = __uint_as_float(p0);
+        hx = __uint_as_float(p1);
+        issue();
+    }
+    __device__ __forceinline__ void finish()
+    {
+        unsigned d0 = 0, d1 = 0;
+        __syncwarp();
+        tmem_wait_ld4(p0, p1, d0, d1);
+    }
+};
+
+// Sweep of one column from its TMEM copy, all lanes of the warp together.
+// Both blocks take the signed-residue form here: it issues fewer instructions per box than
+// the shared-reciprocal form and leans on the special-function unit, which the binning
+// warps sharing the SM sub-partitions do not use.
+template <int SB, int SIGN>
+__device__ __forceinline__ float sweep_tmem(unsigned tbase, int nb, int kmax, int part, int nparts)
+{
+    TmemBins src;
+    src.base = tbase;
+    return sweep_fast<SB, SIGN, TmemBins, 0>(src, nb, kmax, part, nparts);
+}
+
+// Heaviest run of kmax consecutive bins (cyclic), as in sweep_max, from the TMEM copy.
+__device__ float heaviest_run_tmem(unsigned tbase, int nb, int kmax)
+{
+    TmemBins src;
+    src.base = tbase;
+    float win = 0.0f, hw, hx, hw2, hx2;
+    src.start(0, 0);
+    for (int b = 0; b < kmax; ++b) {
+        src.next(hw, hx, hw2, hx2);
+        win += hw;
+    }
+    src.finish();
+    float rmax = win;
+    src.start(0, kmax);   // bin b leaves, bin b + kmax enters
+    for (int b = 0; b + 1 < nb; ++b) {
+        float hout, hin;
+        src.next(hout, hx, hin, hx2);
+        win = __fsub_rn(__fadd_rn(win, hin), hout);
+        rmax = fmaxf(rmax, win);
+    }
+    src.finish();
+    return rmax;
+}
+
+// Descriptor of one work item, written by the sweep group ahead of its use.
+struct TileSlot {
+    CurveDesc cd;
+    int tile;
+    int stop;
+};
+
+// Claims the next work item and writes its descriptor (by the 32 lanes of one warp): the
+// range of the item is found by a 32-way search of the prefix array.
+__device__ void fetch_tile(const FoldParams& p, TileSlot* slot, int lane)
+{
+    int it = 0;
+    if (lane == 0) it = atomicAdd(p.counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= p.total) {
+        if (lane == 0) slot->stop = 1;
+        return;
+    }
+    int lo = 0, hi = p.nranges;   // prefix[lo] <= it < prefix[hi]
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int idx = lo + lane * step;
+        const bool le = idx < hi && p.prefix[idx] <= it;
+        const unsigned m = __ballot_sync(0xffffffffu, le);
+        lo += (31 - __clz(m)) * step;
+        hi = min(hi, lo + step);
+    }
+    const TileRange tr = p.ranges[lo];
+    static_assert(sizeof(CurveDesc) % 8 == 0, "CurveDesc is copied in 8-byte words");
+    const u64* src = reinterpret_cast<const u64*>(&p.curves[tr.curve]);
+    u64* dst = reinterpret_cast<u64*>(&slot->cd);
+    for (int w = lane; w < (int)(sizeof(CurveDesc) / 8); w += 32) dst[w] = src[w];
+    if (lane == 0) {
+        slot->tile = tr.tile_lo + (int)(it - p.prefix[lo]);
+        slot->stop = 0;
+    }
+}
+
+constexpr int kWsMaxThreads = 384;
+
+template <int PHASE, int SIGN>
+__global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long s_bar[2];   // [0] histograms full, [1] empty
+    __shared__ TileSlot s_slot[2];                          // descriptor of tile k at [k & 1]
+    __shared__ float s_wpart[128], s_wpart2[128];           // second sweep part's partials
+    __shared__ unsigned s_tmem;
+    const int T = p.cols;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const bool binner = tid < T;
+    const int col = binner ? tid : (tid - T) % T;
+    const int CH = p.chunk;
+    float4* cpts = reinterpret_cast<float4*>(smem);             // [2][CH]: point pairs
+    double* cdt = reinterpret_cast<double*>(cpts + 2 * CH);     // [2][CH]: FP64 offsets
+    unsigned char* hist_all = reinterpret_cast<unsigned char*>(cdt + 2 * CH);
+    unsigned char* hist = hist_all + (size_t)col * sizeof(float2);
+    const size_t S = (size_t)p.stride;
+    const unsigned hbase = (unsigned)__cvta_generic_to_shared(hist);
+    const unsigned rowb = (unsigned)(S * sizeof(float2));
+    const unsigned full_bar = (unsigned)__cvta_generic_to_shared(&s_bar[0]);
+    const unsigned empty_bar = (unsigned)__cvta_generic_to_shared(&s_bar[1]);
+
+    {   // every histogram row starts at zero (afterwards the sweep group re-zeroes)
+        unsigned dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        const size_t rows = (dyn - (size_t)2 * CH * (sizeof(float4) + sizeof(double))) / rowb;
+        u64* h = reinterpret_cast<u64*>(hist_all);
+        for (size_t e = tid; e < rows * S; e += blockDim.x) h[e] = 0ull;
+    }
+    if (warp == T / 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"((unsigned)__cvta_generic_to_shared(&s_tmem)), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(full_bar, 1);
+        mbar_init(empty_bar, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    if (binner) {
+        unsigned ph = 0;
+        for (int k = 0;; ++k) {
+            int give_up = 0;
+            if (tid == 0) {
+                give_up = !mbar_wait(empty_bar, ph);
+                if (give_up) atomicOr(p.err, kErrTimeout);
+            }
+            ph ^= 1u;
+            give_up = group_or(kBarBin, T, give_up);
+            const TileSlot& sl = s_slot[k & 1];
+            if (give_up || sl.stop) {
+                if (tid == 0) mbar_arrive(full_bar);   // the sweep group reads the stop
+                break;
+            }
+            const CurveDesc cdr = sl.cd;
+            const int tile = sl.tile;
+            const int n = cdr.n, nf = cdr.nf, nb = cdr.nb;
+            const float4* gpts = cdr.pts;
+            const double* gdt = cdr.dt64;
+            const int j = tile * T + col;
+            const bool active = j < nf;
+            const double f = grid_freq(cdr, active ? j : nf - 1);
+            const FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs);
+            const FoldPacked fq = make_fold_packed(fc);
+
+            // a2: chunks of CH points through shared memory (as in fold_sweep_kernel)
+            const int nchunks = (n + CH - 1) / CH;
+            auto stage = [&](int ci) {
+                const int c0 = ci * CH;
+                const int cn = (min(CH, n - c0) + 1) & ~1;
+                const int cpad = (cn + 15) & ~15;
+                float4* dp = cpts + (ci & 1) * CH;
+                double* dd = cdt + (ci & 1) * CH;
+                for (int i = tid; i < cn; i += T) {
+                    cp_async16(&dp[i], &gpts[c0 + i]);
+                    cp_async8(&dd[i], &gdt[c0 + i]);
+                }
+                for (int i = cn + tid; i < cpad; i += T) {
+                    dp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    dd[i] = 0.0;
+                }
+                cp_async_commit();
+            };
+            stage(0);
+            for (int ci = 0; ci < nchunks; ++ci) {
+                if (ci + 1 < nchunks) stage(ci + 1); else cp_async_commit();
+                cp_async_wait1();
+                group_sync(kBarBin, T);
+                const int cnum = min(CH, n - ci * CH);
+                const float4* cp = cpts + (ci & 1) * CH;
+                const double* cd = cdt + (ci & 1) * CH;
+                if (active) {   // a3 + a4
+                    if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok))
+                        bin_fast<PHASE>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                    else
+                        bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
+                }
+                group_sync(kBarBin, T);
+            }
+            if (tid == 0) mbar_arrive(full_bar);
+        }
+    } else {
+        // nparts threads per column (warps of one TMEM lane quadrant when there are two)
+        const int NS = blockDim.x - T;
+        const int nparts = NS / T;
+        const int part = (tid - T) / T;
+        const unsigned tbase = s_tmem + ((unsigned)((warp & 3) * 32) << 16);
+        const bool fetcher = warp == T / 32;
+        unsigned ph = 0;
+        // descriptors of tiles 0 and 1; the histograms start empty
+        if (fetcher) fetch_tile(p, &s_slot[0], lane);
+        group_sync(kBarSweep, NS);
+        if (tid == T) mbar_arrive(empty_bar);
+        if (fetcher) fetch_tile(p, &s_slot[1], lane);
+        for (int k = 0;; ++k) {
+            int give_up = 0;
+            if (tid == T) {
+                give_up = !mbar_wait(full_bar, ph);
+                if (give_up) atomicOr(p.err, kErrTimeout);
+            }
+            ph ^= 1u;
+            give_up = group_or(kBarSweep, NS, give_up);
+            const TileSlot& sl = s_slot[k & 1];
+            if (give_up || sl.stop) break;
+            const int tile = sl.tile;
+            const int nf = sl.cd.nf, nb = sl.cd.nb, kmin = sl.cd.kmin, kmax = sl.cd.kmax;
+            float* const res = sl.cd.res;
+            const int j = tile * T + col;
+            const bool active = j < nf;
+            const int SB = kmax < 15 ? 4 : (wide_sweep_10(nb, 1) ? 10 : 8);
+            // bins read from TMEM: up to nb + kmax + SB - 2 by the fast sweep (with its one
+            // bin of read-ahead), up to 7 more by the copy's last group of 8; the copy's
+            // bins past nb wrap once
+            const bool use_tmem = kmin == 1 && kmax >= SB - 1 && nb + kmax + SB + 8 <= 257 &&
+                                  kmax + SB + 8 <= nb;
+            float v = 0.0f, wmax = 0.0f;
+            if (use_tmem) {
+                // copy bins 0 .. L-1 (bin b >= nb repeats bin b - nb; L <= 2 nb) into the
+                // column's lane, 8 bins per TMEM store (groups dealt to the parts), then zero
+                // the shared column (rows split between the parts)
+                const int L = (nb + kmax + SB - 1 + 7) & ~7;
+                const unsigned wrapb = (unsigned)nb * rowb;
+                for (int g = 8 * part; g < L; g += 8 * nparts) {
+                    const unsigned ag = hbase + (unsigned)g * rowb;
+                    u64 h[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        h[i] = lds64(ag + (unsigned)i * rowb - (g + i >= nb ? wrapb : 0u));
+                    unsigned r[16];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float hw, hx;
+                        upk(h[i], hw, hx);
+                        if (g + i < nb) wmax = fmaxf(wmax, hw);
+                        r[2 * i] = __float_as_uint(hw);
+                        r[2 * i + 1] = __float_as_uint(hx);
+                    }
+                    tmem_st16(tbase + 2u * (unsigned)g, r);
+                }
+                const int zlo = part * nb / nparts, zhi = (part + 1) * nb / nparts;
+                int b = zlo;
+                for (; b + 4 <= zhi; b += 4) {
+                    const unsigned a0 = hbase + (unsigned)b * rowb;
+                    sts64(a0, 0ull);
+                    sts64(a0 + rowb, 0ull);
+                    sts64(a0 + 2u * rowb, 0ull);
+                    sts64(a0 + 3u * rowb, 0ull);
+                }
+                for (; b < zhi; ++b) sts64(hbase + (unsigned)b * rowb, 0ull);
+                if (part == 1) s_wpart[col] = wmax;
+                tmem_wait_st();
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            } else if (part == 0) {
+                if (active)
+                    v = SB == 4 ? sweep_max<0, SIGN, 4>(hist, p.stride, nb, kmin, kmax, 0, 1)
+                        : SB == 10 ? sweep_max<0, SIGN, 10>(hist, p.stride, nb, kmin, kmax, 0, 1)
+                                   : sweep_max<0, SIGN, 8>(hist, p.stride, nb, kmin, kmax, 0, 1);
+                for (int b = 0; b < nb; ++b) sts64(hbase + (unsigned)b * rowb, 0ull);
+            }
+            group_sync(kBarSweep, NS);
+            if (tid == T) mbar_arrive(empty_bar);
+            if (use_tmem) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                bool fast = true;
+                if (part == 0) {
+                    // the fast sweep's condition (as in sweep_max) and the exact sweep
+                    if (nparts == 2) wmax = fmaxf(wmax, s_wpart[col]);
+                    fast = (float)kmax * wmax < 0.89f;
+                    const bool slide = !fast && kmax < nb;
+                    if (__any_sync(0xffffffffu, slide)) {
+                        const float rmax = heaviest_run_tmem(tbase, nb, kmax);
+                        if (slide) fast = rmax < 0.89f;
+                    }
+                    const bool exact = active && !fast;
+                    if (__any_sync(0xffffffffu, exact)) {
+                        TmemStream src;
+                        src.base = tbase;
+                        const Best g = sweep_exact_src<SIGN>(src, nb, kmin, kmax);
+                        if (exact) v = g.num > 0.0f ? __fdiv_rn(g.num, g.den) : 0.0f;
+                    }
+                }
+                __syncwarp();
+                float vf = SB == 4 ? sweep_tmem<4, SIGN>(tbase, nb, kmax, part, nparts)
+                           : SB == 10 ? sweep_tmem<10, SIGN>(tbase, nb, kmax, part, nparts)
+                                      : sweep_tmem<8, SIGN>(tbase, nb, kmax, part, nparts);
+                if (nparts == 2) {   // the parts' maxima meet in shared memory
+                    if (part == 1) s_wpart2[col] = vf;
+                    group_sync(kBarSweep, NS);
+                    if (part == 0) vf = fmaxf(vf, s_wpart2[col]);
+                }
+                if (fast) v = vf;
+            }
+            if (part == 0 && active) res[j] = v;
+            // descriptor of tile k + 2 (slot k & 1 is no longer read: the binning group
+            // copied it before binning tile k, this group above)
+            if (fetcher) fetch_tile(p, &s_slot[k & 1], lane);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == T / 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem),
+                     "r"(kTmemCols) : "memory");
+    }
+}
+
+// The warp-specialised kernel serves every plain-sum tile geometry with T a multiple of 32
+// (at most 128); BLS_FOLD_WS=0 in the environment selects fold_sweep_kernel instead.
+static bool use_ws(int T, int kahan)
+{
+    static const int env = [] {
+        const char* e = getenv("BLS_FOLD_WS");
+        return (e && e[0] == '0') ? 0 : 1;
+    }();
+    return env && !kahan && T % 32 == 0 && T >= 32 && T <= 128;
+}
+
+// Threads of a warp-specialised block: T binning threads, and T sweep threads per column
+// part (two parts when T = 128, whose two sweep warps per TMEM lane quadrant share the
+// lanes; otherwise one).
+static int ws_threads(int T) { return T == 128 ? 3 * T : 2 * T; }
+
+// Dynamic shared memory of a warp-specialised block: at least half of an SM's shared memory,
+// so that no second block (which would wait for the first one's TMEM) lands on the SM.
+static size_t ws_smem(size_t smem)
+{
+    static const size_t half = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+            cudaGetLastError();
+            v = 0;
+        }
+        return (size_t)v / 2 + 1024;
+    }();
+    return smem > half ? smem : half;
+}
+
 template <int PHASE, int KAHAN, int SIGN>
 static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t smem,
                                  cudaStream_t s)
 {
+    FoldParams q = p;
+    q.cols = T;
+    if (use_ws(T, KAHAN)) {
+        auto k = fold_sweep_ws_kernel<PHASE, SIGN>;
+        const size_t sm = ws_smem(smem);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm);
+        if (e != cudaSuccess) return e;
+        k<<<grid, ws_threads(T), sm, s>>>(q);
+        return cudaGetLastError();
+    }
     auto k = fold_sweep_kernel<PHASE, KAHAN, SIGN>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    FoldParams q = p;
-    q.cols = T;
     k<<<grid, fold_block_threads(T), smem, s>>>(q);
     return cudaGetLastError();
 }
@@ -1139,6 +1716,15 @@ static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t sm
 template <int PHASE, int KAHAN, int SIGN>
 static int blocks_t(int T, size_t smem)
 {
+    if (use_ws(T, KAHAN)) {
+        // one block per SM: all of TMEM and (nearly) all of shared memory
+        auto k = fold_sweep_ws_kernel<PHASE, SIGN>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem(smem)) != cudaSuccess) {
+            cudaGetLastError();
+            return 1;
+        }
+        return 1;
+    }
     auto k = fold_sweep_kernel<PHASE, KAHAN, SIGN>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();

@@ -114,10 +114,10 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
         return cuda_fail(e, "device attributes");
 
     // block geometry as in a plan with default settings
-    const size_t avail_all = (size_t)optin - 1024;
+    const size_t avail_all = (size_t)optin - kFoldSmemReserve;
     auto tmax = [&](int chunk) {
         const size_t stage = (size_t)2 * chunk * 24;
-        const size_t avail = avail_all > stage + 64 ? avail_all - stage - 64 : 0;
+        const size_t avail = avail_all > stage ? avail_all - stage : 0;
         const size_t cap = avail / ((size_t)c->nb * 8);
         int T = (int)std::min<size_t>(cap, (size_t)fold_sweep_max_threads()) & ~15;
         while (T >= 16 && fold_smem_bytes(T, T, c->nb, chunk, 0) > avail_all) T -= 16;
