@@ -708,6 +708,20 @@ __device__ __forceinline__ float bin_x(const unsigned char* hist, size_t S, int 
 // Both approximations err by about 2^-22 relative, far inside the spectrum's tolerance.
 constexpr float kEmptyBox = 1e-18f;
 
+// Three-input FP32 min / max (NaN inputs are ignored, as by fminf / fmaxf).
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 template <int SIGN, int FORM>
 __device__ __forceinline__ void eval_pair(u64& R, u64& X, const u64& HW2, const u64& HX2,
                                           bool init, bool use0, bool use1, float& b0, float& b1)
@@ -730,7 +744,9 @@ __device__ __forceinline__ void eval_pair(u64& R, u64& X, const u64& HW2, const 
         const u64 Z = mul2(X, pk(rsqrt_approx(-nd0), rsqrt_approx(-nd1)));
         float z0, z1;
         upk(Z, z0, z1);
-        if (SIGN) {
+        if (use0 && use1) {   // both boxes count: one three-input min/max for the pair
+            b0 = SIGN ? fmax3(b0, fabsf(z0), fabsf(z1)) : fmin3(b0, z0, z1);
+        } else if (SIGN) {
             if (use0) b0 = fmaxf(b0, fabsf(z0));
             if (use1) b1 = fmaxf(b1, fabsf(z1));
         } else {
