@@ -51,8 +51,8 @@ NB, QMIN, QMAX = 200, 0.005, 0.15
 # DRAM traffic of one fold-bin-sweep launch on this workload (dram__bytes_read.sum +
 # dram__bytes_write.sum, one ncu capture of the timed launch after an L2 flush), for the
 # kernel source with the given SHA-256; reported as null once the source changes.
-NCU_TRAFFIC = {"kernel_sha256": "a99556a07ee24a97b05d798f6dbfa6eef40488ff25fb36c862d4f787f40f14fd",
-               "bytes_per_launch": 57669120 + 151185408}
+NCU_TRAFFIC = {"kernel_sha256": "058f7dcb41f8588ecb14478083bfafd86dffca7f204bdbad6b2b48cdbd8ba123",
+               "bytes_per_launch": 58012416 + 150789376}
 
 
 def kernel_sha():
@@ -813,7 +813,9 @@ def main():
             "frac": achieved / peak,
             "traffic": (NCU_TRAFFIC["bytes_per_launch"]
                         if NCU_TRAFFIC["kernel_sha256"] == kernel_sha() else None),
-            "kernel": "fold_sweep_kernel", "peak_source": f"{peak_src}: {sms} SMs x 128 lanes x "
+            "kernel": "fold_sweep_ws_kernel" if os.environ.get("BLS_FOLD_WS", "1") != "0"
+                      else "fold_sweep_kernel",
+            "peak_source": f"{peak_src}: {sms} SMs x 128 lanes x "
                                                           f"{clk_max:.0f} MHz",
             "fold_ms_per_launch": fold_ms,
             "loop_a_units": units, "loop_b_units": evals}

@@ -1,0 +1,131 @@
+"""The warp-specialised fold-sweep kernel (marked gpu).
+
+Tiles of T = 32, 64, 96 and 128 frequencies run in the warp-specialised kernel (a binning
+warp group and a sweep warp group that takes each tile's histograms over through TMEM; one
+sweep thread per column, two when T = 128); other widths and BLS_FOLD_WS=0 select the
+one-group kernel.  Checked here:
+  * the search's spectrum (SR of the kernel's per-frequency powers) against the oracle
+    within the parity tolerance, over several tiles with a ragged tail, for TMEM-copied
+    tiles, tiles swept from shared memory (nb too large for the copy; kmin > 1) and the
+    exact sweep;
+  * identical spectra and peaks for every warp-specialised tile width (the per-frequency
+    arithmetic does not depend on the tile);
+  * the one-group kernel (run in a child process with BLS_FOLD_WS=0) within FP32 rounding
+    of the same spectrum, with the same peaks.
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1112_1701_b300 import bls, build, synth
+from tests.parity import prep_of, sr_tol
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    bls.lib()
+
+
+def _cases():
+    """(name, curve inputs, nb, qmin, qmax) -- every curve of a case shares nb and q."""
+    out = []
+    b = synth.config2(ncurves=3, nf=700, seed=31)   # 700 = 5 x 128 + 60: a ragged tail
+    out.append(("batch_nb200", [bls.CurveInput(c.t, c.y, c.dy, nf=g.nf, fmin=g.fmin, df=g.df,
+                                               nb=200, qmin=b.qmin, qmax=b.qmax)
+                                for c, g in zip(b.curves, b.grids)], 200, b.qmin, b.qmax))
+    rng = np.random.default_rng(12)
+    n = 400
+    t = synth.T0 + np.sort(rng.integers(0, 40, n) + rng.uniform(0, 0.05, n))
+    y = (1 + rng.normal(0, 0.01, n)).astype(np.float32)
+    y[np.abs(np.mod(t - synth.T0, 1.0) - 0.02) < 0.004] -= 0.02
+    freqs = np.concatenate([[1.0, 2.0, 0.5], np.linspace(0.98, 1.02, 150), np.linspace(0.1, 3, 150)])
+    out.append(("crowded_exact_nb100", [bls.CurveInput(t, y, None, freqs=freqs, nb=100, qmin=0.01,
+                                                       qmax=0.3)], 100, 0.01, 0.3))
+    c = b.curves[0]
+    out.append(("shared_sweep_nb240", [bls.CurveInput(c.t, c.y, c.dy, nf=300, fmin=0.2, df=0.01,
+                                                      nb=240, qmin=0.005, qmax=0.1)], 240, 0.005, 0.1))
+    out.append(("shared_sweep_kmin3", [bls.CurveInput(c.t, c.y, c.dy, nf=300, fmin=0.2, df=0.01,
+                                                      nb=100, qmin=0.03, qmax=0.15)], 100, 0.03, 0.15))
+    return out
+
+
+def _search(cis, nb, qmin, qmax, T=0, sign="dips"):
+    nf = sum(len(ci.freqs) if ci.freqs is not None else ci.nf for ci in cis)
+    spec = np.zeros(nf, np.float32)
+    with bls.Plan(nb=nb, qmin=qmin, qmax=qmax, topk=2, sign=sign, freqs_per_block=T) as p:
+        pk = p.search(cis, spectrum=spec)
+    return spec, pk
+
+
+def _oracle_check(cis, spec, nb, qmin, qmax, sign):
+    kmin, kmax = oracle.kminmax(nb, qmin, qmax)
+    o = 0
+    for ci in cis:
+        t, y = np.asarray(ci.t, np.float64), np.asarray(ci.y, np.float32)
+        dy = None if ci.dy is None else np.asarray(ci.dy, np.float32)
+        if ci.freqs is not None:
+            P = oracle.bls(t, y, dy, nb, kmin, kmax, freqs=np.asarray(ci.freqs), sign=sign)[0]
+        else:
+            P = oracle.bls(t, y, dy, nb, kmin, kmax, fmin=ci.fmin, df=ci.df, nf=ci.nf, sign=sign)[0]
+        scal = prep_of(ci)[3]
+        sro = np.sqrt(P)
+        srg = spec[o:o + len(P)].astype(np.float64)   # the spectrum holds SR = sqrt(P)
+        bad = np.abs(srg - sro) > sr_tol(sro, scal[3])
+        assert not bad.any(), (int(bad.sum()), float(np.max(np.abs(srg - sro) - sr_tol(sro, scal[3]))))
+        o += len(P)
+
+
+@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("sign", ["dips", "both"])
+def test_spectrum_matches_oracle_every_tile_width(case, sign):
+    name, cis, nb, qmin, qmax = _cases()[case]
+    ref = None
+    for T in (128, 96, 64, 32, 48):
+        try:
+            spec, pk = _search(cis, nb, qmin, qmax, T=T, sign=sign)
+        except bls.BLSError as e:   # T columns of nb bins exceed shared memory
+            assert "shared memory" in str(e) and ref is None and T > 64
+            continue
+        if ref is None:
+            _oracle_check(cis, spec, nb, qmin, qmax, bls.SIGN[sign])
+            ref = (spec, pk)
+        elif T % 32 == 0:   # warp-specialised: identical to T = 128
+            assert np.array_equal(spec, ref[0]), (name, T)
+            for f in ("j", "i1", "k", "power"):
+                assert np.array_equal(pk[f], ref[1][f]), (name, T, f)
+        else:               # one-group kernel: within FP32 rounding, same peaks
+            np.testing.assert_allclose(spec, ref[0], rtol=1e-6, atol=0)
+            _oracle_check(cis, spec, nb, qmin, qmax, bls.SIGN[sign])
+
+
+_CHILD = r"""
+import sys, numpy as np
+sys.path.insert(0, sys.argv[1])
+from tests import test_gpu_ws as W
+name, cis, nb, qmin, qmax = W._cases()[int(sys.argv[2])]
+spec, pk = W._search(cis, nb, qmin, qmax, sign=sys.argv[3])
+np.save(sys.argv[4], spec)
+np.save(sys.argv[5], pk)
+"""
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_one_group_kernel_agrees(case, tmp_path):
+    name, cis, nb, qmin, qmax = _cases()[case]
+    spec, pk = _search(cis, nb, qmin, qmax)
+    env = dict(os.environ, BLS_FOLD_WS="0")
+    f1, f2 = str(tmp_path / "spec.npy"), str(tmp_path / "pk.npy")
+    subprocess.run([sys.executable, "-c", _CHILD, ROOT, str(case), "dips", f1, f2], env=env,
+                   check=True, timeout=600, cwd=ROOT)
+    spec1, pk1 = np.load(f1), np.load(f2)
+    np.testing.assert_allclose(spec, spec1, rtol=1e-6, atol=0)
+    for f in ("j", "i1", "k", "power"):   # the best peak of each curve
+        assert np.array_equal(pk[:, 0][f], pk1[:, 0][f]), (name, f)
