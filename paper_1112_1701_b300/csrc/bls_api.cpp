@@ -155,7 +155,7 @@ bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, 
     return BLS_OK;
 }
 
-bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g)
+bls_status fold_geometry(const bls_plan_impl* P, int nb, int kmin, int kmax, FoldGeom* g)
 {
     const int kahan = P->d.sum == BLS_SUM_KAHAN;
     const size_t esz = kahan ? 16 : 8;
@@ -174,11 +174,13 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g)
     // maxima at the end of a tile)
     if (P->d.point_chunk > 0) g->chunk = std::max(32, (P->d.point_chunk + 15) & ~15);
     else g->chunk = tmax(512) >= tmax(256) ? 512 : 256;
-    int T = P->d.freqs_per_block > 0 ? P->d.freqs_per_block : tmax(g->chunk);
+    int T = P->d.freqs_per_block > 0 ? P->d.freqs_per_block
+                                     : fold_preferred_cols(tmax(g->chunk), kahan, nb, kmin, kmax);
     if (T < 16) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", nb);
     if (T > maxT) T = maxT;
     g->T = T;
     g->stride = (T + 15) & ~15;
+    g->ws = fold_use_ws(T, kahan, nb, kmin, kmax);
     g->smem = fold_smem_bytes(T, g->stride, nb, g->chunk, kahan);
     if (g->smem + kFoldSmemReserve > P->smem_optin)
         return set_error(BLS_ERR_INVALID, "nb = %d with %d frequencies per block needs %zu B of shared memory (> %zu)",
@@ -315,11 +317,12 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     if (tiled) {
         for (int c = 0; c < nc; ++c) {
             FoldGeom g;
-            bls_status s = fold_geometry(P, specs[g0 + c].nb, &g);
+            bls_status s = fold_geometry(P, specs[g0 + c].nb, specs[g0 + c].kmin, specs[g0 + c].kmax, &g);
             if (s != BLS_OK) return s;
             int k = -1;
             for (size_t q = 0; q < geoms.size(); ++q)
-                if (geoms[q].T == g.T && geoms[q].stride == g.stride && geoms[q].chunk == g.chunk) { k = (int)q; break; }
+                if (geoms[q].T == g.T && geoms[q].stride == g.stride && geoms[q].chunk == g.chunk &&
+                    geoms[q].ws == g.ws) { k = (int)q; break; }
             if (k < 0) { geoms.push_back(g); cls.emplace_back(); k = (int)geoms.size() - 1; }
             else geoms[k].smem = std::max(geoms[k].smem, g.smem);
             cls[k].push_back(c);
@@ -448,7 +451,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     std::vector<int> grids(cls.size());
     for (size_t q = 0; q < cls.size(); ++q) {
         const int bps = fold_blocks_per_sm(geoms[q].T, geoms[q].smem, P->d.phase,
-                                           P->d.sum == BLS_SUM_KAHAN, P->d.sign);
+                                           P->d.sum == BLS_SUM_KAHAN, P->d.sign, geoms[q].ws);
         long long grid = std::min<long long>((long long)P->sm_count * bps, totals[q]);
         grids[q] = (int)std::max<long long>(grid, 1);
     }
@@ -510,7 +513,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
                 fp.chunk = geoms[q].chunk;
                 fp.stride = geoms[q].stride;
                 if ((x = launch_fold_sweep(fp, geoms[q].T, grids[q], P->d.phase, P->d.sum == BLS_SUM_KAHAN,
-                                           P->d.sign, geoms[q].smem, st)) != cudaSuccess)
+                                           geoms[q].ws, P->d.sign, geoms[q].smem, st)) != cudaSuccess)
                     return x;
                 ++launches;
                 ++fold_launches;
@@ -787,7 +790,9 @@ bls_status bls_plan_create(const bls_plan_desc* desc, void* cuda_stream, bls_pla
         if (cudaEventCreate(&P->ev[q]) != cudaSuccess) { cudaGetLastError(); P->ev[0] = nullptr; break; }
     if (d.algo == BLS_ALGO_TILED) {
         FoldGeom g;
-        bls_status s = fold_geometry(P, d.nb, &g);
+        int kmin = 1, kmax = 1;
+        bls_status s = bls_kminmax(d.nb, d.qmin, d.qmax, &kmin, &kmax);
+        if (s == BLS_OK) s = fold_geometry(P, d.nb, kmin, kmax, &g);
         if (s != BLS_OK) {
             if (P->own_stream) cudaStreamDestroy(P->stream);
             delete P;

@@ -125,7 +125,7 @@ size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int kahan);
 
 cudaError_t launch_prep(CurveDesc* d_curves, const int* slots, int ncurves, int* err, int phase,
                         cudaStream_t s);
-cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan,
+cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan, bool ws,
                               int sign, size_t smem, cudaStream_t s);
 cudaError_t launch_reduce(const ReduceParams& p, int ncurves, cudaStream_t s);
 size_t reduce_smem_bytes(int nb_max, int topk, int kahan);
@@ -140,7 +140,11 @@ cudaError_t launch_plain_f64(const CurveDesc* d_curve, const double* w64, const 
 cudaError_t launch_prep_f64(const CurveDesc* d_curves, int ncurves, double* w64, double* wx64,
                             cudaStream_t s);
 int fold_sweep_max_threads();
-int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign);
+// Whether a class of curves (tile width T, nb, widths kmin..kmax) runs in the
+// warp-specialised fold-sweep kernel, and the tile width preferred for it.
+bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax);
+int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax);
+int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, bool ws);
 int fold_block_threads(int cols);   // threads of a fold-sweep block with `cols` columns
 
 }  // namespace blsgpu

@@ -684,7 +684,7 @@ __device__ __forceinline__ float bin_x(const unsigned char* hist, size_t S, int 
 // Fast sweep: the largest power P of any box, without its position.
 //
 // SB consecutive starts share every bin load; their sums are carried as SB/2 packed pairs
-// (one f32x2 instruction updates two starts).  Conditions: kmin = 1, kmax >= SB - 1, and
+// (one f32x2 instruction updates two starts).  Conditions: kmax - kmin + 1 >= SB - 1, and
 // no box can hold more than 0.89 of the weight (checked by the caller).  The starts of the
 // last block may pass nb; they repeat earlier starts and cannot change the maximum.
 //
@@ -722,17 +722,23 @@ __device__ __forceinline__ float fmax3(float a, float b, float c)
     return d;
 }
 
-template <int SIGN, int FORM>
+template <int SIGN, int FORM, bool SEED>
 __device__ __forceinline__ void eval_pair(u64& R, u64& X, const u64& HW2, const u64& HX2,
                                           bool init, bool use0, bool use1, float& b0, float& b1)
 {
     if (init) {
+        // the second start of the pair begins at the next bin; with SEED, (R, X) already
+        // hold the starts' seeds (see sweep_fast)
         float hw, hw1, hx, hx1;
         upk(HW2, hw, hw1);
         upk(HX2, hx, hx1);
-        // the second start of the pair begins at the next bin
-        R = FORM ? pk(-hw - kEmptyBox, -kEmptyBox) : pk(-hw, 0.0f);
-        X = pk(hx, 0.0f);
+        if (SEED) {
+            R = sub2(R, pk(hw, 0.0f));
+            X = add2(X, pk(hx, 0.0f));
+        } else {
+            R = FORM ? pk(-hw - kEmptyBox, -kEmptyBox) : pk(-hw, 0.0f);
+            X = pk(hx, 0.0f);
+        }
     } else {
         R = sub2(R, HW2);
         X = add2(X, HX2);
@@ -768,22 +774,21 @@ __device__ __forceinline__ void eval_pair(u64& R, u64& X, const u64& HW2, const 
 
 // One step of the fast sweep over one block: bin value (hw, hx) for the pairs [Q0, Q1),
 // with the ramp rules given by (init, use0, use1) per pair (see sweep_fast).
-template <int SIGN, int NP, int FORM>
+template <int SIGN, int NP, int FORM, bool SEED>
 __device__ __forceinline__ void sweep_step(float hw, float hx, u64* R, u64* X, float* b0,
-                                           float* b1, int mm, int phase,
-                                           int e)
+                                           float* b1, int mm, int phase, int e)
 {
     const u64 HW2 = pk(hw, hw), HX2 = pk(hx, hx);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         if (phase == 0) {          // ramp-up at bin mm
             if (2 * q > mm) continue;
-            eval_pair<SIGN, FORM>(R[q], X[q], HW2, HX2, 2 * q == mm, true, 2 * q < mm, b0[q], b1[q]);
+            eval_pair<SIGN, FORM, SEED>(R[q], X[q], HW2, HX2, 2 * q == mm, true, 2 * q < mm, b0[q], b1[q]);
         } else if (phase == 1) {   // steady
-            eval_pair<SIGN, FORM>(R[q], X[q], HW2, HX2, false, true, true, b0[q], b1[q]);
+            eval_pair<SIGN, FORM, SEED>(R[q], X[q], HW2, HX2, false, true, true, b0[q], b1[q]);
         } else {                   // ramp-down step e
             if (2 * q + 1 < e + 1) continue;
-            eval_pair<SIGN, FORM>(R[q], X[q], HW2, HX2, false, 2 * q >= e + 1, true, b0[q], b1[q]);
+            eval_pair<SIGN, FORM, SEED>(R[q], X[q], HW2, HX2, false, 2 * q >= e + 1, true, b0[q], b1[q]);
         }
     }
 }
@@ -874,43 +879,72 @@ struct TmemBins {
 // starts [0, half), block B [half, 2 half) with half = SB * ceil(nb / (2 SB)); starts past
 // nb repeat earlier ones (cyclic) and cannot change the maximum.  The outer steps i0 are
 // dealt round-robin to `nparts` threads sharing the histogram; `part` is this thread's.
-// A block reads kmax + SB - 1 consecutive bins (cyclic) from its start.  FB is the form of
-// block B.
-template <int SB, int SIGN, class Bins, int FB = kFormB>
-__device__ __forceinline__ float sweep_fast(Bins& src, int nb, int kmax, int part, int nparts)
+// Widths kmin .. kmax: every box of start s holds bins s .. s + kmin - 2, whose sums (in
+// bin order) seed the start's running sums, and the steps then run over the kx = kmax -
+// kmin + 1 widths as for kmin = 1.  A block reads SB + kmin - 2 bins for the seeds (when
+// kmin > 1) and kx + SB - 1 bins from its start + kmin - 1 (cyclic).  FB is the form of
+// block B.  Condition: kx >= SB - 1.
+template <int SB, int SIGN, class Bins, int FB, bool SEED>
+__device__ __forceinline__ float sweep_fast_t(Bins& src, int nb, int kmin, int kmax, int part,
+                                              int nparts)
 {
     constexpr int NP = SB / 2;
+    const int kx = kmax - kmin + 1;
     float a0[NP], a1[NP], c0[NP], c1[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) { a0[q] = 0.0f; a1[q] = 0.0f; c0[q] = 0.0f; c1[q] = 0.0f; }
     const int half = SB * ((nb + 2 * SB - 1) / (2 * SB));
     for (int i0 = part * SB; i0 < half; i0 += nparts * SB) {
+        // R holds -r (the form-1 block offset by -kEmptyBox, see eval_pair), X holds s;
+        // with kmin > 1 both start from the seeds: start s (s = 0 .. SB-1 of the block)
+        // takes bins s .. s + kmin - 2, in bin order
+        const u64 r0B = FB ? pk(-kEmptyBox, -kEmptyBox) : 0ull;
         u64 RA[NP], XA[NP], RB[NP], XB[NP];
 #pragma unroll
-        for (int q = 0; q < NP; ++q) { RA[q] = 0ull; XA[q] = 0ull; RB[q] = 0ull; XB[q] = 0ull; }
+        for (int q = 0; q < NP; ++q) { RA[q] = 0ull; XA[q] = 0ull; RB[q] = r0B; XB[q] = 0ull; }
         int mb = i0 + half;
         while (mb >= nb) mb -= nb;
-        src.start(i0, mb);
+        if (SEED) {
+            src.start(i0, mb);
+            for (int m = 0; m < SB + kmin - 2; ++m) {
+                float hwa, hxa, hwb, hxb;
+                src.next(hwa, hxa, hwb, hxb);
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    const bool t0 = m >= 2 * q && m <= 2 * q + kmin - 2;
+                    const bool t1 = m >= 2 * q + 1 && m <= 2 * q + kmin - 1;
+                    RA[q] = sub2(RA[q], pk(t0 ? hwa : 0.0f, t1 ? hwa : 0.0f));
+                    XA[q] = add2(XA[q], pk(t0 ? hxa : 0.0f, t1 ? hxa : 0.0f));
+                    RB[q] = sub2(RB[q], pk(t0 ? hwb : 0.0f, t1 ? hwb : 0.0f));
+                    XB[q] = add2(XB[q], pk(t0 ? hxb : 0.0f, t1 ? hxb : 0.0f));
+                }
+            }
+            src.finish();
+        }
+        int ma = i0 + kmin - 1, mc = mb + kmin - 1;
+        while (ma >= nb) ma -= nb;
+        while (mc >= nb) mc -= nb;
+        src.start(ma, mc);
 #pragma unroll
         for (int mm = 0; mm < SB - 1; ++mm) {
             float hwa, hxa, hwb, hxb;
             src.next(hwa, hxa, hwb, hxb);
-            sweep_step<SIGN, NP, 0>(hwa, hxa, RA, XA, a0, a1, mm, 0, 0);
-            sweep_step<SIGN, NP, FB>(hwb, hxb, RB, XB, c0, c1, mm, 0, 0);
+            sweep_step<SIGN, NP, 0, SEED>(hwa, hxa, RA, XA, a0, a1, mm, 0, 0);
+            sweep_step<SIGN, NP, FB, SEED>(hwb, hxb, RB, XB, c0, c1, mm, 0, 0);
         }
 #pragma unroll 2
-        for (int mm = SB - 1; mm < kmax; ++mm) {
+        for (int mm = SB - 1; mm < kx; ++mm) {
             float hwa, hxa, hwb, hxb;
             src.next(hwa, hxa, hwb, hxb);
-            sweep_step<SIGN, NP, 0>(hwa, hxa, RA, XA, a0, a1, 0, 1, 0);
-            sweep_step<SIGN, NP, FB>(hwb, hxb, RB, XB, c0, c1, 0, 1, 0);
+            sweep_step<SIGN, NP, 0, SEED>(hwa, hxa, RA, XA, a0, a1, 0, 1, 0);
+            sweep_step<SIGN, NP, FB, SEED>(hwb, hxb, RB, XB, c0, c1, 0, 1, 0);
         }
 #pragma unroll
         for (int e = 0; e < SB - 1; ++e) {
             float hwa, hxa, hwb, hxb;
             src.next(hwa, hxa, hwb, hxb);
-            sweep_step<SIGN, NP, 0>(hwa, hxa, RA, XA, a0, a1, 0, 2, e);
-            sweep_step<SIGN, NP, FB>(hwb, hxb, RB, XB, c0, c1, 0, 2, e);
+            sweep_step<SIGN, NP, 0, SEED>(hwa, hxa, RA, XA, a0, a1, 0, 2, e);
+            sweep_step<SIGN, NP, FB, SEED>(hwb, hxb, RB, XB, c0, c1, 0, 2, e);
         }
         src.finish();
     }
@@ -923,6 +957,16 @@ __device__ __forceinline__ float sweep_fast(Bins& src, int nb, int kmax, int par
         else zb = SIGN ? fmaxf(zb, fmaxf(c0[q], c1[q])) : fminf(zb, fminf(c0[q], c1[q]));
     }
     return fmaxf(fmaxf(za * za, zb * zb), pb);
+}
+
+// The fast sweep; kmin > 1 takes the seeded variant (a separate instantiation, so that the
+// common kmin = 1 case keeps its registers).
+template <int SB, int SIGN, class Bins, int FB = kFormB>
+__device__ __forceinline__ float sweep_fast(Bins& src, int nb, int kmin, int kmax, int part,
+                                            int nparts)
+{
+    return kmin > 1 ? sweep_fast_t<SB, SIGN, Bins, FB, true>(src, nb, kmin, kmax, part, nparts)
+                    : sweep_fast_t<SB, SIGN, Bins, FB, false>(src, nb, kmin, kmax, part, nparts);
 }
 
 struct Best {
@@ -1048,7 +1092,7 @@ template <int KAHAN, int SIGN, int SB>
 __device__ __forceinline__ float sweep_max(const unsigned char* hist, int stride, int nb,
                                            int kmin, int kmax, int part, int nparts)
 {
-    if (!KAHAN && kmin == 1 && kmax >= SB - 1) {
+    if (!KAHAN && kmax - kmin + 1 >= SB - 1) {
         const unsigned hbase = (unsigned)__cvta_generic_to_shared(hist);
         const unsigned rowb = (unsigned)stride * 8u;
         float wmax = 0.0f;
@@ -1081,7 +1125,7 @@ __device__ __forceinline__ float sweep_max(const unsigned char* hist, int stride
             src.hbase = hbase;
             src.rowb = rowb;
             src.nb = nb;
-            return sweep_fast<SB, SIGN>(src, nb, kmax, part, nparts);
+            return sweep_fast<SB, SIGN>(src, nb, kmin, kmax, part, nparts);
         }
     }
     if (part != 0) return 0.0f;
@@ -1094,10 +1138,26 @@ __device__ __forceinline__ float sweep_max(const unsigned char* hist, int stride
 // Starts per block of the fast sweep for wide boxes (kmax >= 15): 8 or 10, whichever
 // wastes fewer starts once the nb starts are dealt to nparts threads in steps of two
 // blocks (nb = 200 over 2 threads: 10 gives 5 + 5 steps with none wasted, 8 gives 7 + 6).
-__device__ __forceinline__ bool wide_sweep_10(int nb, int nparts)
+__host__ __device__ __forceinline__ bool wide_sweep_10(int nb, int nparts)
 {
     const int s8 = 16 * nparts, s10 = 20 * nparts;
     return ((nb + s10 - 1) / s10) * s10 < ((nb + s8 - 1) / s8) * s8;
+}
+
+// Starts per block of the fast sweep for widths kmin .. kmax (one sweep thread per column).
+__host__ __device__ __forceinline__ int sweep_block(int nb, int kmin, int kmax)
+{
+    return kmax - kmin + 1 < 15 ? 4 : (wide_sweep_10(nb, 1) ? 10 : 8);
+}
+
+// Whether the warp-specialised kernel sweeps a tile from its TMEM copy: the fast sweep
+// covers the widths, and the copy (bins read up to nb + kmax + SB - 2 by the sweep with
+// its one bin of read-ahead, up to 7 more by the copy's last group of 8) fits the 512
+// columns with its bins past nb wrapping once.
+__host__ __device__ __forceinline__ bool ws_tmem_fits(int nb, int kmin, int kmax)
+{
+    const int SB = sweep_block(nb, kmin, kmax);
+    return kmax - kmin + 1 >= SB - 1 && nb + kmax + SB + 8 <= 257 && kmax + SB + 8 <= nb;
 }
 
 constexpr int kFoldMaxThreads = 256;
@@ -1231,7 +1291,7 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
         // than the 4 B x blockDim.x <= 1024 B needed)
         float v = 0.0f;
         if (active)
-            v = kmax < 15 ? sweep_max<KAHAN, SIGN, 4>(hist, p.stride, nb, kmin, kmax, part, nparts)
+            v = kmax - kmin + 1 < 15 ? sweep_max<KAHAN, SIGN, 4>(hist, p.stride, nb, kmin, kmax, part, nparts)
                 : wide_sweep_10(nb, nparts)
                     ? sweep_max<KAHAN, SIGN, 10>(hist, p.stride, nb, kmin, kmax, part, nparts)
                     : sweep_max<KAHAN, SIGN, 8>(hist, p.stride, nb, kmin, kmax, part, nparts);
@@ -1267,9 +1327,9 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
 // the issue slots that the binning chain leaves idle.  With T = 128 the sweep group has
 // two threads per column (two warps per TMEM lane quadrant), which split the copy, the
 // zeroing and the box starts.  The checks of the fast sweep's condition and the exact
-// sweep (rare) read the TMEM copy; tiles whose TMEM copy would not fit 512 columns, or that
-// the fast sweep does not cover (kmin > 1, small kmax), are swept from shared memory before
-// the hand-back.  The bins, the sums and the set of boxes are those of fold_sweep_kernel;
+// sweep (rare) read the TMEM copy; tiles whose TMEM copy would not fit 512 columns (or
+// whose copy would wrap more than once, nb < kmax + SB + 8), or that the fast sweep does not
+// cover (kmax - kmin < SB - 2), are swept from shared memory before the hand-back.  The bins, the sums and the set of boxes are those of fold_sweep_kernel;
 // both sweep blocks rank boxes by the signed residue, so a frequency's power can differ
 // from fold_sweep_kernel's in the last bits (both are within the approximation's 2^-22).
 //
@@ -1371,11 +1431,12 @@ struct TmemStream {
 // the shared-reciprocal form and leans on the special-function unit, which the binning
 // warps sharing the SM sub-partitions do not use.
 template <int SB, int SIGN>
-__device__ __forceinline__ float sweep_tmem(unsigned tbase, int nb, int kmax, int part, int nparts)
+__device__ __forceinline__ float sweep_tmem(unsigned tbase, int nb, int kmin, int kmax, int part,
+                                            int nparts)
 {
     TmemBins src;
     src.base = tbase;
-    return sweep_fast<SB, SIGN, TmemBins, 0>(src, nb, kmax, part, nparts);
+    return sweep_fast<SB, SIGN, TmemBins, 0>(src, nb, kmin, kmax, part, nparts);
 }
 
 // Heaviest run of kmax consecutive bins (cyclic), as in sweep_max, from the TMEM copy.
@@ -1576,12 +1637,8 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             float* const res = sl.cd.res;
             const int j = tile * T + col;
             const bool active = j < nf;
-            const int SB = kmax < 15 ? 4 : (wide_sweep_10(nb, 1) ? 10 : 8);
-            // bins read from TMEM: up to nb + kmax + SB - 2 by the fast sweep (with its one
-            // bin of read-ahead), up to 7 more by the copy's last group of 8; the copy's
-            // bins past nb wrap once
-            const bool use_tmem = kmin == 1 && kmax >= SB - 1 && nb + kmax + SB + 8 <= 257 &&
-                                  kmax + SB + 8 <= nb;
+            const int SB = sweep_block(nb, kmin, kmax);
+            const bool use_tmem = ws_tmem_fits(nb, kmin, kmax);
             float v = 0.0f, wmax = 0.0f;
             if (use_tmem) {
                 // copy bins 0 .. L-1 (bin b >= nb repeats bin b - nb; L <= 2 nb) into the
@@ -1649,9 +1706,9 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                     }
                 }
                 __syncwarp();
-                float vf = SB == 4 ? sweep_tmem<4, SIGN>(tbase, nb, kmax, part, nparts)
-                           : SB == 10 ? sweep_tmem<10, SIGN>(tbase, nb, kmax, part, nparts)
-                                      : sweep_tmem<8, SIGN>(tbase, nb, kmax, part, nparts);
+                float vf = SB == 4 ? sweep_tmem<4, SIGN>(tbase, nb, kmin, kmax, part, nparts)
+                           : SB == 10 ? sweep_tmem<10, SIGN>(tbase, nb, kmin, kmax, part, nparts)
+                                      : sweep_tmem<8, SIGN>(tbase, nb, kmin, kmax, part, nparts);
                 if (nparts == 2) {   // the parts' maxima meet in shared memory
                     if (part == 1) s_wpart2[col] = vf;
                     group_sync(kBarSweep, NS);
@@ -1674,8 +1731,9 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
     }
 }
 
-// The warp-specialised kernel serves every plain-sum tile geometry with T a multiple of 32
-// (at most 128); BLS_FOLD_WS=0 in the environment selects fold_sweep_kernel instead.
+// Tile geometries the warp-specialised kernel can take: plain sums, T a multiple of 32, at
+// most 128 (one binning thread per TMEM lane).  BLS_FOLD_WS=0 in the environment selects
+// fold_sweep_kernel for every class.
 static bool use_ws(int T, int kahan)
 {
     static const int env = [] {
@@ -1689,6 +1747,28 @@ static bool use_ws(int T, int kahan)
 // part (two parts when T = 128, whose two sweep warps per TMEM lane quadrant share the
 // lanes; otherwise one).
 static int ws_threads(int T) { return T == 128 ? 3 * T : 2 * T; }
+
+// Frequencies per tile for plain sums, given the most whose histograms fit (a multiple of
+// 16, at most 256).  Widths strictly between 128 and 256 would leave the one-group kernel
+// with one thread per column, slower than the warp-specialised kernel with 128 columns
+// (e.g. nb = 150: 21.8 ms at 160 columns against 14.8 ms at 128, 256 curves x 20k
+// frequencies); 256 columns (nb <= 100) keep the one-group kernel, whose eight binning
+// warps then win (11.5 ms against 13.1 ms at nb = 100).
+int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax)
+{
+    if (fold_use_ws(128, kahan, nb, kmin, kmax) && tmax > 128 && tmax < 256) return 128;
+    return tmax;
+}
+
+// The warp-specialised kernel takes classes whose tiles it sweeps from TMEM; where the
+// copy does not fit (large nb) or the fast sweep does not apply, its sweep group would
+// sweep from shared memory while the binning group waits, and the one-group kernel, whose
+// threads all bin and then all sweep, is faster (nb = 400: 81.7 ms at 48 columns against
+// 97.3 ms at 64, 256 curves x 20k frequencies).
+bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax)
+{
+    return use_ws(T, kahan) && ws_tmem_fits(nb, kmin, kmax);
+}
 
 // Dynamic shared memory of a warp-specialised block: at least half of an SM's shared memory,
 // so that no second block (which would wait for the first one's TMEM) lands on the SM.
@@ -1708,11 +1788,11 @@ static size_t ws_smem(size_t smem)
 
 template <int PHASE, int KAHAN, int SIGN>
 static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t smem,
-                                 cudaStream_t s)
+                                 cudaStream_t s, bool ws)
 {
     FoldParams q = p;
     q.cols = T;
-    if (use_ws(T, KAHAN)) {
+    if (ws && use_ws(T, KAHAN)) {
         auto k = fold_sweep_ws_kernel<PHASE, SIGN>;
         const size_t sm = ws_smem(smem);
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1730,9 +1810,9 @@ static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t sm
 }
 
 template <int PHASE, int KAHAN, int SIGN>
-static int blocks_t(int T, size_t smem)
+static int blocks_t(int T, size_t smem, bool ws)
 {
-    if (use_ws(T, KAHAN)) {
+    if (ws && use_ws(T, KAHAN)) {
         // one block per SM: all of TMEM and (nearly) all of shared memory
         auto k = fold_sweep_ws_kernel<PHASE, SIGN>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem(smem)) != cudaSuccess) {
@@ -1754,12 +1834,12 @@ static int blocks_t(int T, size_t smem)
     return nb > 0 ? nb : 1;
 }
 
-int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign)
+int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, bool ws)
 {
 #define BLS_OCC(PH)                                                                   \
     if (phase == PH) {                                                                \
-        if (kahan) return sign ? blocks_t<PH, 1, 1>(T, smem) : blocks_t<PH, 1, 0>(T, smem); \
-        return sign ? blocks_t<PH, 0, 1>(T, smem) : blocks_t<PH, 0, 0>(T, smem);      \
+        if (kahan) return sign ? blocks_t<PH, 1, 1>(T, smem, ws) : blocks_t<PH, 1, 0>(T, smem, ws); \
+        return sign ? blocks_t<PH, 0, 1>(T, smem, ws) : blocks_t<PH, 0, 0>(T, smem, ws);      \
     }
     BLS_OCC(kPhaseDF32)
     BLS_OCC(kPhaseF64)
@@ -1769,15 +1849,15 @@ int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign)
     return 1;
 }
 
-cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan,
+cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan, bool ws,
                               int sign, size_t smem, cudaStream_t s)
 {
 #define BLS_DISPATCH(PH)                                                              \
     if (phase == PH) {                                                                \
-        if (kahan) return sign ? launch_fold_t<PH, 1, 1>(p, T, grid, smem, s)         \
-                               : launch_fold_t<PH, 1, 0>(p, T, grid, smem, s);        \
-        return sign ? launch_fold_t<PH, 0, 1>(p, T, grid, smem, s)                    \
-                    : launch_fold_t<PH, 0, 0>(p, T, grid, smem, s);                   \
+        if (kahan) return sign ? launch_fold_t<PH, 1, 1>(p, T, grid, smem, s, ws)         \
+                               : launch_fold_t<PH, 1, 0>(p, T, grid, smem, s, ws);        \
+        return sign ? launch_fold_t<PH, 0, 1>(p, T, grid, smem, s, ws)                    \
+                    : launch_fold_t<PH, 0, 0>(p, T, grid, smem, s, ws);                   \
     }
     BLS_DISPATCH(kPhaseDF32)
     BLS_DISPATCH(kPhaseF64)

@@ -57,6 +57,7 @@ struct FoldGeom {
     int chunk;      // staged points per chunk
     size_t smem;    // dynamic shared memory
     int grid;       // persistent blocks
+    bool ws;        // warp-specialised kernel
 };
 
 struct Server;
@@ -109,7 +110,7 @@ struct ShapeReq {
 };
 void to_peak(const DevPeak& s, bls_peak* d);   // device record -> ABI record
 // Block size / stride / chunk / shared memory for a curve with nb bins.
-bls_status fold_geometry(const bls_plan_impl* P, int nb, FoldGeom* g);
+bls_status fold_geometry(const bls_plan_impl* P, int nb, int kmin, int kmax, FoldGeom* g);
 // Work-list order: curves by decreasing cost (n * nf), ties by index.
 void order_by_cost(const std::vector<CurveSpec>& cs, const std::vector<int>& idx,
                    std::vector<int>* out);

@@ -270,7 +270,8 @@ bool Server::step()
         if (take <= 0) continue;
         int k = -1;
         for (size_t q = 0; q < geoms.size(); ++q)
-            if (geoms[q].T == r->geom.T && geoms[q].stride == r->geom.stride && geoms[q].chunk == r->geom.chunk) { k = (int)q; break; }
+            if (geoms[q].T == r->geom.T && geoms[q].stride == r->geom.stride && geoms[q].chunk == r->geom.chunk &&
+                geoms[q].ws == r->geom.ws) { k = (int)q; break; }
         if (k < 0) { geoms.push_back(r->geom); cls.emplace_back(); k = (int)geoms.size() - 1; }
         else geoms[k].smem = std::max(geoms[k].smem, r->geom.smem);
         cls[k].push_back({r, take});
@@ -316,11 +317,12 @@ bool Server::step()
             fp.chunk = geoms[q].chunk;
             fp.stride = geoms[q].stride;
             const int bps = fold_blocks_per_sm(geoms[q].T, geoms[q].smem, P->d.phase,
-                                               P->d.sum == BLS_SUM_KAHAN, P->d.sign);
+                                               P->d.sum == BLS_SUM_KAHAN, P->d.sign, geoms[q].ws);
             long long grid = std::min<long long>((long long)P->sm_count * bps, tot[q]);
             cudaStream_t sq = nstr > 1 ? cls_stream[q % nstr] : stream;
             if ((e = launch_fold_sweep(fp, geoms[q].T, (int)std::max<long long>(grid, 1), P->d.phase,
-                                       P->d.sum == BLS_SUM_KAHAN, P->d.sign, geoms[q].smem, sq)) != cudaSuccess) {
+                                       P->d.sum == BLS_SUM_KAHAN, geoms[q].ws, P->d.sign, geoms[q].smem,
+                                       sq)) != cudaSuccess) {
                 fail_all(std::string("fold-sweep launch: ") + cudaGetErrorString(e));
                 return false;
             }
@@ -566,7 +568,7 @@ bls_status bls_submit(bls_plan* P, const bls_curve* c, uint64_t* ticket)
     r->spec.y = r->y.data();
     r->spec.dy = s.dy ? r->dy.data() : nullptr;
     r->spec.freqs = s.freqs ? r->freqs.data() : nullptr;
-    if ((st = fold_geometry(P, s.nb, &r->geom)) != BLS_OK) { delete r; return st; }
+    if ((st = fold_geometry(P, s.nb, s.kmin, s.kmax, &r->geom)) != BLS_OK) { delete r; return st; }
     const long long n2 = (s.n + 1) & ~1;
     r->bytes = up256((size_t)s.n * 8) + up256((size_t)s.n * 4) + (s.dy ? up256((size_t)s.n * 4) : 0) +
                (s.freqs ? up256((size_t)s.nf * 8) : 0) + up256((size_t)(n2 + 2) * 16) +

@@ -124,7 +124,8 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
         return T;
     };
     const int chunk = tmax(512) >= tmax(256) ? 512 : 256;
-    const int T = tmax(chunk);
+    const int T = fold_preferred_cols(tmax(chunk), 0, c->nb, kmin, kmax);
+    const bool ws = fold_use_ws(T, 0, c->nb, kmin, kmax);
     if (T < 16) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", c->nb);
     const size_t smem = fold_smem_bytes(T, T, c->nb, chunk, 0);
 
@@ -158,9 +159,9 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
     fp.err = err;
     fp.chunk = chunk;
     fp.stride = T;
-    long long grid = (long long)sms * fold_blocks_per_sm(T, smem, kPhaseFX64, 0, sign);
+    long long grid = (long long)sms * fold_blocks_per_sm(T, smem, kPhaseFX64, 0, sign, ws);
     if (grid > ntiles) grid = ntiles;
-    if ((e = launch_fold_sweep(fp, T, (int)grid, kPhaseFX64, 0, sign, smem, s)) != cudaSuccess)
+    if ((e = launch_fold_sweep(fp, T, (int)grid, kPhaseFX64, 0, ws, sign, smem, s)) != cudaSuccess)
         return cuda_fail(e, "fold-sweep launch");
     ReduceParams rp;
     rp.curves = cdesc;
