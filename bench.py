@@ -676,6 +676,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-shapes", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library's launch rules instead of the autotuner's choice")
     ap.add_argument("--plain-curves", type=int, default=8,
                     help="curves of the plain FP64 baseline timing (0 = skip)")
     ap.add_argument("--serving", action="store_true", help="run the serving benchmark")
@@ -719,7 +721,7 @@ def main():
         return run_unbinned(args)
 
     import torch
-    from paper_1112_1701_b300 import bls, shard
+    from paper_1112_1701_b300 import autotune, bls, shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -742,7 +744,16 @@ def main():
     evals = box_evals(batch)
     dev = bls.curves_from_batch(batch, device="cuda")
     stream = torch.cuda.current_stream()
-    plan = bls.Plan(nb=NB, qmin=QMIN, qmax=QMAX, topk=1, stream=stream.cuda_stream)
+    # launch parameters: the autotuner's (timed on a sample before the timed region)
+    tuned = None
+    launch_kw = {}
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        res = autotune.tune(dev, NB, QMIN, QMAX, stream=stream.cuda_stream,
+                            cache=autotune.TuneCache(None))
+        tuned = dict(res.to_json(), tuning_s=time.perf_counter() - t0)
+        launch_kw = res.best.plan_kwargs()
+    plan = bls.Plan(nb=NB, qmin=QMIN, qmax=QMAX, topk=1, stream=stream.cuda_stream, **launch_kw)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     for _ in range(args.warmup):
@@ -834,6 +845,10 @@ def main():
                           "reduce": prof["reduce_ms"] / args.steps}}
     if e2e:
         line["e2e"] = e2e
+    line["config"]["launch"] = (dict(launch_kw, source="autotuner") if tuned else
+                                {"source": "library rules (--no-autotune)"})
+    if tuned:
+        line["autotune"] = tuned
 
     # trapezoid refit of the peaks: the extra time of a search that also refits them
     if rank == 0 and not args.no_shapes:

@@ -89,6 +89,23 @@ enum {
                                curve; the plan's qmin/qmax apply to every curve. */
 };
 
+/* Fold-sweep kernel of the tiled search.  BLS_FOLD_AUTO chooses per class of curves: the
+ * warp-specialised kernel (a binning warp group and a sweep warp group that takes each
+ * tile's histograms over through tensor memory) where the tile width is 32, 64, 96 or 128
+ * frequencies, the sums are plain FP32 and the class's bins fit its TMEM copy
+ * (nb + kmax + SB + 8 <= 257 and kmax + SB + 8 <= nb, SB = 4 for kmax - kmin < 14, else 8
+ * or 10), otherwise the one-group kernel (every thread bins, then every thread sweeps).
+ * BLS_FOLD_WS asks for the warp-specialised kernel wherever the tile width and the sums
+ * allow it (tiles whose copy does not fit are then swept from shared memory by the sweep
+ * group); BLS_FOLD_ONE_GROUP always takes the one-group kernel.  The environment variable
+ * BLS_FOLD_WS=0 forces the one-group kernel for every plan.  All give the FP64 bins; the
+ * per-frequency powers of the two kernels agree within the sweep's 2^-22 approximation. */
+enum {
+    BLS_FOLD_AUTO = 0,
+    BLS_FOLD_WS = 1,
+    BLS_FOLD_ONE_GROUP = 2
+};
+
 typedef struct {
     int nb;                     /* phase bins (>= 2); a curve may override */
     double qmin, qmax;          /* fractional box duration range, 0 < qmin <= qmax < 1 */
@@ -105,6 +122,7 @@ typedef struct {
                                    multiple of 16, at least 32); 0 = tuned */
     int max_active_requests;    /* serving: requests resident on the device at once; 0 = 64 */
     long long step_point_freqs; /* serving: point x frequency work per step; 0 = tuned */
+    int fold_kernel;            /* BLS_FOLD_*: which fold-sweep kernel runs the tiled search */
 } bls_plan_desc;
 
 /* One light curve and its trial-frequency grid. */

@@ -26,6 +26,7 @@ PHASE = {"fx64": 0, "f64": 1, "f32": 2, "df32": 3}
 SUM = {"f32": 0, "kahan": 1}
 SIGN = {"dips": 0, "both": 1}
 ALGO = {"tiled": 0, "plain_f64": 1, "unbinned": 2}
+FOLD = {"auto": 0, "ws": 1, "one_group": 2}
 
 
 class BLSError(RuntimeError):
@@ -40,7 +41,8 @@ class PlanDesc(C.Structure):
                 ("sum", C.c_int), ("sign", C.c_int), ("algo", C.c_int),
                 ("max_device_bytes", C.c_size_t), ("max_curves_per_launch", C.c_int),
                 ("freqs_per_block", C.c_int), ("point_chunk", C.c_int),
-                ("max_active_requests", C.c_int), ("step_point_freqs", C.c_longlong)]
+                ("max_active_requests", C.c_int), ("step_point_freqs", C.c_longlong),
+                ("fold_kernel", C.c_int)]
 
 
 class CurveStruct(C.Structure):
@@ -300,11 +302,11 @@ class Plan:
     def __init__(self, nb=200, qmin=0.005, qmax=0.15, kmin=0, kmax=0, topk=1, phase="fx64",
                  sum="f32", sign="dips", algo="tiled", max_device_bytes=0,
                  max_curves_per_launch=0, freqs_per_block=0, point_chunk=0,
-                 max_active_requests=0, step_point_freqs=0, stream=None):
+                 max_active_requests=0, step_point_freqs=0, fold_kernel="auto", stream=None):
         self.desc = PlanDesc(nb, qmin, qmax, kmin, kmax, topk, PHASE[phase], SUM[sum],
                              SIGN[sign], ALGO[algo], max_device_bytes, max_curves_per_launch,
                              freqs_per_block, point_chunk, max_active_requests,
-                             step_point_freqs)
+                             step_point_freqs, FOLD[fold_kernel])
         self.topk = topk
         h = C.c_void_p()
         _check(lib().bls_plan_create(C.byref(self.desc), stream, C.byref(h)))

@@ -175,12 +175,13 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, int kmin, int kmax, Fol
     if (P->d.point_chunk > 0) g->chunk = std::max(32, (P->d.point_chunk + 15) & ~15);
     else g->chunk = tmax(512) >= tmax(256) ? 512 : 256;
     int T = P->d.freqs_per_block > 0 ? P->d.freqs_per_block
-                                     : fold_preferred_cols(tmax(g->chunk), kahan, nb, kmin, kmax);
+                                     : fold_preferred_cols(tmax(g->chunk), kahan, nb, kmin, kmax,
+                                                           P->d.fold_kernel);
     if (T < 16) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", nb);
     if (T > maxT) T = maxT;
     g->T = T;
     g->stride = (T + 15) & ~15;
-    g->ws = fold_use_ws(T, kahan, nb, kmin, kmax);
+    g->ws = fold_use_ws(T, kahan, nb, kmin, kmax, P->d.fold_kernel);
     g->smem = fold_smem_bytes(T, g->stride, nb, g->chunk, kahan);
     if (g->smem + kFoldSmemReserve > P->smem_optin)
         return set_error(BLS_ERR_INVALID, "nb = %d with %d frequencies per block needs %zu B of shared memory (> %zu)",
@@ -749,6 +750,8 @@ bls_status bls_plan_create(const bls_plan_desc* desc, void* cuda_stream, bls_pla
         return set_error(BLS_ERR_INVALID, "freqs_per_block = %d, need a multiple of 16 up to %d", d.freqs_per_block,
                          fold_sweep_max_threads());
     if (d.point_chunk < 0 || d.point_chunk > 4096) return set_error(BLS_ERR_INVALID, "point_chunk = %d", d.point_chunk);
+    if (d.fold_kernel < BLS_FOLD_AUTO || d.fold_kernel > BLS_FOLD_ONE_GROUP)
+        return set_error(BLS_ERR_INVALID, "fold_kernel = %d", d.fold_kernel);
     if (d.max_curves_per_launch < 0 || d.max_active_requests < 0 || d.step_point_freqs < 0)
         return set_error(BLS_ERR_INVALID, "negative limit");
     int dev = 0;

@@ -141,9 +141,10 @@ cudaError_t launch_prep_f64(const CurveDesc* d_curves, int ncurves, double* w64,
                             cudaStream_t s);
 int fold_sweep_max_threads();
 // Whether a class of curves (tile width T, nb, widths kmin..kmax) runs in the
-// warp-specialised fold-sweep kernel, and the tile width preferred for it.
-bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax);
-int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax);
+// warp-specialised fold-sweep kernel under the plan's choice (BLS_FOLD_*), and the tile
+// width preferred for it.
+bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax, int choice);
+int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax, int choice);
 int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, bool ws);
 int fold_block_threads(int cols);   // threads of a fold-sweep block with `cols` columns
 

@@ -22,6 +22,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include "bls.h"
 #include "bls_internal.h"
 
 namespace blsgpu {
@@ -1754,9 +1755,9 @@ static int ws_threads(int T) { return T == 128 ? 3 * T : 2 * T; }
 // (e.g. nb = 150: 21.8 ms at 160 columns against 14.8 ms at 128, 256 curves x 20k
 // frequencies); 256 columns (nb <= 100) keep the one-group kernel, whose eight binning
 // warps then win (11.5 ms against 13.1 ms at nb = 100).
-int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax)
+int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax, int choice)
 {
-    if (fold_use_ws(128, kahan, nb, kmin, kmax) && tmax > 128 && tmax < 256) return 128;
+    if (fold_use_ws(128, kahan, nb, kmin, kmax, choice) && tmax > 128 && tmax < 256) return 128;
     return tmax;
 }
 
@@ -1765,9 +1766,10 @@ int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax)
 // sweep from shared memory while the binning group waits, and the one-group kernel, whose
 // threads all bin and then all sweep, is faster (nb = 400: 81.7 ms at 48 columns against
 // 97.3 ms at 64, 256 curves x 20k frequencies).
-bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax)
+bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax, int choice)
 {
-    return use_ws(T, kahan) && ws_tmem_fits(nb, kmin, kmax);
+    if (choice == BLS_FOLD_ONE_GROUP || !use_ws(T, kahan)) return false;
+    return choice == BLS_FOLD_WS || ws_tmem_fits(nb, kmin, kmax);
 }
 
 // Dynamic shared memory of a warp-specialised block: at least half of an SM's shared memory,
