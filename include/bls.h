@@ -92,9 +92,9 @@ enum {
 /* Fold-sweep kernel of the tiled search.  BLS_FOLD_AUTO chooses per class of curves: the
  * warp-specialised kernel (a binning warp group and a sweep warp group that takes each
  * tile's histograms over through tensor memory) where the tile width is 32, 64, 96 or 128
- * frequencies, the sums are plain FP32 and the class's bins fit its TMEM copy
- * (nb + kmax + SB + 8 <= 257 and kmax + SB + 8 <= nb, SB = 4 for kmax - kmin < 14, else 8
- * or 10), otherwise the one-group kernel (every thread bins, then every thread sweeps).
+ * frequencies, the sums are plain FP32, the fast sweep covers the widths (kmax - kmin + 1 >=
+ * SB - 1, SB = 4 for kmax - kmin < 14, else 8 or 10) and nb <= 256 (the bins fit the TMEM
+ * copy), otherwise the one-group kernel (every thread bins, then every thread sweeps).
  * BLS_FOLD_WS asks for the warp-specialised kernel wherever the tile width and the sums
  * allow it (tiles whose copy does not fit are then swept from shared memory by the sweep
  * group); BLS_FOLD_ONE_GROUP always takes the one-group kernel.  The environment variable

@@ -845,10 +845,12 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 
 // TmemBins reads a copy of the histogram column in this thread's TMEM lane: bin b at
 // columns (2b, 2b + 1), laid out linearly past nb (bins nb.. repeat bins 0..), so a block
-// reads consecutive columns.  The next bin of both blocks is always in flight while the
-// current one is evaluated.
+// reads consecutive columns; with WRAP the copy holds bins 0 .. nb-1 only and the reads
+// wrap at nb (for nb too large for the repeated bins).  The next bin of both blocks is
+// always in flight while the current one is evaluated.
+template <bool WRAP>
 struct TmemBins {
-    unsigned base, ta, tb;
+    unsigned base, tend, ta, tb;   // tend: column 2 nb (WRAP: the copy holds bins 0..nb-1 only)
     unsigned pa0, pa1, pb0, pb1;
     __device__ __forceinline__ void issue()
     {
@@ -856,6 +858,10 @@ struct TmemBins {
         tmem_ld2(tb, pb0, pb1);
         ta += 2;
         tb += 2;
+        if (WRAP) {
+            ta = ta == tend ? base : ta;
+            tb = tb == tend ? base : tb;
+        }
     }
     __device__ __forceinline__ void start(int a, int b)
     {
@@ -1151,14 +1157,18 @@ __host__ __device__ __forceinline__ int sweep_block(int nb, int kmin, int kmax)
     return kmax - kmin + 1 < 15 ? 4 : (wide_sweep_10(nb, 1) ? 10 : 8);
 }
 
-// Whether the warp-specialised kernel sweeps a tile from its TMEM copy: the fast sweep
-// covers the widths, and the copy (bins read up to nb + kmax + SB - 2 by the sweep with
-// its one bin of read-ahead, up to 7 more by the copy's last group of 8) fits the 512
-// columns with its bins past nb wrapping once.
-__host__ __device__ __forceinline__ bool ws_tmem_fits(int nb, int kmin, int kmax)
+// How the warp-specialised kernel sweeps a tile from its TMEM copy (0: it cannot, the fast
+// sweep does not cover the widths or nb > 256).  1, linear: the copy repeats the first bins
+// past nb, so the sweep's reads never wrap (they reach bin nb + kmax + SB - 2 with the one
+// bin of read-ahead; the copy's last group of 8 up to 7 more; all within the 512 columns,
+// the copy's reads past nb wrapping once).  2, wrapped: the copy holds bins 0 .. nb-1 and
+// every read wraps at nb (one compare and select per bin and block).
+__host__ __device__ __forceinline__ int ws_tmem_mode(int nb, int kmin, int kmax)
 {
     const int SB = sweep_block(nb, kmin, kmax);
-    return kmax - kmin + 1 >= SB - 1 && nb + kmax + SB + 8 <= 257 && kmax + SB + 8 <= nb;
+    if (kmax - kmin + 1 < SB - 1) return 0;
+    if (nb + kmax + SB + 8 <= 257 && kmax + SB + 8 <= nb) return 1;
+    return nb <= 256 && nb >= 8 ? 2 : 0;
 }
 
 constexpr int kFoldMaxThreads = 256;
@@ -1328,8 +1338,8 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
 // the issue slots that the binning chain leaves idle.  With T = 128 the sweep group has
 // two threads per column (two warps per TMEM lane quadrant), which split the copy, the
 // zeroing and the box starts.  The checks of the fast sweep's condition and the exact
-// sweep (rare) read the TMEM copy; tiles whose TMEM copy would not fit 512 columns (or
-// whose copy would wrap more than once, nb < kmax + SB + 8), or that the fast sweep does not
+// sweep (rare) read the TMEM copy (the first bins repeated past nb where they fit, else
+// wrapped reads, see ws_tmem_mode); tiles with nb > 256, or that the fast sweep does not
 // cover (kmax - kmin < SB - 2), are swept from shared memory before the hand-back.  The bins, the sums and the set of boxes are those of fold_sweep_kernel;
 // both sweep blocks rank boxes by the signed residue, so a frequency's power can differ
 // from fold_sweep_kernel's in the last bits (both are within the approximation's 2^-22).
@@ -1395,15 +1405,17 @@ __device__ __forceinline__ int group_or(int id, int n, int v)
 
 constexpr unsigned kTmemCols = 512;
 
-// Sequential single-bin stream over this thread's TMEM lane (linear layout), for the rare
+// Sequential single-bin stream over this thread's TMEM lane (as TmemBins), for the rare
 // checks; every access is taken by the whole warp together.
+template <bool WRAP>
 struct TmemStream {
-    unsigned base, ta, p0, p1;
+    unsigned base, tend, ta, p0, p1;
     __device__ __forceinline__ void issue()
     {
         __syncwarp();
         tmem_ld2(ta, p0, p1);
         ta += 2;
+        if (WRAP) ta = ta == tend ? base : ta;
     }
     __device__ __forceinline__ void start(int a)
     {
@@ -1431,20 +1443,23 @@ struct TmemStream {
 // Both blocks take the signed-residue form here: it issues fewer instructions per box than
 // the shared-reciprocal form and leans on the special-function unit, which the binning
 // warps sharing the SM sub-partitions do not use.
-template <int SB, int SIGN>
+template <int SB, int SIGN, bool WRAP>
 __device__ __forceinline__ float sweep_tmem(unsigned tbase, int nb, int kmin, int kmax, int part,
                                             int nparts)
 {
-    TmemBins src;
+    TmemBins<WRAP> src;
     src.base = tbase;
-    return sweep_fast<SB, SIGN, TmemBins, 0>(src, nb, kmin, kmax, part, nparts);
+    src.tend = tbase + 2u * (unsigned)nb;
+    return sweep_fast<SB, SIGN, TmemBins<WRAP>, 0>(src, nb, kmin, kmax, part, nparts);
 }
 
 // Heaviest run of kmax consecutive bins (cyclic), as in sweep_max, from the TMEM copy.
+template <bool WRAP>
 __device__ float heaviest_run_tmem(unsigned tbase, int nb, int kmax)
 {
-    TmemBins src;
+    TmemBins<WRAP> src;
     src.base = tbase;
+    src.tend = tbase + 2u * (unsigned)nb;
     float win = 0.0f, hw, hx, hw2, hx2;
     src.start(0, 0);
     for (int b = 0; b < kmax; ++b) {
@@ -1639,13 +1654,14 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             const int j = tile * T + col;
             const bool active = j < nf;
             const int SB = sweep_block(nb, kmin, kmax);
-            const bool use_tmem = ws_tmem_fits(nb, kmin, kmax);
+            const int tmode = ws_tmem_mode(nb, kmin, kmax);
+            const bool use_tmem = tmode != 0;
             float v = 0.0f, wmax = 0.0f;
             if (use_tmem) {
                 // copy bins 0 .. L-1 (bin b >= nb repeats bin b - nb; L <= 2 nb) into the
                 // column's lane, 8 bins per TMEM store (groups dealt to the parts), then zero
                 // the shared column (rows split between the parts)
-                const int L = (nb + kmax + SB - 1 + 7) & ~7;
+                const int L = ((tmode == 1 ? nb + kmax + SB - 1 : nb) + 7) & ~7;
                 const unsigned wrapb = (unsigned)nb * rowb;
                 for (int g = 8 * part; g < L; g += 8 * nparts) {
                     const unsigned ag = hbase + (unsigned)g * rowb;
@@ -1695,21 +1711,37 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                     fast = (float)kmax * wmax < 0.89f;
                     const bool slide = !fast && kmax < nb;
                     if (__any_sync(0xffffffffu, slide)) {
-                        const float rmax = heaviest_run_tmem(tbase, nb, kmax);
+                        const float rmax = tmode == 1 ? heaviest_run_tmem<false>(tbase, nb, kmax)
+                                                      : heaviest_run_tmem<true>(tbase, nb, kmax);
                         if (slide) fast = rmax < 0.89f;
                     }
                     const bool exact = active && !fast;
                     if (__any_sync(0xffffffffu, exact)) {
-                        TmemStream src;
-                        src.base = tbase;
-                        const Best g = sweep_exact_src<SIGN>(src, nb, kmin, kmax);
+                        Best g;
+                        if (tmode == 1) {
+                            TmemStream<false> src;
+                            src.base = tbase;
+                            src.tend = tbase + 2u * (unsigned)nb;
+                            g = sweep_exact_src<SIGN>(src, nb, kmin, kmax);
+                        } else {
+                            TmemStream<true> src;
+                            src.base = tbase;
+                            src.tend = tbase + 2u * (unsigned)nb;
+                            g = sweep_exact_src<SIGN>(src, nb, kmin, kmax);
+                        }
                         if (exact) v = g.num > 0.0f ? __fdiv_rn(g.num, g.den) : 0.0f;
                     }
                 }
                 __syncwarp();
-                float vf = SB == 4 ? sweep_tmem<4, SIGN>(tbase, nb, kmin, kmax, part, nparts)
-                           : SB == 10 ? sweep_tmem<10, SIGN>(tbase, nb, kmin, kmax, part, nparts)
-                                      : sweep_tmem<8, SIGN>(tbase, nb, kmin, kmax, part, nparts);
+                float vf;
+                if (tmode == 1)
+                    vf = SB == 4 ? sweep_tmem<4, SIGN, false>(tbase, nb, kmin, kmax, part, nparts)
+                         : SB == 10 ? sweep_tmem<10, SIGN, false>(tbase, nb, kmin, kmax, part, nparts)
+                                    : sweep_tmem<8, SIGN, false>(tbase, nb, kmin, kmax, part, nparts);
+                else
+                    vf = SB == 4 ? sweep_tmem<4, SIGN, true>(tbase, nb, kmin, kmax, part, nparts)
+                         : SB == 10 ? sweep_tmem<10, SIGN, true>(tbase, nb, kmin, kmax, part, nparts)
+                                    : sweep_tmem<8, SIGN, true>(tbase, nb, kmin, kmax, part, nparts);
                 if (nparts == 2) {   // the parts' maxima meet in shared memory
                     if (part == 1) s_wpart2[col] = vf;
                     group_sync(kBarSweep, NS);
@@ -1749,27 +1781,29 @@ static bool use_ws(int T, int kahan)
 // lanes; otherwise one).
 static int ws_threads(int T) { return T == 128 ? 3 * T : 2 * T; }
 
-// Frequencies per tile for plain sums, given the most whose histograms fit (a multiple of
-// 16, at most 256).  Widths strictly between 128 and 256 would leave the one-group kernel
-// with one thread per column, slower than the warp-specialised kernel with 128 columns
-// (e.g. nb = 150: 21.8 ms at 160 columns against 14.8 ms at 128, 256 curves x 20k
-// frequencies); 256 columns (nb <= 100) keep the one-group kernel, whose eight binning
-// warps then win (11.5 ms against 13.1 ms at nb = 100).
+// Frequencies per tile, given the most whose histograms fit (a multiple of 16, at most 256):
+// where the warp-specialised kernel applies, the widest multiple of 32 up to 128 below it.
+// Measured on 256 curves x 20k frequencies: nb = 150, 160 columns (one-group kernel, one
+// thread per column) 21.8 ms against 14.8 ms at 128 (warp-specialised); nb = 210, 112
+// columns 25.5 ms against 23.6 ms at 96.  256 columns (nb <= 100) keep the one-group kernel,
+// whose eight binning warps then win (11.5 ms against 13.1 ms at nb = 100).
 int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax, int choice)
 {
-    if (fold_use_ws(128, kahan, nb, kmin, kmax, choice) && tmax > 128 && tmax < 256) return 128;
+    if (tmax >= 256) return tmax;
+    const int T32 = tmax > 128 ? 128 : tmax & ~31;
+    if (T32 >= 32 && T32 != tmax && fold_use_ws(T32, kahan, nb, kmin, kmax, choice)) return T32;
     return tmax;
 }
 
-// The warp-specialised kernel takes classes whose tiles it sweeps from TMEM; where the
-// copy does not fit (large nb) or the fast sweep does not apply, its sweep group would
-// sweep from shared memory while the binning group waits, and the one-group kernel, whose
-// threads all bin and then all sweep, is faster (nb = 400: 81.7 ms at 48 columns against
-// 97.3 ms at 64, 256 curves x 20k frequencies).
+// The warp-specialised kernel takes classes whose tiles it sweeps from TMEM; where it
+// cannot (nb > 256) or the fast sweep does not apply, its sweep group would sweep from
+// shared memory while the binning group waits, and the one-group kernel, whose threads all
+// bin and then all sweep, is faster (nb = 400: 81.7 ms at 48 columns against 97.3 ms at
+// 64, 256 curves x 20k frequencies).
 bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax, int choice)
 {
     if (choice == BLS_FOLD_ONE_GROUP || !use_ws(T, kahan)) return false;
-    return choice == BLS_FOLD_WS || ws_tmem_fits(nb, kmin, kmax);
+    return choice == BLS_FOLD_WS || ws_tmem_mode(nb, kmin, kmax) != 0;
 }
 
 // Dynamic shared memory of a warp-specialised block: at least half of an SM's shared memory,

@@ -57,10 +57,10 @@ def test_forced_kernel_choices_agree(kernel):
     # sweeps correctly (from shared memory)
     if kernel == "ws":
         for ci in cis:
-            ci.nb = 240
-        with bls.Plan(nb=240, qmin=b.qmin, qmax=0.1, freqs_per_block=64) as p:
+            ci.nb = 300
+        with bls.Plan(nb=300, qmin=b.qmin, qmax=0.1, freqs_per_block=64) as p:
             pa = p.search(cis, spectrum=s0)
-        with bls.Plan(nb=240, qmin=b.qmin, qmax=0.1, freqs_per_block=64, fold_kernel="ws") as p:
+        with bls.Plan(nb=300, qmin=b.qmin, qmax=0.1, freqs_per_block=64, fold_kernel="ws") as p:
             pb = p.search(cis, spectrum=s1)
         np.testing.assert_allclose(s1, s0, rtol=1e-6, atol=0)
         assert np.array_equal(pa["j"], pb["j"])

@@ -5,9 +5,9 @@ warp group and a sweep warp group that takes each tile's histograms over through
 sweep thread per column, two when T = 128); other widths and BLS_FOLD_WS=0 select the
 one-group kernel.  Checked here:
   * the search's spectrum (SR of the kernel's per-frequency powers) against the oracle
-    within the parity tolerance, over several tiles with a ragged tail, for TMEM-copied
-    tiles, tiles swept from shared memory (nb too large for the copy; kmin > 1) and the
-    exact sweep;
+    within the parity tolerance, over several tiles with a ragged tail, for TMEM copies with
+    repeated bins and with wrapped reads, seeded sweeps (kmin > 1), tiles swept from shared
+    memory by the sweep group (nb > 256) and the exact sweep;
   * identical spectra and peaks for every warp-specialised tile width (the per-frequency
     arithmetic does not depend on the tile);
   * the one-group kernel (run in a child process with BLS_FOLD_WS=0) within FP32 rounding
@@ -50,17 +50,23 @@ def _cases():
     out.append(("crowded_exact_nb100", [bls.CurveInput(t, y, None, freqs=freqs, nb=100, qmin=0.01,
                                                        qmax=0.3)], 100, 0.01, 0.3))
     c = b.curves[0]
-    out.append(("shared_sweep_nb240", [bls.CurveInput(c.t, c.y, c.dy, nf=300, fmin=0.2, df=0.01,
+    out.append(("wrapped_tmem_nb240", [bls.CurveInput(c.t, c.y, c.dy, nf=300, fmin=0.2, df=0.01,
                                                       nb=240, qmin=0.005, qmax=0.1)], 240, 0.005, 0.1))
-    out.append(("shared_sweep_kmin3", [bls.CurveInput(c.t, c.y, c.dy, nf=300, fmin=0.2, df=0.01,
-                                                      nb=100, qmin=0.03, qmax=0.15)], 100, 0.03, 0.15))
+    out.append(("seeded_kmin3", [bls.CurveInput(c.t, c.y, c.dy, nf=300, fmin=0.2, df=0.01,
+                                                nb=100, qmin=0.03, qmax=0.15)], 100, 0.03, 0.15))
+    out.append(("shared_sweep_nb300", [bls.CurveInput(c.t, c.y, c.dy, nf=300, fmin=0.2, df=0.01,
+                                                      nb=300, qmin=0.005, qmax=0.1)], 300, 0.005, 0.1))
     return out
 
 
 def _search(cis, nb, qmin, qmax, T=0, sign="dips"):
     nf = sum(len(ci.freqs) if ci.freqs is not None else ci.nf for ci in cis)
     spec = np.zeros(nf, np.float32)
-    with bls.Plan(nb=nb, qmin=qmin, qmax=qmax, topk=2, sign=sign, freqs_per_block=T) as p:
+    # nb = 300 cannot take the TMEM copy: the plan asks for the warp-specialised kernel, whose
+    # sweep group then sweeps from shared memory (the automatic choice would not take it)
+    kern = "ws" if nb > 256 else "auto"
+    with bls.Plan(nb=nb, qmin=qmin, qmax=qmax, topk=2, sign=sign, freqs_per_block=T,
+                  fold_kernel=kern) as p:
         pk = p.search(cis, spectrum=spec)
     return spec, pk
 
@@ -83,7 +89,7 @@ def _oracle_check(cis, spec, nb, qmin, qmax, sign):
         o += len(P)
 
 
-@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("case", range(5))
 @pytest.mark.parametrize("sign", ["dips", "both"])
 def test_spectrum_matches_oracle_every_tile_width(case, sign):
     name, cis, nb, qmin, qmax = _cases()[case]
