@@ -360,7 +360,6 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         BLS_ENSURE(P->h_ranges, nr * sizeof(TileRange), "pinned work list")
         BLS_ENSURE(P->h_prefix, (nr + cls.size()) * sizeof(long long), "pinned work list")
     } else if (unbinned) {
-        BLS_ENSURE(P->runs, (size_t)nres * sizeof(int2), "allocating runs")
         BLS_ENSURE(P->prefix, (nr + 1) * sizeof(long long), "allocating work list")
         BLS_ENSURE(P->h_prefix, (nr + 1) * sizeof(long long), "pinned work list")
     } else {
@@ -439,7 +438,6 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         up.ncurves = nc;
         up.tile_prefix = P->prefix.as<long long>();
         up.res_base = P->res.as<float>();
-        up.runs = P->runs.as<int2>();
         up.peaks = P->peaks.as<DevPeak>();
         up.spectrum = spectrum ? (spectrum_dev ? spectrum : P->spec.as<float>()) : nullptr;
         up.topk = topk;
@@ -590,7 +588,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         }
         if (unbinned) put(P->h_prefix.p, pp * sizeof(long long));
         void* bufs[] = {P->pts.p, P->res.p, P->peaks.p, P->spec.p, P->err.p, P->h_peaks.p, P->h_err.p, P->ranges.p,
-                        P->shapes.p, P->h_shapes.p, P->runs.p, P->prefix.p};
+                        P->shapes.p, P->h_shapes.p, P->prefix.p};
         put(bufs, sizeof(bufs));
         if (P->graph && sig == P->graph_sig) {
             if ((e = cudaGraphLaunch(P->graph, st)) != cudaSuccess) return cuda_fail(e, "graph launch");

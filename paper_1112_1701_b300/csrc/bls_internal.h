@@ -95,7 +95,6 @@ struct UblsParams {
     int ncurves;
     const long long* tile_prefix;   // ncurves + 1: frequency tiles before curve c
     const float* res_base;          // pool of the per-frequency powers
-    int2* runs;                     // per frequency (indexed like res): best run (start, len)
     DevPeak* peaks;                 // topk per curve
     float* spectrum;                // optional (device): SR per frequency, at spec_off
     int topk, sign;

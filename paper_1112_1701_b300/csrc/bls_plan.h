@@ -75,7 +75,7 @@ struct bls_plan_impl {
     DevBuf raw_t, raw_y, raw_dy, raw_f;   // staging of host inputs
     DevBuf pts, dt64, w64, wx64;          // prepared points
     DevBuf cdesc, ranges, prefix, counter, err;
-    DevBuf res, peaks, spec, plain_hist, jsbuf, binsbuf, shapes, runs;
+    DevBuf res, peaks, spec, plain_hist, jsbuf, binsbuf, shapes;
     // host staging (pinned)
     HostBuf h_cdesc, h_ranges, h_prefix, h_peaks, h_err, h_shapes;
 

@@ -13,14 +13,17 @@
 // Search kernel: one block per (curve, tile of kTile frequencies).  For each frequency the
 // block forms the keys (key << 32 | index) in shared memory, sorts them with a bitonic
 // network, and builds prefix sums of (w, w x) in phase order (FP64, stored as double-float
-// pairs).  Each thread takes a range of run starts; the admissible ends of a start (extent
-// within [QMIN, QMAX]) only move right as the start does, so two pointers give them, and
-// every run's sums are independent prefix differences.  The largest P wins (ties to the
-// smaller start, then the shorter run); a block argmax gives P(f_j) and its run.
+// pairs in four arrays).  Run starts are dealt round-robin to the threads; a start's
+// admissible ends (extent within [QMIN, QMAX]) come from two binary searches, and every
+// run's sums are independent prefix differences.  Runs are ranked by the signed residue
+// z = s / sqrt(r(1-r)) (P = z^2), evaluated two ends at a time as packed FP32 pairs where
+// every run of the curve is known to have 0 < r < 1; only the best z of each frequency is
+// kept, P(f_j) = z^2.
 //
 // Reduce kernel: one block per curve: the top-k local maxima of P(f_j) (as in the binned
-// search), the signal detection efficiency, and for each kept frequency the run's FP64
-// refit -- keys and order recomputed exactly, r and s summed in run order in FP64.
+// search), the signal detection efficiency, and for each kept frequency the best run found
+// again with the search's arithmetic (ties to the smaller start, then the shorter run) and
+// refitted in FP64 -- keys and order recomputed exactly, r and s summed in run order.
 #include <cfloat>
 
 #include "bls_internal.h"
@@ -47,7 +50,7 @@ __device__ __forceinline__ unsigned long long fixed_freq(double f, double dtmax)
 
 // Phase keys (key << 32 | point) of a curve at F, bitonic-sorted ascending in `keys`
 // (M = the power of two >= n; the tail holds all-ones sentinels).
-__device__ void sorted_keys(const CurveDesc& cd, unsigned long long F, unsigned long long* keys, int M)
+__device__ __forceinline__ void sorted_keys(const CurveDesc& cd, unsigned long long F, unsigned long long* keys, int M)
 {
     const unsigned Flo = (unsigned)F, Fhi = (unsigned)(F >> 32);
     const int n = cd.n;
@@ -84,12 +87,6 @@ __device__ __forceinline__ void point_weights(const CurveDesc& cd, int i, float&
     wx = (i & 1) ? B.w : B.y;
 }
 
-// (P, start, len) order: larger P, then smaller start, then shorter run.
-__device__ __forceinline__ bool run_ahead(float pa, int sa, int la, float pb, int sb, int lb)
-{
-    return pa > pb || (pa == pb && (sa < sb || (sa == sb && la < lb)));
-}
-
 // Double-float value (hi + lo) of an FP64 number.
 __device__ __forceinline__ float2 split_df(double v)
 {
@@ -100,29 +97,280 @@ __device__ __forceinline__ float2 split_df(double v)
 // Error-free sum of two floats (Knuth's two-sum): hi + lo == a + b exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& hi, float& lo)
 {
-    hi = a + b;
-    const float bb = hi - a;
-    lo = (a - (hi - bb)) + (b - bb);
+    hi = __fadd_rn(a, b);
+    const float bb = __fsub_rn(hi, a);
+    lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bb)), __fsub_rn(b, bb));
 }
 
-// Score of one run with sums (r, s): P = s^2 / (r(1-r)), dips only unless sign; 0 if the
-// run does not count.  An approximate division suffices: P only ranks the runs of a
-// frequency (the kept run is refitted in FP64).
-__device__ __forceinline__ float run_score(float r, float s, int sign)
+__device__ __forceinline__ float rsqrt_apx(float x)
 {
-    const float d = fmaf(-r, r, r);
-    if (!(d > 0.0f) || (!sign && !(s < 0.0f))) return 0.0f;
-    return __fdividef(s * s, d);
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
-__global__ void __launch_bounds__(kUThreads) ubls_kernel(UblsParams p)
+// Prefix sums of (w, w x) in phase order, C[q] = sums over sorted positions < q (q = 0..n),
+// as double-float pairs in four arrays (w hi, w lo, wx hi, wx lo).  FP64 over each thread's
+// positions, a scan of the thread totals (warp shuffles, then the warp totals in order);
+// the chunking depends only on n and the block size, so every kernel that calls this with
+// the same block size gets the same values.
+struct Prefix {
+    float *wh, *wl, *xh, *xl;
+};
+
+__device__ __forceinline__ void prefix_sums(const CurveDesc& cd, const unsigned long long* keys, const Prefix& C,
+                            double* sred)
+{
+    const int n = cd.n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nt = blockDim.x;
+    const int ch = (n + nt - 1) / nt;
+    const int q0 = min(n, (int)threadIdx.x * ch), q1 = min(n, q0 + ch);
+    double tw = 0.0, tx = 0.0;
+    for (int q = q0; q < q1; ++q) {
+        float w, wx;
+        point_weights(cd, (int)(keys[q] & 0xffffffffu), w, wx);
+        tw = __dadd_rn(tw, (double)w);
+        tx = __dadd_rn(tx, (double)wx);
+    }
+    double iw = tw, ix = tx;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double uw = __shfl_up_sync(0xffffffffu, iw, o);
+        const double ux = __shfl_up_sync(0xffffffffu, ix, o);
+        if (lane >= o) { iw = __dadd_rn(iw, uw); ix = __dadd_rn(ix, ux); }
+    }
+    if (lane == 31) { sred[warp] = iw; sred[nt + warp] = ix; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double aw = 0.0, ax = 0.0;
+        for (int w = 0; w < nt / 32; ++w) {
+            const double vw = sred[w], vx = sred[nt + w];
+            sred[w] = aw;
+            sred[nt + w] = ax;
+            aw = __dadd_rn(aw, vw);
+            ax = __dadd_rn(ax, vx);
+        }
+        const float2 W = split_df(aw), X = split_df(ax);
+        C.wh[n] = W.x; C.wl[n] = W.y; C.xh[n] = X.x; C.xl[n] = X.y;
+    }
+    __syncthreads();
+    double aw = __dsub_rn(__dadd_rn(sred[warp], iw), tw);
+    double ax = __dsub_rn(__dadd_rn(sred[nt + warp], ix), tx);
+    for (int q = q0; q < q1; ++q) {
+        const float2 W = split_df(aw), X = split_df(ax);
+        C.wh[q] = W.x; C.wl[q] = W.y; C.xh[q] = X.x; C.xl[q] = X.y;
+        float w, wx;
+        point_weights(cd, (int)(keys[q] & 0xffffffffu), w, wx);
+        aw = __dadd_rn(aw, (double)w);
+        ax = __dadd_rn(ax, (double)wx);
+    }
+    __syncthreads();
+}
+
+// Admissible ends of the runs starting at sorted position a: unwrapped positions
+// emin..emax (extents within [QMIN, QMAX], at most n - 1 points), extents growing with the
+// end; emin > emax when none.
+__device__ __forceinline__ void run_ends(const unsigned long long* keys, int n, int a, unsigned QMIN,
+                                         unsigned QMAX, int& emin, int& emax)
+{
+    const unsigned k0 = (unsigned)(keys[a] >> 32);
+    auto ext = [&](int e) { return (unsigned)(keys[e < n ? e : e - n] >> 32) - k0; };
+    int lo2 = a, hi2 = a + n - 1;            // ext(lo2) <= QMAX; hi2 out of range
+    while (hi2 - lo2 > 1) {
+        const int mid = (lo2 + hi2) >> 1;
+        if (ext(mid) <= QMAX) lo2 = mid; else hi2 = mid;
+    }
+    emax = lo2;
+    int lo1 = a - 1, hi1 = emax + 1;          // ext(hi1) >= QMIN or hi1 past emax
+    while (hi1 - lo1 > 1) {
+        const int mid = (lo1 + hi1) >> 1;
+        if (ext(mid) >= QMIN) hi1 = mid; else lo1 = mid;
+    }
+    emin = hi1;
+}
+
+// Signed residue of a run with -r = nr and s = s: z = s / sqrt(r (1 - r)), from one fused
+// -d = r^2 - r and an approximate reciprocal square root (P = z^2).  Runs with d <= 0 (r
+// outside (0, 1) in FP32) give NaN, or +-inf for d = 0; the search ranks runs by z.
+__device__ __forceinline__ float run_z(float nr, float s)
+{
+    return __fmul_rn(s, rsqrt_apx(-__fmaf_rn(nr, nr, nr)));
+}
+
+// -r and s of the run (a, e] inside [0, n): prefix differences of double-float pairs.
+__device__ __forceinline__ void run_in(const Prefix& C, float awh, float awl, float axh, float axl,
+                                       int u, float& nr, float& s)
+{
+    nr = __fadd_rn(__fsub_rn(awh, C.wh[u]), __fsub_rn(awl, C.wl[u]));
+    s = __fadd_rn(__fsub_rn(C.xh[u], axh), __fsub_rn(C.xl[u], axl));
+}
+
+// -r and s of a run that wraps past the end: totals T plus the prefix at u, through an
+// error-free sum of the leading terms.
+__device__ __forceinline__ void run_wrap(const Prefix& C, float4 T, float awh, float awl, float axh,
+                                         float axl, int u, float& nr, float& s)
+{
+    float wh, wl, xh, xl;
+    two_sum(T.x, C.wh[u], wh, wl);
+    two_sum(T.z, C.xh[u], xh, xl);
+    nr = __fadd_rn(__fsub_rn(awh, wh), __fsub_rn(awl, __fadd_rn(__fadd_rn(wl, T.y), C.wl[u])));
+    s = __fadd_rn(__fsub_rn(xh, axh), __fsub_rn(__fadd_rn(__fadd_rn(xl, T.w), C.xl[u]), axl));
+}
+
+// Best (most negative for dips, largest |z| for both signs) of an accumulator and z.
+template <int SIGN>
+__device__ __forceinline__ float best_z(float b, float z)
+{
+    return SIGN ? fmaxf(b, fabsf(z)) : fminf(b, z);
+}
+
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float lo, float hi)
+{
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(u64 v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b)
+{
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b)
+{
+    u64 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c)
+{
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b)
+{
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float fmin3f(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fmax3f(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// b updated with one run (-r = nr, s); without FAST, runs with d <= 0 do not count.
+template <int SIGN, bool FAST>
+__device__ __forceinline__ float scored(float b, float nr, float s)
+{
+    const float z = run_z(nr, s);
+    return (FAST || -__fmaf_rn(nr, nr, nr) > 0.0f) ? best_z<SIGN>(b, z) : b;
+}
+
+// The best z over the runs of start a (the search: no positions kept).  FAST: every run has
+// d > 0 (see the caller), so the ends inside [0, n) go two at a time as packed pairs (the
+// prefix arrays read 8 bytes at an even position), with the same per-lane arithmetic as
+// run_in / run_z; otherwise every run is scored alone and runs with d <= 0 are skipped.
+template <int SIGN, bool FAST>
+__device__ __forceinline__ float start_best(const Prefix& C, float4 T, int n, int a, int emin,
+                                            int emax, float b)
+{
+    const float awh = C.wh[a], awl = C.wl[a], axh = C.xh[a], axl = C.xl[a];
+    // ends e in [emin, min(emax, n-1)]: prefix index u = e + 1 in [u0, u1]
+    int u = emin + 1;
+    const int u1 = min(emax, n - 1) + 1;
+    if (FAST) {
+        if ((u & 1) && u <= u1) {
+            float nr, s;
+            run_in(C, awh, awl, axh, axl, u, nr, s);
+            b = scored<SIGN, FAST>(b, nr, s);
+            ++u;
+        }
+        const u64 AWH = pk2(awh, awh), AWL = pk2(awl, awl), AXH = pk2(axh, axh), AXL = pk2(axl, axl);
+        const u64* WH = reinterpret_cast<const u64*>(C.wh);
+        const u64* WL = reinterpret_cast<const u64*>(C.wl);
+        const u64* XH = reinterpret_cast<const u64*>(C.xh);
+        const u64* XL = reinterpret_cast<const u64*>(C.xl);
+#pragma unroll 2
+        for (; u + 1 <= u1; u += 2) {
+            const int h = u >> 1;
+            const u64 NR = add2(sub2(AWH, WH[h]), sub2(AWL, WL[h]));
+            const u64 S = add2(sub2(XH[h], AXH), sub2(XL[h], AXL));
+            float nd0, nd1;
+            upk2(fma2(NR, NR, NR), nd0, nd1);
+            float z0, z1;
+            upk2(mul2(S, pk2(rsqrt_apx(-nd0), rsqrt_apx(-nd1))), z0, z1);
+            b = SIGN ? fmax3f(b, fabsf(z0), fabsf(z1)) : fmin3f(b, z0, z1);
+        }
+    }
+    for (; u <= u1; ++u) {
+        float nr, s;
+        run_in(C, awh, awl, axh, axl, u, nr, s);
+        b = scored<SIGN, FAST>(b, nr, s);
+    }
+    // ends past n - 1: prefix index e + 1 - n
+    for (int e = max(emin, n); e <= emax; ++e) {
+        float nr, s;
+        run_wrap(C, T, awh, awl, axh, axl, e + 1 - n, nr, s);
+        b = scored<SIGN, FAST>(b, nr, s);
+    }
+    return b;
+}
+
+// Shared-memory layout of both kernels: keys [M] (8 B), then the four prefix arrays of
+// n1 = n + 1 rounded up to even entries each (so that 8-byte pair reads stay aligned).
+__device__ __forceinline__ Prefix prefix_layout(unsigned char* dsm, int M, int n)
+{
+    const int n1 = (n + 2) & ~1;
+    float* base = reinterpret_cast<float*>(dsm + (size_t)M * sizeof(unsigned long long));
+    Prefix C;
+    C.wh = base;
+    C.wl = base + n1;
+    C.xh = base + 2 * n1;
+    C.xl = base + 3 * n1;
+    return C;
+}
+
+// Whether every run of the curve has d = r (1 - r) > 0 in FP32: the lightest point holds
+// at least 2^-23 of the weight, so a run of at most n - 1 points has r <= 1 - 2^-23 (up to
+// the rounding of r, below 2^-24), and r > 0 since weights are positive.
+__device__ __forceinline__ bool runs_positive(const CurveDesc& cd, float* red)
+{
+    float m = FLT_MAX;
+    for (int i = threadIdx.x; i < cd.n; i += blockDim.x) {
+        float w, wx;
+        point_weights(cd, i, w, wx);
+        m = fminf(m, w);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = FLT_MAX;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fminf(m, red[w]);
+    __syncthreads();
+    return m >= 1.1920929e-7f;   // 2^-23
+}
+
+template <int SIGN>
+__device__ __forceinline__ void ubls_search(UblsParams p)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ float sP[kUThreads / 32];
-    __shared__ int sS[kUThreads / 32], sL[kUThreads / 32];
+    __shared__ float sZ[kUThreads / 32];
     __shared__ double sred[2 * kUThreads];
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(dsm);
-    float4* C = reinterpret_cast<float4*>(keys + p.M);      // n + 1 prefix entries
     // work item -> (curve, tile)
     const long long it = blockIdx.x;
     int lo = 0, hi = p.ncurves;
@@ -135,124 +383,42 @@ __global__ void __launch_bounds__(kUThreads) ubls_kernel(UblsParams p)
     const int j0 = (int)(it - p.tile_prefix[lo]) * kTile;
     int M = 1;
     while (M < n) M <<= 1;
+    const Prefix C = prefix_layout(dsm, M, n);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nt = blockDim.x;
-    const int ch = (n + nt - 1) / nt;                 // positions per thread
-    const int q0 = min(n, (int)threadIdx.x * ch), q1 = min(n, q0 + ch);
+    const bool fast = runs_positive(cd, reinterpret_cast<float*>(sred));
     for (int j = j0; j < min(j0 + kTile, cd.nf); ++j) {
         const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
         sorted_keys(cd, fixed_freq(f, cd.dtmax), keys, M);
-        // prefix sums in phase order: FP64 over each thread's positions, a scan of the
-        // thread totals, then double-float values in shared memory
-        double tw = 0.0, tx = 0.0;
-        for (int q = q0; q < q1; ++q) {
-            float w, wx;
-            point_weights(cd, (int)(keys[q] & 0xffffffffu), w, wx);
-            tw = __dadd_rn(tw, (double)w);
-            tx = __dadd_rn(tx, (double)wx);
-        }
-        // exclusive scan of the thread totals: inclusive scans within warps (shuffles),
-        // then the warp totals in order
-        double iw = tw, ix = tx;
-        for (int o = 1; o < 32; o <<= 1) {
-            const double uw = __shfl_up_sync(0xffffffffu, iw, o);
-            const double ux = __shfl_up_sync(0xffffffffu, ix, o);
-            if (lane >= o) { iw = __dadd_rn(iw, uw); ix = __dadd_rn(ix, ux); }
-        }
-        if (lane == 31) { sred[warp] = iw; sred[nt + warp] = ix; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double aw = 0.0, ax = 0.0;
-            for (int w = 0; w < nt / 32; ++w) {
-                const double vw = sred[w], vx = sred[nt + w];
-                sred[w] = aw;
-                sred[nt + w] = ax;
-                aw = __dadd_rn(aw, vw);
-                ax = __dadd_rn(ax, vx);
-            }
-            const float2 W = split_df(aw), X = split_df(ax);
-            C[n] = make_float4(W.x, W.y, X.x, X.y);
-        }
-        __syncthreads();
-        const double base_w = __dsub_rn(__dadd_rn(sred[warp], iw), tw);
-        const double base_x = __dsub_rn(__dadd_rn(sred[nt + warp], ix), tx);
-        __syncthreads();
-        {
-            double aw = base_w, ax = base_x;
-            for (int q = q0; q < q1; ++q) {
-                const float2 W = split_df(aw), X = split_df(ax);
-                C[q] = make_float4(W.x, W.y, X.x, X.y);
-                float w, wx;
-                point_weights(cd, (int)(keys[q] & 0xffffffffu), w, wx);
-                aw = __dadd_rn(aw, (double)w);
-                ax = __dadd_rn(ax, (double)wx);
-            }
-        }
-        __syncthreads();
-        const float4 T = C[n];
-        // runs: starts dealt round-robin to the threads (phases clump, so contiguous ranges
-        // would leave the threads unevenly loaded); the ends [emin, emax] of a start
-        // (unwrapped positions; extents within [QMIN, QMAX], at most n - 1 points) by
-        // binary search, extents growing with the end.  Run sums are prefix differences;
-        // runs past the end add the totals with an error-free sum, so both cases keep
-        // double-float accuracy.
-        float bp = 0.0f;
-        int bs = 0x7fffffff, bl = 0x7fffffff;
+        prefix_sums(cd, keys, C, sred);
+        const float4 T = make_float4(C.wh[n], C.wl[n], C.xh[n], C.xl[n]);
+        // starts dealt round-robin to the threads (phases clump, so contiguous ranges would
+        // load the threads unevenly); each start's best z over its admissible runs
+        float b = 0.0f;
         for (int a = threadIdx.x; a < n; a += nt) {
-            const unsigned k0 = (unsigned)(keys[a] >> 32);
-            auto ext = [&](int e) { return (unsigned)(keys[e < n ? e : e - n] >> 32) - k0; };
-            // largest e in [a, a + n - 2] with ext(e) <= QMAX (ext(a) = 0)
-            int lo2 = a, hi2 = a + n - 1;            // ext(lo2) <= QMAX; hi2 out of range
-            while (hi2 - lo2 > 1) {
-                const int mid = (lo2 + hi2) >> 1;
-                if (ext(mid) <= p.QMAX) lo2 = mid; else hi2 = mid;
-            }
-            const int emax = lo2;
-            // smallest e in [a, emax] with ext(e) >= QMIN
-            int lo1 = a - 1, hi1 = emax + 1;          // ext(hi1) >= QMIN or hi1 past emax
-            while (hi1 - lo1 > 1) {
-                const int mid = (lo1 + hi1) >> 1;
-                if (ext(mid) >= p.QMIN) hi1 = mid; else lo1 = mid;
-            }
-            const int emin = hi1;
-            const float4 ca = C[a];
-            const int e1 = min(emax, n - 1);
-#pragma unroll 4
-            for (int e = emin; e <= e1; ++e) {            // runs inside [a, n)
-                const float4 cb = C[e + 1];
-                const float r = (cb.x - ca.x) + (cb.y - ca.y);
-                const float s = (cb.z - ca.z) + (cb.w - ca.w);
-                const float P = run_score(r, s, p.sign);
-                if (P > bp) { bp = P; bs = a; bl = e - a + 1; }
-            }
-            for (int e = max(emin, n); e <= emax; ++e) {  // runs that wrap past the end
-                const float4 c = C[e + 1 - n];
-                float wh, wl, xh, xl;
-                two_sum(T.x, c.x, wh, wl);
-                two_sum(T.z, c.z, xh, xl);
-                const float r = (wh - ca.x) + ((wl + T.y + c.y) - ca.y);
-                const float s = (xh - ca.z) + ((xl + T.w + c.w) - ca.w);
-                const float P = run_score(r, s, p.sign);
-                if (P > bp) { bp = P; bs = a; bl = e - a + 1; }
-            }
+            int emin, emax;
+            run_ends(keys, n, a, p.QMIN, p.QMAX, emin, emax);
+            b = fast ? start_best<SIGN, true>(C, T, n, a, emin, emax, b)
+                     : start_best<SIGN, false>(C, T, n, a, emin, emax, b);
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float op = __shfl_xor_sync(0xffffffffu, bp, o);
-            const int os = __shfl_xor_sync(0xffffffffu, bs, o);
-            const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-            if (run_ahead(op, os, ol, bp, bs, bl)) { bp = op; bs = os; bl = ol; }
-        }
-        if (lane == 0) { sP[warp] = bp; sS[warp] = bs; sL[warp] = bl; }
+        for (int o = 16; o > 0; o >>= 1) b = best_z<SIGN>(b, __shfl_xor_sync(0xffffffffu, b, o));
+        if (lane == 0) sZ[warp] = b;
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                if (run_ahead(sP[w], sS[w], sL[w], sP[0], sS[0], sL[0])) { sP[0] = sP[w]; sS[0] = sS[w]; sL[0] = sL[w]; }
-            const long long o = cd.res - p.res_base;
-            cd.res[j] = sP[0];
-            p.runs[o + j] = make_int2(sP[0] > 0.0f ? sS[0] : 0, sP[0] > 0.0f ? sL[0] : 0);
+            float z = sZ[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) z = best_z<SIGN>(z, sZ[w]);
+            cd.res[j] = __fmul_rn(z, z);
         }
         __syncthreads();
     }
+}
+
+// Search kernel: one block per (curve, tile of kTile frequencies); P(f_j) = z^2 of the best
+// run (its position is found again by the reduce kernel for the kept frequencies only).
+__global__ void __launch_bounds__(kUThreads, 1) ubls_kernel(UblsParams p)
+{
+    if (p.sign) ubls_search<1>(p);
+    else ubls_search<0>(p);
 }
 
 __device__ double sum_block(double v, double* red)
@@ -273,11 +439,63 @@ __device__ __forceinline__ bool freq_ahead(float pa, int ja, float pb, int jb)
     return pa > pb || (pa == pb && ja < jb);
 }
 
+// (z, start, len) order of the best run: the more extreme z (P = z^2; dips: the most
+// negative), then the smaller start, then the shorter run.
+template <int SIGN>
+__device__ __forceinline__ bool run_first(float za, int sa, int la, float zb, int sb, int lb)
+{
+    const bool more = SIGN ? fabsf(za) > fabsf(zb) : za < zb;
+    const bool same = SIGN ? fabsf(za) == fabsf(zb) : za == zb;
+    return more || (same && (sa < sb || (sa == sb && la < lb)));
+}
+
+// The best run of one frequency (keys and prefix sums in place), with the search kernel's
+// arithmetic, so its z is the one the search kept; (start, len), len = 0 if no run counts.
+template <int SIGN>
+__device__ int2 best_run(const unsigned long long* keys, const Prefix& C, int n, unsigned QMIN,
+                         unsigned QMAX, bool fast, float* sz, int* ss, int* sl)
+{
+    const float4 T = make_float4(C.wh[n], C.wl[n], C.xh[n], C.xl[n]);
+    float bz = 0.0f;
+    int bs = 0x7fffffff, bl = 0x7fffffff;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) {
+        int emin, emax;
+        run_ends(keys, n, a, QMIN, QMAX, emin, emax);
+        const float awh = C.wh[a], awl = C.wl[a], axh = C.xh[a], axl = C.xl[a];
+        for (int e = emin; e <= emax; ++e) {
+            float nr, sx;
+            if (e < n) run_in(C, awh, awl, axh, axl, e + 1, nr, sx);
+            else run_wrap(C, T, awh, awl, axh, axl, e + 1 - n, nr, sx);
+            if (!fast && !(-__fmaf_rn(nr, nr, nr) > 0.0f)) continue;
+            const float z = run_z(nr, sx);
+            if ((SIGN ? fabsf(z) > 0.0f : z < 0.0f) && run_first<SIGN>(z, a, e - a + 1, bz, bs, bl)) {
+                bz = z; bs = a; bl = e - a + 1;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oz = __shfl_xor_sync(0xffffffffu, bz, o);
+        const int os = __shfl_xor_sync(0xffffffffu, bs, o);
+        const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        if (run_first<SIGN>(oz, os, ol, bz, bs, bl)) { bz = oz; bs = os; bl = ol; }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { sz[warp] = bz; ss[warp] = bs; sl[warp] = bl; }
+    __syncthreads();
+    bz = sz[0]; bs = ss[0]; bl = sl[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (run_first<SIGN>(sz[w], ss[w], sl[w], bz, bs, bl)) { bz = sz[w]; bs = ss[w]; bl = sl[w]; }
+    __syncthreads();
+    return bs == 0x7fffffff ? make_int2(0, 0) : make_int2(bs, bl);
+}
+
 __global__ void __launch_bounds__(kUThreads) ubls_reduce_kernel(UblsParams p)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(dsm);
-    __shared__ double red[kUThreads];
+    __shared__ double red[2 * kUThreads];
+    __shared__ float bzs[kUThreads / 32];
+    __shared__ int bss[kUThreads / 32], bls[kUThreads / 32];
     __shared__ float sP[kUThreads / 32];
     __shared__ int sJ[kUThreads / 32], sT[kUThreads / 32];
     __shared__ int sel[kMaxTopK];
@@ -338,7 +556,8 @@ __global__ void __launch_bounds__(kUThreads) ubls_reduce_kernel(UblsParams p)
     }
     int M = 1;
     while (M < cd.n) M <<= 1;
-    const long long o = cd.res - p.res_base;
+    const Prefix C = prefix_layout(dsm, M, cd.n);
+    const bool fast = runs_positive(cd, reinterpret_cast<float*>(red));
     for (int q = 0; q < K; ++q) {
         DevPeak* out = &p.peaks[(size_t)blockIdx.x * K + q];
         const int j = sel[q];
@@ -348,8 +567,10 @@ __global__ void __launch_bounds__(kUThreads) ubls_reduce_kernel(UblsParams p)
         }
         const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
         sorted_keys(cd, fixed_freq(f, cd.dtmax), keys, M);
+        prefix_sums(cd, keys, C, red);
+        const int2 run = p.sign ? best_run<1>(keys, C, cd.n, p.QMIN, p.QMAX, fast, bzs, bss, bls)
+                                : best_run<0>(keys, C, cd.n, p.QMIN, p.QMAX, fast, bzs, bss, bls);
         if (threadIdx.x == 0) {
-            const int2 run = p.runs[o + j];
             const int a = run.x, len = run.y;
             DevPeak pk = {};
             pk.j = j; pk.i1 = a; pk.k = len;
@@ -395,7 +616,7 @@ size_t ubls_smem_bytes(int nmax)
 {
     int M = 1;
     while (M < nmax) M <<= 1;
-    return (size_t)M * sizeof(unsigned long long) + (size_t)(nmax + 1) * sizeof(float4);
+    return (size_t)M * sizeof(unsigned long long) + (size_t)4 * ((nmax + 2) & ~1) * sizeof(float);
 }
 
 int ubls_tile() { return kTile; }
@@ -413,9 +634,7 @@ cudaError_t launch_ubls(const UblsParams& p, long long nitems, cudaStream_t s)
 cudaError_t launch_ubls_reduce(const UblsParams& p, cudaStream_t s)
 {
     if (p.ncurves <= 0) return cudaSuccess;
-    int M = 1;
-    while (M < p.nmax) M <<= 1;
-    const size_t smem = (size_t)M * sizeof(unsigned long long);
+    const size_t smem = ubls_smem_bytes(p.nmax);
     cudaError_t e = cudaFuncSetAttribute(ubls_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ubls_reduce_kernel<<<p.ncurves, kUThreads, smem, s>>>(p);
