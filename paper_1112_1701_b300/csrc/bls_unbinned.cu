@@ -11,8 +11,9 @@
 // exact integer decisions, the same in every implementation.
 //
 // Search kernel: one block per (curve, tile of kTile frequencies).  For each frequency the
-// block forms the keys (key << 32 | index) in shared memory, sorts them with a bitonic
-// network, and builds prefix sums of (w, w x) in phase order (FP64, stored as double-float
+// block forms the keys (key << 32 | index) in shared memory, sorts them (buckets on the top
+// bits of the phase with an insertion sort per bucket; a bitonic network when phases
+// clump), and builds prefix sums of (w, w x) in phase order (FP64, stored as double-float
 // pairs in four arrays).  Run starts are dealt round-robin to the threads; a start's
 // admissible ends (extent within [QMIN, QMAX]) come from two binary searches, and every
 // run's sums are independent prefix differences.  Runs are ranked by the signed residue
@@ -78,6 +79,95 @@ __device__ __forceinline__ void sorted_keys(const CurveDesc& cd, unsigned long l
             __syncthreads();
         }
     }
+}
+
+// Phase key (key << 32 | point) of point i at F = (Fhi, Flo).
+__device__ __forceinline__ unsigned long long phase_key(const CurveDesc& cd, int i, unsigned Flo,
+                                                        unsigned Fhi)
+{
+    const float4 A = cd.pts[(i >> 1) * 2];
+    const unsigned lo = __float_as_uint((i & 1) ? A.y : A.x);
+    const unsigned hi = __float_as_uint((i & 1) ? A.w : A.z);
+    const unsigned q = __umulhi(lo, Flo) + lo * Fhi + hi * Flo;
+    return ((unsigned long long)q << 32) | (unsigned)i;
+}
+
+constexpr int kBucketMax = 48;   // largest bucket left to an insertion sort
+
+// Phase keys of a curve at F in ascending (key, point) order in keys[0 .. n): a counting
+// pass over the top B bits of the phase into nbk = M/2 buckets (shared-memory atomics), an
+// exclusive scan, a scatter, and an insertion sort of every bucket by one thread.  When a
+// bucket holds more than kBucketMax keys (phases clumped) the bitonic network sorts
+// instead.  The keys are distinct, so both give the same order.  `cnt` is scratch for
+// M + 1 ints.
+__device__ __forceinline__ void sort_keys(const CurveDesc& cd, unsigned long long F,
+                                          unsigned long long* keys, int M, int* cnt)
+{
+    __shared__ int s_tot[kUThreads / 32 + 1];
+    const unsigned Flo = (unsigned)F, Fhi = (unsigned)(F >> 32);
+    const int n = cd.n, tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nbk = M >= 2 ? M >> 1 : 1;
+    int B = 0;
+    while ((1 << B) < nbk) ++B;
+    int* start = cnt;              // nbk + 1
+    int* cur = cnt + nbk + 1;      // nbk (after the scan)
+    for (int b = tid; b < nbk; b += nt) start[b] = 0;
+    if (tid == 0) s_tot[kUThreads / 32] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {
+        const unsigned long long k = phase_key(cd, i, Flo, Fhi);
+        atomicAdd(&start[B ? (int)(k >> (64 - B)) : 0], 1);
+    }
+    __syncthreads();
+    // exclusive scan of the bucket counts (contiguous runs per thread, then warp and block
+    // scans of the run totals) and the largest count
+    const int per = (nbk + nt - 1) / nt;
+    const int b0 = min(nbk, tid * per), b1 = min(nbk, b0 + per);
+    int tot = 0, mx = 0;
+    for (int b = b0; b < b1; ++b) { tot += start[b]; mx = max(mx, start[b]); }
+    int inc = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 31) s_tot[warp] = inc;
+    if (lane == 0) atomicMax(&s_tot[kUThreads / 32], mx);
+    __syncthreads();
+    int wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += s_tot[w];
+    const bool clumped = s_tot[kUThreads / 32] > kBucketMax;
+    {
+        int run = wbase + inc - tot;
+        for (int b = b0; b < b1; ++b) {
+            const int c = start[b];
+            start[b] = run;
+            cur[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (clumped) {
+        sorted_keys(cd, F, keys, M);
+        return;
+    }
+    if (tid == 0) start[nbk] = n;
+    for (int i = tid; i < n; i += nt) {
+        const unsigned long long k = phase_key(cd, i, Flo, Fhi);
+        keys[atomicAdd(&cur[B ? (int)(k >> (64 - B)) : 0], 1)] = k;
+    }
+    __syncthreads();
+    for (int b = tid; b < nbk; b += nt) {
+        const int s0 = start[b], s1 = start[b + 1];
+        for (int x = s0 + 1; x < s1; ++x) {
+            const unsigned long long v = keys[x];
+            int y = x - 1;
+            while (y >= s0 && keys[y] > v) { keys[y + 1] = keys[y]; --y; }
+            keys[y + 1] = v;
+        }
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ void point_weights(const CurveDesc& cd, int i, float& w, float& wx)
@@ -389,7 +479,7 @@ __device__ __forceinline__ void ubls_search(UblsParams p)
     const bool fast = runs_positive(cd, reinterpret_cast<float*>(sred));
     for (int j = j0; j < min(j0 + kTile, cd.nf); ++j) {
         const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
-        sorted_keys(cd, fixed_freq(f, cd.dtmax), keys, M);
+        sort_keys(cd, fixed_freq(f, cd.dtmax), keys, M, reinterpret_cast<int*>(C.wh));
         prefix_sums(cd, keys, C, sred);
         const float4 T = make_float4(C.wh[n], C.wl[n], C.xh[n], C.xl[n]);
         // starts dealt round-robin to the threads (phases clump, so contiguous ranges would
@@ -489,7 +579,7 @@ __device__ int2 best_run(const unsigned long long* keys, const Prefix& C, int n,
     return bs == 0x7fffffff ? make_int2(0, 0) : make_int2(bs, bl);
 }
 
-__global__ void __launch_bounds__(kUThreads) ubls_reduce_kernel(UblsParams p)
+__global__ void __launch_bounds__(kUThreads, 1) ubls_reduce_kernel(UblsParams p)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(dsm);
@@ -566,7 +656,7 @@ __global__ void __launch_bounds__(kUThreads) ubls_reduce_kernel(UblsParams p)
             continue;
         }
         const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
-        sorted_keys(cd, fixed_freq(f, cd.dtmax), keys, M);
+        sort_keys(cd, fixed_freq(f, cd.dtmax), keys, M, reinterpret_cast<int*>(C.wh));
         prefix_sums(cd, keys, C, red);
         const int2 run = p.sign ? best_run<1>(keys, C, cd.n, p.QMIN, p.QMAX, fast, bzs, bss, bls)
                                 : best_run<0>(keys, C, cd.n, p.QMIN, p.QMAX, fast, bzs, bss, bls);
