@@ -623,27 +623,41 @@ __device__ __forceinline__ void rmw_sub(unsigned hbase, unsigned rowb, const uns
 // chain, so the fold arithmetic fills the shared-memory latency of the chain; the rare
 // FP64 re-fold runs after the stores.  hbase is the shared-memory address of this
 // thread's bin 0, rowb the byte stride between bins.
-template <int PHASE>
+template <int PHASE, bool PINGPONG>
 __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int nsub,
                                          unsigned hbase, unsigned rowb, const FoldConst& fc,
                                          const FoldPacked& fq)
 {
-    unsigned b[16];
-    float4 Bw[8];
-    if (fold_sub<PHASE>(cp, fc, fq, b, Bw)) fix_sub<PHASE>(cp, cd, fc, fq, b);
-    for (int sc = 0; sc + 1 < nsub; ++sc) {
-        unsigned bn[16];
-        float4 Bn[8];
-        const float4* np = cp + 16 * (sc + 1);
-        const bool edge = fold_sub<PHASE>(np, fc, fq, bn, Bn);
-        rmw_sub(hbase, rowb, b, Bw);
-        if (edge) fix_sub<PHASE>(np, cd + 16 * (sc + 1), fc, fq, bn);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) b[i] = bn[i];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) Bw[q] = Bn[q];
+    unsigned b0[16], b1[16];
+    float4 W0[8], W1[8];
+    if (fold_sub<PHASE>(cp, fc, fq, b0, W0)) fix_sub<PHASE>(cp, cd, fc, fq, b0);
+    int sc = 0;
+    if (PINGPONG) {
+        // the two buffers used in turn (the loop body covers two sub-chunks): no register
+        // copies between sub-chunks (faster in the warp-specialised kernel, whose binning
+        // warps are the critical path; slower in the one-group kernel)
+        for (; sc + 2 < nsub; sc += 2) {
+            const float4* n1 = cp + 16 * (sc + 1);
+            const bool e1 = fold_sub<PHASE>(n1, fc, fq, b1, W1);
+            rmw_sub(hbase, rowb, b0, W0);
+            if (e1) fix_sub<PHASE>(n1, cd + 16 * (sc + 1), fc, fq, b1);
+            const float4* n2 = cp + 16 * (sc + 2);
+            const bool e2 = fold_sub<PHASE>(n2, fc, fq, b0, W0);
+            rmw_sub(hbase, rowb, b1, W1);
+            if (e2) fix_sub<PHASE>(n2, cd + 16 * (sc + 2), fc, fq, b0);
+        }
     }
-    rmw_sub(hbase, rowb, b, Bw);
+    for (; sc + 1 < nsub; ++sc) {
+        const float4* n1 = cp + 16 * (sc + 1);
+        const bool e1 = fold_sub<PHASE>(n1, fc, fq, b1, W1);
+        rmw_sub(hbase, rowb, b0, W0);
+        if (e1) fix_sub<PHASE>(n1, cd + 16 * (sc + 1), fc, fq, b1);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) b0[i] = b1[i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) W0[q] = W1[q];
+    }
+    rmw_sub(hbase, rowb, b0, W0);
 }
 
 // Generic binning (FP64 or FP32 phase modes, precision studies): pair by pair.
@@ -1289,7 +1303,7 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
                         kahan_add(reinterpret_cast<float4*>(hist) + b1 * S, B.z, B.w);
                     }
                 } else if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
-                    bin_fast<PHASE>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                    bin_fast<PHASE, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
                 } else {
                     bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
                 }
@@ -1617,7 +1631,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                 const double* cd = cdt + (ci & 1) * CH;
                 if (active) {   // a3 + a4
                     if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok))
-                        bin_fast<PHASE>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                        bin_fast<PHASE, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
                     else
                         bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
                 }
