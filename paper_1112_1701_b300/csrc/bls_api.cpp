@@ -181,7 +181,7 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, int kmin, int kmax, Fol
     if (T > maxT) T = maxT;
     g->T = T;
     g->stride = (T + 15) & ~15;
-    g->ws = fold_use_ws(T, kahan, nb, kmin, kmax, P->d.fold_kernel);
+    g->ws = fold_ws_mode(T, kahan, nb, kmin, kmax, P->d.fold_kernel);
     g->smem = fold_smem_bytes(T, g->stride, nb, g->chunk, kahan);
     if (g->smem + kFoldSmemReserve > P->smem_optin)
         return set_error(BLS_ERR_INVALID, "nb = %d with %d frequencies per block needs %zu B of shared memory (> %zu)",

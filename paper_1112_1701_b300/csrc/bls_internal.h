@@ -124,7 +124,7 @@ size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int kahan);
 
 cudaError_t launch_prep(CurveDesc* d_curves, const int* slots, int ncurves, int* err, int phase,
                         cudaStream_t s);
-cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan, bool ws,
+cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan, int ws,
                               int sign, size_t smem, cudaStream_t s);
 cudaError_t launch_reduce(const ReduceParams& p, int ncurves, cudaStream_t s);
 size_t reduce_smem_bytes(int nb_max, int topk, int kahan);
@@ -144,7 +144,9 @@ int fold_sweep_max_threads();
 // width preferred for it.
 bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax, int choice);
 int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax, int choice);
-int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, bool ws);
+int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, int ws);
+// Kernel of a class: 0 one-group, 1 warp-specialised.
+int fold_ws_mode(int T, int kahan, int nb, int kmin, int kmax, int choice);
 int fold_block_threads(int cols);   // threads of a fold-sweep block with `cols` columns
 
 }  // namespace blsgpu

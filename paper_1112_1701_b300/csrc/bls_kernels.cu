@@ -1531,6 +1531,149 @@ __device__ void fetch_tile(const FoldParams& p, TileSlot* slot, int lane)
     }
 }
 
+// The sweep group's loop of fold_sweep_ws_kernel: threads sg0 .. sg0 + NS - 1, NS = T x
+// nparts, two parts sharing each column when NS = 2T.  Its first warp claims the work items
+// and writes the tile descriptors ahead; per tile it copies the histograms into TMEM, zeroes
+// them, hands them back and sweeps the boxes from TMEM.
+template <int SIGN>
+__device__ __forceinline__ void sweep_group_loop(const FoldParams& p, int sg0, int NS, int col,
+                                                 unsigned s_tmem, TileSlot* s_slot,
+                                                 unsigned full_bar, unsigned empty_bar,
+                                                 float* s_wpart, float* s_wpart2,
+                                                 unsigned char* hist, unsigned hbase,
+                                                 unsigned rowb)
+{
+    const int T = p.cols;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // nparts threads per column (warps of one TMEM lane quadrant when there are two)
+    const int nparts = NS / T;
+    const int part = (tid - sg0) / T;
+    const unsigned tbase = s_tmem + ((unsigned)((warp & 3) * 32) << 16);
+    const bool fetcher = warp == sg0 / 32;
+    unsigned ph = 0;
+    // descriptors of tiles 0 and 1; the histograms start empty
+    if (fetcher) fetch_tile(p, &s_slot[0], lane);
+    group_sync(kBarSweep, NS);
+    if (tid == sg0) mbar_arrive(empty_bar);
+    if (fetcher) fetch_tile(p, &s_slot[1], lane);
+    for (int k = 0;; ++k) {
+        int give_up = 0;
+        if (tid == sg0) {
+            give_up = !mbar_wait(full_bar, ph);
+            if (give_up) atomicOr(p.err, kErrTimeout);
+        }
+        ph ^= 1u;
+        give_up = group_or(kBarSweep, NS, give_up);
+        const TileSlot& sl = s_slot[k & 1];
+        if (give_up || sl.stop) break;
+        const int tile = sl.tile;
+        const int nf = sl.cd.nf, nb = sl.cd.nb, kmin = sl.cd.kmin, kmax = sl.cd.kmax;
+        float* const res = sl.cd.res;
+        const int j = tile * T + col;
+        const bool active = j < nf;
+        const int SB = sweep_block(nb, kmin, kmax);
+        const int tmode = ws_tmem_mode(nb, kmin, kmax);
+        const bool use_tmem = tmode != 0;
+        float v = 0.0f, wmax = 0.0f;
+        if (use_tmem) {
+            // copy bins 0 .. L-1 (bin b >= nb repeats bin b - nb; L <= 2 nb) into the
+            // column's lane, 8 bins per TMEM store (groups dealt to the parts), then zero
+            // the shared column (rows split between the parts)
+            const int L = ((tmode == 1 ? nb + kmax + SB - 1 : nb) + 7) & ~7;
+            const unsigned wrapb = (unsigned)nb * rowb;
+            for (int g = 8 * part; g < L; g += 8 * nparts) {
+                const unsigned ag = hbase + (unsigned)g * rowb;
+                u64 h[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    h[i] = lds64(ag + (unsigned)i * rowb - (g + i >= nb ? wrapb : 0u));
+                unsigned r[16];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float hw, hx;
+                    upk(h[i], hw, hx);
+                    if (g + i < nb) wmax = fmaxf(wmax, hw);
+                    r[2 * i] = __float_as_uint(hw);
+                    r[2 * i + 1] = __float_as_uint(hx);
+                }
+                tmem_st16(tbase + 2u * (unsigned)g, r);
+            }
+            const int zlo = part * nb / nparts, zhi = (part + 1) * nb / nparts;
+            int b = zlo;
+            for (; b + 4 <= zhi; b += 4) {
+                const unsigned a0 = hbase + (unsigned)b * rowb;
+                sts64(a0, 0ull);
+                sts64(a0 + rowb, 0ull);
+                sts64(a0 + 2u * rowb, 0ull);
+                sts64(a0 + 3u * rowb, 0ull);
+            }
+            for (; b < zhi; ++b) sts64(hbase + (unsigned)b * rowb, 0ull);
+            if (part == 1) s_wpart[col] = wmax;
+            tmem_wait_st();
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        } else if (part == 0) {
+            if (active)
+                v = SB == 4 ? sweep_max<0, SIGN, 4>(hist, p.stride, nb, kmin, kmax, 0, 1)
+                    : SB == 10 ? sweep_max<0, SIGN, 10>(hist, p.stride, nb, kmin, kmax, 0, 1)
+                               : sweep_max<0, SIGN, 8>(hist, p.stride, nb, kmin, kmax, 0, 1);
+            for (int b = 0; b < nb; ++b) sts64(hbase + (unsigned)b * rowb, 0ull);
+        }
+        group_sync(kBarSweep, NS);
+        if (tid == sg0) mbar_arrive(empty_bar);
+        if (use_tmem) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            bool fast = true;
+            if (part == 0) {
+                // the fast sweep's condition (as in sweep_max) and the exact sweep
+                if (nparts == 2) wmax = fmaxf(wmax, s_wpart[col]);
+                fast = (float)kmax * wmax < 0.89f;
+                const bool slide = !fast && kmax < nb;
+                if (__any_sync(0xffffffffu, slide)) {
+                    const float rmax = tmode == 1 ? heaviest_run_tmem<false>(tbase, nb, kmax)
+                                                  : heaviest_run_tmem<true>(tbase, nb, kmax);
+                    if (slide) fast = rmax < 0.89f;
+                }
+                const bool exact = active && !fast;
+                if (__any_sync(0xffffffffu, exact)) {
+                    Best g;
+                    if (tmode == 1) {
+                        TmemStream<false> src;
+                        src.base = tbase;
+                        src.tend = tbase + 2u * (unsigned)nb;
+                        g = sweep_exact_src<SIGN>(src, nb, kmin, kmax);
+                    } else {
+                        TmemStream<true> src;
+                        src.base = tbase;
+                        src.tend = tbase + 2u * (unsigned)nb;
+                        g = sweep_exact_src<SIGN>(src, nb, kmin, kmax);
+                    }
+                    if (exact) v = g.num > 0.0f ? __fdiv_rn(g.num, g.den) : 0.0f;
+                }
+            }
+            __syncwarp();
+            float vf;
+            if (tmode == 1)
+                vf = SB == 4 ? sweep_tmem<4, SIGN, false>(tbase, nb, kmin, kmax, part, nparts)
+                     : SB == 10 ? sweep_tmem<10, SIGN, false>(tbase, nb, kmin, kmax, part, nparts)
+                                : sweep_tmem<8, SIGN, false>(tbase, nb, kmin, kmax, part, nparts);
+            else
+                vf = SB == 4 ? sweep_tmem<4, SIGN, true>(tbase, nb, kmin, kmax, part, nparts)
+                     : SB == 10 ? sweep_tmem<10, SIGN, true>(tbase, nb, kmin, kmax, part, nparts)
+                                : sweep_tmem<8, SIGN, true>(tbase, nb, kmin, kmax, part, nparts);
+            if (nparts == 2) {   // the parts' maxima meet in shared memory
+                if (part == 1) s_wpart2[col] = vf;
+                group_sync(kBarSweep, NS);
+                if (part == 0) vf = fmaxf(vf, s_wpart2[col]);
+            }
+            if (fast) v = vf;
+        }
+        if (part == 0 && active) res[j] = v;
+        // descriptor of tile k + 2 (slot k & 1 is no longer read: the binning group
+        // copied it before binning tile k, this group above)
+        if (fetcher) fetch_tile(p, &s_slot[k & 1], lane);
+    }
+}
+
 constexpr int kWsMaxThreads = 384;
 
 template <int PHASE, int SIGN>
@@ -1640,134 +1783,8 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             if (tid == 0) mbar_arrive(full_bar);
         }
     } else {
-        // nparts threads per column (warps of one TMEM lane quadrant when there are two)
-        const int NS = blockDim.x - T;
-        const int nparts = NS / T;
-        const int part = (tid - T) / T;
-        const unsigned tbase = s_tmem + ((unsigned)((warp & 3) * 32) << 16);
-        const bool fetcher = warp == T / 32;
-        unsigned ph = 0;
-        // descriptors of tiles 0 and 1; the histograms start empty
-        if (fetcher) fetch_tile(p, &s_slot[0], lane);
-        group_sync(kBarSweep, NS);
-        if (tid == T) mbar_arrive(empty_bar);
-        if (fetcher) fetch_tile(p, &s_slot[1], lane);
-        for (int k = 0;; ++k) {
-            int give_up = 0;
-            if (tid == T) {
-                give_up = !mbar_wait(full_bar, ph);
-                if (give_up) atomicOr(p.err, kErrTimeout);
-            }
-            ph ^= 1u;
-            give_up = group_or(kBarSweep, NS, give_up);
-            const TileSlot& sl = s_slot[k & 1];
-            if (give_up || sl.stop) break;
-            const int tile = sl.tile;
-            const int nf = sl.cd.nf, nb = sl.cd.nb, kmin = sl.cd.kmin, kmax = sl.cd.kmax;
-            float* const res = sl.cd.res;
-            const int j = tile * T + col;
-            const bool active = j < nf;
-            const int SB = sweep_block(nb, kmin, kmax);
-            const int tmode = ws_tmem_mode(nb, kmin, kmax);
-            const bool use_tmem = tmode != 0;
-            float v = 0.0f, wmax = 0.0f;
-            if (use_tmem) {
-                // copy bins 0 .. L-1 (bin b >= nb repeats bin b - nb; L <= 2 nb) into the
-                // column's lane, 8 bins per TMEM store (groups dealt to the parts), then zero
-                // the shared column (rows split between the parts)
-                const int L = ((tmode == 1 ? nb + kmax + SB - 1 : nb) + 7) & ~7;
-                const unsigned wrapb = (unsigned)nb * rowb;
-                for (int g = 8 * part; g < L; g += 8 * nparts) {
-                    const unsigned ag = hbase + (unsigned)g * rowb;
-                    u64 h[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        h[i] = lds64(ag + (unsigned)i * rowb - (g + i >= nb ? wrapb : 0u));
-                    unsigned r[16];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        float hw, hx;
-                        upk(h[i], hw, hx);
-                        if (g + i < nb) wmax = fmaxf(wmax, hw);
-                        r[2 * i] = __float_as_uint(hw);
-                        r[2 * i + 1] = __float_as_uint(hx);
-                    }
-                    tmem_st16(tbase + 2u * (unsigned)g, r);
-                }
-                const int zlo = part * nb / nparts, zhi = (part + 1) * nb / nparts;
-                int b = zlo;
-                for (; b + 4 <= zhi; b += 4) {
-                    const unsigned a0 = hbase + (unsigned)b * rowb;
-                    sts64(a0, 0ull);
-                    sts64(a0 + rowb, 0ull);
-                    sts64(a0 + 2u * rowb, 0ull);
-                    sts64(a0 + 3u * rowb, 0ull);
-                }
-                for (; b < zhi; ++b) sts64(hbase + (unsigned)b * rowb, 0ull);
-                if (part == 1) s_wpart[col] = wmax;
-                tmem_wait_st();
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            } else if (part == 0) {
-                if (active)
-                    v = SB == 4 ? sweep_max<0, SIGN, 4>(hist, p.stride, nb, kmin, kmax, 0, 1)
-                        : SB == 10 ? sweep_max<0, SIGN, 10>(hist, p.stride, nb, kmin, kmax, 0, 1)
-                                   : sweep_max<0, SIGN, 8>(hist, p.stride, nb, kmin, kmax, 0, 1);
-                for (int b = 0; b < nb; ++b) sts64(hbase + (unsigned)b * rowb, 0ull);
-            }
-            group_sync(kBarSweep, NS);
-            if (tid == T) mbar_arrive(empty_bar);
-            if (use_tmem) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                bool fast = true;
-                if (part == 0) {
-                    // the fast sweep's condition (as in sweep_max) and the exact sweep
-                    if (nparts == 2) wmax = fmaxf(wmax, s_wpart[col]);
-                    fast = (float)kmax * wmax < 0.89f;
-                    const bool slide = !fast && kmax < nb;
-                    if (__any_sync(0xffffffffu, slide)) {
-                        const float rmax = tmode == 1 ? heaviest_run_tmem<false>(tbase, nb, kmax)
-                                                      : heaviest_run_tmem<true>(tbase, nb, kmax);
-                        if (slide) fast = rmax < 0.89f;
-                    }
-                    const bool exact = active && !fast;
-                    if (__any_sync(0xffffffffu, exact)) {
-                        Best g;
-                        if (tmode == 1) {
-                            TmemStream<false> src;
-                            src.base = tbase;
-                            src.tend = tbase + 2u * (unsigned)nb;
-                            g = sweep_exact_src<SIGN>(src, nb, kmin, kmax);
-                        } else {
-                            TmemStream<true> src;
-                            src.base = tbase;
-                            src.tend = tbase + 2u * (unsigned)nb;
-                            g = sweep_exact_src<SIGN>(src, nb, kmin, kmax);
-                        }
-                        if (exact) v = g.num > 0.0f ? __fdiv_rn(g.num, g.den) : 0.0f;
-                    }
-                }
-                __syncwarp();
-                float vf;
-                if (tmode == 1)
-                    vf = SB == 4 ? sweep_tmem<4, SIGN, false>(tbase, nb, kmin, kmax, part, nparts)
-                         : SB == 10 ? sweep_tmem<10, SIGN, false>(tbase, nb, kmin, kmax, part, nparts)
-                                    : sweep_tmem<8, SIGN, false>(tbase, nb, kmin, kmax, part, nparts);
-                else
-                    vf = SB == 4 ? sweep_tmem<4, SIGN, true>(tbase, nb, kmin, kmax, part, nparts)
-                         : SB == 10 ? sweep_tmem<10, SIGN, true>(tbase, nb, kmin, kmax, part, nparts)
-                                    : sweep_tmem<8, SIGN, true>(tbase, nb, kmin, kmax, part, nparts);
-                if (nparts == 2) {   // the parts' maxima meet in shared memory
-                    if (part == 1) s_wpart2[col] = vf;
-                    group_sync(kBarSweep, NS);
-                    if (part == 0) vf = fmaxf(vf, s_wpart2[col]);
-                }
-                if (fast) v = vf;
-            }
-            if (part == 0 && active) res[j] = v;
-            // descriptor of tile k + 2 (slot k & 1 is no longer read: the binning group
-            // copied it before binning tile k, this group above)
-            if (fetcher) fetch_tile(p, &s_slot[k & 1], lane);
-        }
+        sweep_group_loop<SIGN>(p, T, blockDim.x - T, col, s_tmem, s_slot, full_bar, empty_bar,
+                               s_wpart, s_wpart2, hist, hbase, rowb);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -1820,6 +1837,11 @@ bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax, int choice)
     return choice == BLS_FOLD_WS || ws_tmem_mode(nb, kmin, kmax) != 0;
 }
 
+int fold_ws_mode(int T, int kahan, int nb, int kmin, int kmax, int choice)
+{
+    return fold_use_ws(T, kahan, nb, kmin, kmax, choice) ? 1 : 0;
+}
+
 // Dynamic shared memory of a warp-specialised block: at least half of an SM's shared memory,
 // so that no second block (which would wait for the first one's TMEM) lands on the SM.
 static size_t ws_smem(size_t smem)
@@ -1838,7 +1860,7 @@ static size_t ws_smem(size_t smem)
 
 template <int PHASE, int KAHAN, int SIGN>
 static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t smem,
-                                 cudaStream_t s, bool ws)
+                                 cudaStream_t s, int ws)
 {
     FoldParams q = p;
     q.cols = T;
@@ -1860,7 +1882,7 @@ static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t sm
 }
 
 template <int PHASE, int KAHAN, int SIGN>
-static int blocks_t(int T, size_t smem, bool ws)
+static int blocks_t(int T, size_t smem, int ws)
 {
     if (ws && use_ws(T, KAHAN)) {
         // one block per SM: all of TMEM and (nearly) all of shared memory
@@ -1884,7 +1906,7 @@ static int blocks_t(int T, size_t smem, bool ws)
     return nb > 0 ? nb : 1;
 }
 
-int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, bool ws)
+int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, int ws)
 {
 #define BLS_OCC(PH)                                                                   \
     if (phase == PH) {                                                                \
@@ -1899,7 +1921,7 @@ int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, bool 
     return 1;
 }
 
-cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan, bool ws,
+cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan, int ws,
                               int sign, size_t smem, cudaStream_t s)
 {
 #define BLS_DISPATCH(PH)                                                              \

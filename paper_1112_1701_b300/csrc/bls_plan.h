@@ -57,7 +57,7 @@ struct FoldGeom {
     int chunk;      // staged points per chunk
     size_t smem;    // dynamic shared memory
     int grid;       // persistent blocks
-    bool ws;        // warp-specialised kernel
+    int ws;         // fold-sweep kernel: 0 one-group, 1 warp-specialised
 };
 
 struct Server;

@@ -125,7 +125,7 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
     };
     const int chunk = tmax(512) >= tmax(256) ? 512 : 256;
     const int T = fold_preferred_cols(tmax(chunk), 0, c->nb, kmin, kmax, BLS_FOLD_AUTO);
-    const bool ws = fold_use_ws(T, 0, c->nb, kmin, kmax, BLS_FOLD_AUTO);
+    const int ws = fold_ws_mode(T, 0, c->nb, kmin, kmax, BLS_FOLD_AUTO);
     if (T < 16) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", c->nb);
     const size_t smem = fold_smem_bytes(T, T, c->nb, chunk, 0);
 
