@@ -37,6 +37,19 @@ __device__ __forceinline__ double butterfly(double v)
     return v;
 }
 
+// FP32 -> FP64, exact, built from the bits with integer operations: the hardware conversion
+// runs on the FP64 pipe, which this kernel's sums already saturate (B300 runs FP64 at about
+// 1/64 of the FP32 rate).  Normal numbers: same sign, exponent rebiased by 1023 - 127 = 896,
+// mantissa widened; zeros, subnormals, infinities and NaNs take the hardware conversion.
+__device__ __forceinline__ double widen(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)x;
+    const unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 __global__ void star_kernel(const long long* off, const float* m, int nstars, double* mag,
                             double* rms, int* bin, int* err)
 {
@@ -49,12 +62,12 @@ __global__ void star_kernel(const long long* off, const float* m, int nstars, do
         return;
     }
     double part = 0.0;
-    for (long long i = a + lane; i < b; i += 32) part = __dadd_rn(part, (double)m[i]);
+    for (long long i = a + lane; i < b; i += 32) part = __dadd_rn(part, widen(m[i]));
     const double n = (double)(b - a);
     const double mu = __ddiv_rn(butterfly(part), n);
     part = 0.0;
     for (long long i = a + lane; i < b; i += 32) {
-        const double d = __dsub_rn((double)m[i], mu);
+        const double d = __dsub_rn(widen(m[i]), mu);
         part = __dadd_rn(part, __dmul_rn(d, d));
     }
     const double v = butterfly(part);
