@@ -482,10 +482,10 @@ def run_efficiency(args):
     ms = statistics.median(ts)
     units = len(t) * nf * nphi
     value = units / (ms / 1000.0)
-    # FP64-pipe roofline: 5 FP64 instructions per (time, phase, frequency): u = v - phi,
-    # u + 1/2, floor, r = u - c, |r| <= h; peak = the part's nominal 1.25 TFLOP/s FP64
-    # (0.625 T FP64 instructions/s)
-    peak = 0.625e12 / 5.0
+    # FP64-pipe roofline: 3 FP64 instructions per (time, phase, frequency): u = v - phi,
+    # u + 1/2, r = u - c (the floor and |r| <= h are integer operations on the bits); peak =
+    # the part's nominal 1.25 TFLOP/s FP64 (0.625 T FP64 instructions/s)
+    peak = 0.625e12 / 3.0
     # the oracle (one thread) on a bounded sample: the first kf frequencies; its result
     # also checks the timed configuration's output there
     kf = max(1, min(nf, int(args.eff_cpu_freqs)))
@@ -507,7 +507,7 @@ def run_efficiency(args):
                                    f"exposures, {nf} freqs in [0.1, 10]/d, {nphi} phases, "
                                    f"eclipse 0.04 d", "l2": "inputs (4.6 KB) stay in L2"},
             "roofline": {"bound": "alu", "achieved": value, "peak": peak,
-                         "unit": "time*phase*freq/s (FP64 pipe, 5 instructions each)",
+                         "unit": "time*phase*freq/s (FP64 pipe, 3 instructions each)",
                          "frac": value / peak, "traffic": None,
                          "peak_source": "nominal 1.25 TFLOP/s FP64 of the part"},
             "gpu_launches": args.steps * 2,

@@ -50,6 +50,27 @@ struct WindowParams {
     int* counts;
 };
 
+// floor(x) for x >= -0.5, exact, with integer operations on the bits (floor and compares
+// would otherwise share the FP64 pipe with the subtractions, and B300 runs FP64 at about 1/64
+// of the FP32 rate): x < 0 gives -1 (-0 itself); otherwise the fraction bits below the binary point are
+// cleared (x < 1 gives +0, x >= 2^52 is already an integer).
+__device__ __forceinline__ double floor_from_half(double x)
+{
+    const long long b = __double_as_longlong(x);
+    if (b < 0) return b == (long long)0x8000000000000000ull ? x : -1.0;   // -0 stays -0
+    const int e = (int)(b >> 52) - 1023;
+    if (e < 0) return 0.0;
+    if (e >= 52) return x;
+    return __longlong_as_double(b & ~((1ll << (52 - e)) - 1));
+}
+
+// |d| <= h for finite d and h >= 0: IEEE magnitudes order like their bit patterns.
+__device__ __forceinline__ bool abs_le(double d, double h)
+{
+    return (unsigned long long)(__double_as_longlong(d) & 0x7fffffffffffffffll) <=
+           (unsigned long long)__double_as_longlong(h);
+}
+
 __global__ void __launch_bounds__(kWinThreads) window_kernel(WindowParams p)
 {
     __shared__ double v[kChunk];
@@ -74,10 +95,11 @@ __global__ void __launch_bounds__(kWinThreads) window_kernel(WindowParams p)
                 __syncthreads();
                 if (live) {
                     for (int i = 0; i < cn; ++i) {
+                        // u >= -phi > -1 (times ascending from t0, f > 0), so RN(u + 0.5) >= -0.5
                         const double u = __dsub_rn(v[i], phi);
-                        const double c = floor(__dadd_rn(u, 0.5));
-                        if (fabs(__dsub_rn(u, c)) <= h) {
-                            if (!have || c != cur) {
+                        const double c = floor_from_half(__dadd_rn(u, 0.5));
+                        if (abs_le(__dsub_rn(u, c), h)) {
+                            if (!have || __double_as_longlong(c) != __double_as_longlong(cur)) {
                                 if (have && cnt >= p.min_points) ++ecl;
                                 cur = c;
                                 have = true;
