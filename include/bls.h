@@ -261,8 +261,11 @@ bls_status bls_server_stats_get(bls_plan* plan, bls_server_stats* out);
 bls_status bls_kminmax(int nb, double qmin, double qmax, int* kmin, int* kmax);
 
 /* Diagnostic: the phase bin of every point of one curve at frequencies js[0..nj), as
- * the search kernels compute them (plan's phase mode); bins_out[q*n + i] (host).
- * Errors: BLS_ERR_INVALID, BLS_ERR_CUDA. */
+ * the search kernels compute them (plan's phase mode); bins_out[q*n + i] (host).  In the
+ * FX64 mode on a uniform grid the incremental fold of the warp-specialised kernel is
+ * evaluated too (frequency js[q] at its place in a 128-frequency tile); a point where it
+ * disagrees with the direct fold is reported as -1 - bin, so every value is a valid bin
+ * exactly when both folds agree.  Errors: BLS_ERR_INVALID, BLS_ERR_CUDA. */
 bls_status bls_debug_fold(bls_plan* plan, const bls_curve* curve, const int* js, int nj,
                           int* bins_out);
 

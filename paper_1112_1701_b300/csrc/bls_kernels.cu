@@ -59,6 +59,10 @@ struct FoldConst {
     unsigned ftol;       // edge window: bin certain iff ftol <= r < 2^32 - ftol - nb
     unsigned fspan;      // 2^32 - 2 ftol - nb
     bool fxok;           // the fixed-point path is valid for this (curve, frequency)
+    // incremental fixed-point fold of a uniform-grid tile (see make_fold_const_inc)
+    unsigned tau;        // j - jc (two's complement): this column's offset from the reference
+    unsigned Fclo, Fchi; // Fc = RN_int(f_jc 2^(64 - fxs))
+    unsigned dFlo, dFhi; // dF = RN_int(df 2^(96 - fxs)) < 2^63
 };
 
 // Fixed-point scale of a curve's offsets: DT = RN_int(dt 2^s) with dt < 2^L.  The fold
@@ -125,6 +129,62 @@ __device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dt
     return fc;
 }
 
+// Incremental fixed-point fold of a uniform-grid tile.  The tile's columns j share one
+// reference column jc; per point, the tile's staging step forms once
+//   Qi = the FX64 phase word of dt_i at f_jc   (floor(DT Fc 2^-32) mod 2^32, as above),
+//   Di = RN(DT dF 2^-64) mod 2^32               (the phase step frac(dt_i df) in 2^-32 units),
+// and the column with offset tau = j - jc takes q = Qi + tau Di (mod 2^32): one integer
+// multiply-add per point and frequency instead of three.  Relative to dt f_j (mod 1), with
+// f_j = RN(fmin + RN(j df)):
+//   Qi 2^-32 lies in (X - 2^-32, X] with |X - dt f_jc| <= f_jc 2^-(s+1) + dtmax 2^(s-65) + 2^-66,
+//   |Di 2^-32 - dt df| <= 2^-33 + df 2^-(s+1) + dtmax 2^(s-97) + 2^-98 (multiplied by |tau|),
+//   |dt f_j - dt (f_jc + tau df)| <= dtmax fmax 2^-51 (1.01) (both grid roundings),
+// and the FP64 definition is within 2^-52 (dt f_j + 1) of dt f_j, so the window test of the
+// direct fold applies with tol = (sum of these) nb 2^32 (1.01) + 4.  Valid (fxok) while
+// Fc < 2^64, dF < 2^63 and tol < 10^9; the window keeps fewer than 10^-5 of the points of
+// the typical workloads for the exact re-fold.
+__device__ __forceinline__ bool inc_tile_ok(double fc, double df, int fxs)
+{
+    return df > 0.0 && fc >= 0.0 && ldexp(fc, 64 - fxs) < 18446744073709551616.0 &&
+           ldexp(df, 96 - fxs) < 9223372036854775808.0;
+}
+
+__device__ __forceinline__ void make_fold_const_inc(FoldConst& fc, double f, double fcen, int tau,
+                                                    double df, int nb, double dtmax, int fxs)
+{
+    const unsigned long long Fc = __double2ull_rn(ldexp(fcen, 64 - fxs));
+    const unsigned long long dF = __double2ull_rn(ldexp(df, 96 - fxs));
+    fc.Fclo = (unsigned)Fc;
+    fc.Fchi = (unsigned)(Fc >> 32);
+    fc.dFlo = (unsigned)dF;
+    fc.dFhi = (unsigned)(dF >> 32);
+    fc.tau = (unsigned)tau;
+    const double at = fabs((double)tau);
+    const double fhi = fmax(f, fcen);
+    const double E = fcen * ldexp(1.0, -(fxs + 1)) + dtmax * ldexp(1.0, fxs - 65) + ldexp(1.0, -66)
+                   + at * (ldexp(1.0, -33) + df * ldexp(1.0, -(fxs + 1)) + dtmax * ldexp(1.0, fxs - 97)
+                           + ldexp(1.0, -98))
+                   + dtmax * fhi * ldexp(1.0, -51) * 1.01
+                   + ldexp(1.0, -52) * (dtmax * f + 1.0);
+    const double tolu = E * nb * 4294967296.0 * 1.01 + 4.0;
+    fc.fxok = tolu < 1.0e9;
+    const unsigned tol = fc.fxok ? (unsigned)ceil(tolu) : 0u;
+    fc.ftol = tol;
+    fc.fspan = fc.fxok ? (unsigned)(4294967296.0 - 2.0 * tol - nb) : 0u;
+}
+
+// (Qi, Di) of one point from DT = (hi:lo) and the tile's Fc, dF (see make_fold_const_inc).
+__device__ __forceinline__ void inc_point(unsigned lo, unsigned hi, const FoldConst& fc,
+                                          unsigned& Q, unsigned& D)
+{
+    Q = __umulhi(lo, fc.Fclo) + lo * fc.Fchi + hi * fc.Fclo;
+    // bits 64..95 of DT dF rounded to nearest: DT dF = p00 + 2^32 (p01 + p10) + 2^64 hi dFhi
+    typedef unsigned long long w64;
+    const w64 p00 = (w64)lo * fc.dFlo, p01 = (w64)lo * fc.dFhi, p10 = (w64)hi * fc.dFlo;
+    const w64 mid = (p00 >> 32) + (w64)(unsigned)p01 + (w64)(unsigned)p10 + 0x80000000ull;
+    D = (unsigned)(mid >> 32) + (unsigned)(p01 >> 32) + (unsigned)(p10 >> 32) + hi * fc.dFhi;
+}
+
 // FP32 fold (precision study): no error bound, no fallback.
 __device__ __forceinline__ unsigned fold_f32(float dt32, const FoldConst& fc)
 {
@@ -179,6 +239,11 @@ __device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c)
     upk(c, c0, c1);
     return pk(__fmaf_rn(a0, b0, c0), __fmaf_rn(a1, b1, c1));
 }
+// acc + x where i == j, else acc.
+__device__ __forceinline__ u64 add2_if_eq(u64 acc, u64 x, unsigned i, unsigned j)
+{
+    return i == j ? add2(acc, x) : acc;
+}
 #else
 __device__ __forceinline__ u64 add2(u64 a, u64 b)
 {
@@ -203,6 +268,13 @@ __device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c)
     u64 d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
+}
+// acc + x where i == j, else acc: one compare and one predicated packed add.
+__device__ __forceinline__ u64 add2_if_eq(u64 acc, u64 x, unsigned i, unsigned j)
+{
+    asm("{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %2, %3;\n\t@p add.rn.f32x2 %0, %0, %1;\n\t}"
+        : "+l"(acc) : "l"(x), "r"(i), "r"(j));
+    return acc;
 }
 
 #endif
@@ -265,16 +337,25 @@ __device__ __forceinline__ void fold_df32_pair(const float4& A, const FoldPacked
     e1 = !(fabsf(d1) <= q.lim);
 }
 
-// Fixed-point fold of two points at once; A = (DT0 lo, DT1 lo, DT0 hi, DT1 hi) as bit
-// patterns.  The high word of the low 64 bits of DT*F is lo*Fhi + hi*Flo + the carry word
-// of lo*Flo (mod 2^32): three integer multiply-adds per point, then one for the bin.
+// Fixed-point fold of two points at once.  Direct (INC = false): A = (DT0 lo, DT1 lo, DT0 hi,
+// DT1 hi) as bit patterns; the high word of the low 64 bits of DT*F is lo*Fhi + hi*Flo +
+// the carry word of lo*Flo (mod 2^32): three integer multiply-adds per point.  Incremental
+// (INC = true, a uniform-grid tile after its staging step): A = (Q0, Q1, D0, D1) and the
+// phase word is Q + tau D, one multiply-add.  Then one multiply-add for the bin.
+template <bool INC = false>
 __device__ __forceinline__ void fold_fx_pair(const float4& A, const FoldConst& fc,
                                              unsigned& b0, unsigned& b1, bool& e0, bool& e1)
 {
     const unsigned lo0 = __float_as_uint(A.x), lo1 = __float_as_uint(A.y);
     const unsigned hi0 = __float_as_uint(A.z), hi1 = __float_as_uint(A.w);
-    const unsigned q0 = __umulhi(lo0, fc.Flo) + lo0 * fc.Fhi + hi0 * fc.Flo;
-    const unsigned q1 = __umulhi(lo1, fc.Flo) + lo1 * fc.Fhi + hi1 * fc.Flo;
+    unsigned q0, q1;
+    if (INC) {
+        q0 = lo0 + hi0 * fc.tau;
+        q1 = lo1 + hi1 * fc.tau;
+    } else {
+        q0 = __umulhi(lo0, fc.Flo) + lo0 * fc.Fhi + hi0 * fc.Flo;
+        q1 = __umulhi(lo1, fc.Flo) + lo1 * fc.Fhi + hi1 * fc.Flo;
+    }
     const unsigned nbu = (unsigned)fc.nb;
     b0 = __umulhi(q0, nbu);
     b1 = __umulhi(q1, nbu);
@@ -552,7 +633,7 @@ __device__ __forceinline__ void sts64(unsigned addr, u64 v)
 
 // Bins of the 8 point pairs of a 16-point sub-chunk, with their weight pairs; returns
 // whether any bin is not certain (then fix_sub must run before the bins are used).
-template <int PHASE>
+template <int PHASE, bool INC>
 __device__ __forceinline__ bool fold_sub(const float4* cp, const FoldConst& fc, const FoldPacked& fq,
                                          unsigned* b, float4* Bw)
 {
@@ -562,7 +643,7 @@ __device__ __forceinline__ bool fold_sub(const float4* cp, const FoldConst& fc, 
         const float4 A = cp[2 * q];
         Bw[q] = cp[2 * q + 1];
         bool e0, e1;
-        if (PHASE == kPhaseFX64) fold_fx_pair(A, fc, b[2 * q], b[2 * q + 1], e0, e1);
+        if (PHASE == kPhaseFX64) fold_fx_pair<INC>(A, fc, b[2 * q], b[2 * q + 1], e0, e1);
         else fold_df32_pair(A, fq, b[2 * q], b[2 * q + 1], e0, e1);
         edge = edge | e0 | e1;
     }
@@ -570,7 +651,7 @@ __device__ __forceinline__ bool fold_sub(const float4* cp, const FoldConst& fc, 
 }
 
 // Rare path: re-fold in FP64 the points of a sub-chunk whose bin is not certain.
-template <int PHASE>
+template <int PHASE, bool INC>
 __device__ __forceinline__ void fix_sub(const float4* cp, const double* cd, const FoldConst& fc,
                                      const FoldPacked& fq, unsigned* b)
 {
@@ -578,42 +659,49 @@ __device__ __forceinline__ void fix_sub(const float4* cp, const double* cd, cons
     for (int q = 0; q < 8; ++q) {
         unsigned b0, b1;
         bool e0, e1;
-        if (PHASE == kPhaseFX64) fold_fx_pair(cp[2 * q], fc, b0, b1, e0, e1);
+        if (PHASE == kPhaseFX64) fold_fx_pair<INC>(cp[2 * q], fc, b0, b1, e0, e1);
         else fold_df32_pair(cp[2 * q], fq, b0, b1, e0, e1);
         if (e0) b[2 * q] = fold_exact(cd[2 * q], fc.f, fc.nb);
         if (e1) b[2 * q + 1] = fold_exact(cd[2 * q + 1], fc.f, fc.nb);
     }
 }
 
-// Read-modify-write of the 16 points of a sub-chunk in groups of 4: all four bins of a
-// group are read before any is written, and a point that lands in the bin of an earlier
-// point of the group adds onto that point's new value (the later store carries the
-// total), so the result equals adding the points one by one in order.
+// Read-modify-write of the 16 points of a sub-chunk in groups of kRmwGroup: all bins of a
+// group are read before any is written.  Points of a group that share a bin are merged
+// before the read: each point's addend is its own weights plus those of the earlier points
+// of the group in its bin, so the last of them stores the bin's full total (the earlier
+// stores are overwritten).  The addends depend only on the fold, so the loaded value feeds
+// one packed add and the store; a bin hit by several points of one group receives their
+// pre-summed weights in one addition.
+constexpr int kRmwGroup = 4;
+
 __device__ __forceinline__ void rmw_sub(unsigned hbase, unsigned rowb, const unsigned* b,
                                         const float4* Bw)
 {
+    constexpr int G = kRmwGroup;
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        unsigned a[4];
-        u64 h[4], v[4], q[4];
+    for (int g = 0; g < 16 / G; ++g) {
+        const unsigned* bg = b + G * g;
+        unsigned a[G];
+        u64 h[G], q[G];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            a[i] = hbase + b[4 * g + i] * rowb;
+        for (int i = 0; i < G; ++i) {
+            a[i] = hbase + bg[i] * rowb;
             h[i] = lds64(a[i]);
         }
-        q[0] = pk(Bw[2 * g].x, Bw[2 * g].y);
-        q[1] = pk(Bw[2 * g].z, Bw[2 * g].w);
-        q[2] = pk(Bw[2 * g + 1].x, Bw[2 * g + 1].y);
-        q[3] = pk(Bw[2 * g + 1].z, Bw[2 * g + 1].w);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            u64 base = h[i];
+        for (int i = 0; i < G; ++i) {
+            const float4& w = Bw[(G * g + i) >> 1];
+            q[i] = (i & 1) ? pk(w.z, w.w) : pk(w.x, w.y);
+        }
+        // later points first, so that every q[j] added is still a single point's weights
 #pragma unroll
-            for (int j = 0; j < i; ++j) base = b[4 * g + i] == b[4 * g + j] ? v[j] : base;
-            v[i] = add2(base, q[i]);
+        for (int i = G - 1; i > 0; --i) {
+#pragma unroll
+            for (int j = 0; j < i; ++j) q[i] = add2_if_eq(q[i], q[j], bg[i], bg[j]);
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) sts64(a[i], v[i]);
+        for (int i = 0; i < G; ++i) sts64(a[i], add2(h[i], q[i]));
     }
 }
 
@@ -623,14 +711,14 @@ __device__ __forceinline__ void rmw_sub(unsigned hbase, unsigned rowb, const uns
 // chain, so the fold arithmetic fills the shared-memory latency of the chain; the rare
 // FP64 re-fold runs after the stores.  hbase is the shared-memory address of this
 // thread's bin 0, rowb the byte stride between bins.
-template <int PHASE, bool PINGPONG>
+template <int PHASE, bool PINGPONG, bool INC>
 __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int nsub,
                                          unsigned hbase, unsigned rowb, const FoldConst& fc,
                                          const FoldPacked& fq)
 {
     unsigned b0[16], b1[16];
     float4 W0[8], W1[8];
-    if (fold_sub<PHASE>(cp, fc, fq, b0, W0)) fix_sub<PHASE>(cp, cd, fc, fq, b0);
+    if (fold_sub<PHASE, INC>(cp, fc, fq, b0, W0)) fix_sub<PHASE, INC>(cp, cd, fc, fq, b0);
     int sc = 0;
     if (PINGPONG) {
         // the two buffers used in turn (the loop body covers two sub-chunks): no register
@@ -638,20 +726,20 @@ __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int
         // warps are the critical path; slower in the one-group kernel)
         for (; sc + 2 < nsub; sc += 2) {
             const float4* n1 = cp + 16 * (sc + 1);
-            const bool e1 = fold_sub<PHASE>(n1, fc, fq, b1, W1);
+            const bool e1 = fold_sub<PHASE, INC>(n1, fc, fq, b1, W1);
             rmw_sub(hbase, rowb, b0, W0);
-            if (e1) fix_sub<PHASE>(n1, cd + 16 * (sc + 1), fc, fq, b1);
+            if (e1) fix_sub<PHASE, INC>(n1, cd + 16 * (sc + 1), fc, fq, b1);
             const float4* n2 = cp + 16 * (sc + 2);
-            const bool e2 = fold_sub<PHASE>(n2, fc, fq, b0, W0);
+            const bool e2 = fold_sub<PHASE, INC>(n2, fc, fq, b0, W0);
             rmw_sub(hbase, rowb, b1, W1);
-            if (e2) fix_sub<PHASE>(n2, cd + 16 * (sc + 2), fc, fq, b0);
+            if (e2) fix_sub<PHASE, INC>(n2, cd + 16 * (sc + 2), fc, fq, b0);
         }
     }
     for (; sc + 1 < nsub; ++sc) {
         const float4* n1 = cp + 16 * (sc + 1);
-        const bool e1 = fold_sub<PHASE>(n1, fc, fq, b1, W1);
+        const bool e1 = fold_sub<PHASE, INC>(n1, fc, fq, b1, W1);
         rmw_sub(hbase, rowb, b0, W0);
-        if (e1) fix_sub<PHASE>(n1, cd + 16 * (sc + 1), fc, fq, b1);
+        if (e1) fix_sub<PHASE, INC>(n1, cd + 16 * (sc + 1), fc, fq, b1);
 #pragma unroll
         for (int i = 0; i < 16; ++i) b0[i] = b1[i];
 #pragma unroll
@@ -1303,7 +1391,7 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
                         kahan_add(reinterpret_cast<float4*>(hist) + b1 * S, B.z, B.w);
                     }
                 } else if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
-                    bin_fast<PHASE, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                    bin_fast<PHASE, false, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
                 } else {
                     bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
                 }
@@ -1742,8 +1830,16 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             const double* gdt = cdr.dt64;
             const int j = tile * T + col;
             const bool active = j < nf;
-            const double f = grid_freq(cdr, active ? j : nf - 1);
-            const FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs);
+            const int jt = active ? j : nf - 1;
+            const double f = grid_freq(cdr, jt);
+            FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs);
+            // FX64 tiles of a uniform grid take the incremental fold, with the tile's middle
+            // column (at most its last frequency) as the reference column
+            const int jc = min(tile * T + T / 2, nf - 1);
+            const double fcen = grid_freq(cdr, jc);
+            const bool inc = PHASE == kPhaseFX64 && cdr.freqs == nullptr &&
+                             inc_tile_ok(fcen, cdr.df, cdr.fxs);
+            if (inc) make_fold_const_inc(fc, f, fcen, jt - jc, cdr.df, nb, cdr.dtmax, cdr.fxs);
             const FoldPacked fq = make_fold_packed(fc);
 
             // a2: chunks of CH points through shared memory (as in fold_sweep_kernel)
@@ -1768,14 +1864,31 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             for (int ci = 0; ci < nchunks; ++ci) {
                 if (ci + 1 < nchunks) stage(ci + 1); else cp_async_commit();
                 cp_async_wait1();
+                if (inc && !(tid & 1)) {
+                    // staging step of the incremental fold, on this thread's own copies (the
+                    // even slots, DT of a point pair): (lo0, lo1, hi0, hi1) -> (Q0, Q1, D0, D1)
+                    float4* dp = cpts + (ci & 1) * CH;
+                    const int cn = (min(CH, n - ci * CH) + 1) & ~1;
+                    for (int i = tid; i < cn; i += T) {
+                        const float4 A = dp[i];
+                        unsigned Q0, D0, Q1, D1;
+                        inc_point(__float_as_uint(A.x), __float_as_uint(A.z), fc, Q0, D0);
+                        inc_point(__float_as_uint(A.y), __float_as_uint(A.w), fc, Q1, D1);
+                        dp[i] = make_float4(__uint_as_float(Q0), __uint_as_float(Q1),
+                                            __uint_as_float(D0), __uint_as_float(D1));
+                    }
+                }
                 group_sync(kBarBin, T);
                 const int cnum = min(CH, n - ci * CH);
                 const float4* cp = cpts + (ci & 1) * CH;
                 const double* cd = cdt + (ci & 1) * CH;
                 if (active) {   // a3 + a4
-                    if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok))
-                        bin_fast<PHASE, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
-                    else
+                    if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
+                        if (inc)
+                            bin_fast<PHASE, true, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                        else
+                            bin_fast<PHASE, true, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                    } else
                         bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
                 }
                 group_sync(kBarBin, T);
@@ -1942,8 +2055,10 @@ cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, i
 // ------------------------------------------------------------------------- best box
 
 // The best box (exact tie-break) of one frequency: bins the curve point by point into a
-// private histogram column with the same arithmetic and order as the hot kernel, then
-// runs the exact sweep.
+// private histogram column with the hot kernel's fold, then runs the exact sweep.  The
+// FP32 bin sums follow point order; where points of one read-modify-write group of the hot
+// kernel share a bin, that kernel adds their pre-summed weights, so such a bin can differ
+// from this one in its last bit.
 __device__ Best best_box_at(const CurveDesc& cd, double f, unsigned char* hist, int stride,
                             int phase, int kahan, int sign)
 {
@@ -2182,17 +2297,43 @@ cudaError_t launch_reduce(const ReduceParams& p, int ncurves, cudaStream_t s)
 
 // ------------------------------------------------------------------------- diagnostics
 
+// Per-point bins of one curve at frequencies js, by the fold of the given phase mode.  In
+// FX64 mode on a uniform grid the incremental fold of the warp-specialised kernel is run as
+// well, for the frequency's place in a tile of kDebugTile columns; a point where the two
+// disagree is reported as -1 - bin.
+constexpr int kDebugTile = 128;
+
 template <int PHASE>
 __global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bins)
 {
     const CurveDesc cd = *curve;
     const int q = blockIdx.x;
-    const double f = grid_freq(cd, js[q]);
+    const int j = js[q];
+    const double f = grid_freq(cd, j);
     const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax, cd.fxs);
     const FoldPacked fq = make_fold_packed(fc);
+    FoldConst fi = fc;
+    const int jc = min(j / kDebugTile * kDebugTile + kDebugTile / 2, cd.nf - 1);
+    const double fcen = grid_freq(cd, jc);
+    const bool inc = PHASE == kPhaseFX64 && cd.freqs == nullptr && inc_tile_ok(fcen, cd.df, cd.fxs);
+    if (inc) make_fold_const_inc(fi, f, fcen, j - jc, cd.df, cd.nb, cd.dtmax, cd.fxs);
     for (int pi = threadIdx.x; 2 * pi < cd.n; pi += blockDim.x) {
         unsigned b0, b1;
         fold_pair<PHASE>(cd.pts[2 * pi], &cd.dt64[2 * pi], fc, fq, b0, b1);
+        if (inc && fi.fxok) {
+            const float4 A = cd.pts[2 * pi];
+            unsigned Q0, D0, Q1, D1, c0, c1;
+            bool e0, e1;
+            inc_point(__float_as_uint(A.x), __float_as_uint(A.z), fi, Q0, D0);
+            inc_point(__float_as_uint(A.y), __float_as_uint(A.w), fi, Q1, D1);
+            fold_fx_pair<true>(make_float4(__uint_as_float(Q0), __uint_as_float(Q1),
+                                           __uint_as_float(D0), __uint_as_float(D1)),
+                               fi, c0, c1, e0, e1);
+            if (e0) c0 = fold_exact(cd.dt64[2 * pi], f, cd.nb);
+            if (e1) c1 = fold_exact(cd.dt64[2 * pi + 1], f, cd.nb);
+            if (c0 != b0) b0 = (unsigned)(-1 - (int)b0);
+            if (c1 != b1) b1 = (unsigned)(-1 - (int)b1);
+        }
         bins[(size_t)q * cd.n + 2 * pi] = (int)b0;
         if (2 * pi + 1 < cd.n) bins[(size_t)q * cd.n + 2 * pi + 1] = (int)b1;
     }

@@ -77,11 +77,19 @@ def test_bins_bit_exact_plain_and_long_baseline(phase):
 
 
 @pytest.mark.parametrize("phase", ["df32", "fx64"])
-def test_bins_bit_exact_on_exact_edges(phase):
+@pytest.mark.parametrize("grid", ["coarse", "fine"])
+def test_bins_bit_exact_on_exact_edges(phase, grid):
     """Points placed exactly on bin edges (and on integer cycles) at grid frequencies:
-    every one lands within the error bound and takes the exact FP64 re-fold."""
-    nb, f0, df = 64, 0.5, 0.25
-    js = [0, 1, 2, 6, 10]
+    every one lands within the error bound and takes the exact FP64 re-fold.  On the fine
+    grid the FX64 debug fold also runs the incremental fold of 128-frequency tiles (offsets
+    -64 .. 63 from the tile's middle column, and a ragged last tile), which must agree."""
+    nb = 64
+    if grid == "coarse":
+        f0, df, nf = 0.5, 0.25, 11
+        js = [0, 1, 2, 6, 10]
+    else:
+        f0, df, nf = 0.5, 0.001, 1000
+        js = [0, 1, 2, 63, 64, 65, 100, 127, 128, 500, 998, 999]
     rng = np.random.default_rng(5)
     dts = []
     for j in js:
@@ -92,7 +100,7 @@ def test_bins_bit_exact_on_exact_edges(phase):
     dt = np.sort(np.concatenate(dts + [np.array([0.0])]))
     t = synth.T0 + dt
     y = np.ones(len(t), np.float32)
-    ci = bls.CurveInput(t, y, None, nf=11, fmin=f0, df=df, nb=nb, qmin=0.02, qmax=0.2)
+    ci = bls.CurveInput(t, y, None, nf=nf, fmin=f0, df=df, nb=nb, qmin=0.02, qmax=0.2)
     with _plan(nb, 0.02, 0.2, phase=phase) as p:
         bg = p.debug_fold(ci, js)
     bo = oracle.bins(t, [oracle.freq(j, f0, df) for j in js], nb)
