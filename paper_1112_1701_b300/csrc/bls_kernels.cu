@@ -185,6 +185,24 @@ __device__ __forceinline__ void inc_point(unsigned lo, unsigned hi, const FoldCo
     D = (unsigned)(mid >> 32) + (unsigned)(p01 >> 32) + (unsigned)(p10 >> 32) + hi * fc.dFhi;
 }
 
+// Staging step of the incremental fold on the copies this thread made of a chunk (slots
+// i = tid + m*nthreads < cn; nthreads even, so the thread's slots are all point-pair DT
+// slots or all weight slots): (lo0, lo1, hi0, hi1) -> (Q0, Q1, D0, D1).  Runs after the
+// thread's cp.async copies of the chunk completed and before the barrier that publishes it.
+__device__ __forceinline__ void inc_stage(float4* dp, int cn, int tid, int nthreads,
+                                          const FoldConst& fc)
+{
+    if (tid & 1) return;
+    for (int i = tid; i < cn; i += nthreads) {
+        const float4 A = dp[i];
+        unsigned Q0, D0, Q1, D1;
+        inc_point(__float_as_uint(A.x), __float_as_uint(A.z), fc, Q0, D0);
+        inc_point(__float_as_uint(A.y), __float_as_uint(A.w), fc, Q1, D1);
+        dp[i] = make_float4(__uint_as_float(Q0), __uint_as_float(Q1), __uint_as_float(D0),
+                            __uint_as_float(D1));
+    }
+}
+
 // FP32 fold (precision study): no error bound, no fallback.
 __device__ __forceinline__ unsigned fold_f32(float dt32, const FoldConst& fc)
 {
@@ -1339,8 +1357,16 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
         const int tile = tr.tile_lo + (int)(it - p.prefix[lo]);
         const int j = tile * T + col;
         const bool active = j < nf;
-        const double f = grid_freq(cdr, active ? j : nf - 1);
-        const FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs);
+        const int jt = active ? j : nf - 1;
+        const double f = grid_freq(cdr, jt);
+        FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs);
+        // FX64 tiles of a uniform grid (plain sums) take the incremental fold, with the
+        // tile's middle column (at most its last frequency) as the reference column
+        const int jc = min(tile * T + T / 2, nf - 1);
+        const double fcen = grid_freq(cdr, jc);
+        const bool inc = PHASE == kPhaseFX64 && !KAHAN && cdr.freqs == nullptr &&
+                         inc_tile_ok(fcen, cdr.df, cdr.fxs);
+        if (inc) make_fold_const_inc(fc, f, fcen, jt - jc, cdr.df, nb, cdr.dtmax, cdr.fxs);
         const FoldPacked fq = make_fold_packed(fc);
 
         for (int b = 0; b < nb && part == 0; ++b) {
@@ -1376,6 +1402,7 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
         for (int ci = 0; ci < nchunks; ++ci) {
             if (ci + 1 < nchunks) stage(ci + 1); else cp_async_commit();
             cp_async_wait1();
+            if (inc) inc_stage(cpts + (ci & 1) * CH, (min(CH, n - ci * CH) + 1) & ~1, tid, NT, fc);
             __syncthreads();
             const int cnum = min(CH, n - ci * CH);
             const float4* cp = cpts + (ci & 1) * CH;
@@ -1391,7 +1418,10 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
                         kahan_add(reinterpret_cast<float4*>(hist) + b1 * S, B.z, B.w);
                     }
                 } else if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
-                    bin_fast<PHASE, false, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                    if (inc)
+                        bin_fast<PHASE, false, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                    else
+                        bin_fast<PHASE, false, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
                 } else {
                     bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
                 }
@@ -1867,6 +1897,8 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                 if (inc && !(tid & 1)) {
                     // staging step of the incremental fold, on this thread's own copies (the
                     // even slots, DT of a point pair): (lo0, lo1, hi0, hi1) -> (Q0, Q1, D0, D1)
+                    // (written out here rather than through inc_stage: the binning loop
+                    // below is measurably faster with this form)
                     float4* dp = cpts + (ci & 1) * CH;
                     const int cn = (min(CH, n - ci * CH) + 1) & ~1;
                     for (int i = tid; i < cn; i += T) {
