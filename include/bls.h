@@ -175,6 +175,10 @@ void bls_plan_destroy(bls_plan* plan);
  * and a later call whose group has the same layout (same pointers, sizes, options)
  * replays it with one launch; the arrays' contents may change between calls.  The
  * environment variable BLS_NO_GRAPHS=1, read at plan creation, turns this off.
+ * Sizes, grids and widths are checked on the host before any work is queued; the values
+ * (finite t and y, finite dy > 0, explicit frequencies > 0) are checked on the device on
+ * the copies, for host and device inputs alike, and a bad value makes the call return
+ * BLS_ERR_INVALID after the launch group ran (its outputs are then undefined).
  * Errors: BLS_ERR_INVALID, BLS_ERR_NOMEM, BLS_ERR_CUDA, BLS_ERR_INTERNAL. */
 bls_status bls_search(bls_plan* plan, const bls_curve* curves, int ncurves,
                       bls_peak* out, float* spectrum);

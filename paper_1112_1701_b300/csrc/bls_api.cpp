@@ -98,7 +98,7 @@ static bls_status kminmax_impl(int nb, double qmin, double qmax, int* kmin, int*
 }
 
 bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* o,
-                         const int* kinds)
+                         const int* kinds, bool scan_values)
 {
     if (!c) return set_error(BLS_ERR_INVALID, "curve %d: NULL descriptor", index);
     if (c->n < 2) return set_error(BLS_ERR_INVALID, "curve %d: n = %d, need n >= 2", index, c->n);
@@ -137,7 +137,9 @@ bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, 
     o->dy_dev = c->dy ? kd == 2 : false;
     o->f_dev = c->freqs ? kf == 2 : false;
     o->capturable = kt != 0 && ky != 0 && kd != 0 && kf != 0;   // no pageable host copies
-    // host values are checked here; device values by the prep kernel
+    // host values are checked here (unless the caller's prep kernel checks them after the
+    // copy); device values by the prep kernel
+    if (!scan_values) return BLS_OK;
     if (!o->t_dev)
         for (int i = 0; i < c->n; ++i)
             if (!std::isfinite(c->t[i])) return set_error(BLS_ERR_INVALID, "curve %d: t[%d] is not finite", index, i);
@@ -682,7 +684,9 @@ bls_status search_impl(bls_plan_impl* P, const bls_curve* curves, int ncurves, b
             kinds[a] = run_kind[a];
             run_end[a] = static_cast<const char*>(ptrs[a]) + (cnt[a] > 0 ? cnt[a] : 0) * sz[a];
         }
-        bls_status s = resolve_curve(P, &cv, c, &specs[c], kinds);
+        // values are checked by the prep kernel on the device copies (one pass over the
+        // points on the device instead of three on the host)
+        bls_status s = resolve_curve(P, &cv, c, &specs[c], kinds, false);
         if (s != BLS_OK) return s;
     }
     const bool spec_dev = spectrum && is_device_ptr(spectrum);

@@ -96,8 +96,11 @@ struct bls_plan_impl {
 
 // Resolve and validate one curve against the plan (host checks only).  kinds (optional):
 // the memory kind of t, y, dy, freqs (0 pageable, 1 pinned, 2 device) when already known.
+// scan_values: also check every host-resident value (finite t and y, finite dy > 0, grid
+// frequencies > 0); callers whose kernels check the values on the device after the copy
+// (the prep kernel of a search) pass false.
 bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* out,
-                         const int* kinds = nullptr);
+                         const int* kinds = nullptr, bool scan_values = true);
 int ptr_kind(const void* p);
 void ubls_extents(double qmin, double qmax, unsigned* QMIN, unsigned* QMAX);
 constexpr int kUblsMaxPoints = 8192;   // the unbinned search sorts a curve in shared memory
