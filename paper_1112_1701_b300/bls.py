@@ -207,15 +207,78 @@ def _struct(c: CurveInput, keep: list) -> CurveStruct:
                        float(c.df), int(c.nb), float(c.qmin), float(c.qmax))
 
 
+class PackedCurves:
+    """Many curves stored back to back in three arrays (t FP64, y and dy FP32: numpy, or
+    torch tensors on the host or a CUDA device; dy may be None), each with a uniform grid.
+    The bls_curve descriptors are written with vectorised numpy from the per-curve point
+    counts, so a search call does no per-curve Python work.  counts, nf, fmin, df, nb, qmin
+    and qmax are per-curve sequences or scalars (0 = the plan's default for nb, qmin, qmax)."""
+
+    def __init__(self, t, y, dy, counts, nf, fmin, df, nb=0, qmin=0.0, qmax=0.0):
+        counts = np.asarray(counts, np.int64)
+        m = len(counts)
+        self.keep = [_host(t, np.float64), _host(y, np.float32), _host(dy, np.float32)]
+        off = np.zeros(m, np.int64)
+        np.cumsum(counts[:-1], out=off[1:])
+        npts = int(counts.sum())
+        for a in self.keep:
+            if a is not None and int(a.shape[0]) < npts:
+                raise ValueError(f"packed array holds {int(a.shape[0])} points, counts sum to {npts}")
+        F = CurveStruct
+        dt = np.dtype({"names": [f for f, _ in F._fields_],
+                       "formats": ["u8", "u8", "u8", "i4", "u8", "i4", "f8", "f8", "i4", "f8", "f8"],
+                       "offsets": [getattr(F, f).offset for f, _ in F._fields_],
+                       "itemsize": C.sizeof(F)})
+        rec = np.zeros(m, dt)
+        for name, a, w in (("t", self.keep[0], 8), ("y", self.keep[1], 4), ("dy", self.keep[2], 4)):
+            rec[name] = 0 if a is None else np.uint64(_ptr(a)) + (off * w).astype(np.uint64)
+        rec["n"] = counts
+        rec["freqs"] = 0
+        rec["nf"] = nf
+        rec["fmin"] = fmin
+        rec["df"] = df
+        rec["nb"] = nb
+        rec["qmin"] = qmin
+        rec["qmax"] = qmax
+        self.rec = rec
+        self.arr = (F * m).from_buffer(rec)
+        self.total_nf = int(np.asarray(rec["nf"], np.int64).sum())
+
+    def __len__(self):
+        return len(self.rec)
+
+
+def _curve_array(curves, keep: list):
+    if isinstance(curves, PackedCurves):
+        return curves.arr
+    return (CurveStruct * len(curves))(*[_struct(c, keep) for c in curves])
+
+
 def _check_spectrum(spectrum, arr) -> None:
     """The spectrum output must hold the sum of the curves' frequency counts (the library
     writes that many floats)."""
     if spectrum is None:
         return
-    need = sum(int(c.nf) for c in arr)
+    need = int(np.asarray(arr.rec["nf"], np.int64).sum()) if isinstance(arr, PackedCurves) \
+        else sum(int(c.nf) for c in arr)
     have = int(spectrum.numel()) if hasattr(spectrum, "numel") else int(np.asarray(spectrum).size)
     if have < need:
         raise ValueError(f"spectrum holds {have} values, the curves have {need} frequencies")
+
+
+def packed_from_batch(batch, device=None, pinned: bool = False) -> PackedCurves:
+    """PackedCurves of a synth.Batch (arrays placed as by curves_from_batch)."""
+    ts = np.concatenate([c.t for c in batch.curves])
+    ys = np.concatenate([c.y for c in batch.curves])
+    dys = np.concatenate([c.dy for c in batch.curves])
+    if device is not None or pinned:
+        import torch
+        conv = (lambda a: torch.from_numpy(a).to(device)) if device is not None else \
+            (lambda a: torch.from_numpy(a).pin_memory())
+        ts, ys, dys = conv(ts), conv(ys), conv(dys)
+    return PackedCurves(ts, ys, dys, [len(c.t) for c in batch.curves],
+                        [g.nf for g in batch.grids], [g.fmin for g in batch.grids],
+                        [g.df for g in batch.grids], list(batch.nb), batch.qmin, batch.qmax)
 
 
 def curves_from_batch(batch, device=None, pinned: bool = False) -> List[CurveInput]:
@@ -329,11 +392,12 @@ class Plan:
     def __exit__(self, *a):
         self.close()
 
-    def search(self, curves: Sequence[CurveInput], spectrum=None) -> np.ndarray:
-        """Peaks of every curve: structured array of shape (ncurves, topk)."""
+    def search(self, curves, spectrum=None) -> np.ndarray:
+        """Peaks of every curve (a sequence of CurveInput, or PackedCurves): structured array
+        of shape (ncurves, topk)."""
         keep: list = []
-        arr = (CurveStruct * len(curves))(*[_struct(c, keep) for c in curves])
-        _check_spectrum(spectrum, arr)
+        arr = _curve_array(curves, keep)
+        _check_spectrum(spectrum, curves if isinstance(curves, PackedCurves) else arr)
         out = np.zeros((len(curves), self.topk), dtype=PEAK_DTYPE)
         _check(lib().bls_search(self._h, arr, len(curves), out.ctypes.data, _ptr(spectrum)))
         return out

@@ -87,3 +87,27 @@ def test_plan_rejects_bad_descriptors_before_touching_cuda(L):
             bls.Plan(**kw)
         assert ei.value.status == bls.ERR_INVALID
         assert bls.lib().bls_last_error()
+
+
+def test_packed_curves_descriptors():
+    """PackedCurves writes the same bls_curve descriptors as one CurveInput per curve
+    (pointers at each curve's offset into the packed arrays)."""
+    import numpy as np
+    from paper_1112_1701_b300 import synth
+    b = synth.config2(ncurves=5, nf=100, seed=4)
+    pc = bls.packed_from_batch(b)
+    t, y, dy = pc.keep
+    keep = []
+    ref = [bls._struct(ci, keep) for ci in bls.curves_from_batch(b)]
+    o = 0
+    for k, c in enumerate(b.curves):
+        a, r = pc.arr[k], ref[k]
+        for f, _ in bls.CurveStruct._fields_:
+            if f not in ("t", "y", "dy"):
+                assert (getattr(a, f) or 0) == (getattr(r, f) or 0), (k, f)
+        assert (a.t, a.y, a.dy) == (t.ctypes.data + 8 * o, y.ctypes.data + 4 * o,
+                                    dy.ctypes.data + 4 * o)
+        o += len(c.t)
+    assert len(pc) == 5 and pc.total_nf == 500
+    with pytest.raises(ValueError):
+        bls.PackedCurves(t[:10], y, dy, [len(c.t) for c in b.curves], 100, 0.1, 0.01)

@@ -323,6 +323,23 @@ def test_device_inputs_match_host_inputs():
         assert np.array_equal(s_h, s_d.cpu().numpy())
 
 
+def test_packed_curves_match_curve_lists():
+    """PackedCurves (descriptors written by numpy) give the same search as CurveInput lists,
+    from host numpy arrays, pinned host tensors and device tensors."""
+    torch = pytest.importorskip("torch")
+    b = synth.config2(ncurves=7, nf=800, seed=13)
+    with _plan(200, b.qmin, b.qmax, topk=2,
+               stream=torch.cuda.current_stream().cuda_stream) as p:
+        s0 = np.zeros(7 * 800, np.float32)
+        pk0 = p.search(bls.curves_from_batch(b), spectrum=s0)
+        for kw in ({}, {"pinned": True}, {"device": "cuda"}):
+            pc = bls.packed_from_batch(b, **kw)
+            s1 = np.zeros(7 * 800, np.float32)
+            pk1 = p.search(pc, spectrum=s1)
+            assert np.array_equal(pk0, pk1), kw
+            assert np.array_equal(s0, s1), kw
+
+
 def test_invalid_inputs_rejected():
     rng = np.random.default_rng(1)
     t = synth.T0 + np.sort(rng.uniform(0, 10, 100))
