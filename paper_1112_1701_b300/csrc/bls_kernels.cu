@@ -1133,8 +1133,11 @@ struct SmemStream {
 // Candidates are compared as exact (num, den) pairs, num * den_best > num_best * den, so a
 // box with bit-identical sums never replaces an earlier one and equal powers resolve to
 // the smallest (i1, k).  The bins come from a sequential stream (start, next, finish).
-template <int SIGN, class Stream>
-__device__ Best sweep_exact_src(Stream& src, int nb, int kmin, int kmax)
+// With PART, only the starts i1 = i1_first, i1_first + i1_step, ... are swept (a share of
+// the starts for one of several threads; their results meet in better_box).
+template <int SIGN, class Stream, bool PART = false>
+__device__ Best sweep_exact_src(Stream& src, int nb, int kmin, int kmax, int i1_first = 0,
+                                int i1_step = 1)
 {
     int first = -1, last = -1, run = 0, gap = 0, gap_end = 0;
     src.start(0);
@@ -1159,7 +1162,7 @@ __device__ Best sweep_exact_src(Stream& src, int nb, int kmin, int kmax)
     }
     Best g;
     g.num = 0.0f; g.den = 1.0f; g.i1 = 0; g.k = kmin;
-    for (int i1 = 0; i1 < nb; ++i1) {
+    for (int i1 = PART ? i1_first : 0; i1 < nb; i1 += PART ? i1_step : 1) {
         float rh = 0.0f, rl = 0.0f, s = 0.0f, cs = 0.0f;
         src.start(i1);
         for (int k = 1; k <= kmax; ++k) {
@@ -1205,6 +1208,39 @@ __device__ __forceinline__ Best sweep_exact_rt(int sign, const unsigned char* hi
 {
     return sign ? sweep_exact<1>(hist, stride, kahan, nb, kmin, kmax)
                 : sweep_exact<0>(hist, stride, kahan, nb, kmin, kmax);
+}
+
+// Whether candidate h beats g under the exact sweep's order: the larger power (compared as
+// num_h den_g > num_g den_h, as the sweep compares), equal cross products to the smaller
+// (i1, k).
+__device__ __forceinline__ bool better_box(const Best& h, const Best& g)
+{
+    const float a = __fmul_rn(h.num, g.den), b = __fmul_rn(g.num, h.den);
+    return a > b || (a == b && (h.i1 < g.i1 || (h.i1 == g.i1 && h.k < g.k)));
+}
+
+// The exact sweep by the 32 lanes of a warp: lane l sweeps the starts l, l + 32, ..., then
+// the lanes' bests meet by shuffles under better_box.  Every lane returns the result.
+template <int SIGN>
+__device__ Best sweep_exact_warp(const unsigned char* hist, int stride, int kahan, int nb,
+                                 int kmin, int kmax, int lane)
+{
+    SmemStream src;
+    src.hist = hist;
+    src.S = (size_t)stride;
+    src.kahan = kahan;
+    src.nb = nb;
+    Best g = sweep_exact_src<SIGN, SmemStream, true>(src, nb, kmin, kmax, lane, 32);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Best h;
+        h.num = __shfl_xor_sync(0xffffffffu, g.num, o);
+        h.den = __shfl_xor_sync(0xffffffffu, g.den, o);
+        h.i1 = __shfl_xor_sync(0xffffffffu, g.i1, o);
+        h.k = __shfl_xor_sync(0xffffffffu, g.k, o);
+        if (better_box(h, g)) g = h;
+    }
+    return g;
 }
 
 // Largest power of one private histogram: fast sweep when its conditions hold, else the
@@ -2086,13 +2122,12 @@ cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, i
 
 // ------------------------------------------------------------------------- best box
 
-// The best box (exact tie-break) of one frequency: bins the curve point by point into a
-// private histogram column with the hot kernel's fold, then runs the exact sweep.  The
-// FP32 bin sums follow point order; where points of one read-modify-write group of the hot
-// kernel share a bin, that kernel adds their pre-summed weights, so such a bin can differ
-// from this one in its last bit.
-__device__ Best best_box_at(const CurveDesc& cd, double f, unsigned char* hist, int stride,
-                            int phase, int kahan, int sign)
+// One frequency's histogram of a curve, binned point by point into a private histogram
+// column with the hot kernel's fold.  The FP32 bin sums follow point order; where points of
+// one read-modify-write group of the hot kernel share a bin, that kernel adds their
+// pre-summed weights, so such a bin can differ from this one in its last bit.
+__device__ void bin_column(const CurveDesc& cd, double f, unsigned char* hist, int stride,
+                           int phase, int kahan)
 {
     const size_t S = (size_t)stride;
     const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax, cd.fxs);
@@ -2114,7 +2149,24 @@ __device__ Best best_box_at(const CurveDesc& cd, double f, unsigned char* hist, 
             H[b1 * S] = add2(H[b1 * S], pk(B.z, B.w));
         }
     }
+}
+
+// The best box (exact tie-break) of one frequency, by one thread.
+__device__ Best best_box_at(const CurveDesc& cd, double f, unsigned char* hist, int stride,
+                            int phase, int kahan, int sign)
+{
+    bin_column(cd, f, hist, stride, phase, kahan);
     return sweep_exact_rt(sign, hist, stride, kahan, cd.nb, cd.kmin, cd.kmax);
+}
+
+// The same by the 32 lanes of a warp: lane 0 bins, the lanes share the exact sweep.
+__device__ Best best_box_warp(const CurveDesc& cd, double f, unsigned char* hist, int stride,
+                              int phase, int kahan, int sign, int lane)
+{
+    if (lane == 0) bin_column(cd, f, hist, stride, phase, kahan);
+    __syncwarp();
+    return sign ? sweep_exact_warp<1>(hist, stride, kahan, cd.nb, cd.kmin, cd.kmax, lane)
+                : sweep_exact_warp<0>(hist, stride, kahan, cd.nb, cd.kmin, cd.kmax, lane);
 }
 
 // Diagnostics: (P, i1, k) of the best box at frequencies j0 .. j0 + count of one curve.
@@ -2234,20 +2286,24 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
         if (sT[0] == (int)threadIdx.x) ++head;
         __syncthreads();
     }
-    // best box of each kept frequency, one thread per frequency, in rounds that fit
+    // best box of each kept frequency, one warp per frequency (lane 0 bins, the lanes share
+    // the exact sweep), in rounds of at most one frequency per warp that fit the histograms
     {
         const int esz = p.kahan ? 16 : 8;
+        const int nwarps = (int)(blockDim.x >> 5);
         int R = (int)(p.smem_bytes / ((size_t)cd.nb * esz));
-        R = R < 1 ? 1 : (R > K ? K : R);
+        R = R < 1 ? 1 : (R > K ? K : (R > nwarps ? nwarps : R));
         for (int q0 = 0; q0 < K; q0 += R) {
-            const int q = q0 + (int)threadIdx.x;
-            if ((int)threadIdx.x < R && q < K) {
+            const int q = q0 + warp;
+            if (warp < R && q < K) {
                 if (sel[q] >= 0) {
-                    const Best g = best_box_at(cd, grid_freq(cd, sel[q]), smem + (size_t)threadIdx.x * esz,
-                                               R, p.phase, p.kahan, p.sign);
-                    sel_i1[q] = g.i1;
-                    sel_k[q] = g.k;
-                } else {
+                    const Best g = best_box_warp(cd, grid_freq(cd, sel[q]), smem + (size_t)warp * esz,
+                                                 R, p.phase, p.kahan, p.sign, lane);
+                    if (lane == 0) {
+                        sel_i1[q] = g.i1;
+                        sel_k[q] = g.k;
+                    }
+                } else if (lane == 0) {
                     sel_i1[q] = 0;
                     sel_k[q] = cd.kmin;
                 }
