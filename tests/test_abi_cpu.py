@@ -111,3 +111,16 @@ def test_packed_curves_descriptors():
     assert len(pc) == 5 and pc.total_nf == 500
     with pytest.raises(ValueError):
         bls.PackedCurves(t[:10], y, dy, [len(c.t) for c in b.curves], 100, 0.1, 0.01)
+
+
+def test_packed_curves_without_errors_and_scalar_grids():
+    """dy = None packs as NULL (unit weights); scalar grid fields apply to every curve."""
+    import numpy as np
+    t = np.linspace(0.0, 10.0, 30)
+    y = np.ones(30, np.float32)
+    pc = bls.PackedCurves(t, y, None, [10, 20], 500, 0.2, 0.001, nb=150, qmin=0.01, qmax=0.1)
+    assert [pc.arr[k].dy for k in range(2)] == [None, None]
+    assert [pc.arr[k].n for k in range(2)] == [10, 20]
+    assert pc.arr[1].t == t.ctypes.data + 8 * 10 and pc.arr[1].y == y.ctypes.data + 4 * 10
+    assert all(pc.arr[k].nf == 500 and pc.arr[k].nb == 150 for k in range(2))
+    assert pc.total_nf == 1000
