@@ -399,6 +399,15 @@ def test_batched_workload_full_size_sampled():
         assert abs(pk[c, 0]["power"] - Pb) <= 1e-9 * Pb
         # no sampled frequency beats the reported peak beyond the tolerance
         assert spec[c].max() == pytest.approx(np.sqrt(pk[c, 0]["power"]), rel=2e-5)
+    # bins of sampled frequencies, bit-exact (the FX64 debug fold also runs the incremental
+    # fold of the bench's 128-frequency tiles and flags any disagreement)
+    with _plan(nb, b.qmin, b.qmax) as p:
+        for c in rng.choice(len(cis), 3, replace=False):
+            ci = cis[c]
+            js = sorted(set(int(j) for j in rng.choice(nf, 24, replace=False)) | {0, 63, 64, nf - 1})
+            bg = p.debug_fold(ci, js)
+            bo = oracle.bins(np.asarray(ci.t), [oracle.freq(j, ci.fmin, ci.df) for j in js], nb)
+            assert np.array_equal(bg, bo), (c, int((bg != bo).sum()))
 
 
 # ------------------------------------------------------------------------------ CUDA graphs
