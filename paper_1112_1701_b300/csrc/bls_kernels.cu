@@ -1490,12 +1490,13 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
 // Variant of the hot kernel in which binning and sweeping overlap.  The block has two warp
 // groups (T a multiple of 32, at most 128):
 //
-//   binning group (T threads, warps 0 .. T/32-1): stages the points, folds and bins tile
-//     i into the private shared-memory histograms (one column per frequency), then hands
-//     them over;
+//   binning group (T threads, warps 0 .. T/32-1): zeroes its warps' histogram columns,
+//     stages the points, folds and bins tile i into the private shared-memory histograms
+//     (one column per frequency), then hands them over;
 //   sweep group (the other warps): copies column c of tile i into its TMEM lane (bins
-//     laid out linearly, the first bins repeated past nb) while zeroing the shared column,
-//     hands the histograms back, then sweeps the boxes of tile i from TMEM while the
+//     laid out linearly, the first bins repeated past nb; the two sweep threads of a
+//     column copy interleaved groups of bins and only read the histograms), hands the
+//     histograms back, then sweeps the boxes of tile i from TMEM while the
 //     binning group already bins tile i + 1.  Its first warp also claims the work items
 //     and writes each tile's descriptor (the curve's CurveDesc and the tile index) into
 //     one of two shared slots ahead of time, so that the binning group's path from one
@@ -1687,8 +1688,8 @@ __device__ void fetch_tile(const FoldParams& p, TileSlot* slot, int lane)
 
 // The sweep group's loop of fold_sweep_ws_kernel: threads sg0 .. sg0 + NS - 1, NS = T x
 // nparts, two parts sharing each column when NS = 2T.  Its first warp claims the work items
-// and writes the tile descriptors ahead; per tile it copies the histograms into TMEM, zeroes
-// them, hands them back and sweeps the boxes from TMEM.
+// and writes the tile descriptors ahead; per tile it copies the histograms into TMEM, hands
+// them back (the binning group zeroes them) and sweeps the boxes from TMEM.
 template <int SIGN>
 __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, int sg0, int NS, int col,
                                                  unsigned s_tmem, TileSlot* s_slot,
@@ -1731,8 +1732,7 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, int sg0, i
         float v = 0.0f, wmax = 0.0f;
         if (use_tmem) {
             // copy bins 0 .. L-1 (bin b >= nb repeats bin b - nb; L <= 2 nb) into the
-            // column's lane, 8 bins per TMEM store (groups dealt to the parts), then zero
-            // the shared column (rows split between the parts)
+            // column's lane, 8 bins per TMEM store (groups dealt to the parts)
             const int L = ((tmode == 1 ? nb + kmax + SB - 1 : nb) + 7) & ~7;
             const unsigned wrapb = (unsigned)nb * rowb;
             for (int g = 8 * part; g < L; g += 8 * nparts) {
@@ -1752,16 +1752,6 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, int sg0, i
                 }
                 tmem_st16(tbase + 2u * (unsigned)g, r);
             }
-            const int zlo = part * nb / nparts, zhi = (part + 1) * nb / nparts;
-            int b = zlo;
-            for (; b + 4 <= zhi; b += 4) {
-                const unsigned a0 = hbase + (unsigned)b * rowb;
-                sts64(a0, 0ull);
-                sts64(a0 + rowb, 0ull);
-                sts64(a0 + 2u * rowb, 0ull);
-                sts64(a0 + 3u * rowb, 0ull);
-            }
-            for (; b < zhi; ++b) sts64(hbase + (unsigned)b * rowb, 0ull);
             if (part == 1) s_wpart[col] = wmax;
             tmem_wait_st();
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1770,8 +1760,9 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, int sg0, i
                 v = SB == 4 ? sweep_max<0, SIGN, 4>(hist, p.stride, nb, kmin, kmax, 0, 1)
                     : SB == 10 ? sweep_max<0, SIGN, 10>(hist, p.stride, nb, kmin, kmax, 0, 1)
                                : sweep_max<0, SIGN, 8>(hist, p.stride, nb, kmin, kmax, 0, 1);
-            for (int b = 0; b < nb; ++b) sts64(hbase + (unsigned)b * rowb, 0ull);
         }
+        // the histograms are only read here: the binning group zeroes them when it starts
+        // the next tile (after this hand-over)
         group_sync(kBarSweep, NS);
         if (tid == sg0) mbar_arrive(empty_bar);
         if (use_tmem) {
@@ -1854,7 +1845,8 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
     const unsigned full_bar = (unsigned)__cvta_generic_to_shared(&s_bar[0]);
     const unsigned empty_bar = (unsigned)__cvta_generic_to_shared(&s_bar[1]);
 
-    {   // every histogram row starts at zero (afterwards the sweep group re-zeroes)
+    {   // every histogram row starts at zero (afterwards each binning warp re-zeroes its
+        // columns at the start of every tile)
         unsigned dyn;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
         const size_t rows = (dyn - (size_t)2 * CH * (sizeof(float4) + sizeof(double))) / rowb;
@@ -1892,6 +1884,16 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             const CurveDesc cdr = sl.cd;
             const int tile = sl.tile;
             const int n = cdr.n, nf = cdr.nf, nb = cdr.nb;
+            {   // zero this warp's 32 histogram columns (16 B per lane, two rows per store);
+                // the sweep group has finished reading them (the empty hand-over above)
+                const unsigned zb = (unsigned)__cvta_generic_to_shared(hist_all) +
+                                    (unsigned)(warp * 32) * 8u + (unsigned)(lane & 15) * 16u;
+                for (int b = lane >> 4; b < nb; b += 2) {
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};"
+                                 ::"r"(zb + (unsigned)b * rowb), "r"(0u));
+                }
+                __syncwarp();
+            }
             const float4* gpts = cdr.pts;
             const double* gdt = cdr.dt64;
             const int j = tile * T + col;
