@@ -332,7 +332,10 @@ bls_status bls_window_efficiency(const bls_window_desc* desc, void* cuda_stream,
  * stars in star order: mu and sd (population) of the kept values, keep |rms - mu| <=
  * clip * sd, at most `iters` rounds, stop when the kept set no longer changes; a star is
  * flagged when its bin has at least min_stars stars and rms > mu + nsig * sd.  All sums
- * in FP64 in the order given, so the results equal the definition's exactly. */
+ * are FP64 in a fixed order (a warp's partial sums and butterfly; the paper gives none),
+ * so results are deterministic and within the FP64 summation bound, (n - 1) 2^-53 sum |v|
+ * per sum, of plain sequential sums; a decision can differ from the sequential order's
+ * only for a value within that bound of its threshold. */
 typedef struct {
     const long long* off;   /* nstars + 1 offsets into m (host or device) */
     const float* m;         /* magnitudes of all light curves, concatenated (host or device) */

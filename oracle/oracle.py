@@ -109,8 +109,8 @@ def _load():
             lib.oracle_shape.argtypes = [I, P, P, P, D, I, I, I, I, I, I, D, D, D,
                                          C.POINTER(_Shape), P]
             lib.oracle_star_stats.argtypes = [I, P, C.POINTER(D), C.POINTER(D)]
-            lib.oracle_clip.argtypes = [I, P, D, I, C.POINTER(D), C.POINTER(D)]
-            lib.oracle_variability.argtypes = [I, P, P, P, I, D, I, D, I, P, P, P, P, P, P]
+            lib.oracle_clip.argtypes = [I, P, D, I, C.POINTER(D), C.POINTER(D), P]
+            lib.oracle_variability.argtypes = [I, P, P, P, I, D, I, D, I, P, P, P, P, P, P, P]
             lib.oracle_fx_shift.argtypes = [D]
             lib.oracle_ubls_keys.argtypes = [I, P, D, D, P]
             lib.oracle_ubls_power.argtypes = [I, P, P, P, D, D, D, D, I, C.POINTER(I), C.POINTER(I),
@@ -322,27 +322,33 @@ def star_stats(m):
     return mag.value, rms.value
 
 
-def clip(vals, clip: float = 3.0, iters: int = 5):
-    """Sigma-clipped (mu, sd, kept) of a set of values (``oracle_clip``)."""
+def clip(vals, clip: float = 3.0, iters: int = 5, with_margin: bool = False):
+    """Sigma-clipped (mu, sd, kept) of a set of values (``oracle_clip``); with_margin adds
+    the smallest distance of any keep-or-drop decision from its threshold."""
     vals = np.ascontiguousarray(vals, dtype=np.float64)
-    mu, sd = C.c_double(), C.c_double()
-    kept = _load().oracle_clip(len(vals), _p(vals), clip, iters, C.byref(mu), C.byref(sd))
+    mu, sd, mg = C.c_double(), C.c_double(), C.c_double()
+    kept = _load().oracle_clip(len(vals), _p(vals), clip, iters, C.byref(mu), C.byref(sd),
+                               C.addressof(mg))
+    if with_margin:
+        return mu.value, sd.value, kept, mg.value
     return mu.value, sd.value, kept
 
 
 def variability(off, m, chip, nchips: int, clip: float = 3.0, iters: int = 5,
                 nsig: float = 2.0, min_stars: int = 5):
     """High-variability flags (``oracle_variability``): dict of per-star arrays mag, rms,
-    bin, mu, sd, flag."""
+    bin, mu, sd, flag, and margin (the clip margin of the star's (chip, bin) group: the
+    smallest distance of any clipping decision from its threshold)."""
     off = np.ascontiguousarray(off, dtype=np.int64)
     m = np.ascontiguousarray(m, dtype=np.float32)
     chip = np.ascontiguousarray(chip, dtype=np.int32)
     n = len(chip)
     out = dict(mag=np.zeros(n), rms=np.zeros(n), bin=np.zeros(n, np.int32), mu=np.zeros(n),
-               sd=np.zeros(n), flag=np.zeros(n, np.uint8))
+               sd=np.zeros(n), flag=np.zeros(n, np.uint8), margin=np.zeros(n))
     rc = _load().oracle_variability(n, _p(off), _p(m), _p(chip), nchips, clip, iters, nsig,
                                     min_stars, _p(out["mag"]), _p(out["rms"]), _p(out["bin"]),
-                                    _p(out["mu"]), _p(out["sd"]), _p(out["flag"]))
+                                    _p(out["mu"]), _p(out["sd"]), _p(out["flag"]),
+                                    _p(out["margin"]))
     if rc != 0:
         raise ValueError("oracle_variability: bad arguments")
     return out

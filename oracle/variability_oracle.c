@@ -22,30 +22,27 @@
  *   last round);  star flagged  <=>  rms_s > mu + nsig * sd  (the paper: nsig = 2), and
  *   never in a bin with fewer than min_stars stars (R: too few to estimate a scatter).
  *
- * Summation order (R: the paper gives none; this one is plain and runs as well on 32 SIMD
- * lanes): every sum of values v_0..v_{k-1} is taken as 32 interleaved partial sums,
- * lane l adding v_l, v_{l+32}, ... in order, then combined pairwise in a butterfly:
- * for o = 16, 8, 4, 2, 1, every lane l adds lane (l xor o)'s value to its own (the two
- * operands in the order own + other).  IEEE FP64 round-to-nearest, no contraction.
+ * Summation order (R: the paper gives none): every sum is the plain one, values added one
+ * at a time in their index order (points in light-curve order, stars in catalog order),
+ * IEEE FP64 round-to-nearest, no contraction.  Another order (a GPU's tree of partial
+ * sums) gives sums that differ from these by at most the FP64 summation bound
+ * (n - 1) 2^-53 sum |v|, which is what parity with them is measured against.
+ *
+ * Diagnostic output (for tests only): the clip margin of a (chip, bin) group, the
+ * smallest | |rms - mu| - clip sd | over every keep-or-drop decision of every clipping
+ * round.  A decision whose margin is below the rounding error of its operands may go
+ * either way in another summation order.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
-/* Sum in the order stated above: 32 interleaved partial sums, then the butterfly. */
-static double sum32(int k, const double* v)
+/* Plain sum of v[0..k) in index order. */
+static double sum_seq(int k, const double* v)
 {
-    double lane[32];
-    for (int l = 0; l < 32; ++l) {
-        lane[l] = 0.0;
-        for (int i = l; i < k; i += 32) lane[l] += v[i];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        double nxt[32];
-        for (int l = 0; l < 32; ++l) nxt[l] = lane[l] + lane[l ^ o];
-        for (int l = 0; l < 32; ++l) lane[l] = nxt[l];
-    }
-    return lane[0];
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s += v[i];
+    return s;
 }
 
 /* mean and population RMS of one light curve (two passes) */
@@ -53,39 +50,47 @@ void oracle_star_stats(int n, const float* m, double* mag, double* rms)
 {
     double* v = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
     for (int i = 0; i < n; ++i) v[i] = (double)m[i];
-    double mu = sum32(n, v) / (double)n;
+    double mu = sum_seq(n, v) / (double)n;
     for (int i = 0; i < n; ++i) {
         double d = (double)m[i] - mu;
         v[i] = d * d;
     }
     *mag = mu;
-    *rms = sqrt(sum32(n, v) / (double)n);
+    *rms = sqrt(sum_seq(n, v) / (double)n);
     free(v);
 }
 
-/* sigma-clipped (mu, sd) of vals[0..k); returns the number kept */
-int oracle_clip(int k, const double* vals, double clip, int iters, double* mu_out, double* sd_out)
+/*
+ * Sigma-clipped (mu, sd) of vals[0..k); returns the number kept.  Each round takes the mean
+ * and the population sd of the values kept so far (plain sums over them, in index order),
+ * then keeps exactly the values with |v - mu| <= clip sd; it stops after `iters` rounds or
+ * when the kept set no longer changes, and (mu, sd) are those of the final kept set.
+ * margin (optional): the smallest | |v - mu| - clip sd | over every decision taken.
+ */
+int oracle_clip(int k, const double* vals, double clip, int iters, double* mu_out, double* sd_out,
+                double* margin)
 {
     char* keep = (char*)malloc((size_t)(k > 0 ? k : 1));
     double* t = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
     for (int i = 0; i < k; ++i) keep[i] = 1;
-    double mu = 0.0, sd = 0.0;
+    double mu = 0.0, sd = 0.0, mg = INFINITY;
     int kept = k;
     for (int it = 0; it <= iters; ++it) {
-        /* sums over the kept values, the dropped ones counting as zero in their places */
         int c = 0;
-        for (int i = 0; i < k; ++i) { t[i] = keep[i] ? vals[i] : 0.0; c += keep[i]; }
-        mu = c > 0 ? sum32(k, t) / (double)c : 0.0;
-        for (int i = 0; i < k; ++i) {
-            double d = vals[i] - mu;
-            t[i] = keep[i] ? d * d : 0.0;
-        }
-        sd = c > 0 ? sqrt(sum32(k, t) / (double)c) : 0.0;
+        for (int i = 0; i < k; ++i) if (keep[i]) t[c++] = vals[i];
+        mu = c > 0 ? sum_seq(c, t) / (double)c : 0.0;
+        c = 0;
+        for (int i = 0; i < k; ++i)
+            if (keep[i]) { double d = vals[i] - mu; t[c++] = d * d; }
+        sd = c > 0 ? sqrt(sum_seq(c, t) / (double)c) : 0.0;
         kept = c;
         if (it == iters) break;
         int changed = 0;
         for (int i = 0; i < k; ++i) {
-            char nk = fabs(vals[i] - mu) <= clip * sd;
+            double a = fabs(vals[i] - mu), lim = clip * sd;
+            double gap = fabs(a - lim);
+            if (gap < mg) mg = gap;
+            char nk = a <= lim;
             if (nk != keep[i]) { keep[i] = nk; changed = 1; }
         }
         if (!changed) break;
@@ -94,18 +99,20 @@ int oracle_clip(int k, const double* vals, double clip, int iters, double* mu_ou
     free(t);
     *mu_out = mu;
     *sd_out = sd;
+    if (margin) *margin = mg;
     return kept;
 }
 
 /*
  * Flags for nstars stars: light curve s is m[off[s] .. off[s+1]) (magnitudes), chip[s]
  * its chip (0 .. nchips-1).  Outputs per star (any may be NULL except flag): mag, rms,
- * bin, the bin's mu and sd, flag (0/1).  Returns 0, or -1 on bad arguments.
+ * bin, the bin's mu and sd, flag (0/1), and the clip margin of the star's group.
+ * Returns 0, or -1 on bad arguments.
  */
 int oracle_variability(int nstars, const long long* off, const float* m, const int* chip,
                        int nchips, double clip, int iters, double nsig, int min_stars,
                        double* mag, double* rms, int* bin, double* mu, double* sd,
-                       unsigned char* flag)
+                       unsigned char* flag, double* margin)
 {
     if (nstars < 0 || nchips < 1 || !(clip > 0.0) || iters < 0 || !(nsig >= 0.0) || min_stars < 1)
         return -1;
@@ -127,8 +134,8 @@ int oracle_variability(int nstars, const long long* off, const float* m, const i
         int k = 0;
         for (int u = s; u < nstars; ++u)
             if (!done[u] && chip[u] == chip[s] && bn[u] == bn[s]) { members[k] = u; vals[k] = rm[u]; k++; }
-        double bmu, bsd;
-        oracle_clip(k, vals, clip, iters, &bmu, &bsd);
+        double bmu, bsd, bmg;
+        oracle_clip(k, vals, clip, iters, &bmu, &bsd, &bmg);
         for (int q = 0; q < k; ++q) {
             int u = members[q];
             done[u] = 1;
@@ -137,6 +144,7 @@ int oracle_variability(int nstars, const long long* off, const float* m, const i
             if (bin) bin[u] = bn[u];
             if (mu) mu[u] = bmu;
             if (sd) sd[u] = bsd;
+            if (margin) margin[u] = bmg;
             flag[u] = (unsigned char)(k >= min_stars && rm[u] > bmu + nsig * bsd);
         }
     }

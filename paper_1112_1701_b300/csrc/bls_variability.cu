@@ -8,12 +8,14 @@
 // (mu, sd of the kept; keep |rms - mu| <= clip * sd; at most `iters` rounds, stop when the
 // kept set no longer changes); flag = (bin has >= min_stars stars) && rms > mu + nsig * sd.
 //
-// Every floating-point decision here (bins, kept sets, flags) must come out as in the
-// definition, so every sum is taken in FP64 in the definition's order: 32 interleaved
-// partial sums (lane l adds elements l, l+32, ... in order) combined by an xor butterfly
-// over offsets 16, 8, 4, 2, 1 -- exactly what one warp computes with coalesced loads and
-// shuffles.  One warp per star takes the two passes over its light curve; one warp per
-// (chip, bin) runs the clipping over the bin's stars in star order (dropped stars add
+// Every sum is taken in FP64 (the paper gives no summation order): 32 interleaved partial
+// sums (lane l adds elements l, l+32, ... in order) combined by an xor butterfly over
+// offsets 16, 8, 4, 2, 1 -- what one warp computes with coalesced loads and shuffles.  Any
+// order is within the FP64 summation bound (n - 1) 2^-53 sum |v| of the plain sequential
+// sum, so a decision (bin, kept set, flag) can differ from the sequential order's only for
+// a value within that bound of its threshold.  The order is fixed, so results are
+// deterministic.  One warp per star takes the two passes over its light curve; one warp
+// per (chip, bin) runs the clipping over the bin's stars in star order (dropped stars add
 // zero in their places).  Around them, the grouping: a chip's stars are compacted in star
 // order (warp ballots), counted per bin and laid out bin by bin, still in star order.
 //
@@ -30,7 +32,7 @@ namespace {
 constexpr int kVarThreads = 256;
 constexpr int kMaxBinsPerChip = 4096;   // 409.6 mag of range within one chip
 
-// FP64 sum of one value per lane in the definition's order: the xor butterfly.
+// FP64 sum of one value per lane, in a fixed order: the xor butterfly.
 __device__ __forceinline__ double butterfly(double v)
 {
     for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(kVarThreads) chip_kernel(ChipParams p)
     if (staged)
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) srms[i] = p.rms[srt[i]];
     __syncthreads();
-    // (e) sigma clipping, one warp per bin, sums in the definition's order; (f) flags
+    // (e) sigma clipping, one warp per bin, sums in the warp's fixed order; (f) flags
     for (int b = warp; b < nbins; b += nw) {
         const int a = bcount[b], k = bcount[b + 1] - a;
         if (k == 0) continue;

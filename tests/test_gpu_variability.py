@@ -1,7 +1,21 @@
 """High-variability pre-filter: CUDA path vs the FP64 oracle (marked gpu).
 
-Every statistic is summed in FP64 in the definition's order on both sides, so the
-per-star magnitudes, RMS values, bins, bin expectations and flags must be identical."""
+The oracle sums in plain index order; the GPU sums the same FP64 values as a tree of
+partial sums (warp lanes, then a butterfly).  Neither order is the paper's (it gives none),
+so the two are compared within the FP64 summation bound, derived term by term:
+
+  u = 2^-53; a star of n points with largest |m| = M and RMS rho:
+    |d mag| <= 2 (n + 1) u M                         (each side: an n-term sum, one divide)
+    |d rms| <= 2 [(n + 1) u M + (n + 4) u rho]       (each side: the mean's error e enters
+                                                      as sqrt(rho^2 + e^2); the squares'
+                                                      sum, divide and square root)
+  a (chip, bin) group of k stars whose RMS values differ by at most e_r:
+    |d mu|, |d sd| <= 4 e_r + 4 (k + 4) u max rms     (the same argument on k values)
+and every bound is taken twice over.  A decision taken on these values -- a star's bin
+floor(10 mag), a clipping decision, a flag rms > mu + nsig sd -- must agree unless the
+oracle's value lies within that bound of the threshold; such near-threshold stars (and
+groups whose clipping had a near-threshold decision, from the oracle's clip margin) are
+counted and reported, and they must be rare."""
 import numpy as np
 import pytest
 
@@ -9,6 +23,7 @@ import oracle
 from paper_1112_1701_b300 import bls, build, synth
 
 pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -17,17 +32,53 @@ def _lib():
     bls.lib()
 
 
-def _compare(off, m, chip, nchips, **kw):
+def _compare(off, m, chip, nchips, clip=3.0, iters=5, nsig=2.0, min_stars=5):
+    kw = dict(clip=clip, iters=iters, nsig=nsig, min_stars=min_stars)
     g = bls.variability(off, m, chip, nchips, **kw)
     o = oracle.variability(off, m, chip, nchips, **kw)
-    for f in ("mag", "rms", "bin", "mu", "sd", "flag"):
-        assert np.array_equal(g[f], o[f]), f
-    return g
+    ns = len(chip)
+    n = np.diff(off).astype(np.float64)
+    M = np.array([np.abs(m[off[s]:off[s + 1]]).max() for s in range(ns)], np.float64)
+    tol_mag = 2 * 2 * (n + 1) * U * M
+    tol_rms = 2 * 2 * ((n + 1) * U * M + (n + 4) * U * o["rms"])
+    assert np.all(np.abs(g["mag"] - o["mag"]) <= tol_mag), "mag"
+    assert np.all(np.abs(g["rms"] - o["rms"]) <= tol_rms), "rms"
+    # bins: floor(10 mag) -- equal unless 10 mag is within the bound of an integer
+    x = o["mag"] * 10.0
+    near_bin = np.abs(x - np.round(x)) <= 10 * tol_mag + 4 * U * np.abs(x)
+    assert np.array_equal(g["bin"][~near_bin], o["bin"][~near_bin]), "bin"
+    stats = {"stars": ns, "near_bin": int(near_bin.sum()), "near_clip_groups": 0,
+             "near_flag": 0}
+    # groups of the oracle (chip, bin); skipped where a member's bin is near an edge
+    key = chip.astype(np.int64) * (1 << 32) + o["bin"].astype(np.int64)
+    for kv in np.unique(key):
+        idx = np.nonzero(key == kv)[0]
+        if near_bin[idx].any():
+            continue
+        k = len(idx)
+        e_r = tol_rms[idx].max()
+        tol_g = 2 * (4 * e_r + 4 * (k + 4) * U * o["rms"][idx].max())
+        # (a one-star group is exact on both sides: mu = its rms, sd = 0)
+        if k > 1 and o["margin"][idx[0]] <= (2 + clip) * tol_g:
+            stats["near_clip_groups"] += 1   # a clipping decision near its threshold
+            continue
+        assert np.all(np.abs(g["mu"][idx] - o["mu"][idx]) <= tol_g), "mu"
+        assert np.all(np.abs(g["sd"][idx] - o["sd"][idx]) <= tol_g), "sd"
+        thr = o["mu"][idx] + nsig * o["sd"][idx]
+        near = np.abs(o["rms"][idx] - thr) <= tol_rms[idx] + (1 + nsig) * tol_g
+        near &= k > 1          # one star: rms > rms + 0 is false on both sides
+        stats["near_flag"] += int(near.sum())
+        assert np.array_equal(g["flag"][idx][~near], o["flag"][idx][~near]), "flag"
+    # the bound is tiny (~1e-12 of the values); a near-threshold case is a rare event
+    assert (stats["near_bin"] + stats["near_flag"] + stats["near_clip_groups"]
+            <= max(1, ns // 1000)), stats
+    return g, stats
 
 
 def test_survey_field_catalog():
     c = synth.chip_catalog(nchips=11, stars_per_chip=1200, npts=400, seed=31)
-    g = _compare(c.off, c.m, c.chip, c.nchips)
+    g, st = _compare(c.off, c.m, c.chip, c.nchips)
+    print("variability parity:", st)
     f = g["flag"].astype(bool)
     assert f[c.variable].mean() > 0.85
 
@@ -64,7 +115,7 @@ def test_device_inputs_and_outputs():
 def test_single_star_chip_and_invalid():
     off = np.array([0, 5, 9], np.int64)
     m = np.array([15.0, 15.1, 15.0, 15.1, 15.0, 17.0, 17.0, 17.2, 17.2], np.float32)
-    g = _compare(off, m, np.array([0, 1], np.int32), 2, min_stars=1)
+    g, _ = _compare(off, m, np.array([0, 1], np.int32), 2, min_stars=1)
     assert g["flag"].sum() == 0          # one star per bin: sd 0, not above itself
     with pytest.raises(bls.BLSError):
         bls.variability(off, m, np.array([0, 2], np.int32), 2)       # chip out of range

@@ -19,6 +19,49 @@ def test_star_stats_closed_forms():
     assert mag == 18.125 and rms == 0.0
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_star_stats_against_exact_rationals(seed):
+    """Mean magnitude and population RMS against exact rational arithmetic on the FP32
+    magnitudes: each within the FP64 bound of a plain n-term sum (n 2^-53 of the sum of
+    magnitudes, plus the roundings of the division and the square root).  A sample sd
+    (n - 1), a dropped square or a shifted mean would miss by far more."""
+    from fractions import Fraction
+    rng = np.random.default_rng(40 + seed)
+    n = int(rng.integers(5, 400))
+    m = (rng.uniform(14, 20) + rng.normal(0, 10 ** rng.uniform(-3, -1), n)).astype(np.float32)
+    mag, rms = oracle.star_stats(m)
+    q = [Fraction(float(v)) for v in m]
+    mean = sum(q) / n
+    var = sum((v - mean) ** 2 for v in q) / n
+    u = 2.0 ** -53
+    M = float(np.max(np.abs(m)))
+    assert abs(Fraction(mag) - mean) <= (n + 1) * u * M
+    exact_rms = float(var) ** 0.5
+    assert abs(rms - exact_rms) <= (n + 1) * u * M + (n + 4) * u * exact_rms
+
+
+def test_clip_margin_is_the_closest_decision():
+    """The clip margin is the smallest | |v - mu| - clip sd | over the decisions of every
+    round, recomputed here round by round in plain Python."""
+    rng = np.random.default_rng(9)
+    v = np.concatenate([rng.normal(0.02, 0.003, 60), [0.05, 0.2]])
+    keep = np.ones(len(v), bool)
+    best = np.inf
+    for _ in range(5):
+        kv = v[keep]
+        mu = sum(kv.tolist()) / len(kv)
+        sd = (sum(((x - mu) ** 2 for x in kv.tolist())) / len(kv)) ** 0.5
+        gap = np.abs(np.abs(v - mu) - 3.0 * sd)
+        best = min(best, float(gap.min()))
+        nk = np.abs(v - mu) <= 3.0 * sd
+        if np.array_equal(nk, keep):
+            break
+        keep = nk
+    mu, sd, kept, mg = oracle.clip(v, 3.0, 5, with_margin=True)
+    assert kept == int(keep.sum())
+    assert mg == pytest.approx(best, rel=1e-9, abs=1e-15)
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_clip_equals_scipy_sigmaclip(seed):
     """With enough rounds to converge, the clipping is SciPy's sigmaclip (3 sigma both
