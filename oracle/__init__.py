@@ -8,5 +8,5 @@ import this package. It shares no code with the CUDA library and never imports i
 from .oracle import (  # noqa: F401
     OraclePeak, build, kminmax, freq, fold, prep, bins, power, box, bls, bls_many, lib_path,
     window, window_count, OracleShape, shape, shape_point, star_stats, clip, variability,
-    UnbinnedPeak, fx_shift, ubls_keys, ubls_power, ubls,
+    UnbinnedPeak, ubls_phases, ubls_order, ubls_extent, ubls_power, ubls,
 )

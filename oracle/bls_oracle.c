@@ -278,6 +278,21 @@ static double grid_freq(const oracle_curve* c, int j)
     return c->freqs ? c->freqs[j] : oracle_freq(j, c->fmin, c->df);
 }
 
+/* Mean and population sd of SR = sqrt(P) over a spectrum (plain sums in frequency order),
+ * the statistics of the signal detection efficiency. */
+static void sr_stats(int nf, const double* P, double* mean_out, double* sd_out)
+{
+    double mean = 0.0, var = 0.0;
+    for (int j = 0; j < nf; j++) mean += sqrt(P[j]);
+    mean /= (double)nf;
+    for (int j = 0; j < nf; j++) {
+        double d = sqrt(P[j]) - mean;
+        var += d * d;
+    }
+    *mean_out = mean;
+    *sd_out = sqrt(var / (double)nf);
+}
+
 /* Full periodogram of one curve.  P, i1, k (length nf, each may be NULL) receive the
  * per-frequency best box; peaks (length topk) the ranked peaks. */
 int oracle_bls(const oracle_curve* c, int sign, double* P, int* i1, int* k,
@@ -304,14 +319,8 @@ int oracle_bls(const oracle_curve* c, int sign, double* P, int* i1, int* k,
         /* signal detection efficiency (Kovacs, Zucker & Mazeh 2002, the BLS paper cited in
          * Sec. 2.2.2): SDE = (SR_peak - <SR>) / sd(SR) over the curve's whole spectrum,
          * sd the population standard deviation; 0 for a flat spectrum */
-        double mean = 0.0, var = 0.0;
-        for (int j = 0; j < nf; j++) mean += sqrt(Pl[j]);
-        mean /= (double)nf;
-        for (int j = 0; j < nf; j++) {
-            double d = sqrt(Pl[j]) - mean;
-            var += d * d;
-        }
-        double sd = sqrt(var / (double)nf);
+        double mean, sd;
+        sr_stats(nf, Pl, &mean, &sd);
         int js[64];
         int kk = topk > 64 ? 64 : topk;
         top_peaks(nf, Pl, kk, js);
@@ -422,6 +431,8 @@ int oracle_bls_many(int nc, const oracle_curve* cv, int sign, int nthreads,
             const oracle_curve* q = &cv[c];
             double* H = (double*)malloc(sizeof(double) * 2 * (size_t)q->nb);
             int* Hn = (int*)malloc(sizeof(int) * (size_t)q->nb);
+            double mean, sd;
+            sr_stats(q->nf, m.Pc[c], &mean, &sd);
             top_peaks(q->nf, m.Pc[c], kk, js);
             for (int e = 0; e < kk; e++) {
                 oracle_peak* pk = &peaks[(size_t)c * topk + e];
@@ -432,6 +443,7 @@ int oracle_bls_many(int nc, const oracle_curve* cv, int sign, int nthreads,
                 box_sums(q->nb, H, H + q->nb, m.I1c[c][j], m.Kc[c][j], &r, &s);
                 derive(pk, j, f, q->nb, m.I1c[c][j], m.Kc[c][j], m.Pc[c][j], r, s,
                        m.pp[c].scal[0], m.pp[c].scal[1]);
+                pk->sde = sd > 0.0 ? (pk->sr - mean) / sd : 0.0;
             }
             free(H);
             free(Hn);

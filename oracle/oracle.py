@@ -111,9 +111,11 @@ def _load():
             lib.oracle_star_stats.argtypes = [I, P, C.POINTER(D), C.POINTER(D)]
             lib.oracle_clip.argtypes = [I, P, D, I, C.POINTER(D), C.POINTER(D), P]
             lib.oracle_variability.argtypes = [I, P, P, P, I, D, I, D, I, P, P, P, P, P, P, P]
-            lib.oracle_fx_shift.argtypes = [D]
-            lib.oracle_ubls_keys.argtypes = [I, P, D, D, P]
-            lib.oracle_ubls_power.argtypes = [I, P, P, P, D, D, D, D, I, C.POINTER(I), C.POINTER(I),
+            lib.oracle_ubls_phases.argtypes = [I, P, D, P]
+            lib.oracle_ubls_order.argtypes = [I, P, P]
+            lib.oracle_ubls_extent.argtypes = [I, P, P, I, I]
+            lib.oracle_ubls_extent.restype = D
+            lib.oracle_ubls_power.argtypes = [I, P, P, P, D, D, D, I, C.POINTER(I), C.POINTER(I),
                                               C.POINTER(D), C.POINTER(D), P]
             lib.oracle_ubls_power.restype = D
             lib.oracle_ubls.argtypes = [I, P, P, P, I, P, D, D, D, D, I, P, C.POINTER(_UPeak)]
@@ -369,25 +371,36 @@ class UnbinnedPeak:
     snr: float
 
 
-def fx_shift(dtmax: float) -> int:
-    return _load().oracle_fx_shift(float(dtmax))
-
-
-def ubls_keys(dt, dtmax: float, f: float) -> np.ndarray:
-    """32-bit fixed-point phase keys of every point (``oracle_ubls_keys``)."""
+def ubls_phases(dt, f: float) -> np.ndarray:
+    """FP64 phases frac(RN(dt f)) of every point (``oracle_ubls_phases``)."""
     dt = np.ascontiguousarray(dt, dtype=np.float64)
-    key = np.zeros(len(dt), np.uint32)
-    _load().oracle_ubls_keys(len(dt), _p(dt), dtmax, f, _p(key))
-    return key
+    phi = np.zeros(len(dt))
+    _load().oracle_ubls_phases(len(dt), _p(dt), f, _p(phi))
+    return phi
 
 
-def ubls_power(dt, w, x, dtmax: float, f: float, qmin: float, qmax: float, sign: int = 0):
+def ubls_order(phi) -> np.ndarray:
+    """Points in (phase, index) order (``oracle_ubls_order``)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    ord_ = np.zeros(len(phi), np.int32)
+    _load().oracle_ubls_order(len(phi), _p(phi), _p(ord_))
+    return ord_
+
+
+def ubls_extent(phi, order, first: int, length: int) -> float:
+    """Phase extent of a run of the phase order (``oracle_ubls_extent``)."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    return _load().oracle_ubls_extent(len(phi), _p(phi), _p(order), first, length)
+
+
+def ubls_power(dt, w, x, f: float, qmin: float, qmax: float, sign: int = 0):
     """Best unbinned box of one frequency: (P, first, len, r, s, order)."""
     dt, w, x = (np.ascontiguousarray(a, dtype=np.float64) for a in (dt, w, x))
     a, l = C.c_int(), C.c_int()
     r, s = C.c_double(), C.c_double()
     order = np.zeros(len(dt), np.int32)
-    P = _load().oracle_ubls_power(len(dt), _p(dt), _p(w), _p(x), dtmax, f, qmin, qmax, sign,
+    P = _load().oracle_ubls_power(len(dt), _p(dt), _p(w), _p(x), f, qmin, qmax, sign,
                                   C.byref(a), C.byref(l), C.byref(r), C.byref(s), _p(order))
     return P, a.value, l.value, r.value, s.value, order
 

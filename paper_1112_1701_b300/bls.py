@@ -172,12 +172,28 @@ def _ptr(a):
     return a.ctypes.data
 
 
-def _host(a, dtype):
+_TORCH_DTYPE = {np.dtype(np.float64): "torch.float64", np.dtype(np.float32): "torch.float32",
+                np.dtype(np.int64): "torch.int64", np.dtype(np.int32): "torch.int32"}
+
+
+def _host(a, dtype, name="array"):
+    """numpy arrays are converted (a contiguous copy of the stated dtype when needed);
+    torch tensors are passed by address, so they must already have that dtype and be
+    contiguous -- the library reads them as plain arrays of it."""
     if a is None:
         return None
     if hasattr(a, "data_ptr"):
+        want = _TORCH_DTYPE[np.dtype(dtype)]
+        if str(a.dtype) != want:
+            raise BLSError(ERR_INVALID, f"{name}: tensor of {a.dtype}, expected {want}")
+        if not a.is_contiguous():
+            raise BLSError(ERR_INVALID, f"{name}: tensor is not contiguous")
         return a
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _len(a) -> int:
+    return int(a.numel()) if hasattr(a, "numel") else int(a.size)
 
 
 @dataclass
@@ -196,13 +212,16 @@ class CurveInput:
 
 
 def _struct(c: CurveInput, keep: list) -> CurveStruct:
-    t = _host(c.t, np.float64)
-    y = _host(c.y, np.float32)
-    dy = _host(c.dy, np.float32)
-    fr = _host(c.freqs, np.float64)
+    t = _host(c.t, np.float64, "t")
+    y = _host(c.y, np.float32, "y")
+    dy = _host(c.dy, np.float32, "dy")
+    fr = _host(c.freqs, np.float64, "freqs")
     keep += [t, y, dy, fr]
-    n = int(t.shape[0])
-    nf = int(fr.shape[0]) if fr is not None else int(c.nf)
+    n = _len(t)
+    for name, a in (("y", y), ("dy", dy)):
+        if a is not None and _len(a) != n:
+            raise BLSError(ERR_INVALID, f"{name} holds {_len(a)} values, t holds {n}")
+    nf = _len(fr) if fr is not None else int(c.nf)
     return CurveStruct(_ptr(t), _ptr(y), _ptr(dy), n, _ptr(fr), nf, float(c.fmin),
                        float(c.df), int(c.nb), float(c.qmin), float(c.qmax))
 
@@ -217,13 +236,14 @@ class PackedCurves:
     def __init__(self, t, y, dy, counts, nf, fmin, df, nb=0, qmin=0.0, qmax=0.0):
         counts = np.asarray(counts, np.int64)
         m = len(counts)
-        self.keep = [_host(t, np.float64), _host(y, np.float32), _host(dy, np.float32)]
+        self.keep = [_host(t, np.float64, "t"), _host(y, np.float32, "y"),
+                     _host(dy, np.float32, "dy")]
         off = np.zeros(m, np.int64)
         np.cumsum(counts[:-1], out=off[1:])
         npts = int(counts.sum())
         for a in self.keep:
-            if a is not None and int(a.shape[0]) < npts:
-                raise ValueError(f"packed array holds {int(a.shape[0])} points, counts sum to {npts}")
+            if a is not None and _len(a) < npts:
+                raise ValueError(f"packed array holds {_len(a)} points, counts sum to {npts}")
         F = CurveStruct
         dt = np.dtype({"names": [f for f, _ in F._fields_],
                        "formats": ["u8", "u8", "u8", "i4", "u8", "i4", "f8", "f8", "i4", "f8", "f8"],
@@ -349,6 +369,20 @@ def search_static(curve: CurveInput, topk: int = 1, sign: str = "dips", stream=N
     the peak records (read them back with ``peaks_to_numpy``)."""
     keep: list = []
     cs = _struct(curve, keep)
+    # the library cannot see the size of a device buffer: check the outputs here
+    if peaks is None or not hasattr(peaks, "element_size"):
+        raise BLSError(ERR_INVALID, "peaks must be a CUDA tensor")
+    need = int(topk) * PEAK_DTYPE.itemsize
+    if _len(peaks) * peaks.element_size() < need or not peaks.is_contiguous():
+        raise BLSError(ERR_INVALID, f"peaks holds {_len(peaks) * peaks.element_size()} bytes, "
+                                    f"topk = {int(topk)} records need {need}")
+    if spectrum is not None:
+        if not hasattr(spectrum, "element_size") or str(spectrum.dtype) != "torch.float32" \
+                or not spectrum.is_contiguous():
+            raise BLSError(ERR_INVALID, "spectrum must be a contiguous float32 CUDA tensor")
+        if _len(spectrum) < cs.nf:
+            raise BLSError(ERR_INVALID, f"spectrum holds {_len(spectrum)} values, the curve "
+                                        f"has {cs.nf} frequencies")
     _check(lib().bls_search_static(C.byref(cs), int(topk), SIGN[sign], stream, _ptr(peaks),
                                    _ptr(spectrum)))
 

@@ -258,16 +258,6 @@ size_t curve_bytes(const bls_plan_impl* P, const CurveSpec& c, bool host_spec)
 }
 
 
-// Run extents of the unbinned search in units of 2^-32 cycle: QMIN = ceil(qmin 2^32),
-// QMAX = floor(qmax 2^32), capped at 2^32 - 1.
-void ubls_extents(double qmin, double qmax, unsigned* QMIN, unsigned* QMAX)
-{
-    const double two32 = 4294967296.0;
-    const double lo = ceil(qmin * two32), hi = floor(qmax * two32);
-    *QMIN = lo >= two32 ? 0xffffffffu : (unsigned)lo;
-    *QMAX = hi >= two32 ? 0xffffffffu : (unsigned)hi;
-}
-
 // One launch group: curves [g0, g1) of `specs`.  Writes peaks to out (host), optionally the
 // SR spectra, and (diagnostics) the per-frequency powers into res_dump.
 //
@@ -444,7 +434,8 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         up.spectrum = spectrum ? (spectrum_dev ? spectrum : P->spec.as<float>()) : nullptr;
         up.topk = topk;
         up.sign = P->d.sign;
-        ubls_extents(P->d.qmin, P->d.qmax, &up.QMIN, &up.QMAX);
+        up.qmin = P->d.qmin;
+        up.qmax = P->d.qmax;
         up.nmax = nmax;
         up.M = 1;
         while (up.M < nmax) up.M <<= 1;

@@ -98,7 +98,7 @@ struct UblsParams {
     DevPeak* peaks;                 // topk per curve
     float* spectrum;                // optional (device): SR per frequency, at spec_off
     int topk, sign;
-    unsigned QMIN, QMAX;            // run extents in units of 2^-32 cycle
+    double qmin, qmax;              // run extent bounds, in cycles
     int nmax, M;                    // largest curve of the group and the power of two >= it
 };
 

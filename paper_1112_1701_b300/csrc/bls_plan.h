@@ -102,7 +102,6 @@ struct bls_plan_impl {
 bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* out,
                          const int* kinds = nullptr, bool scan_values = true);
 int ptr_kind(const void* p);
-void ubls_extents(double qmin, double qmax, unsigned* QMIN, unsigned* QMAX);
 constexpr int kUblsMaxPoints = 8192;   // the unbinned search sorts a curve in shared memory
 
 // A validated trapezoid-refit request of bls_search_shapes.

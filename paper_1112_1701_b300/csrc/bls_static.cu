@@ -11,6 +11,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cstddef>
+
 #include "bls_plan.h"
 
 namespace blsgpu {
@@ -166,7 +168,23 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
     ReduceParams rp;
     rp.curves = cdesc;
     rp.slots = nullptr;
-    rp.peaks = reinterpret_cast<DevPeak*>(peaks_dev);   // same layout as bls_peak
+    // the reduce kernel writes the caller's bls_peak records directly
+    static_assert(sizeof(DevPeak) == sizeof(bls_peak), "DevPeak mirrors bls_peak");
+    static_assert(offsetof(DevPeak, j) == offsetof(bls_peak, best_j) &&
+                  offsetof(DevPeak, i1) == offsetof(bls_peak, i1) &&
+                  offsetof(DevPeak, k) == offsetof(bls_peak, k) &&
+                  offsetof(DevPeak, pad) == offsetof(bls_peak, pad_) &&
+                  offsetof(DevPeak, freq) == offsetof(bls_peak, freq) &&
+                  offsetof(DevPeak, period) == offsetof(bls_peak, period) &&
+                  offsetof(DevPeak, epoch) == offsetof(bls_peak, epoch) &&
+                  offsetof(DevPeak, duration) == offsetof(bls_peak, duration) &&
+                  offsetof(DevPeak, depth) == offsetof(bls_peak, depth) &&
+                  offsetof(DevPeak, snr) == offsetof(bls_peak, snr) &&
+                  offsetof(DevPeak, sr) == offsetof(bls_peak, sr) &&
+                  offsetof(DevPeak, power) == offsetof(bls_peak, power) &&
+                  offsetof(DevPeak, sde) == offsetof(bls_peak, sde),
+                  "DevPeak fields sit where bls_peak's do");
+    rp.peaks = reinterpret_cast<DevPeak*>(peaks_dev);
     rp.spectrum = spectrum_dev;
     rp.topk = topk;
     rp.sign = sign;

@@ -3,28 +3,35 @@
 // At every trial frequency the points are ordered by phase and every cyclic run of
 // consecutive points whose phase extent lies in [qmin, qmax] is a box, scored with the
 // binned search's statistic (r = sum w, s = sum w x over the run, P = s^2/(r(1-r)), dips
-// only by default).  Phases are 64-bit fixed-point fractions: with DT = RN_int(dt 2^s)
-// (written by the prep kernel in the fixed-point layout) and F = RN_int(f 2^(64-s)), a
-// point's key is the high word of (DT F) mod 2^64, three integer multiply-adds.  The order
-// is (key, point index); a run's extent is (key_last - key_first) mod 2^32, compared with
-// QMIN = ceil(qmin 2^32) and QMAX = floor(qmax 2^32).  Ordering and extents are therefore
-// exact integer decisions, the same in every implementation.
+// only by default).  A point's phase is the binned search's FP64 fold, phi = p - floor(p)
+// with p = RN(dt f); the order is (phi, point index); a run's extent is RN(phi_last -
+// phi_first), plus one cycle (RN(d + 1)) when the run wraps through phase 0.
+//
+// Keys.  The sort works on 64-bit keys (K << 32 | point) with K = floor(phi 2^32), taken
+// from the bits of p with integer operations (phi = frac(p) is exact, so K is exact); the
+// FP64 product p is the only floating-point operation per point.  Points with equal K are
+// then put in (phi, point) order by one thread per run of equal keys (rare: phases closer
+// than 2^-32 cycle), which makes the order the definition's exactly.  Extents come from the
+// keys: E64 = K_last - K_first (+ 2^32 past the end) is within 1 + 2^-20 of the definition's
+// extent times 2^32 (K truncates by less than one unit; the extent's FP64 roundings add at
+// most 2^-52 cycle), so a bound qmin or qmax is decided from E64 when it lies two or more
+// units away, and otherwise from the phases in FP64, as the definition computes it.
 //
 // Search kernel: one block per (curve, tile of kTile frequencies).  For each frequency the
-// block forms the keys (key << 32 | index) in shared memory, sorts them (buckets on the top
-// bits of the phase with an insertion sort per bucket; a bitonic network when phases
-// clump), and builds prefix sums of (w, w x) in phase order (FP64, stored as double-float
-// pairs in four arrays).  Run starts are dealt round-robin to the threads; a start's
-// admissible ends (extent within [QMIN, QMAX]) come from two binary searches, and every
-// run's sums are independent prefix differences.  Runs are ranked by the signed residue
-// z = s / sqrt(r(1-r)) (P = z^2), evaluated two ends at a time as packed FP32 pairs where
-// every run of the curve is known to have 0 < r < 1; only the best z of each frequency is
-// kept, P(f_j) = z^2.
+// block forms the keys in shared memory, sorts them (buckets on the top bits of the phase
+// with an insertion sort per bucket; a bitonic network when phases clump), fixes the order
+// of equal keys, and builds prefix sums of (w, w x) in phase order (FP64, stored as
+// double-float pairs in four arrays).  Run starts are dealt round-robin to the threads; a
+// start's admissible ends (extent within [qmin, qmax]) come from two binary searches, and
+// every run's sums are independent prefix differences.  Runs are ranked by the signed
+// residue z = s / sqrt(r(1-r)) (P = z^2), evaluated two ends at a time as packed FP32 pairs
+// where every run of the curve is known to have 0 < r < 1; only the best z of each
+// frequency is kept, P(f_j) = z^2.
 //
 // Reduce kernel: one block per curve: the top-k local maxima of P(f_j) (as in the binned
 // search), the signal detection efficiency, and for each kept frequency the best run found
 // again with the search's arithmetic (ties to the smaller start, then the shorter run) and
-// refitted in FP64 -- keys and order recomputed exactly, r and s summed in run order.
+// refitted in FP64 -- order recomputed exactly, r and s summed in run order.
 #include <cfloat>
 
 #include "bls_internal.h"
@@ -35,37 +42,42 @@ namespace {
 constexpr int kUThreads = 512;
 constexpr int kTile = 16;
 
-__host__ __device__ __forceinline__ int shift_of(double dtmax)
+typedef unsigned long long u64;
+
+// The FP64 phase of point i at frequency f, as the definition folds it.
+__device__ __forceinline__ double point_phase(const CurveDesc& cd, int i, double f)
 {
-    int L = 0;
-    if (dtmax > 0.0) L = ilogb(dtmax) + 1;
-    int s = 34 - (L + 1) / 2;
-    if (s > 62 - L) s = 62 - L;
-    return s < 1 ? 1 : s;
+    const double p = __dmul_rn(cd.dt64[i], f);
+    return __dsub_rn(p, floor(p));
 }
 
-__device__ __forceinline__ unsigned long long fixed_freq(double f, double dtmax)
+// K = floor(frac(p) 2^32) of a finite non-negative p, from its bits with integer
+// operations: p = m 2^(e-52) with the 53-bit significand m, so p 2^32 = m 2^(e-20) and K is
+// that value's integer part modulo 2^32 (a shift of m either way; zero for p < 2^-1022 and
+// for p >= 2^84, whose fraction is zero).
+__device__ __forceinline__ unsigned key32(double p)
 {
-    return __double2ull_rn(ldexp(f, 64 - shift_of(dtmax)));
+    const u64 b = (u64)__double_as_longlong(p);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return 0u;
+    const u64 m = (b & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = 1043 - ex;            // 20 - (ex - 1023)
+    if (sh >= 64 || sh <= -64) return 0u;
+    return sh >= 0 ? (unsigned)(m >> sh) : (unsigned)(m << (-sh));
 }
 
-// Phase keys (key << 32 | point) of a curve at F, bitonic-sorted ascending in `keys`
-// (M = the power of two >= n; the tail holds all-ones sentinels).
-__device__ __forceinline__ void sorted_keys(const CurveDesc& cd, unsigned long long F, unsigned long long* keys, int M)
+// Sort key (K << 32 | point) of point i at frequency f.
+__device__ __forceinline__ u64 phase_key(const CurveDesc& cd, int i, double f)
 {
-    const unsigned Flo = (unsigned)F, Fhi = (unsigned)(F >> 32);
+    return ((u64)key32(__dmul_rn(cd.dt64[i], f)) << 32) | (unsigned)i;
+}
+
+// Phase keys of a curve at f, bitonic-sorted ascending in `keys` (M = the power of two
+// >= n; the tail holds all-ones sentinels).
+__device__ __forceinline__ void sorted_keys(const CurveDesc& cd, double f, u64* keys, int M)
+{
     const int n = cd.n;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        unsigned long long k = ~0ull;
-        if (i < n) {
-            const float4 A = cd.pts[(i >> 1) * 2];
-            const unsigned lo = __float_as_uint((i & 1) ? A.y : A.x);
-            const unsigned hi = __float_as_uint((i & 1) ? A.w : A.z);
-            const unsigned q = __umulhi(lo, Flo) + lo * Fhi + hi * Flo;
-            k = ((unsigned long long)q << 32) | (unsigned)i;
-        }
-        keys[i] = k;
-    }
+    for (int i = threadIdx.x; i < M; i += blockDim.x) keys[i] = i < n ? phase_key(cd, i, f) : ~0ull;
     __syncthreads();
     for (int size = 2; size <= M; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -73,7 +85,7 @@ __device__ __forceinline__ void sorted_keys(const CurveDesc& cd, unsigned long l
                 const int lo = 2 * t - (t & (stride - 1));
                 const int hi = lo + stride;
                 const bool up = (lo & size) == 0;
-                const unsigned long long a = keys[lo], b = keys[hi];
+                const u64 a = keys[lo], b = keys[hi];
                 if ((a > b) == up) { keys[lo] = b; keys[hi] = a; }
             }
             __syncthreads();
@@ -81,30 +93,45 @@ __device__ __forceinline__ void sorted_keys(const CurveDesc& cd, unsigned long l
     }
 }
 
-// Phase key (key << 32 | point) of point i at F = (Fhi, Flo).
-__device__ __forceinline__ unsigned long long phase_key(const CurveDesc& cd, int i, unsigned Flo,
-                                                        unsigned Fhi)
+// Runs of equal K in keys[0 .. n) (sorted by (K, point)) reordered by (phi, point): one
+// thread per run, an insertion sort on the FP64 phases (a run already in phase order --
+// equal phases -- costs one comparison per point).
+__device__ __forceinline__ void order_equal_keys(const CurveDesc& cd, double f, u64* keys, int n)
 {
-    const float4 A = cd.pts[(i >> 1) * 2];
-    const unsigned lo = __float_as_uint((i & 1) ? A.y : A.x);
-    const unsigned hi = __float_as_uint((i & 1) ? A.w : A.z);
-    const unsigned q = __umulhi(lo, Flo) + lo * Fhi + hi * Flo;
-    return ((unsigned long long)q << 32) | (unsigned)i;
+    for (int q = threadIdx.x; q + 1 < n; q += blockDim.x) {
+        const unsigned K = (unsigned)(keys[q] >> 32);
+        if ((unsigned)(keys[q + 1] >> 32) != K || (q > 0 && (unsigned)(keys[q - 1] >> 32) == K)) continue;
+        int q1 = q + 2;
+        while (q1 < n && (unsigned)(keys[q1] >> 32) == K) ++q1;
+        for (int x = q + 1; x < q1; ++x) {
+            const u64 v = keys[x];
+            const int iv = (int)(v & 0xffffffffu);
+            const double pv = point_phase(cd, iv, f);
+            int y = x - 1;
+            while (y >= q) {
+                const int iy = (int)(keys[y] & 0xffffffffu);
+                const double py = point_phase(cd, iy, f);
+                if (py < pv || (py == pv && iy < iv)) break;
+                keys[y + 1] = keys[y];
+                --y;
+            }
+            keys[y + 1] = v;
+        }
+    }
+    __syncthreads();
 }
 
 constexpr int kBucketMax = 48;   // largest bucket left to an insertion sort
 
-// Phase keys of a curve at F in ascending (key, point) order in keys[0 .. n): a counting
-// pass over the top B bits of the phase into nbk = M/2 buckets (shared-memory atomics), an
-// exclusive scan, a scatter, and an insertion sort of every bucket by one thread.  When a
-// bucket holds more than kBucketMax keys (phases clumped) the bitonic network sorts
-// instead.  The keys are distinct, so both give the same order.  `cnt` is scratch for
-// M + 1 ints.
-__device__ __forceinline__ void sort_keys(const CurveDesc& cd, unsigned long long F,
-                                          unsigned long long* keys, int M, int* cnt)
+// Points of a curve at f in the definition's (phi, point) order in keys[0 .. n): keys
+// (K, point) sorted by a counting pass over the top B bits of K into nbk = M/2 buckets
+// (shared-memory atomics), an exclusive scan, a scatter, and an insertion sort of every
+// bucket by one thread -- or, when a bucket holds more than kBucketMax keys (phases
+// clumped), by the bitonic network; the keys are distinct, so both give the same order --
+// then equal K put in phase order.  `cnt` is scratch for M + 1 ints.
+__device__ __forceinline__ void sort_keys(const CurveDesc& cd, double f, u64* keys, int M, int* cnt)
 {
     __shared__ int s_tot[kUThreads / 32 + 1];
-    const unsigned Flo = (unsigned)F, Fhi = (unsigned)(F >> 32);
     const int n = cd.n, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int nbk = M >= 2 ? M >> 1 : 1;
@@ -116,7 +143,7 @@ __device__ __forceinline__ void sort_keys(const CurveDesc& cd, unsigned long lon
     if (tid == 0) s_tot[kUThreads / 32] = 0;
     __syncthreads();
     for (int i = tid; i < n; i += nt) {
-        const unsigned long long k = phase_key(cd, i, Flo, Fhi);
+        const u64 k = phase_key(cd, i, f);
         atomicAdd(&start[B ? (int)(k >> (64 - B)) : 0], 1);
     }
     __syncthreads();
@@ -149,25 +176,27 @@ __device__ __forceinline__ void sort_keys(const CurveDesc& cd, unsigned long lon
     }
     __syncthreads();
     if (clumped) {
-        sorted_keys(cd, F, keys, M);
+        sorted_keys(cd, f, keys, M);
+        order_equal_keys(cd, f, keys, n);
         return;
     }
     if (tid == 0) start[nbk] = n;
     for (int i = tid; i < n; i += nt) {
-        const unsigned long long k = phase_key(cd, i, Flo, Fhi);
+        const u64 k = phase_key(cd, i, f);
         keys[atomicAdd(&cur[B ? (int)(k >> (64 - B)) : 0], 1)] = k;
     }
     __syncthreads();
     for (int b = tid; b < nbk; b += nt) {
         const int s0 = start[b], s1 = start[b + 1];
         for (int x = s0 + 1; x < s1; ++x) {
-            const unsigned long long v = keys[x];
+            const u64 v = keys[x];
             int y = x - 1;
             while (y >= s0 && keys[y] > v) { keys[y + 1] = keys[y]; --y; }
             keys[y + 1] = v;
         }
     }
     __syncthreads();
+    order_equal_keys(cd, f, keys, n);
 }
 
 __device__ __forceinline__ void point_weights(const CurveDesc& cd, int i, float& w, float& wx)
@@ -208,7 +237,7 @@ struct Prefix {
     float *wh, *wl, *xh, *xl;
 };
 
-__device__ __forceinline__ void prefix_sums(const CurveDesc& cd, const unsigned long long* keys, const Prefix& C,
+__device__ __forceinline__ void prefix_sums(const CurveDesc& cd, const u64* keys, const Prefix& C,
                             double* sred)
 {
     const int n = cd.n;
@@ -257,24 +286,67 @@ __device__ __forceinline__ void prefix_sums(const CurveDesc& cd, const unsigned 
     __syncthreads();
 }
 
-// Admissible ends of the runs starting at sorted position a: unwrapped positions
-// emin..emax (extents within [QMIN, QMAX], at most n - 1 points), extents growing with the
-// end; emin > emax when none.
-__device__ __forceinline__ void run_ends(const unsigned long long* keys, int n, int a, unsigned QMIN,
-                                         unsigned QMAX, int& emin, int& emax)
+// The definition's bounds of a run's extent and the frequency (for the exact re-check).
+struct Bounds {
+    double qmin, qmax;    // extent bounds, in cycles
+    double lo, hi;        // the same in units of 2^-32 cycle (exact scalings)
+    double f;
+};
+
+__device__ __forceinline__ Bounds make_bounds(double qmin, double qmax, double f)
 {
-    const unsigned k0 = (unsigned)(keys[a] >> 32);
-    auto ext = [&](int e) { return (unsigned)(keys[e < n ? e : e - n] >> 32) - k0; };
-    int lo2 = a, hi2 = a + n - 1;            // ext(lo2) <= QMAX; hi2 out of range
+    Bounds B;
+    B.qmin = qmin;
+    B.qmax = qmax;
+    B.lo = qmin * 4294967296.0;
+    B.hi = qmax * 4294967296.0;
+    B.f = f;
+    return B;
+}
+
+// The definition's extent of the run from sorted position a to unwrapped position e.
+__device__ __forceinline__ double exact_extent(const CurveDesc& cd, const u64* keys, int n, int a, int e,
+                                               double f)
+{
+    const double pa = point_phase(cd, (int)(keys[a] & 0xffffffffu), f);
+    const double pe = point_phase(cd, (int)(keys[e < n ? e : e - n] & 0xffffffffu), f);
+    const double d = __dsub_rn(pe, pa);
+    return e >= n ? __dadd_rn(d, 1.0) : d;
+}
+
+// Admissible ends of the runs starting at sorted position a: unwrapped positions
+// emin..emax (extents within [qmin, qmax], at most n - 1 points), extents growing with the
+// end; emin > emax when none.  Each bound is decided from the keys' extent E64 when it lies
+// two or more units of 2^-32 away, else from the FP64 phases.
+__device__ __forceinline__ void run_ends(const CurveDesc& cd, const u64* keys, int n, int a,
+                                         const Bounds& B, int& emin, int& emax)
+{
+    const long long k0 = (long long)(keys[a] >> 32);
+    auto e64 = [&](int e) {
+        return (double)((long long)(keys[e < n ? e : e - n] >> 32) - k0 + (e >= n ? (1ll << 32) : 0ll));
+    };
+    auto le_max = [&](int e) {
+        const double x = e64(e);
+        if (x + 2.0 <= B.hi) return true;
+        if (x - 2.0 >= B.hi) return false;
+        return exact_extent(cd, keys, n, a, e, B.f) <= B.qmax;
+    };
+    auto ge_min = [&](int e) {
+        const double x = e64(e);
+        if (x - 2.0 >= B.lo) return true;
+        if (x + 2.0 <= B.lo) return false;
+        return exact_extent(cd, keys, n, a, e, B.f) >= B.qmin;
+    };
+    int lo2 = a, hi2 = a + n - 1;            // extent(lo2) = 0 <= qmax; hi2 out of range
     while (hi2 - lo2 > 1) {
         const int mid = (lo2 + hi2) >> 1;
-        if (ext(mid) <= QMAX) lo2 = mid; else hi2 = mid;
+        if (le_max(mid)) lo2 = mid; else hi2 = mid;
     }
     emax = lo2;
-    int lo1 = a - 1, hi1 = emax + 1;          // ext(hi1) >= QMIN or hi1 past emax
+    int lo1 = a - 1, hi1 = emax + 1;          // extent(hi1) >= qmin or hi1 past emax
     while (hi1 - lo1 > 1) {
         const int mid = (lo1 + hi1) >> 1;
-        if (ext(mid) >= QMIN) hi1 = mid; else lo1 = mid;
+        if (ge_min(mid)) hi1 = mid; else lo1 = mid;
     }
     emin = hi1;
 }
@@ -314,7 +386,6 @@ __device__ __forceinline__ float best_z(float b, float z)
     return SIGN ? fmaxf(b, fabsf(z)) : fminf(b, z);
 }
 
-typedef unsigned long long u64;
 __device__ __forceinline__ u64 pk2(float lo, float hi)
 {
     u64 r;
@@ -460,7 +531,7 @@ __device__ __forceinline__ void ubls_search(UblsParams p)
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ float sZ[kUThreads / 32];
     __shared__ double sred[2 * kUThreads];
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(dsm);
+    u64* keys = reinterpret_cast<u64*>(dsm);
     // work item -> (curve, tile)
     const long long it = blockIdx.x;
     int lo = 0, hi = p.ncurves;
@@ -479,15 +550,16 @@ __device__ __forceinline__ void ubls_search(UblsParams p)
     const bool fast = runs_positive(cd, reinterpret_cast<float*>(sred));
     for (int j = j0; j < min(j0 + kTile, cd.nf); ++j) {
         const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
-        sort_keys(cd, fixed_freq(f, cd.dtmax), keys, M, reinterpret_cast<int*>(C.wh));
+        sort_keys(cd, f, keys, M, reinterpret_cast<int*>(C.wh));
         prefix_sums(cd, keys, C, sred);
+        const Bounds Bq = make_bounds(p.qmin, p.qmax, f);
         const float4 T = make_float4(C.wh[n], C.wl[n], C.xh[n], C.xl[n]);
         // starts dealt round-robin to the threads (phases clump, so contiguous ranges would
         // load the threads unevenly); each start's best z over its admissible runs
         float b = 0.0f;
         for (int a = threadIdx.x; a < n; a += nt) {
             int emin, emax;
-            run_ends(keys, n, a, p.QMIN, p.QMAX, emin, emax);
+            run_ends(cd, keys, n, a, Bq, emin, emax);
             b = fast ? start_best<SIGN, true>(C, T, n, a, emin, emax, b)
                      : start_best<SIGN, false>(C, T, n, a, emin, emax, b);
         }
@@ -542,15 +614,15 @@ __device__ __forceinline__ bool run_first(float za, int sa, int la, float zb, in
 // The best run of one frequency (keys and prefix sums in place), with the search kernel's
 // arithmetic, so its z is the one the search kept; (start, len), len = 0 if no run counts.
 template <int SIGN>
-__device__ int2 best_run(const unsigned long long* keys, const Prefix& C, int n, unsigned QMIN,
-                         unsigned QMAX, bool fast, float* sz, int* ss, int* sl)
+__device__ int2 best_run(const CurveDesc& cd, const u64* keys, const Prefix& C, int n, const Bounds& Bq,
+                         bool fast, float* sz, int* ss, int* sl)
 {
     const float4 T = make_float4(C.wh[n], C.wl[n], C.xh[n], C.xl[n]);
     float bz = 0.0f;
     int bs = 0x7fffffff, bl = 0x7fffffff;
     for (int a = threadIdx.x; a < n; a += blockDim.x) {
         int emin, emax;
-        run_ends(keys, n, a, QMIN, QMAX, emin, emax);
+        run_ends(cd, keys, n, a, Bq, emin, emax);
         const float awh = C.wh[a], awl = C.wl[a], axh = C.xh[a], axl = C.xl[a];
         for (int e = emin; e <= emax; ++e) {
             float nr, sx;
@@ -582,7 +654,7 @@ __device__ int2 best_run(const unsigned long long* keys, const Prefix& C, int n,
 __global__ void __launch_bounds__(kUThreads, 1) ubls_reduce_kernel(UblsParams p)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    unsigned long long* keys = reinterpret_cast<unsigned long long*>(dsm);
+    u64* keys = reinterpret_cast<u64*>(dsm);
     __shared__ double red[2 * kUThreads];
     __shared__ float bzs[kUThreads / 32];
     __shared__ int bss[kUThreads / 32], bls[kUThreads / 32];
@@ -656,10 +728,11 @@ __global__ void __launch_bounds__(kUThreads, 1) ubls_reduce_kernel(UblsParams p)
             continue;
         }
         const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
-        sort_keys(cd, fixed_freq(f, cd.dtmax), keys, M, reinterpret_cast<int*>(C.wh));
+        sort_keys(cd, f, keys, M, reinterpret_cast<int*>(C.wh));
         prefix_sums(cd, keys, C, red);
-        const int2 run = p.sign ? best_run<1>(keys, C, cd.n, p.QMIN, p.QMAX, fast, bzs, bss, bls)
-                                : best_run<0>(keys, C, cd.n, p.QMIN, p.QMAX, fast, bzs, bss, bls);
+        const Bounds Bq = make_bounds(p.qmin, p.qmax, f);
+        const int2 run = p.sign ? best_run<1>(cd, keys, C, cd.n, Bq, fast, bzs, bss, bls)
+                                : best_run<0>(cd, keys, C, cd.n, Bq, fast, bzs, bss, bls);
         if (threadIdx.x == 0) {
             const int a = run.x, len = run.y;
             DevPeak pk = {};
@@ -678,14 +751,13 @@ __global__ void __launch_bounds__(kUThreads, 1) ubls_reduce_kernel(UblsParams p)
                     r = __dadd_rn(r, w);
                     s = __dadd_rn(s, __dmul_rn(w, __dsub_rn((double)cd.y[i], cd.ybar)));
                 }
-                int ql = a + len - 1;
-                if (ql >= cd.n) ql -= cd.n;
-                const unsigned k0 = (unsigned)(keys[a] >> 32);
-                const unsigned E = (unsigned)(keys[ql] >> 32) - k0;
-                double mid = ((double)k0 + 0.5 * (double)E) / 4294967296.0;
-                mid = mid - floor(mid);
-                pk.epoch = cd.t_ref + mid / f;
-                pk.duration = (double)E / 4294967296.0 / f;
+                // extent and mid-box phase as the definition computes them
+                const double E = exact_extent(cd, keys, cd.n, a, a + len - 1, f);
+                const double ph0 = point_phase(cd, (int)(keys[a] & 0xffffffffu), f);
+                double mid = __dadd_rn(ph0, __dmul_rn(0.5, E));
+                mid = __dsub_rn(mid, floor(mid));
+                pk.epoch = __dadd_rn(cd.t_ref, __ddiv_rn(mid, f));
+                pk.duration = __ddiv_rn(E, f);
                 if (r > 0.0 && r < 1.0 && (p.sign || s < 0.0)) {
                     pk.power = s * s / (r * (1.0 - r));
                     pk.depth = -s / (r * (1.0 - r));

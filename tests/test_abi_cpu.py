@@ -124,3 +124,45 @@ def test_packed_curves_without_errors_and_scalar_grids():
     assert pc.arr[1].t == t.ctypes.data + 8 * 10 and pc.arr[1].y == y.ctypes.data + 4 * 10
     assert all(pc.arr[k].nf == 500 and pc.arr[k].nb == 150 for k in range(2))
     assert pc.total_nf == 1000
+
+
+def test_binding_rejects_mistyped_and_short_tensors():
+    """Tensors are passed to the library by address, so the binding checks their dtype,
+    contiguity and length first (no GPU needed: CPU tensors take the same checks)."""
+    torch = pytest.importorskip("torch")
+    t = torch.linspace(0, 10, 50, dtype=torch.float64)
+    y = torch.ones(50, dtype=torch.float32)
+    cases = [
+        bls.CurveInput(t.float(), y, None, nf=5, fmin=0.1, df=0.1),          # t not FP64
+        bls.CurveInput(t, y.double(), None, nf=5, fmin=0.1, df=0.1),         # y not FP32
+        bls.CurveInput(t, y, y.double(), nf=5, fmin=0.1, df=0.1),            # dy not FP32
+        bls.CurveInput(t, y[:40], None, nf=5, fmin=0.1, df=0.1),             # y short
+        bls.CurveInput(t, y, y[:49], nf=5, fmin=0.1, df=0.1),                # dy short
+        bls.CurveInput(t[::2], y[:25], None, nf=5, fmin=0.1, df=0.1),        # not contiguous
+        bls.CurveInput(t, y, None, freqs=torch.ones(5, dtype=torch.float32)),  # freqs FP32
+    ]
+    for c in cases:
+        with pytest.raises(bls.BLSError) as ei:
+            bls._struct(c, [])
+        assert ei.value.status == bls.ERR_INVALID
+    import numpy as np
+    with pytest.raises(bls.BLSError):                                      # numpy, y short
+        bls._struct(bls.CurveInput(np.zeros(5), np.zeros(4, np.float32), None, nf=2), [])
+    ok = bls._struct(bls.CurveInput(t, y, None, nf=5, fmin=0.1, df=0.1), [])
+    assert ok.n == 50 and ok.nf == 5
+
+
+def test_static_search_checks_output_sizes_before_the_call():
+    """bls_search_static cannot see the size of a device buffer: the binding refuses
+    outputs smaller than what the call writes (topk records, nf spectrum values)."""
+    torch = pytest.importorskip("torch")
+    t = torch.linspace(0, 10, 50, dtype=torch.float64)
+    c = bls.CurveInput(t, torch.ones(50, dtype=torch.float32), None, nf=10, fmin=0.1, df=0.1,
+                       nb=20, qmin=0.05, qmax=0.2)
+    one = torch.zeros(bls.PEAK_DTYPE.itemsize, dtype=torch.uint8)
+    for kw in (dict(topk=2, peaks=one), dict(peaks=None),
+               dict(peaks=one, spectrum=torch.zeros(9, dtype=torch.float32)),
+               dict(peaks=one, spectrum=torch.zeros(10, dtype=torch.float64))):
+        with pytest.raises(bls.BLSError) as ei:
+            bls.search_static(c, **kw)
+        assert ei.value.status == bls.ERR_INVALID

@@ -1,8 +1,9 @@
 """Unbinned (edge-to-edge) BLS, CUDA path vs the oracle (marked gpu).
 
-The phase order and the run extents are exact integer decisions on both sides; the run sums
-are FP32 on the GPU's search and FP64 in the oracle, so SR per frequency must agree within
-the search's tolerance, the best frequency and run must agree wherever the oracle's best is
+Both sides order points by the FP64 phase frac(RN(dt f)) (ties by index) and decide run
+extents in FP64, so the order and the admissible runs are identical; the run sums are FP32
+on the GPU's search and FP64 in the oracle, so SR per frequency must agree within the
+search's tolerance, the best frequency and run must agree wherever the oracle's best is
 separated, and the reported peak (refit in FP64 in run order) must then equal the
 oracle's."""
 import numpy as np
@@ -82,6 +83,49 @@ def test_large_curve_both_signs_explicit_grid():
         pk, spec = _run([ci], sign=sign)
         _check(ci, pk[0, 0], spec, sign=s)
         assert pk[0, 0]["j"] == 10
+
+
+def test_equal_phases_and_extents_on_the_bounds():
+    """Times on a 2^-7-day lattice, shuffled (inputs need not be sorted): at f = 1 and 0.5
+    many phases are exactly equal (order by index) and many run extents equal qmin or qmax
+    exactly (both bounds admit); at f = 1 +- 2^-40 phases differ by less than 2^-32 of a
+    cycle, so equal 32-bit keys must be put in phase order, and at 1 - 2^-40 integer times
+    fold to just below phase 1 (a wrap).  The GPU's order and bounds are the oracle's."""
+    rng = np.random.default_rng(77)
+    n = 700
+    dt = rng.integers(0, 40 * 128, n).astype(np.float64) / 128.0
+    dt[rng.choice(n, 60, replace=False)] = 7.0                 # repeated times
+    t = synth.T0 + dt
+    y = (1 + rng.normal(0, 0.01, n) - 0.02 * (np.mod(dt, 1.0) < 0.125)).astype(np.float32)
+    dy = rng.uniform(0.008, 0.012, n).astype(np.float32)
+    freqs = np.array([1.0, 1.0 + 2.0 ** -40, 1.0 - 2.0 ** -40, 0.5, 2.0, 0.75])
+    qmin, qmax = 2.0 ** -6, 0.125
+    ci = bls.CurveInput(t, y, dy, freqs=freqs, nb=100, qmin=qmin, qmax=qmax)
+    for sign, sg in (("dips", 0), ("both", 1)):
+        pk, spec = _run([ci], sign=sign, qmin=qmin, qmax=qmax)
+        _check(ci, pk[0, 0], spec, sign=sg, qmin=qmin, qmax=qmax)
+    # each frequency alone: the GPU's best run (a position range of its phase order) read
+    # in the oracle's order must be admissible, within tolerance of the best power, and
+    # carry the oracle's FP64 extent exactly (duration = E / f)
+    d, w, x, scal = oracle.prep(t, y, dy)
+    for f in freqs:
+        one = bls.CurveInput(t, y, dy, freqs=np.array([f]), nb=100, qmin=qmin, qmax=qmax)
+        pk, spec = _run([one], qmin=qmin, qmax=qmax)
+        Pb, *_ = oracle.ubls_power(d, w, x, f, qmin, qmax)
+        phi = oracle.ubls_phases(d, f)
+        order = oracle.ubls_order(phi)
+        i1, k = int(pk[0, 0]["i1"]), int(pk[0, 0]["k"])
+        assert 1 <= k <= n - 1
+        E = oracle.ubls_extent(phi, order, i1, k)
+        assert qmin <= E <= qmax
+        assert pk[0, 0]["duration"] == E / f
+        run = order[(i1 + np.arange(k)) % n]
+        r, sx = float(np.sum(w[run])), float(np.sum(w[run] * x[run]))
+        Prun = sx * sx / (r * (1 - r))
+        assert sx < 0
+        tol = sr_tol(np.sqrt(Pb), scal[3])
+        assert np.sqrt(Prun) >= np.sqrt(Pb) - 2 * tol
+        assert pk[0, 0]["power"] == pytest.approx(Prun, rel=1e-9)
 
 
 def test_tiny_and_edge_cases():

@@ -368,6 +368,10 @@ def test_many_matches_single_and_threads():
                                  nf=g.nf, topk=2)
         assert np.array_equal(P, P1[q * 700:(q + 1) * 700])
         assert [p.j for p in pk] == [p.j for p in pk1[q]]
+        # the threaded driver reports the same records, SDE included
+        for a, b_ in zip(pk, pk1[q]):
+            assert a == b_
+            assert a.sde != 0.0
 
 
 # ------------------------------------------------------------------------------ SDE

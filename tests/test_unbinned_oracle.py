@@ -1,11 +1,12 @@
 """Pins of the unbinned (edge-to-edge) BLS oracle (``oracle/unbinned_oracle.c``).
 
-Boxes are cyclic runs of consecutive points in phase order whose phase extent lies in
-[qmin, qmax]; phases are 64-bit fixed-point fractions (so ordering and extents are exact
-integer decisions).  The pins recompute the phase keys with Python integers, enumerate every
-run on tiny inputs with an explicit least-squares fit, and check the relation to the binned
-search and a noise-free box."""
+Boxes are cyclic runs of consecutive points in (phase, index) order whose phase extent lies
+in [qmin, qmax]; phases are the binned search's FP64 fold frac(RN(dt f)).  The pins check
+the phases against exact rational arithmetic, the order against a plain sort, enumerate
+every run on tiny inputs with an explicit least-squares fit, and check the relation to the
+binned search and a noise-free box."""
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -14,44 +15,51 @@ import oracle
 from paper_1112_1701_b300 import synth
 
 
-def _keys_py(dt, f):
-    dtmax = float(np.max(dt))
-    L = (math.frexp(dtmax)[1]) if dtmax > 0 else 0      # dtmax < 2^L
-    s = 34 - int((L + 1) / 2)
-    s = max(1, min(s, 62 - L))
-    F = round(math.ldexp(f, 64 - s))
-    return np.array([((round(math.ldexp(float(d), s)) * F) % 2 ** 64) >> 32 for d in dt],
-                    dtype=np.uint64), s
-
-
 @pytest.mark.parametrize("seed", range(5))
-def test_phase_keys_match_integer_arithmetic(seed):
+def test_phases_within_one_rounding_of_exact(seed):
+    """phi = frac(RN(dt f)): the product rounds once (relative 2^-53) and the fraction is
+    exact, so phi is within 2^-53 dt f of the exact frac(dt f), modulo one cycle (a product
+    that rounds up to an integer gives phase 0 for an exact fraction just below 1)."""
     rng = np.random.default_rng(seed)
     dt = np.concatenate([[0.0], np.sort(rng.uniform(0, 10 ** rng.uniform(-1, 3.5), 50))])
-    dtmax = float(dt.max())
     for f in rng.uniform(0.05, 20.0, 5):
-        kc = oracle.ubls_keys(dt, dtmax, f)
-        kp, s = _keys_py(dt, f)
-        assert oracle.fx_shift(dtmax) == s
-        assert np.array_equal(kc.astype(np.uint64), kp)
+        phi = oracle.ubls_phases(dt, f)
+        assert np.all((phi >= 0.0) & (phi < 1.0))
+        for d, ph in zip(dt, phi):
+            ex = Fraction(float(d)) * Fraction(float(f))
+            fr = ex - math.floor(ex)
+            err = min(abs(Fraction(float(ph)) - fr), abs(Fraction(float(ph)) + 1 - fr))
+            assert err <= Fraction(2) ** -53 * ex + Fraction(2) ** -80
+
+
+def test_order_is_phase_then_index():
+    """Equal phases (repeated times, and times a whole number of periods apart) keep their
+    index order; otherwise ascending phase."""
+    dt = np.array([3.0, 0.5, 3.0, 1.0, 0.0, 2.5, 5.0, 0.25])
+    phi = oracle.ubls_phases(dt, 1.0)
+    order = oracle.ubls_order(phi)
+    expect = sorted(range(len(dt)), key=lambda i: (phi[i], i))
+    assert order.tolist() == expect
+    assert order.tolist()[:4] == [0, 2, 3, 4]          # phase 0: indices ascending
+    # extents: a run wrapping through phase 0 adds a cycle
+    q = order.tolist().index(7)                        # phase 0.25, then 0.5, 0.5
+    assert oracle.ubls_extent(phi, order, q, 3) == 0.25
+    assert oracle.ubls_extent(phi, order, q, 6) == 0.75  # 0.25 .. 0.5, then 0 (+1)
 
 
 def _brute(dt, w, x, f, qmin, qmax):
-    """Every cyclic run of the phase order, its extent from the keys, P from an explicit
-    weighted least-squares fit of a two-level step."""
+    """Every cyclic run of the (phase, index) order, its extent in FP64 from the phases,
+    P from an explicit weighted least-squares fit of a two-level step."""
     n = len(dt)
-    key, _ = _keys_py(dt, f)
-    order = sorted(range(n), key=lambda i: (int(key[i]), i))
-    QMIN = math.ceil(qmin * 2 ** 32)
-    QMAX = math.floor(qmax * 2 ** 32)
+    phi = [float(d) * float(f) - math.floor(float(d) * float(f)) for d in dt]
+    order = sorted(range(n), key=lambda i: (phi[i], i))
     best = 0.0
     for a in range(n):
         for ln in range(1, n):
             run = [order[(a + q) % n] for q in range(ln)]
-            E = (int(key[run[-1]]) - int(key[run[0]])) % 2 ** 32
-            if E > QMAX:
-                break
-            if E < QMIN:
+            d = phi[run[-1]] - phi[run[0]]
+            E = d + 1.0 if a + ln - 1 >= n else d
+            if E > qmax or E < qmin:
                 continue
             s_ind = np.zeros(n)
             s_ind[run] = 1.0
@@ -74,7 +82,7 @@ def test_best_box_equals_brute_force(seed):
     dt, w, x, _ = oracle.prep(t, y, dy)
     for f in rng.uniform(0.1, 3.0, 3):
         for qmin, qmax in ((0.0, 0.3), (0.02, 0.5)):
-            P, a, ln, r, s, order = oracle.ubls_power(dt, w, x, float(dt.max()), f, qmin, qmax)
+            P, a, ln, r, s, order = oracle.ubls_power(dt, w, x, f, qmin, qmax)
             assert P == pytest.approx(_brute(dt, w, x, f, qmin, qmax), rel=1e-9, abs=1e-15)
 
 
@@ -89,7 +97,8 @@ def test_unbinned_at_least_binned_when_qmin_is_zero():
     for j in (0, 250, 1000, 1876):
         f = oracle.freq(j, g.fmin, g.df)
         Pb, *_ = oracle.power(dt, w, x, f, 100, kmin, kmax)
-        Pu, *_ = oracle.ubls_power(dt, w, x, float(dt.max()), f, 0.0, kmax / 100)
+        # (a hair above kmax/nb: the box's FP64 extent may exceed k/nb by an ulp)
+        Pu, *_ = oracle.ubls_power(dt, w, x, f, 0.0, kmax / 100 + 1e-12)
         assert Pu >= Pb * (1 - 1e-12)
 
 

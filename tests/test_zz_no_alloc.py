@@ -53,6 +53,32 @@ def test_static_search_matches_search_on_two_calls_in_a_row():
                 assert got[e][f] == pytest.approx(ref[e][f], rel=1e-9, abs=1e-12), f
 
 
+def test_static_search_allocates_no_device_memory():
+    """After a warm-up call (the first call on a device resolves the static array's
+    address and loads the kernels), further calls leave the device's free memory and
+    torch's allocation count unchanged."""
+    torch = pytest.importorskip("torch")
+    build.build()
+    b = synth.config2(ncurves=1, nf=2000)
+    c, g = b.curves[0], b.grids[0]
+    dev = bls.CurveInput(torch.tensor(c.t, device="cuda"), torch.tensor(c.y, device="cuda"),
+                         torch.tensor(c.dy, device="cuda"), nf=g.nf, fmin=g.fmin, df=g.df,
+                         nb=200, qmin=b.qmin, qmax=b.qmax)
+    peaks_buf = torch.zeros(2 * bls.PEAK_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    spec = torch.zeros(g.nf, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    bls.search_static(dev, topk=2, stream=stream, peaks=peaks_buf, spectrum=spec)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(2):
+        bls.search_static(dev, topk=2, stream=stream, peaks=peaks_buf, spectrum=spec)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
 def test_static_search_rejects_oversized_and_host_inputs():
     torch = pytest.importorskip("torch")
     build.build()
@@ -68,4 +94,13 @@ def test_static_search_rejects_oversized_and_host_inputs():
                              fmin=0.1, df=0.1, nb=50, qmin=0.02, qmax=0.2)
     with pytest.raises(bls.BLSError) as ei:
         bls.search_static(host_in, peaks=peaks)
+    assert ei.value.status == bls.ERR_INVALID
+    # outputs too small for what the call would write
+    ok = bls.CurveInput(t, y, None, nf=10, fmin=0.1, df=0.1, nb=50, qmin=0.02, qmax=0.2)
+    with pytest.raises(bls.BLSError) as ei:
+        bls.search_static(ok, topk=2, peaks=peaks)                   # room for one record
+    assert ei.value.status == bls.ERR_INVALID
+    short = torch.zeros(9, dtype=torch.float32, device="cuda")
+    with pytest.raises(bls.BLSError) as ei:
+        bls.search_static(ok, peaks=peaks, spectrum=short)           # 10 frequencies
     assert ei.value.status == bls.ERR_INVALID
