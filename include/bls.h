@@ -234,6 +234,9 @@ bls_status bls_search_shapes(bls_plan* plan, const bls_curve* curves, int ncurve
 /* Serving: queue one curve.  The input is copied before the call returns; the call
  * never waits for the GPU.  Requests are admitted to the device as memory and slots
  * free up and share the GPU with requests already running (continuous batching).
+ * Plans of the other algorithms (BLS_ALGO_PLAIN_F64, BLS_ALGO_UNBINNED) are served
+ * sequentially through the same queue: one request at a time, oldest first, each run as
+ * one search of one curve (a search error fails that request only).
  * *ticket identifies the request.  Errors: BLS_ERR_INVALID, BLS_ERR_NOMEM. */
 bls_status bls_submit(bls_plan* plan, const bls_curve* curve, uint64_t* ticket);
 

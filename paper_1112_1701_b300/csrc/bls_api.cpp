@@ -708,6 +708,14 @@ bls_status search_impl(bls_plan_impl* P, const bls_curve* curves, int ncurves, b
 
 }  // namespace
 
+namespace blsgpu {
+bls_status search_one_locked(bls_plan_impl* P, const bls_curve* curve, bls_peak* out)
+{
+    std::lock_guard<std::mutex> lk(P->mu);
+    return search_impl(P, curve, 1, out, nullptr, nullptr);
+}
+}  // namespace blsgpu
+
 // ------------------------------------------------------------------------------ C ABI
 
 extern "C" {

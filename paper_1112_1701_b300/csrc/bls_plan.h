@@ -118,6 +118,9 @@ void order_by_cost(const std::vector<CurveSpec>& cs, const std::vector<int>& idx
                    std::vector<int>* out);
 
 void server_destroy(bls_plan_impl* P);
+// One curve searched as bls_search does (the plan's lock held for the call); the server's
+// sequential mode runs a plain or unbinned request this way.
+bls_status search_one_locked(bls_plan_impl* P, const bls_curve* curve, bls_peak* out);
 
 }  // namespace blsgpu
 

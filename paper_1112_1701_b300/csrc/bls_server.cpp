@@ -13,8 +13,13 @@
 // host finishes k-1 and prepares k+1.  Admission copies run on a copy stream (the curve
 // arrays are pageable) that the compute stream waits for.  Requests that arrive while
 // others are on the GPU join at the next step, so their work overlaps on the device
-// (iteration-level continuous batching); no kernel waits on the host.  The per-frequency arithmetic is the batched search's, so a request's result is
-// the same alone and in a mix.
+// (iteration-level continuous batching); no kernel waits on the host.  The per-frequency
+// arithmetic is the batched search's, so a request's result is the same alone and in a mix.
+//
+// Plans of the other algorithms (the plain FP64 baseline, the unbinned search) are served
+// sequentially through the same queue: the scheduler takes the oldest request, runs it as
+// one search of one curve, and retires it before taking the next -- first come, first
+// served, no batching, which is how a one-curve-per-launch code serves a stream.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -52,6 +57,7 @@ struct Request {
     std::vector<double> t, freqs;
     std::vector<float> y, dy;
     CurveSpec spec{};
+    bls_curve src{};              // the submitted descriptor, pointing at the copies above
     FoldGeom geom{};
     size_t bytes = 0;
     void* dmem = nullptr;
@@ -109,6 +115,7 @@ struct Server {
 
     void run();
     bool step();
+    bool step_sequential();
     bool retire_inflight();
     void fail_all(const std::string& why);
 };
@@ -143,9 +150,52 @@ void Server::run()
     }
 }
 
+// One request of a sequentially served plan: the oldest queued one, searched alone.
+bool Server::step_sequential()
+{
+    Request* r = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (queue.empty()) return true;
+        r = queue.front();
+        queue.pop_front();
+        r->state = RState::Active;
+        r->t_admit = now_ms();
+    }
+    std::vector<bls_peak> pk((size_t)P->d.topk);
+    const bls_status st = search_one_locked(P, &r->src, pk.data());
+    const std::string why = st == BLS_OK ? std::string() : std::string(bls_last_error());
+    std::lock_guard<std::mutex> lk(mu);
+    if (r->cancel) {
+        r->state = RState::Cancelled;
+        r->status = BLS_ERR_CANCELLED;
+        ++cancelled;
+    } else if (st == BLS_OK) {
+        r->peaks = std::move(pk);
+        r->state = RState::Done;
+        r->status = BLS_OK;
+        ++completed;
+    } else {
+        r->state = RState::Failed;
+        r->status = st;
+        r->error = why;
+        ++failed;
+    }
+    r->t_done = now_ms();
+    latencies.push_back(r->t_done - r->t_submit);
+    ++steps;
+    r->t.clear(); r->t.shrink_to_fit();
+    r->y.clear(); r->y.shrink_to_fit();
+    r->dy.clear(); r->dy.shrink_to_fit();
+    r->freqs.clear(); r->freqs.shrink_to_fit();
+    cv_done.notify_all();
+    return true;
+}
+
 // One scheduler step; returns false when the device failed.
 bool Server::step()
 {
+    if (P->d.algo != BLS_ALGO_TILED) return step_sequential();
     cudaError_t e;
     std::vector<Request*> admitted, retire_cancel;
     {
@@ -532,7 +582,7 @@ extern "C" {
 bls_status bls_submit(bls_plan* P, const bls_curve* c, uint64_t* ticket)
 {
     if (!P || !c || !ticket) return set_error(BLS_ERR_INVALID, "NULL argument");
-    if (P->d.algo != BLS_ALGO_TILED) return set_error(BLS_ERR_INVALID, "serving needs the tiled algorithm");
+    const bool sequential = P->d.algo != BLS_ALGO_TILED;
     cudaError_t e = cudaSetDevice(P->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     CurveSpec s;
@@ -568,18 +618,25 @@ bls_status bls_submit(bls_plan* P, const bls_curve* c, uint64_t* ticket)
     r->spec.y = r->y.data();
     r->spec.dy = s.dy ? r->dy.data() : nullptr;
     r->spec.freqs = s.freqs ? r->freqs.data() : nullptr;
-    if ((st = fold_geometry(P, s.nb, s.kmin, s.kmax, &r->geom)) != BLS_OK) { delete r; return st; }
-    const long long n2 = (s.n + 1) & ~1;
-    r->bytes = up256((size_t)s.n * 8) + up256((size_t)s.n * 4) + (s.dy ? up256((size_t)s.n * 4) : 0) +
-               (s.freqs ? up256((size_t)s.nf * 8) : 0) + up256((size_t)(n2 + 2) * 16) +
-               up256((size_t)(n2 + 2) * 8) + up256((size_t)s.nf * 4);
-    if (r->bytes > P->budget) {
-        const size_t need = r->bytes;
-        delete r;
-        return set_error(BLS_ERR_NOMEM, "the request needs %zu device bytes, over the plan's budget", need);
+    r->src = *c;
+    r->src.t = r->t.data();
+    r->src.y = r->y.data();
+    r->src.dy = s.dy ? r->dy.data() : nullptr;
+    r->src.freqs = s.freqs ? r->freqs.data() : nullptr;
+    if (!sequential) {
+        if ((st = fold_geometry(P, s.nb, s.kmin, s.kmax, &r->geom)) != BLS_OK) { delete r; return st; }
+        const long long n2 = (s.n + 1) & ~1;
+        r->bytes = up256((size_t)s.n * 8) + up256((size_t)s.n * 4) + (s.dy ? up256((size_t)s.n * 4) : 0) +
+                   (s.freqs ? up256((size_t)s.nf * 8) : 0) + up256((size_t)(n2 + 2) * 16) +
+                   up256((size_t)(n2 + 2) * 8) + up256((size_t)s.nf * 4);
+        if (r->bytes > P->budget) {
+            const size_t need = r->bytes;
+            delete r;
+            return set_error(BLS_ERR_NOMEM, "the request needs %zu device bytes, over the plan's budget", need);
+        }
+        r->ntiles = (s.nf + r->geom.T - 1) / r->geom.T;
+        r->tile_cost = (double)r->geom.T * ((double)s.n + kEvalCost * (double)s.nb * (double)(s.kmax - s.kmin + 1));
     }
-    r->ntiles = (s.nf + r->geom.T - 1) / r->geom.T;
-    r->tile_cost = (double)r->geom.T * ((double)s.n + kEvalCost * (double)s.nb * (double)(s.kmax - s.kmin + 1));
     Server* S = nullptr;
     if ((st = server_start(P, &S)) != BLS_OK) { delete r; return st; }
     {

@@ -53,6 +53,40 @@ def test_served_results_equal_results_alone():
             assert not diff, (diff, alone[diff], pk[diff])
 
 
+def test_plain_and_unbinned_plans_are_served_sequentially():
+    """Plans of the plain FP64 baseline and of the unbinned search take requests through
+    the same queue, one at a time, oldest first: each served result equals the same plan's
+    bls_search of that curve bit for bit, and a request the algorithm refuses fails alone."""
+    reqs = _requests(5, seed=11)
+    for algo in ("plain_f64", "unbinned"):
+        with bls.Plan(nb=200, topk=2, algo=algo) as p:
+            tickets = [p.submit(ci) for ci in reqs]
+            served = []
+            for tk in tickets:
+                st, pk = p.poll(tk, timeout_ms=WAIT)
+                assert st == bls.OK
+                served.append(pk)
+            stats = p.stats()
+            assert stats["completed"] == len(reqs) and stats["steps"] == len(reqs)
+            for ci, pk in zip(reqs, served):
+                alone = p.search([ci])[0]
+                diff = [f for f in bls.PEAK_DTYPE.names if not np.array_equal(alone[f], pk[f])]
+                assert not diff, (algo, diff)
+    # the unbinned search refuses curves above its point limit: that request fails, the
+    # next one is served
+    rng = np.random.default_rng(2)
+    t = synth.T0 + np.sort(rng.uniform(0, 30, 40000))
+    big = bls.CurveInput(t, np.ones(len(t), np.float32), None, nf=100, fmin=0.2, df=0.01,
+                         nb=200, qmin=0.005, qmax=0.15)
+    with bls.Plan(nb=200, algo="unbinned") as p:
+        tb = p.submit(big)
+        tg = p.submit(reqs[1])
+        with pytest.raises(bls.BLSError):
+            p.poll(tb, timeout_ms=WAIT)
+        st, _ = p.poll(tg, timeout_ms=WAIT)
+        assert st == bls.OK
+
+
 def test_admission_respects_memory_budget():
     reqs = _requests(10, seed=7)
     # room for a few requests at a time: each needs ~40 B per point + 4 B per frequency
