@@ -1488,12 +1488,14 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
 // ------------------------------------------------------------------------- a2-a6: warp-specialised
 
 // Variant of the hot kernel in which binning and sweeping overlap.  The block has two warp
-// groups (T a multiple of 32, at most 128):
+// groups (T a multiple of 8, at most 128; the T columns are spread evenly over the four SM
+// sub-partitions, C = T/4 per warp, lanes past C shadowing the warp's first column):
 //
-//   binning group (T threads, warps 0 .. T/32-1): zeroes its warps' histogram columns,
-//     stages the points, folds and bins tile i into the private shared-memory histograms
-//     (one column per frequency), then hands them over;
-//   sweep group (the other warps): copies column c of tile i into its TMEM lane (bins
+//   binning group (warps 0-3): zeroes its warps' histogram columns, stages the points,
+//     folds and bins tile i into the private shared-memory histograms (one column per
+//     frequency), then hands them over;
+//   sweep group (warps 4-11, two threads per column on the column's TMEM lane quadrant):
+//     copies column c of tile i into its TMEM lane (bins
 //     laid out linearly, the first bins repeated past nb; the two sweep threads of a
 //     column copy interleaved groups of bins and only read the histograms), hands the
 //     histograms back, then sweeps the boxes of tile i from TMEM while the
@@ -1610,8 +1612,8 @@ struct TmemStream {
 
 // Sweep of one column from its TMEM copy, all lanes of the warp together.
 // Both blocks take the signed-residue form here: it issues fewer instructions per box than
-// the shared-reciprocal form and leans on the special-function unit, which the binning
-// warps sharing the SM sub-partitions do not use.
+// the shared-reciprocal form or a division-free threshold test, and leans on the
+// special-function unit, which the binning warps sharing the SM sub-partitions do not use.
 template <int SB, int SIGN, bool WRAP>
 __device__ __forceinline__ float sweep_tmem(unsigned tbase, int nb, int kmin, int kmax, int part,
                                             int nparts)
@@ -1686,12 +1688,15 @@ __device__ void fetch_tile(const FoldParams& p, TileSlot* slot, int lane)
     }
 }
 
-// The sweep group's loop of fold_sweep_ws_kernel: threads sg0 .. sg0 + NS - 1, NS = T x
-// nparts, two parts sharing each column when NS = 2T.  Its first warp claims the work items
-// and writes the tile descriptors ahead; per tile it copies the histograms into TMEM, hands
-// them back (the binning group zeroes them) and sweeps the boxes from TMEM.
+// The sweep group's loop of fold_sweep_ws_kernel: warps 4-7 (part 0) and 8-11 (part 1),
+// the two threads of a column in warps of the same TMEM lane quadrant; lane_ok is false
+// for a lane that shadows its warp's first column.  Warp 4 claims the work items and
+// writes the tile descriptors ahead; per tile the group copies the histograms into TMEM,
+// hands them back (the binning group zeroes them) and sweeps the boxes from TMEM.
+constexpr int kWsBinThreads = 128, kWsSweepThreads = 256, kWsSweep0 = 128;
+
 template <int SIGN>
-__device__ __forceinline__ void sweep_group_loop(const FoldParams& p, int sg0, int NS, int col,
+__device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_ok, int col,
                                                  unsigned s_tmem, TileSlot* s_slot,
                                                  unsigned full_bar, unsigned empty_bar,
                                                  float* s_wpart, float* s_wpart2,
@@ -1700,9 +1705,10 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, int sg0, i
 {
     const int T = p.cols;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // nparts threads per column (warps of one TMEM lane quadrant when there are two)
-    const int nparts = NS / T;
-    const int part = (tid - sg0) / T;
+    const int NS = kWsSweepThreads, sg0 = kWsSweep0;
+    // nparts = 2 threads per column, in warps of one TMEM lane quadrant
+    const int nparts = 2;
+    const int part = (warp - sg0 / 32) >> 2;
     const unsigned tbase = s_tmem + ((unsigned)((warp & 3) * 32) << 16);
     const bool fetcher = warp == sg0 / 32;
     unsigned ph = 0;
@@ -1725,7 +1731,7 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, int sg0, i
         const int nf = sl.cd.nf, nb = sl.cd.nb, kmin = sl.cd.kmin, kmax = sl.cd.kmax;
         float* const res = sl.cd.res;
         const int j = tile * T + col;
-        const bool active = j < nf;
+        const bool active = lane_ok && j < nf;
         const int SB = sweep_block(nb, kmin, kmax);
         const int tmode = ws_tmem_mode(nb, kmin, kmax);
         const bool use_tmem = tmode != 0;
@@ -1752,7 +1758,7 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, int sg0, i
                 }
                 tmem_st16(tbase + 2u * (unsigned)g, r);
             }
-            if (part == 1) s_wpart[col] = wmax;
+            if (part == 1 && lane_ok) s_wpart[col] = wmax;
             tmem_wait_st();
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         } else if (part == 0) {
@@ -1806,7 +1812,7 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, int sg0, i
                      : SB == 10 ? sweep_tmem<10, SIGN, true>(tbase, nb, kmin, kmax, part, nparts)
                                 : sweep_tmem<8, SIGN, true>(tbase, nb, kmin, kmax, part, nparts);
             if (nparts == 2) {   // the parts' maxima meet in shared memory
-                if (part == 1) s_wpart2[col] = vf;
+                if (part == 1 && lane_ok) s_wpart2[col] = vf;
                 group_sync(kBarSweep, NS);
                 if (part == 0) vf = fmaxf(vf, s_wpart2[col]);
             }
@@ -1832,8 +1838,16 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
     const int T = p.cols;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const bool binner = tid < T;
-    const int col = binner ? tid : (tid - T) % T;
+    // The T columns are spread evenly over the four SM sub-partitions: C = T/4 per TMEM
+    // lane quadrant.  Binning warps 0-3 and sweep warps 4-7 (part 0) and 8-11 (part 1):
+    // lane l < C of a warp on quadrant q = warp & 3 owns column q C + l, and both sweep
+    // threads of a column run on the quadrant where its histogram is copied.  Lanes l >= C
+    // (T < 128) shadow their warp's first column: they execute the warp-wide instructions
+    // alongside it and write nothing.
+    const int C = T / 4;
+    const bool binner = warp < 4;
+    const bool lane_ok = lane < C;
+    const int col = (warp & 3) * C + (lane_ok ? lane : 0);
     const int CH = p.chunk;
     float4* cpts = reinterpret_cast<float4*>(smem);             // [2][CH]: point pairs
     double* cdt = reinterpret_cast<double*>(cpts + 2 * CH);     // [2][CH]: FP64 offsets
@@ -1853,7 +1867,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
         u64* h = reinterpret_cast<u64*>(hist_all);
         for (size_t e = tid; e < rows * S; e += blockDim.x) h[e] = 0ull;
     }
-    if (warp == T / 32) {
+    if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"((unsigned)__cvta_generic_to_shared(&s_tmem)), "r"(kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -1875,7 +1889,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                 if (give_up) atomicOr(p.err, kErrTimeout);
             }
             ph ^= 1u;
-            give_up = group_or(kBarBin, T, give_up);
+            give_up = group_or(kBarBin, kWsBinThreads, give_up);
             const TileSlot& sl = s_slot[k & 1];
             if (give_up || sl.stop) {
                 if (tid == 0) mbar_arrive(full_bar);   // the sweep group reads the stop
@@ -1884,21 +1898,16 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             const CurveDesc cdr = sl.cd;
             const int tile = sl.tile;
             const int n = cdr.n, nf = cdr.nf, nb = cdr.nb;
-            {   // zero this warp's 32 histogram columns (16 B per lane, two rows per store);
-                // the sweep group has finished reading them (the empty hand-over above)
-                const unsigned zb = (unsigned)__cvta_generic_to_shared(hist_all) +
-                                    (unsigned)(warp * 32) * 8u + (unsigned)(lane & 15) * 16u;
-                for (int b = lane >> 4; b < nb; b += 2) {
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %1, %1, %1};"
-                                 ::"r"(zb + (unsigned)b * rowb), "r"(0u));
-                }
-                __syncwarp();
+            if (lane_ok) {   // zero this thread's histogram column; the sweep group has
+                             // finished reading it (the empty hand-over above)
+                for (int b = 0; b < nb; ++b) sts64(hbase + (unsigned)b * rowb, 0ull);
             }
+            __syncwarp();
             const float4* gpts = cdr.pts;
             const double* gdt = cdr.dt64;
             const int j = tile * T + col;
-            const bool active = j < nf;
-            const int jt = active ? j : nf - 1;
+            const bool active = lane_ok && j < nf;
+            const int jt = j < nf ? j : nf - 1;
             const double f = grid_freq(cdr, jt);
             FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs);
             // FX64 tiles of a uniform grid take the incremental fold, with the tile's middle
@@ -1918,11 +1927,11 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                 const int cpad = (cn + 15) & ~15;
                 float4* dp = cpts + (ci & 1) * CH;
                 double* dd = cdt + (ci & 1) * CH;
-                for (int i = tid; i < cn; i += T) {
+                for (int i = tid; i < cn; i += kWsBinThreads) {
                     cp_async16(&dp[i], &gpts[c0 + i]);
                     cp_async8(&dd[i], &gdt[c0 + i]);
                 }
-                for (int i = cn + tid; i < cpad; i += T) {
+                for (int i = cn + tid; i < cpad; i += kWsBinThreads) {
                     dp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
                     dd[i] = 0.0;
                 }
@@ -1939,7 +1948,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                     // below is measurably faster with this form)
                     float4* dp = cpts + (ci & 1) * CH;
                     const int cn = (min(CH, n - ci * CH) + 1) & ~1;
-                    for (int i = tid; i < cn; i += T) {
+                    for (int i = tid; i < cn; i += kWsBinThreads) {
                         const float4 A = dp[i];
                         unsigned Q0, D0, Q1, D1;
                         inc_point(__float_as_uint(A.x), __float_as_uint(A.z), fc, Q0, D0);
@@ -1948,7 +1957,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                                             __uint_as_float(D0), __uint_as_float(D1));
                     }
                 }
-                group_sync(kBarBin, T);
+                group_sync(kBarBin, kWsBinThreads);
                 const int cnum = min(CH, n - ci * CH);
                 const float4* cp = cpts + (ci & 1) * CH;
                 const double* cd = cdt + (ci & 1) * CH;
@@ -1961,25 +1970,25 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                     } else
                         bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
                 }
-                group_sync(kBarBin, T);
+                group_sync(kBarBin, kWsBinThreads);
             }
             if (tid == 0) mbar_arrive(full_bar);
         }
     } else {
-        sweep_group_loop<SIGN>(p, T, blockDim.x - T, col, s_tmem, s_slot, full_bar, empty_bar,
-                               s_wpart, s_wpart2, hist, hbase, rowb);
+        sweep_group_loop<SIGN>(p, lane_ok, col, s_tmem, s_slot, full_bar, empty_bar, s_wpart,
+                               s_wpart2, hist, hbase, rowb);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == T / 32) {
+    if (warp == 4) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem),
                      "r"(kTmemCols) : "memory");
     }
 }
 
-// Tile geometries the warp-specialised kernel can take: plain sums, T a multiple of 32, at
-// most 128 (one binning thread per TMEM lane).  BLS_FOLD_WS=0 in the environment selects
+// Tile geometries the warp-specialised kernel can take: plain sums, T a multiple of 8, at
+// most 128 (T/4 columns per TMEM lane quadrant).  BLS_FOLD_WS=0 in the environment selects
 // fold_sweep_kernel for every class.
 static bool use_ws(int T, int kahan)
 {
@@ -1987,25 +1996,24 @@ static bool use_ws(int T, int kahan)
         const char* e = getenv("BLS_FOLD_WS");
         return (e && e[0] == '0') ? 0 : 1;
     }();
-    return env && !kahan && T % 32 == 0 && T >= 32 && T <= 128;
+    return env && !kahan && T % 8 == 0 && T >= 8 && T <= 128;
 }
 
-// Threads of a warp-specialised block: T binning threads, and T sweep threads per column
-// part (two parts when T = 128, whose two sweep warps per TMEM lane quadrant share the
-// lanes; otherwise one).
-static int ws_threads(int T) { return T == 128 ? 3 * T : 2 * T; }
+// Threads of a warp-specialised block: binning warps 0-3, sweep warps 4-11, whatever the
+// tile width (T/4 columns per warp).
+static int ws_threads(int) { return kWsMaxThreads; }
 
 // Frequencies per tile, given the most whose histograms fit (a multiple of 16, at most 256):
-// where the warp-specialised kernel applies, the widest multiple of 32 up to 128 below it.
+// where the warp-specialised kernel applies, that width itself up to 128, else 128.
 // Measured on 256 curves x 20k frequencies: nb = 150, 160 columns (one-group kernel, one
-// thread per column) 21.8 ms against 14.8 ms at 128 (warp-specialised); nb = 210, 112
-// columns 25.5 ms against 23.6 ms at 96.  256 columns (nb <= 100) keep the one-group kernel,
-// whose eight binning warps then win (11.5 ms against 13.1 ms at nb = 100).
+// thread per column) 21.8 ms against 14.8 ms at 128 (warp-specialised).  256 columns
+// (nb <= 100) keep the one-group kernel, whose eight binning warps then win (11.5 ms
+// against 13.1 ms at nb = 100).
 int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax, int choice)
 {
     if (tmax >= 256) return tmax;
-    const int T32 = tmax > 128 ? 128 : tmax & ~31;
-    if (T32 >= 32 && T32 != tmax && fold_use_ws(T32, kahan, nb, kmin, kmax, choice)) return T32;
+    const int Tw = tmax > 128 ? 128 : tmax & ~7;
+    if (Tw >= 8 && fold_use_ws(Tw, kahan, nb, kmin, kmax, choice)) return Tw;
     return tmax;
 }
 

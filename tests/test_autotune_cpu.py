@@ -22,7 +22,7 @@ def test_candidates_fit_shared_memory_and_kernel_rules():
         assert c.freqs_per_block % 16 == 0 and 16 <= c.freqs_per_block <= 256
         assert 2 * c.point_chunk * 24 + 2048 + c.freqs_per_block * 200 * 8 <= 232448
         if c.fold_kernel == "ws":
-            assert c.freqs_per_block % 32 == 0 and c.freqs_per_block <= 128
+            assert c.freqs_per_block % 8 == 0 and c.freqs_per_block <= 128
     widths = {c.freqs_per_block for c in cands if c.point_chunk == 512}
     assert max(widths) == 128 and 96 in widths and 64 in widths
     assert any(c.fold_kernel == "ws" and c.freqs_per_block == 128 for c in cands)
