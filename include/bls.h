@@ -179,6 +179,13 @@ void bls_plan_destroy(bls_plan* plan);
  * (finite t and y, finite dy > 0, explicit frequencies > 0) are checked on the device on
  * the copies, for host and device inputs alike, and a bad value makes the call return
  * BLS_ERR_INVALID after the launch group ran (its outputs are then undefined).
+ * BLS_ERR_INTERNAL: a device-side consistency check failed -- a bounded wait between the
+ * warp groups of the hot kernel gave up (limit 30 s; the test setting BLS_HANDOFF_LIMIT_US,
+ * in microseconds, read at every launch group, lowers it), or, in libbls_debug.so (the same
+ * library with device-side checks on every histogram bin, shared-memory row and TMEM column
+ * index, built beside libbls.so), an index check failed and the access was skipped.  The
+ * plan stays usable after either.  Host-side NVTX ranges (bls.search, bls.prep,
+ * bls.fold_sweep, bls.reduce, bls.server.step, bls.server.retire) mark the calls' phases.
  * Errors: BLS_ERR_INVALID, BLS_ERR_NOMEM, BLS_ERR_CUDA, BLS_ERR_INTERNAL. */
 bls_status bls_search(bls_plan* plan, const bls_curve* curves, int ncurves,
                       bls_peak* out, float* spectrum);
@@ -269,8 +276,9 @@ bls_status bls_kminmax(int nb, double qmin, double qmax, int* kmin, int* kmax);
 
 /* Diagnostic: the phase bin of every point of one curve at frequencies js[0..nj), as
  * the search kernels compute them (plan's phase mode); bins_out[q*n + i] (host).  In the
- * FX64 mode on a uniform grid the incremental fold of the warp-specialised kernel is
- * evaluated too (frequency js[q] at its place in a 128-frequency tile); a point where it
+ * FX64 mode on a uniform grid with plain sums the incremental fold of the search kernels
+ * is evaluated too, for frequency js[q] at its place in a tile of the width the plan's
+ * search uses for this curve (so with the search's reference column); a point where it
  * disagrees with the direct fold is reported as -1 - bin, so every value is a valid bin
  * exactly when both folds agree.  Errors: BLS_ERR_INVALID, BLS_ERR_CUDA. */
 bls_status bls_debug_fold(bls_plan* plan, const bls_curve* curve, const int* js, int nj,

@@ -18,7 +18,9 @@ from typing import Iterable, List, Optional, Sequence
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libbls.so")
+# BLS_DEBUG=1 in the environment (read when the library is first loaded) selects the build
+# with device-side index checks, whose failures make a call return ERR_INTERNAL.
+LIB_PATH = os.path.join(_PKG, "libbls_debug.so" if os.environ.get("BLS_DEBUG") == "1" else "libbls.so")
 
 OK, PENDING = 0, 1
 ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL, ERR_CANCELLED = -1, -2, -3, -4, -5, -6

@@ -8,6 +8,8 @@
 #include <cstring>
 #include <numeric>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bls_plan.h"
 
 using namespace blsgpu;
@@ -25,6 +27,23 @@ bls_status set_error(bls_status s, const char* fmt, ...)
     va_end(ap);
     g_last_error = buf;
     return s;
+}
+
+unsigned long long handoff_limit_ns()
+{
+    if (const char* v = getenv("BLS_HANDOFF_LIMIT_US")) {
+        const long long us = atoll(v);
+        if (us > 0) return (unsigned long long)us * 1000ull;
+    }
+    return 30ull * 1000000000ull;
+}
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
+void NvtxRange::next(const char* name)
+{
+    nvtxRangePop();
+    nvtxRangePushA(name);
 }
 
 bls_status cuda_fail(cudaError_t e, const char* what)
@@ -436,6 +455,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         up.sign = P->d.sign;
         up.qmin = P->d.qmin;
         up.qmax = P->d.qmax;
+        up.err = P->err.as<int>();
         up.nmax = nmax;
         up.M = 1;
         while (up.M < nmax) up.M <<= 1;
@@ -459,6 +479,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         int nbmax = 2;
         for (int c = 0; c < nc; ++c) nbmax = std::max(nbmax, specs[g0 + c].nb);
         rp.smem_bytes = reduce_smem_bytes(nbmax, topk, rp.kahan);
+        rp.err = P->err.as<int>();
     }
     rp.spectrum = spectrum ? (spectrum_dev ? spectrum : P->spec.as<float>()) : nullptr;
     const bool prof = P->ev[0] != nullptr;
@@ -472,6 +493,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         if (capturing) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
         else cudaEventRecord(ev, st);
     };
+    const unsigned long long wait_ns = handoff_limit_ns();
     auto enqueue = [&]() -> cudaError_t {
         cudaError_t x;
         launches = 0;
@@ -482,12 +504,13 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
             return x;
         if ((x = cudaMemsetAsync(P->err.p, 0, 64, st)) != cudaSuccess) return x;
         if (prof) record(P->ev[0]);
-        // (the unbinned search reads the fixed-point offsets of the FX64 layout)
+        NvtxRange r_prep("bls.prep");   // then fold_sweep, reduce (host enqueue spans)
         if ((x = launch_prep(P->cdesc.as<CurveDesc>(), nullptr, nc, P->err.as<int>(),
                              unbinned ? kPhaseFX64 : P->d.phase, st)) != cudaSuccess)
             return x;
         ++launches;
         if (prof) record(P->ev[1]);
+        r_prep.next("bls.fold_sweep");
         if (tiled) {
             if ((x = cudaMemcpyAsync(P->ranges.p, P->h_ranges.p, nr * sizeof(TileRange), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
                 (x = cudaMemcpyAsync(P->prefix.p, P->h_prefix.p, pp * sizeof(long long), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
@@ -504,6 +527,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
                 fp.err = P->err.as<int>();
                 fp.chunk = geoms[q].chunk;
                 fp.stride = geoms[q].stride;
+                fp.wait_ns = wait_ns;
                 if ((x = launch_fold_sweep(fp, geoms[q].T, grids[q], P->d.phase, P->d.sum == BLS_SUM_KAHAN,
                                            geoms[q].ws, P->d.sign, geoms[q].smem, st)) != cudaSuccess)
                     return x;
@@ -529,6 +553,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
             }
         }
         if (prof) record(P->ev[2]);
+        r_prep.next("bls.reduce");
         if ((x = unbinned ? launch_ubls_reduce(up, st) : launch_reduce(rp, nc, st)) != cudaSuccess) return x;
         ++launches;
         if (shape) {
@@ -570,6 +595,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         for (const Copy& cp : copies) put(&cp, sizeof(cp));
         put(&spectrum, sizeof(spectrum));
         put(&P->d, sizeof(P->d));
+        put(&wait_ns, sizeof(wait_ns));
         const int shp[3] = {shape ? shape->nc : 0, shape ? shape->nw : 0, shape ? shape->na : 0};
         const double shd[3] = {shape ? shape->wlo : 0.0, shape ? shape->whi : 0.0, shape ? shape->amax : 0.0};
         put(shp, sizeof(shp));
@@ -838,6 +864,7 @@ bls_status bls_profile_get(bls_plan* P, bls_profile* out, int reset)
 bls_status bls_search(bls_plan* P, const bls_curve* curves, int ncurves, bls_peak* out, float* spectrum)
 {
     if (!P) return set_error(BLS_ERR_INVALID, "NULL plan");
+    NvtxRange r("bls.search");
     std::lock_guard<std::mutex> lk(P->mu);
     return search_impl(P, curves, ncurves, out, spectrum, nullptr);
 }
@@ -973,7 +1000,16 @@ bls_status bls_debug_fold(bls_plan* P, const bls_curve* curve, const int* js, in
     if ((e = P->binsbuf.ensure((size_t)nj * s.n * 4)) != cudaSuccess) return cuda_fail(e, "allocating");
     if ((e = cudaMemcpyAsync(P->jsbuf.p, js, (size_t)nj * 4, cudaMemcpyHostToDevice, P->stream)) != cudaSuccess)
         return cuda_fail(e, "copy");
-    if ((e = launch_debug_fold(P->cdesc.as<CurveDesc>(), P->jsbuf.as<int>(), nj, P->d.phase,
+    // the tile width the search used for this curve (the incremental fold's reference
+    // column depends on it)
+    FoldGeom g;
+    if (P->d.algo == BLS_ALGO_TILED) {
+        if ((st = fold_geometry(P, s.nb, s.kmin, s.kmax, &g)) != BLS_OK) return st;
+    } else {
+        g.T = 1;   // no tiles: the incremental fold is not used
+    }
+    if ((e = launch_debug_fold(P->cdesc.as<CurveDesc>(), P->jsbuf.as<int>(), nj, P->d.phase, g.T,
+                               P->d.algo == BLS_ALGO_TILED ? P->d.sum == BLS_SUM_KAHAN : 1,
                                P->binsbuf.as<int>(), P->stream)) != cudaSuccess)
         return cuda_fail(e, "debug fold launch");
     if ((e = cudaMemcpyAsync(bins_out, P->binsbuf.p, (size_t)nj * s.n * 4, cudaMemcpyDeviceToHost, P->stream)) != cudaSuccess)

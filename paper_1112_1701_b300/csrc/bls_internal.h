@@ -55,6 +55,22 @@ enum : int {
     kErrTimeout = 4,    // a bounded wait between a kernel's warp groups gave up
 };
 
+// Device-side index checks of the BLS_DEBUG build (libbls_debug.so): bls_ok(cond, err)
+// records kErrBounds in the error word when cond is false and returns cond, so the caller
+// skips or redirects the access; the search then fails with BLS_ERR_INTERNAL.  In the
+// regular build it is the constant true and the check compiles away.
+#ifdef __CUDACC__
+#ifdef BLS_DEBUG
+__device__ __forceinline__ bool bls_ok(bool cond, int* err)
+{
+    if (!cond && err) atomicOr(err, kErrBounds);
+    return cond;
+}
+#else
+__device__ __forceinline__ constexpr bool bls_ok(bool, int*) { return true; }
+#endif
+#endif
+
 // Shared memory per fold-sweep block kept free for the kernels' static arrays (the
 // warp-specialised kernel's hand-over slots and partial maxima).
 constexpr size_t kFoldSmemReserve = 2048;
@@ -70,6 +86,7 @@ struct FoldParams {
     int chunk;                 // points per staged chunk (a multiple of 16)
     int stride;                // histogram stride in entries (multiple of 16, >= cols)
     int cols;                  // frequencies per tile (set by launch_fold_sweep)
+    unsigned long long wait_ns;   // limit of each warp-group hand-over wait (0: 30 s)
 };
 
 // Trapezoid refit of a peak (same layout as bls_shape).
@@ -100,6 +117,7 @@ struct UblsParams {
     int topk, sign;
     double qmin, qmax;              // run extent bounds, in cycles
     int nmax, M;                    // largest curve of the group and the power of two >= it
+    int* err;                       // error word (index checks of the BLS_DEBUG build)
 };
 
 cudaError_t launch_ubls(const UblsParams& p, long long nitems, cudaStream_t s);
@@ -117,6 +135,7 @@ struct ReduceParams {
     int phase;                 // fold mode of the search (for the best-box recomputation)
     int kahan;                 // Kahan histograms
     size_t smem_bytes;         // dynamic shared memory of the launch (reduce_smem_bytes)
+    int* err;                  // error word (index checks of the BLS_DEBUG build)
 };
 
 // Shared memory a fold-sweep block needs.
@@ -131,8 +150,9 @@ size_t reduce_smem_bytes(int nb_max, int topk, int kahan);
 // Diagnostics: (P, i1, k) of the best box at every frequency of one prepared curve.
 cudaError_t launch_argmax(const CurveDesc* d_curve, int nb, int nf, int phase, int kahan,
                           int sign, float* P, int* i1, int* k, cudaStream_t s);
+// T, kahan: the tile width and sum mode the plan's search uses for this curve.
 cudaError_t launch_debug_fold(const CurveDesc* d_curve, const int* js, int nj, int phase,
-                              int* bins, cudaStream_t s);
+                              int T, int kahan, int* bins, cudaStream_t s);
 // Baseline: one curve, one thread per frequency, FP64 histograms in global scratch.
 cudaError_t launch_plain_f64(const CurveDesc* d_curve, const double* w64, const double* wx64,
                              int nf, double* hist, int sign, cudaStream_t s);

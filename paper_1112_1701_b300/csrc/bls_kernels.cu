@@ -694,7 +694,7 @@ __device__ __forceinline__ void fix_sub(const float4* cp, const double* cd, cons
 constexpr int kRmwGroup = 4;
 
 __device__ __forceinline__ void rmw_sub(unsigned hbase, unsigned rowb, const unsigned* b,
-                                        const float4* Bw)
+                                        const float4* Bw, unsigned nbu, int* err)
 {
     constexpr int G = kRmwGroup;
 #pragma unroll
@@ -704,7 +704,7 @@ __device__ __forceinline__ void rmw_sub(unsigned hbase, unsigned rowb, const uns
         u64 h[G], q[G];
 #pragma unroll
         for (int i = 0; i < G; ++i) {
-            a[i] = hbase + bg[i] * rowb;
+            a[i] = hbase + (bls_ok(bg[i] < nbu, err) ? bg[i] : 0u) * rowb;
             h[i] = lds64(a[i]);
         }
 #pragma unroll
@@ -732,8 +732,9 @@ __device__ __forceinline__ void rmw_sub(unsigned hbase, unsigned rowb, const uns
 template <int PHASE, bool PINGPONG, bool INC>
 __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int nsub,
                                          unsigned hbase, unsigned rowb, const FoldConst& fc,
-                                         const FoldPacked& fq)
+                                         const FoldPacked& fq, int* err)
 {
+    const unsigned nbu = (unsigned)fc.nb;
     unsigned b0[16], b1[16];
     float4 W0[8], W1[8];
     if (fold_sub<PHASE, INC>(cp, fc, fq, b0, W0)) fix_sub<PHASE, INC>(cp, cd, fc, fq, b0);
@@ -745,38 +746,40 @@ __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int
         for (; sc + 2 < nsub; sc += 2) {
             const float4* n1 = cp + 16 * (sc + 1);
             const bool e1 = fold_sub<PHASE, INC>(n1, fc, fq, b1, W1);
-            rmw_sub(hbase, rowb, b0, W0);
+            rmw_sub(hbase, rowb, b0, W0, nbu, err);
             if (e1) fix_sub<PHASE, INC>(n1, cd + 16 * (sc + 1), fc, fq, b1);
             const float4* n2 = cp + 16 * (sc + 2);
             const bool e2 = fold_sub<PHASE, INC>(n2, fc, fq, b0, W0);
-            rmw_sub(hbase, rowb, b1, W1);
+            rmw_sub(hbase, rowb, b1, W1, nbu, err);
             if (e2) fix_sub<PHASE, INC>(n2, cd + 16 * (sc + 2), fc, fq, b0);
         }
     }
     for (; sc + 1 < nsub; ++sc) {
         const float4* n1 = cp + 16 * (sc + 1);
         const bool e1 = fold_sub<PHASE, INC>(n1, fc, fq, b1, W1);
-        rmw_sub(hbase, rowb, b0, W0);
+        rmw_sub(hbase, rowb, b0, W0, nbu, err);
         if (e1) fix_sub<PHASE, INC>(n1, cd + 16 * (sc + 1), fc, fq, b1);
 #pragma unroll
         for (int i = 0; i < 16; ++i) b0[i] = b1[i];
 #pragma unroll
         for (int q = 0; q < 8; ++q) W0[q] = W1[q];
     }
-    rmw_sub(hbase, rowb, b0, W0);
+    rmw_sub(hbase, rowb, b0, W0, nbu, err);
 }
 
 // Generic binning (FP64 or FP32 phase modes, precision studies): pair by pair.
 template <int PHASE>
 __device__ __forceinline__ void bin_generic(const float4* cp, const double* cd, int npairs,
                                             unsigned hbase, unsigned rowb, const FoldConst& fc,
-                                            const FoldPacked& fq)
+                                            const FoldPacked& fq, int* err)
 {
     for (int pi = 0; pi < npairs; ++pi) {
         const float4 A = cp[2 * pi], B = cp[2 * pi + 1];
         unsigned b0, b1;
         fold_pair<PHASE>(A, &cd[2 * pi], fc, fq, b0, b1);
-        const unsigned a0 = hbase + b0 * rowb, a1 = hbase + b1 * rowb;
+        const unsigned nbu = (unsigned)fc.nb;
+        const unsigned a0 = hbase + (bls_ok(b0 < nbu, err) ? b0 : 0u) * rowb;
+        const unsigned a1 = hbase + (bls_ok(b1 < nbu, err) ? b1 : 0u) * rowb;
         sts64(a0, add2(lds64(a0), pk(B.x, B.y)));
         sts64(a1, add2(lds64(a1), pk(B.z, B.w)));
     }
@@ -928,9 +931,11 @@ constexpr int kFormB = BLS_SWEEP_MIX;
 struct SmemBins {
     unsigned hbase, rowb;
     int nb, ma, mb;
+    int* err = nullptr;
     __device__ __forceinline__ void start(int a, int b) { ma = a; mb = b; }
     __device__ __forceinline__ void next(float& hwa, float& hxa, float& hwb, float& hxb)
     {
+        if (!bls_ok((unsigned)ma < (unsigned)nb && (unsigned)mb < (unsigned)nb, err)) ma = mb = 0;
         upk(lds64(hbase + (unsigned)ma * rowb), hwa, hxa);
         upk(lds64(hbase + (unsigned)mb * rowb), hwb, hxb);
         ma = (ma + 1 == nb) ? 0 : ma + 1;
@@ -972,8 +977,11 @@ template <bool WRAP>
 struct TmemBins {
     unsigned base, tend, ta, tb;   // tend: column 2 nb (WRAP: the copy holds bins 0..nb-1 only)
     unsigned pa0, pa1, pb0, pb1;
+    int* err = nullptr;
     __device__ __forceinline__ void issue()
     {
+        // the two columns read at ta and at tb lie in the 512-column allocation
+        if (!bls_ok(ta - base <= 510u && tb - base <= 510u, err)) ta = tb = base;
         tmem_ld2(ta, pa0, pa1);
         tmem_ld2(tb, pb0, pb1);
         ta += 2;
@@ -1253,7 +1261,8 @@ __device__ Best sweep_exact_warp(const unsigned char* hist, int stride, int kaha
 // part 0 alone (the others return 0, below any power a box can reach).
 template <int KAHAN, int SIGN, int SB>
 __device__ __forceinline__ float sweep_max(const unsigned char* hist, int stride, int nb,
-                                           int kmin, int kmax, int part, int nparts)
+                                           int kmin, int kmax, int part, int nparts,
+                                           int* err = nullptr)
 {
     if (!KAHAN && kmax - kmin + 1 >= SB - 1) {
         const unsigned hbase = (unsigned)__cvta_generic_to_shared(hist);
@@ -1288,6 +1297,7 @@ __device__ __forceinline__ float sweep_max(const unsigned char* hist, int stride
             src.hbase = hbase;
             src.rowb = rowb;
             src.nb = nb;
+            src.err = err;
             return sweep_fast<SB, SIGN>(src, nb, kmin, kmax, part, nparts);
         }
     }
@@ -1450,16 +1460,17 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
                         const float4 A = cp[2 * pi], B = cp[2 * pi + 1];
                         unsigned b0, b1;
                         fold_pair<PHASE>(A, &cd[2 * pi], fc, fq, b0, b1);
+                        if (!bls_ok(b0 < (unsigned)nb && b1 < (unsigned)nb, p.err)) continue;
                         kahan_add(reinterpret_cast<float4*>(hist) + b0 * S, B.x, B.y);
                         kahan_add(reinterpret_cast<float4*>(hist) + b1 * S, B.z, B.w);
                     }
                 } else if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
                     if (inc)
-                        bin_fast<PHASE, false, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                        bin_fast<PHASE, false, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                     else
-                        bin_fast<PHASE, false, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                        bin_fast<PHASE, false, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                 } else {
-                    bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
+                    bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq, p.err);
                 }
             }
             __syncthreads();
@@ -1470,10 +1481,10 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
         // than the 4 B x blockDim.x <= 1024 B needed)
         float v = 0.0f;
         if (active)
-            v = kmax - kmin + 1 < 15 ? sweep_max<KAHAN, SIGN, 4>(hist, p.stride, nb, kmin, kmax, part, nparts)
+            v = kmax - kmin + 1 < 15 ? sweep_max<KAHAN, SIGN, 4>(hist, p.stride, nb, kmin, kmax, part, nparts, p.err)
                 : wide_sweep_10(nb, nparts)
-                    ? sweep_max<KAHAN, SIGN, 10>(hist, p.stride, nb, kmin, kmax, part, nparts)
-                    : sweep_max<KAHAN, SIGN, 8>(hist, p.stride, nb, kmin, kmax, part, nparts);
+                    ? sweep_max<KAHAN, SIGN, 10>(hist, p.stride, nb, kmin, kmax, part, nparts, p.err)
+                    : sweep_max<KAHAN, SIGN, 8>(hist, p.stride, nb, kmin, kmax, part, nparts, p.err);
         if (nparts == 1) {
             if (active) cdr.res[j] = v;
         } else {
@@ -1516,8 +1527,8 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
 // from fold_sweep_kernel's in the last bits (both are within the approximation's 2^-22).
 //
 // Hand-over: two mbarriers (count 1, arrived by a group's first thread after a group
-// barrier); each wait is bounded in time and, if it gives up, the kernel records
-// kErrTimeout and both groups stop.
+// barrier); each wait is bounded in time (FoldParams::wait_ns, 30 s by default) and, if it
+// gives up, the kernel records kErrTimeout and both groups stop.
 
 constexpr unsigned long long kHandoffTimeoutNs = 30ull * 1000000000ull;
 constexpr int kBarBin = 1, kBarSweep = 2;   // named barriers of the two groups
@@ -1540,23 +1551,24 @@ __device__ __forceinline__ void mbar_arrive(unsigned a)
 // One bounded test: the thread is suspended until the phase completes or about
 // kSuspendNs pass, so a waiting thread takes no issue slots from the working warps.
 constexpr unsigned kSuspendNs = 1000000;
-__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity)
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity, unsigned suspend_ns)
 {
     unsigned ok;
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(a), "r"(parity), "r"(kSuspendNs) : "memory");
+                 : "=r"(ok) : "r"(a), "r"(parity), "r"(suspend_ns) : "memory");
     return ok != 0;
 }
 // Waits until the phase of the given parity has completed; false if it has not within
-// kHandoffTimeoutNs.
-__device__ __noinline__ bool mbar_wait(unsigned a, unsigned parity)
+// limit_ns (each test suspends the thread for at most min(kSuspendNs, limit_ns)).
+__device__ __noinline__ bool mbar_wait(unsigned a, unsigned parity, unsigned long long limit_ns)
 {
-    if (mbar_try(a, parity)) return true;
+    const unsigned sus = limit_ns < kSuspendNs ? (unsigned)limit_ns : kSuspendNs;
+    if (mbar_try(a, parity, sus)) return true;
     const unsigned long long t0 = globaltimer_ns();
     for (unsigned it = 0; it < 0x7fffffffu; ++it) {
-        if (mbar_try(a, parity)) return true;
-        if (globaltimer_ns() - t0 > kHandoffTimeoutNs) break;
+        if (mbar_try(a, parity, sus)) return true;
+        if (globaltimer_ns() - t0 > limit_ns) break;
     }
     return false;
 }
@@ -1581,9 +1593,11 @@ constexpr unsigned kTmemCols = 512;
 template <bool WRAP>
 struct TmemStream {
     unsigned base, tend, ta, p0, p1;
+    int* err = nullptr;
     __device__ __forceinline__ void issue()
     {
         __syncwarp();
+        if (!bls_ok(ta - base <= kTmemCols - 2u, err)) ta = base;
         tmem_ld2(ta, p0, p1);
         ta += 2;
         if (WRAP) ta = ta == tend ? base : ta;
@@ -1616,9 +1630,10 @@ struct TmemStream {
 // special-function unit, which the binning warps sharing the SM sub-partitions do not use.
 template <int SB, int SIGN, bool WRAP>
 __device__ __forceinline__ float sweep_tmem(unsigned tbase, int nb, int kmin, int kmax, int part,
-                                            int nparts)
+                                            int nparts, int* err)
 {
     TmemBins<WRAP> src;
+    src.err = err;
     src.base = tbase;
     src.tend = tbase + 2u * (unsigned)nb;
     return sweep_fast<SB, SIGN, TmemBins<WRAP>, 0>(src, nb, kmin, kmax, part, nparts);
@@ -1626,9 +1641,10 @@ __device__ __forceinline__ float sweep_tmem(unsigned tbase, int nb, int kmin, in
 
 // Heaviest run of kmax consecutive bins (cyclic), as in sweep_max, from the TMEM copy.
 template <bool WRAP>
-__device__ float heaviest_run_tmem(unsigned tbase, int nb, int kmax)
+__device__ float heaviest_run_tmem(unsigned tbase, int nb, int kmax, int* err)
 {
     TmemBins<WRAP> src;
+    src.err = err;
     src.base = tbase;
     src.tend = tbase + 2u * (unsigned)nb;
     float win = 0.0f, hw, hx, hw2, hx2;
@@ -1720,7 +1736,7 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
     for (int k = 0;; ++k) {
         int give_up = 0;
         if (tid == sg0) {
-            give_up = !mbar_wait(full_bar, ph);
+            give_up = !mbar_wait(full_bar, ph, p.wait_ns ? p.wait_ns : kHandoffTimeoutNs);
             if (give_up) atomicOr(p.err, kErrTimeout);
         }
         ph ^= 1u;
@@ -1746,7 +1762,8 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
                 u64 h[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    h[i] = lds64(ag + (unsigned)i * rowb - (g + i >= nb ? wrapb : 0u));
+                    h[i] = bls_ok(g + i < 2 * nb, p.err)
+                               ? lds64(ag + (unsigned)i * rowb - (g + i >= nb ? wrapb : 0u)) : 0ull;
                 unsigned r[16];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -1756,16 +1773,16 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
                     r[2 * i] = __float_as_uint(hw);
                     r[2 * i + 1] = __float_as_uint(hx);
                 }
-                tmem_st16(tbase + 2u * (unsigned)g, r);
+                tmem_st16(tbase + (bls_ok(2 * g + 16 <= (int)kTmemCols, p.err) ? 2u * (unsigned)g : 0u), r);
             }
             if (part == 1 && lane_ok) s_wpart[col] = wmax;
             tmem_wait_st();
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         } else if (part == 0) {
             if (active)
-                v = SB == 4 ? sweep_max<0, SIGN, 4>(hist, p.stride, nb, kmin, kmax, 0, 1)
-                    : SB == 10 ? sweep_max<0, SIGN, 10>(hist, p.stride, nb, kmin, kmax, 0, 1)
-                               : sweep_max<0, SIGN, 8>(hist, p.stride, nb, kmin, kmax, 0, 1);
+                v = SB == 4 ? sweep_max<0, SIGN, 4>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err)
+                    : SB == 10 ? sweep_max<0, SIGN, 10>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err)
+                               : sweep_max<0, SIGN, 8>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err);
         }
         // the histograms are only read here: the binning group zeroes them when it starts
         // the next tile (after this hand-over)
@@ -1780,8 +1797,8 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
                 fast = (float)kmax * wmax < 0.89f;
                 const bool slide = !fast && kmax < nb;
                 if (__any_sync(0xffffffffu, slide)) {
-                    const float rmax = tmode == 1 ? heaviest_run_tmem<false>(tbase, nb, kmax)
-                                                  : heaviest_run_tmem<true>(tbase, nb, kmax);
+                    const float rmax = tmode == 1 ? heaviest_run_tmem<false>(tbase, nb, kmax, p.err)
+                                                  : heaviest_run_tmem<true>(tbase, nb, kmax, p.err);
                     if (slide) fast = rmax < 0.89f;
                 }
                 const bool exact = active && !fast;
@@ -1789,11 +1806,13 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
                     Best g;
                     if (tmode == 1) {
                         TmemStream<false> src;
+                        src.err = p.err;
                         src.base = tbase;
                         src.tend = tbase + 2u * (unsigned)nb;
                         g = sweep_exact_src<SIGN>(src, nb, kmin, kmax);
                     } else {
                         TmemStream<true> src;
+                        src.err = p.err;
                         src.base = tbase;
                         src.tend = tbase + 2u * (unsigned)nb;
                         g = sweep_exact_src<SIGN>(src, nb, kmin, kmax);
@@ -1804,13 +1823,13 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
             __syncwarp();
             float vf;
             if (tmode == 1)
-                vf = SB == 4 ? sweep_tmem<4, SIGN, false>(tbase, nb, kmin, kmax, part, nparts)
-                     : SB == 10 ? sweep_tmem<10, SIGN, false>(tbase, nb, kmin, kmax, part, nparts)
-                                : sweep_tmem<8, SIGN, false>(tbase, nb, kmin, kmax, part, nparts);
+                vf = SB == 4 ? sweep_tmem<4, SIGN, false>(tbase, nb, kmin, kmax, part, nparts, p.err)
+                     : SB == 10 ? sweep_tmem<10, SIGN, false>(tbase, nb, kmin, kmax, part, nparts, p.err)
+                                : sweep_tmem<8, SIGN, false>(tbase, nb, kmin, kmax, part, nparts, p.err);
             else
-                vf = SB == 4 ? sweep_tmem<4, SIGN, true>(tbase, nb, kmin, kmax, part, nparts)
-                     : SB == 10 ? sweep_tmem<10, SIGN, true>(tbase, nb, kmin, kmax, part, nparts)
-                                : sweep_tmem<8, SIGN, true>(tbase, nb, kmin, kmax, part, nparts);
+                vf = SB == 4 ? sweep_tmem<4, SIGN, true>(tbase, nb, kmin, kmax, part, nparts, p.err)
+                     : SB == 10 ? sweep_tmem<10, SIGN, true>(tbase, nb, kmin, kmax, part, nparts, p.err)
+                                : sweep_tmem<8, SIGN, true>(tbase, nb, kmin, kmax, part, nparts, p.err);
             if (nparts == 2) {   // the parts' maxima meet in shared memory
                 if (part == 1 && lane_ok) s_wpart2[col] = vf;
                 group_sync(kBarSweep, NS);
@@ -1885,7 +1904,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
         for (int k = 0;; ++k) {
             int give_up = 0;
             if (tid == 0) {
-                give_up = !mbar_wait(empty_bar, ph);
+                give_up = !mbar_wait(empty_bar, ph, p.wait_ns ? p.wait_ns : kHandoffTimeoutNs);
                 if (give_up) atomicOr(p.err, kErrTimeout);
             }
             ph ^= 1u;
@@ -1964,11 +1983,11 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                 if (active) {   // a3 + a4
                     if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
                         if (inc)
-                            bin_fast<PHASE, true, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                            bin_fast<PHASE, true, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                         else
-                            bin_fast<PHASE, true, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq);
+                            bin_fast<PHASE, true, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                     } else
-                        bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq);
+                        bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq, p.err);
                 }
                 group_sync(kBarBin, kWsBinThreads);
             }
@@ -2137,7 +2156,7 @@ cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, i
 // one read-modify-write group of the hot kernel share a bin, that kernel adds their
 // pre-summed weights, so such a bin can differ from this one in its last bit.
 __device__ void bin_column(const CurveDesc& cd, double f, unsigned char* hist, int stride,
-                           int phase, int kahan)
+                           int phase, int kahan, int* err = nullptr)
 {
     const size_t S = (size_t)stride;
     const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax, cd.fxs);
@@ -2150,6 +2169,7 @@ __device__ void bin_column(const CurveDesc& cd, double f, unsigned char* hist, i
         const float4 A = cd.pts[2 * pi], B = cd.pts[2 * pi + 1];
         unsigned b0, b1;
         fold_pair_rt(phase, A, &cd.dt64[2 * pi], fc, fq, b0, b1);
+        if (!bls_ok(b0 < (unsigned)cd.nb && b1 < (unsigned)cd.nb, err)) continue;
         if (kahan) {
             kahan_add(reinterpret_cast<float4*>(hist) + b0 * S, B.x, B.y);
             kahan_add(reinterpret_cast<float4*>(hist) + b1 * S, B.z, B.w);
@@ -2171,9 +2191,9 @@ __device__ Best best_box_at(const CurveDesc& cd, double f, unsigned char* hist, 
 
 // The same by the 32 lanes of a warp: lane 0 bins, the lanes share the exact sweep.
 __device__ Best best_box_warp(const CurveDesc& cd, double f, unsigned char* hist, int stride,
-                              int phase, int kahan, int sign, int lane)
+                              int phase, int kahan, int sign, int lane, int* err)
 {
-    if (lane == 0) bin_column(cd, f, hist, stride, phase, kahan);
+    if (lane == 0) bin_column(cd, f, hist, stride, phase, kahan, err);
     __syncwarp();
     return sign ? sweep_exact_warp<1>(hist, stride, kahan, cd.nb, cd.kmin, cd.kmax, lane)
                 : sweep_exact_warp<0>(hist, stride, kahan, cd.nb, cd.kmin, cd.kmax, lane);
@@ -2308,7 +2328,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
             if (warp < R && q < K) {
                 if (sel[q] >= 0) {
                     const Best g = best_box_warp(cd, grid_freq(cd, sel[q]), smem + (size_t)warp * esz,
-                                                 R, p.phase, p.kahan, p.sign, lane);
+                                                 R, p.phase, p.kahan, p.sign, lane, p.err);
                     if (lane == 0) {
                         sel_i1[q] = g.i1;
                         sel_k[q] = g.k;
@@ -2396,13 +2416,12 @@ cudaError_t launch_reduce(const ReduceParams& p, int ncurves, cudaStream_t s)
 // ------------------------------------------------------------------------- diagnostics
 
 // Per-point bins of one curve at frequencies js, by the fold of the given phase mode.  In
-// FX64 mode on a uniform grid the incremental fold of the warp-specialised kernel is run as
-// well, for the frequency's place in a tile of kDebugTile columns; a point where the two
-// disagree is reported as -1 - bin.
-constexpr int kDebugTile = 128;
-
+// FX64 mode on a uniform grid (plain sums) the incremental fold of the search kernels is
+// run as well, for the frequency's place in a tile of T columns -- the tile width the
+// plan's search uses for this curve, so the reference column jc is the search's; a point
+// where the two folds disagree is reported as -1 - bin.
 template <int PHASE>
-__global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bins)
+__global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bins, int T, int kahan)
 {
     const CurveDesc cd = *curve;
     const int q = blockIdx.x;
@@ -2411,9 +2430,10 @@ __global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bi
     const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax, cd.fxs);
     const FoldPacked fq = make_fold_packed(fc);
     FoldConst fi = fc;
-    const int jc = min(j / kDebugTile * kDebugTile + kDebugTile / 2, cd.nf - 1);
+    const int jc = min(j / T * T + T / 2, cd.nf - 1);
     const double fcen = grid_freq(cd, jc);
-    const bool inc = PHASE == kPhaseFX64 && cd.freqs == nullptr && inc_tile_ok(fcen, cd.df, cd.fxs);
+    const bool inc = PHASE == kPhaseFX64 && !kahan && cd.freqs == nullptr &&
+                     inc_tile_ok(fcen, cd.df, cd.fxs);
     if (inc) make_fold_const_inc(fi, f, fcen, j - jc, cd.df, cd.nb, cd.dtmax, cd.fxs);
     for (int pi = threadIdx.x; 2 * pi < cd.n; pi += blockDim.x) {
         unsigned b0, b1;
@@ -2438,17 +2458,18 @@ __global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bi
 }
 
 cudaError_t launch_debug_fold(const CurveDesc* d_curve, const int* js, int nj, int phase,
-                              int* bins, cudaStream_t s)
+                              int T, int kahan, int* bins, cudaStream_t s)
 {
     if (nj <= 0) return cudaSuccess;
+    if (T < 1) return cudaErrorInvalidValue;
     if (phase == kPhaseF64)
-        debug_fold_kernel<kPhaseF64><<<nj, 256, 0, s>>>(d_curve, js, bins);
+        debug_fold_kernel<kPhaseF64><<<nj, 256, 0, s>>>(d_curve, js, bins, T, kahan);
     else if (phase == kPhaseF32)
-        debug_fold_kernel<kPhaseF32><<<nj, 256, 0, s>>>(d_curve, js, bins);
+        debug_fold_kernel<kPhaseF32><<<nj, 256, 0, s>>>(d_curve, js, bins, T, kahan);
     else if (phase == kPhaseDF32)
-        debug_fold_kernel<kPhaseDF32><<<nj, 256, 0, s>>>(d_curve, js, bins);
+        debug_fold_kernel<kPhaseDF32><<<nj, 256, 0, s>>>(d_curve, js, bins, T, kahan);
     else
-        debug_fold_kernel<kPhaseFX64><<<nj, 256, 0, s>>>(d_curve, js, bins);
+        debug_fold_kernel<kPhaseFX64><<<nj, 256, 0, s>>>(d_curve, js, bins, T, kahan);
     return cudaGetLastError();
 }
 

@@ -118,6 +118,16 @@ void order_by_cost(const std::vector<CurveSpec>& cs, const std::vector<int>& idx
                    std::vector<int>* out);
 
 void server_destroy(bls_plan_impl* P);
+// Limit of each hand-over wait of the warp-specialised kernel, in ns: 30 s, or the test
+// setting BLS_HANDOFF_LIMIT_US (microseconds, read at every launch group) when it is set.
+unsigned long long handoff_limit_ns();
+// NVTX range over a scope (a named span on the host timeline of a profiler); next() ends
+// it and starts the following phase's range.
+struct NvtxRange {
+    explicit NvtxRange(const char* name);
+    ~NvtxRange();
+    void next(const char* name);
+};
 // One curve searched as bls_search does (the plan's lock held for the call); the server's
 // sequential mode runs a plain or unbinned request this way.
 bls_status search_one_locked(bls_plan_impl* P, const bls_curve* curve, bls_peak* out);

@@ -195,6 +195,7 @@ bool Server::step_sequential()
 // One scheduler step; returns false when the device failed.
 bool Server::step()
 {
+    NvtxRange r_step("bls.server.step");
     if (P->d.algo != BLS_ALGO_TILED) return step_sequential();
     cudaError_t e;
     std::vector<Request*> admitted, retire_cancel;
@@ -366,6 +367,7 @@ bool Server::step()
             fp.err = err.as<int>();
             fp.chunk = geoms[q].chunk;
             fp.stride = geoms[q].stride;
+            fp.wait_ns = handoff_limit_ns();
             const int bps = fold_blocks_per_sm(geoms[q].T, geoms[q].smem, P->d.phase,
                                                P->d.sum == BLS_SUM_KAHAN, P->d.sign, geoms[q].ws);
             long long grid = std::min<long long>((long long)P->sm_count * bps, tot[q]);
@@ -401,6 +403,7 @@ bool Server::step()
         rp.phase = P->d.phase;
         rp.kahan = P->d.sum == BLS_SUM_KAHAN;
         rp.smem_bytes = reduce_smem_bytes(nbmax, topk, rp.kahan);
+        rp.err = err.as<int>();
         if ((e = launch_reduce(rp, nf, stream)) != cudaSuccess) {
             fail_all(std::string("reduce launch: ") + cudaGetErrorString(e));
             return false;
@@ -430,6 +433,7 @@ bool Server::step()
 bool Server::retire_inflight()
 {
     if (!inflight) return true;
+    NvtxRange r_retire("bls.server.retire");
     inflight = false;
     cudaError_t e;
     if ((e = cudaEventSynchronize(ev_step[fl_parity])) != cudaSuccess) {

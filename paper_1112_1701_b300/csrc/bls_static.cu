@@ -161,6 +161,7 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
     fp.err = err;
     fp.chunk = chunk;
     fp.stride = T;
+    fp.wait_ns = 0;
     long long grid = (long long)sms * fold_blocks_per_sm(T, smem, kPhaseFX64, 0, sign, ws);
     if (grid > ntiles) grid = ntiles;
     if ((e = launch_fold_sweep(fp, T, (int)grid, kPhaseFX64, 0, ws, sign, smem, s)) != cudaSuccess)
@@ -191,6 +192,7 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
     rp.phase = kPhaseFX64;
     rp.kahan = 0;
     rp.smem_bytes = reduce_smem_bytes(c->nb, topk, 0);
+    rp.err = err;
     if ((e = launch_reduce(rp, 1, s)) != cudaSuccess) return cuda_fail(e, "reduce launch");
     int host_err = 0;
     if ((e = cudaMemcpyAsync(&host_err, err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)

@@ -129,7 +129,8 @@ constexpr int kBucketMax = 48;   // largest bucket left to an insertion sort
 // bucket by one thread -- or, when a bucket holds more than kBucketMax keys (phases
 // clumped), by the bitonic network; the keys are distinct, so both give the same order --
 // then equal K put in phase order.  `cnt` is scratch for M + 1 ints.
-__device__ __forceinline__ void sort_keys(const CurveDesc& cd, double f, u64* keys, int M, int* cnt)
+__device__ __forceinline__ void sort_keys(const CurveDesc& cd, double f, u64* keys, int M, int* cnt,
+                                          int* err)
 {
     __shared__ int s_tot[kUThreads / 32 + 1];
     const int n = cd.n, tid = threadIdx.x, nt = blockDim.x;
@@ -183,7 +184,8 @@ __device__ __forceinline__ void sort_keys(const CurveDesc& cd, double f, u64* ke
     if (tid == 0) start[nbk] = n;
     for (int i = tid; i < n; i += nt) {
         const u64 k = phase_key(cd, i, f);
-        keys[atomicAdd(&cur[B ? (int)(k >> (64 - B)) : 0], 1)] = k;
+        const int at = atomicAdd(&cur[B ? (int)(k >> (64 - B)) : 0], 1);
+        if (bls_ok(at < n, err)) keys[at] = k;
     }
     __syncthreads();
     for (int b = tid; b < nbk; b += nt) {
@@ -550,7 +552,7 @@ __device__ __forceinline__ void ubls_search(UblsParams p)
     const bool fast = runs_positive(cd, reinterpret_cast<float*>(sred));
     for (int j = j0; j < min(j0 + kTile, cd.nf); ++j) {
         const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
-        sort_keys(cd, f, keys, M, reinterpret_cast<int*>(C.wh));
+        sort_keys(cd, f, keys, M, reinterpret_cast<int*>(C.wh), p.err);
         prefix_sums(cd, keys, C, sred);
         const Bounds Bq = make_bounds(p.qmin, p.qmax, f);
         const float4 T = make_float4(C.wh[n], C.wl[n], C.xh[n], C.xl[n]);
@@ -560,6 +562,7 @@ __device__ __forceinline__ void ubls_search(UblsParams p)
         for (int a = threadIdx.x; a < n; a += nt) {
             int emin, emax;
             run_ends(cd, keys, n, a, Bq, emin, emax);
+            if (!bls_ok(emin >= a && emax <= a + n - 2, p.err)) continue;
             b = fast ? start_best<SIGN, true>(C, T, n, a, emin, emax, b)
                      : start_best<SIGN, false>(C, T, n, a, emin, emax, b);
         }
@@ -728,7 +731,7 @@ __global__ void __launch_bounds__(kUThreads, 1) ubls_reduce_kernel(UblsParams p)
             continue;
         }
         const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
-        sort_keys(cd, f, keys, M, reinterpret_cast<int*>(C.wh));
+        sort_keys(cd, f, keys, M, reinterpret_cast<int*>(C.wh), p.err);
         prefix_sums(cd, keys, C, red);
         const Bounds Bq = make_bounds(p.qmin, p.qmax, f);
         const int2 run = p.sign ? best_run<1>(cd, keys, C, cd.n, Bq, fast, bzs, bss, bls)

@@ -42,6 +42,16 @@ def test_library_exports_every_declared_symbol(L):
         assert hasattr(L, name)
 
 
+def test_debug_library_exports_the_same_symbols(L):
+    """libbls_debug.so (device-side index checks, loaded with BLS_DEBUG=1) is built beside
+    libbls.so from the same sources and exports the same boundary."""
+    path = os.path.join(os.path.dirname(bls.LIB_PATH), "libbls_debug.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", path], check=True,
+                         capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (bls_[a-z_]+)", out))
+    assert set(declared_functions()) <= exported
+
+
 def test_struct_layout_matches_c(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text(

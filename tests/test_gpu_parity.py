@@ -81,8 +81,9 @@ def test_bins_bit_exact_plain_and_long_baseline(phase):
 def test_bins_bit_exact_on_exact_edges(phase, grid):
     """Points placed exactly on bin edges (and on integer cycles) at grid frequencies:
     every one lands within the error bound and takes the exact FP64 re-fold.  On the fine
-    grid the FX64 debug fold also runs the incremental fold of 128-frequency tiles (offsets
-    -64 .. 63 from the tile's middle column, and a ragged last tile), which must agree."""
+    grid the FX64 debug fold also runs the incremental fold of the search's tiles (at
+    nb = 64, 128-frequency tiles: offsets -64 .. 63 from the tile's middle column, and a
+    ragged last tile), which must agree."""
     nb = 64
     if grid == "coarse":
         f0, df, nf = 0.5, 0.25, 11
@@ -105,6 +106,29 @@ def test_bins_bit_exact_on_exact_edges(phase, grid):
         bg = p.debug_fold(ci, js)
     bo = oracle.bins(t, [oracle.freq(j, f0, df) for j in js], nb)
     assert np.array_equal(bg, bo)
+
+
+@pytest.mark.parametrize("T", [0, 80, 48])
+def test_bins_bit_exact_at_survey_tile_geometry(T):
+    """The survey sweep's shape (2000 points over 90 nights, 200,000 frequencies, nb = 256):
+    the search runs 96-frequency tiles there (T = 0: the plan's rules), or the width given.
+    Bins of the first, reference (middle), last and ragged-tile columns of such tiles, in
+    the incremental fold with the search's reference column, equal the FP64 oracle's."""
+    b = synth.config5(ncurves=2)
+    nb = 256
+    for c, g in zip(b.curves, b.grids):
+        ci = _ci(c, g, nb, b.qmin, b.qmax)
+        Tw = T or 96
+        js = []
+        for tile in (0, 1, 1041, (g.nf - 1) // Tw - 1, (g.nf - 1) // Tw):
+            t0 = tile * Tw
+            js += [t0, t0 + Tw // 2 - 1, t0 + Tw // 2, t0 + Tw - 1]
+        js = sorted({j for j in js if 0 <= j < g.nf} | {g.nf - 1})
+        kw = dict(freqs_per_block=T, point_chunk=256) if T else {}
+        with _plan(nb, b.qmin, b.qmax, **kw) as p:
+            bg = p.debug_fold(ci, js)
+        bo = oracle.bins(c.t, [oracle.freq(j, g.fmin, g.df) for j in js], nb)
+        assert np.array_equal(bg, bo), f"T={Tw}: {int((bg != bo).sum())} of {bg.size} differ"
 
 
 def test_fast_phase_modes_give_identical_searches():
