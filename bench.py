@@ -54,6 +54,15 @@ METRIC = "BLS point x freq evals/s"
 UNIT = "point*freq/s"
 NB, QMIN, QMAX = 200, 0.005, 0.15
 
+# DRAM traffic of one fold-bin-sweep launch of the headline workload (dram__bytes_read.sum +
+# dram__bytes_write.sum, one ncu capture of the timed launch after an L2 flush,
+# profiles/fold_sweep_survey_2048x200k_dram.md), valid for the kernel source with the given
+# SHA-256; reported as null once the source changes.
+NCU_TRAFFIC = {"workload": "survey", "ncurves": 2048,
+               "kernel_sha256": "65a94b97fa43c13a5b4291678e41e5abd4904ddd25d34ea3134a0fba6b10ba3d",
+               "bytes_per_launch": 174520064 + 1623165952}
+
+
 def kernel_sha():
     p = os.path.join(ROOT, "paper_1112_1701_b300", "csrc", "bls_kernels.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()
@@ -841,6 +850,9 @@ def main():
             "roofline": m["roofline"], "clocks": m["clocks"], "gpu_launches": m["gpu_launches"],
             "box_evals_per_s": m["box_evals_per_s"], "kernel_ms": m["kernel_ms"]}
     line["config"]["launch"] = m["launch"]
+    if (NCU_TRAFFIC["kernel_sha256"] == kernel_sha() and len(batch) == NCU_TRAFFIC["ncurves"]
+            and batch.grids[0].nf == 200000):
+        line["roofline"]["traffic"] = NCU_TRAFFIC["bytes_per_launch"]
     line["config"]["full_100k_curves_s_extrapolated"] = m["ms_per_step"] / 1000.0 * 100000 / len(batch)
     if "e2e" in m:
         line["e2e"] = m["e2e"]
