@@ -79,14 +79,15 @@ enum {
     BLS_ALGO_PLAIN_F64 = 1, /* baseline: one launch per curve, one thread per frequency, FP64 */
     BLS_ALGO_UNBINNED = 2   /* unbinned (edge-to-edge) boxes: at every frequency the points are
                                ordered by phase and every cyclic run of consecutive points whose
-                               phase extent lies in [qmin, qmax] is a box.  Phases are 64-bit
-                               fixed-point fractions: with s = 34 - (L+1)/2 (dtmax < 2^L, capped
-                               to [1, 62-L]), DT = RN_int(dt 2^s), F = RN_int(f 2^(64-s)), the key
-                               is ((DT F) mod 2^64) >> 32; order (key, point); extent
-                               (key_last - key_first) mod 2^32 in [ceil(qmin 2^32),
-                               floor(qmax 2^32)].  Peaks report i1 = the run's first position in
-                               phase order and k = its number of points.  Up to 8192 points per
-                               curve; the plan's qmin/qmax apply to every curve. */
+                               phase extent lies in [qmin, qmax] is a box.  A point's phase is
+                               the FP64 fold frac(RN(dt f)); order (phase, point index); a run's
+                               extent RN(phase_last - phase_first), plus one cycle (RN(d + 1))
+                               when the run wraps through phase 0, compared in FP64.  Peaks
+                               report i1 = the run's first position in phase order and k = its
+                               number of points.  Up to 32768 points per curve (beyond ~8k the
+                               working arrays live in a global scratch buffer of about 0.6 MB
+                               per SM at 20,000 points); the plan's qmin/qmax apply to every
+                               curve. */
 };
 
 /* Fold-sweep kernel of the tiled search.  BLS_FOLD_AUTO chooses per class of curves: the

@@ -459,6 +459,16 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         up.nmax = nmax;
         up.M = 1;
         while (up.M < nmax) up.M <<= 1;
+        up.nitems = utiles;
+        // curves too long for a block's shared memory work in a global slice per block
+        const size_t wb = ubls_work_bytes(nmax);
+        if (wb > P->smem_optin) {
+            up.grid = (int)std::min<long long>(utiles, (long long)P->sm_count);
+            up.scratch_stride = (wb + 255) & ~(size_t)255;
+            if ((e = P->ubls_scratch.ensure(up.scratch_stride * (size_t)up.grid)) != cudaSuccess)
+                return cuda_fail(e, "allocating the unbinned working arrays");
+            up.scratch = P->ubls_scratch.as<unsigned char>();
+        }
     }
     std::vector<int> grids(cls.size());
     for (size_t q = 0; q < cls.size(); ++q) {
@@ -537,7 +547,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         } else if (unbinned) {
             if ((x = cudaMemcpyAsync(P->prefix.p, P->h_prefix.p, pp * sizeof(long long), cudaMemcpyHostToDevice, st)) != cudaSuccess)
                 return x;
-            if ((x = launch_ubls(up, utiles, st)) != cudaSuccess) return x;
+            if ((x = launch_ubls(up, st)) != cudaSuccess) return x;
             ++launches;
             ++fold_launches;
         } else {
@@ -607,7 +617,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         }
         if (unbinned) put(P->h_prefix.p, pp * sizeof(long long));
         void* bufs[] = {P->pts.p, P->res.p, P->peaks.p, P->spec.p, P->err.p, P->h_peaks.p, P->h_err.p, P->ranges.p,
-                        P->shapes.p, P->h_shapes.p, P->prefix.p};
+                        P->shapes.p, P->h_shapes.p, P->prefix.p, P->ubls_scratch.p};
         put(bufs, sizeof(bufs));
         if (P->graph && sig == P->graph_sig) {
             if ((e = cudaGraphLaunch(P->graph, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
@@ -841,9 +851,10 @@ void bls_plan_destroy(bls_plan* P)
     if (P->stream) cudaStreamSynchronize(P->stream);
     DevBuf* bufs[] = {&P->raw_t, &P->raw_y, &P->raw_dy, &P->raw_f, &P->pts, &P->dt64, &P->w64,
                       &P->wx64, &P->cdesc, &P->ranges, &P->prefix, &P->counter, &P->err, &P->res,
-                      &P->peaks, &P->spec, &P->plain_hist, &P->jsbuf, &P->binsbuf};
+                      &P->peaks, &P->spec, &P->plain_hist, &P->jsbuf, &P->binsbuf, &P->shapes,
+                      &P->ubls_scratch};
     for (DevBuf* b : bufs) b->release();
-    HostBuf* hb[] = {&P->h_cdesc, &P->h_ranges, &P->h_prefix, &P->h_peaks, &P->h_err};
+    HostBuf* hb[] = {&P->h_cdesc, &P->h_ranges, &P->h_prefix, &P->h_peaks, &P->h_err, &P->h_shapes};
     for (HostBuf* b : hb) b->release();
     for (int q = 0; q < 4; ++q)
         if (P->ev[q]) cudaEventDestroy(P->ev[q]);

@@ -118,11 +118,19 @@ struct UblsParams {
     double qmin, qmax;              // run extent bounds, in cycles
     int nmax, M;                    // largest curve of the group and the power of two >= it
     int* err;                       // error word (index checks of the BLS_DEBUG build)
+    long long nitems;               // work items (curve, frequency tile) of the search
+    // working arrays of curves too long for shared memory: block b's keys and prefix sums
+    // at scratch + b * scratch_stride, grid persistent blocks (nullptr: shared memory, one
+    // block per item or curve)
+    unsigned char* scratch;
+    size_t scratch_stride;
+    int grid;
 };
 
-cudaError_t launch_ubls(const UblsParams& p, long long nitems, cudaStream_t s);
+cudaError_t launch_ubls(const UblsParams& p, cudaStream_t s);
 cudaError_t launch_ubls_reduce(const UblsParams& p, cudaStream_t s);
-size_t ubls_smem_bytes(int nmax);
+// Bytes of one block's working arrays (keys and prefix sums) for curves of up to nmax points.
+size_t ubls_work_bytes(int nmax);
 int ubls_tile();
 
 struct ReduceParams {

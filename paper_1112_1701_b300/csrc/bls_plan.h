@@ -76,6 +76,7 @@ struct bls_plan_impl {
     DevBuf pts, dt64, w64, wx64;          // prepared points
     DevBuf cdesc, ranges, prefix, counter, err;
     DevBuf res, peaks, spec, plain_hist, jsbuf, binsbuf, shapes;
+    DevBuf ubls_scratch;                  // unbinned working arrays of long curves
     // host staging (pinned)
     HostBuf h_cdesc, h_ranges, h_prefix, h_peaks, h_err, h_shapes;
 
@@ -102,7 +103,9 @@ struct bls_plan_impl {
 bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, CurveSpec* out,
                          const int* kinds = nullptr, bool scan_values = true);
 int ptr_kind(const void* p);
-constexpr int kUblsMaxPoints = 8192;   // the unbinned search sorts a curve in shared memory
+// The unbinned search sorts a curve in shared memory up to ~8k points, beyond that in a
+// global scratch slice per persistent block (about 0.6 MB per block at 20,000 points).
+constexpr int kUblsMaxPoints = 32768;
 
 // A validated trapezoid-refit request of bls_search_shapes.
 struct ShapeReq {

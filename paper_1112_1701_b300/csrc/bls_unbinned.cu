@@ -527,15 +527,20 @@ __device__ __forceinline__ bool runs_positive(const CurveDesc& cd, float* red)
     return m >= 1.1920929e-7f;   // 2^-23
 }
 
-template <int SIGN>
-__device__ __forceinline__ void ubls_search(UblsParams p)
+// Working arrays of a block (keys, prefix sums): its dynamic shared memory, or, for curves
+// too long for it, the block's own slice of a global scratch buffer (persistent blocks, so
+// the scratch is bounded by the grid, not by the number of work items).
+__device__ __forceinline__ unsigned char* ubls_work(const UblsParams& p, unsigned char* dsm)
 {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ float sZ[kUThreads / 32];
-    __shared__ double sred[2 * kUThreads];
-    u64* keys = reinterpret_cast<u64*>(dsm);
+    return p.scratch ? p.scratch + (size_t)blockIdx.x * p.scratch_stride : dsm;
+}
+
+// One work item (curve, tile of kTile frequencies) of the search.
+template <int SIGN>
+__device__ __forceinline__ void ubls_item(const UblsParams& p, long long it, unsigned char* work,
+                                          u64* keys, float* sZ, double* sred)
+{
     // work item -> (curve, tile)
-    const long long it = blockIdx.x;
     int lo = 0, hi = p.ncurves;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -546,7 +551,7 @@ __device__ __forceinline__ void ubls_search(UblsParams p)
     const int j0 = (int)(it - p.tile_prefix[lo]) * kTile;
     int M = 1;
     while (M < n) M <<= 1;
-    const Prefix C = prefix_layout(dsm, M, n);
+    const Prefix C = prefix_layout(work, M, n);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nt = blockDim.x;
     const bool fast = runs_positive(cd, reinterpret_cast<float*>(sred));
@@ -578,8 +583,22 @@ __device__ __forceinline__ void ubls_search(UblsParams p)
     }
 }
 
-// Search kernel: one block per (curve, tile of kTile frequencies); P(f_j) = z^2 of the best
-// run (its position is found again by the reduce kernel for the kept frequencies only).
+// The search of a block: its work items (curve, tile), one after another.
+template <int SIGN>
+__device__ __forceinline__ void ubls_search(const UblsParams& p)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ float sZ[kUThreads / 32];
+    __shared__ double sred[2 * kUThreads];
+    unsigned char* const work = ubls_work(p, dsm);
+    u64* keys = reinterpret_cast<u64*>(work);
+    for (long long it = blockIdx.x; it < p.nitems; it += gridDim.x)
+        ubls_item<SIGN>(p, it, work, keys, sZ, sred);
+}
+
+// Search kernel: blocks take (curve, tile of kTile frequencies) items (one each with the
+// working arrays in shared memory; persistent with the global scratch); P(f_j) = z^2 of the
+// best run (its position is found again by the reduce kernel for the kept frequencies only).
 __global__ void __launch_bounds__(kUThreads, 1) ubls_kernel(UblsParams p)
 {
     if (p.sign) ubls_search<1>(p);
@@ -657,127 +676,132 @@ __device__ int2 best_run(const CurveDesc& cd, const u64* keys, const Prefix& C, 
 __global__ void __launch_bounds__(kUThreads, 1) ubls_reduce_kernel(UblsParams p)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    u64* keys = reinterpret_cast<u64*>(dsm);
+    unsigned char* const work = ubls_work(p, dsm);
+    u64* keys = reinterpret_cast<u64*>(work);
     __shared__ double red[2 * kUThreads];
     __shared__ float bzs[kUThreads / 32];
     __shared__ int bss[kUThreads / 32], bls[kUThreads / 32];
     __shared__ float sP[kUThreads / 32];
     __shared__ int sJ[kUThreads / 32], sT[kUThreads / 32];
     __shared__ int sel[kMaxTopK];
-    const CurveDesc& cd = p.curves[blockIdx.x];
-    const float* res = cd.res;
-    const int nf = cd.nf, K = p.topk;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // local maxima, best K per thread; spectrum; SR sums for the SDE
-    float lp[kMaxTopK];
-    int lj[kMaxTopK];
-    int cnt = 0;
-    double srsum = 0.0;
-    for (int j = threadIdx.x; j < nf; j += blockDim.x) {
-        const float P = res[j];
-        const float sr = sqrtf(P);
-        if (p.spectrum) p.spectrum[cd.spec_off + j] = sr;
-        srsum = __dadd_rn(srsum, (double)sr);
-        const bool lm = (j == 0 || P > res[j - 1]) && (j == nf - 1 || P >= res[j + 1]);
-        if (!lm) continue;
-        int pos = cnt < K ? cnt : K;
-        for (int q = 0; q < cnt; ++q)
-            if (freq_ahead(P, j, lp[q], lj[q])) { pos = q; break; }
-        if (pos >= K) continue;
-        for (int q = (cnt < K ? cnt : K - 1); q > pos; --q) { lp[q] = lp[q - 1]; lj[q] = lj[q - 1]; }
-        lp[pos] = P;
-        lj[pos] = j;
-        if (cnt < K) ++cnt;
-    }
-    const double srmean = __ddiv_rn(sum_block(srsum, red), (double)nf);
-    double srvar = 0.0;
-    for (int j = threadIdx.x; j < nf; j += blockDim.x) {
-        const double d = __dsub_rn((double)sqrtf(res[j]), srmean);
-        srvar = __dadd_rn(srvar, __dmul_rn(d, d));
-    }
-    const double srsd = sqrt(__ddiv_rn(sum_block(srvar, red), (double)nf));
-    int head = 0;
-    for (int q = 0; q < K; ++q) {
-        float bp = head < cnt ? lp[head] : -1.0f;
-        int bj = head < cnt ? lj[head] : 0x7fffffff;
-        int bt = threadIdx.x;
-        for (int o = 16; o > 0; o >>= 1) {
-            const float op = __shfl_xor_sync(0xffffffffu, bp, o);
-            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-            const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
-            if (freq_ahead(op, oj, bp, bj)) { bp = op; bj = oj; bt = ot; }
+    // one curve after another (one per block with the working arrays in shared memory)
+    for (int c = blockIdx.x; c < p.ncurves; c += gridDim.x) {
+        const CurveDesc& cd = p.curves[c];
+        const float* res = cd.res;
+        const int nf = cd.nf, K = p.topk;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        // local maxima, best K per thread; spectrum; SR sums for the SDE
+        float lp[kMaxTopK];
+        int lj[kMaxTopK];
+        int cnt = 0;
+        double srsum = 0.0;
+        for (int j = threadIdx.x; j < nf; j += blockDim.x) {
+            const float P = res[j];
+            const float sr = sqrtf(P);
+            if (p.spectrum) p.spectrum[cd.spec_off + j] = sr;
+            srsum = __dadd_rn(srsum, (double)sr);
+            const bool lm = (j == 0 || P > res[j - 1]) && (j == nf - 1 || P >= res[j + 1]);
+            if (!lm) continue;
+            int pos = cnt < K ? cnt : K;
+            for (int q = 0; q < cnt; ++q)
+                if (freq_ahead(P, j, lp[q], lj[q])) { pos = q; break; }
+            if (pos >= K) continue;
+            for (int q = (cnt < K ? cnt : K - 1); q > pos; --q) { lp[q] = lp[q - 1]; lj[q] = lj[q - 1]; }
+            lp[pos] = P;
+            lj[pos] = j;
+            if (cnt < K) ++cnt;
         }
-        if (lane == 0) { sP[warp] = bp; sJ[warp] = bj; sT[warp] = bt; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                if (freq_ahead(sP[w], sJ[w], sP[0], sJ[0])) { sP[0] = sP[w]; sJ[0] = sJ[w]; sT[0] = sT[w]; }
-            sel[q] = sP[0] >= 0.0f ? sJ[0] : -1;
-            sT[0] = sP[0] >= 0.0f ? sT[0] : -1;
+        const double srmean = __ddiv_rn(sum_block(srsum, red), (double)nf);
+        double srvar = 0.0;
+        for (int j = threadIdx.x; j < nf; j += blockDim.x) {
+            const double d = __dsub_rn((double)sqrtf(res[j]), srmean);
+            srvar = __dadd_rn(srvar, __dmul_rn(d, d));
         }
-        __syncthreads();
-        if (sT[0] == (int)threadIdx.x) ++head;
-        __syncthreads();
-    }
-    int M = 1;
-    while (M < cd.n) M <<= 1;
-    const Prefix C = prefix_layout(dsm, M, cd.n);
-    const bool fast = runs_positive(cd, reinterpret_cast<float*>(red));
-    for (int q = 0; q < K; ++q) {
-        DevPeak* out = &p.peaks[(size_t)blockIdx.x * K + q];
-        const int j = sel[q];
-        if (j < 0) {
-            if (threadIdx.x == 0) { DevPeak z = {}; z.j = -1; *out = z; }
-            continue;
-        }
-        const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
-        sort_keys(cd, f, keys, M, reinterpret_cast<int*>(C.wh), p.err);
-        prefix_sums(cd, keys, C, red);
-        const Bounds Bq = make_bounds(p.qmin, p.qmax, f);
-        const int2 run = p.sign ? best_run<1>(cd, keys, C, cd.n, Bq, fast, bzs, bss, bls)
-                                : best_run<0>(cd, keys, C, cd.n, Bq, fast, bzs, bss, bls);
-        if (threadIdx.x == 0) {
-            const int a = run.x, len = run.y;
-            DevPeak pk = {};
-            pk.j = j; pk.i1 = a; pk.k = len;
-            pk.freq = f;
-            pk.period = 1.0 / f;
-            if (len > 0) {
-                double r = 0.0, s = 0.0;
-                for (int l = 0; l < len; ++l) {
-                    int qq = a + l;
-                    if (qq >= cd.n) qq -= cd.n;
-                    const int i = (int)(keys[qq] & 0xffffffffu);
-                    double inv = 1.0;
-                    if (cd.dy) { const double dd = (double)cd.dy[i]; inv = __ddiv_rn(1.0, __dmul_rn(dd, dd)); }
-                    const double w = __ddiv_rn(inv, cd.W);
-                    r = __dadd_rn(r, w);
-                    s = __dadd_rn(s, __dmul_rn(w, __dsub_rn((double)cd.y[i], cd.ybar)));
-                }
-                // extent and mid-box phase as the definition computes them
-                const double E = exact_extent(cd, keys, cd.n, a, a + len - 1, f);
-                const double ph0 = point_phase(cd, (int)(keys[a] & 0xffffffffu), f);
-                double mid = __dadd_rn(ph0, __dmul_rn(0.5, E));
-                mid = __dsub_rn(mid, floor(mid));
-                pk.epoch = __dadd_rn(cd.t_ref, __ddiv_rn(mid, f));
-                pk.duration = __ddiv_rn(E, f);
-                if (r > 0.0 && r < 1.0 && (p.sign || s < 0.0)) {
-                    pk.power = s * s / (r * (1.0 - r));
-                    pk.depth = -s / (r * (1.0 - r));
-                    pk.sr = sqrt(pk.power);
-                    pk.snr = pk.sr * sqrt(cd.W);
-                }
+        const double srsd = sqrt(__ddiv_rn(sum_block(srvar, red), (double)nf));
+        int head = 0;
+        for (int q = 0; q < K; ++q) {
+            float bp = head < cnt ? lp[head] : -1.0f;
+            int bj = head < cnt ? lj[head] : 0x7fffffff;
+            int bt = threadIdx.x;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float op = __shfl_xor_sync(0xffffffffu, bp, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+                if (freq_ahead(op, oj, bp, bj)) { bp = op; bj = oj; bt = ot; }
             }
-            pk.sde = srsd > 0.0 ? (pk.sr - srmean) / srsd : 0.0;
-            *out = pk;
+            if (lane == 0) { sP[warp] = bp; sJ[warp] = bj; sT[warp] = bt; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                    if (freq_ahead(sP[w], sJ[w], sP[0], sJ[0])) { sP[0] = sP[w]; sJ[0] = sJ[w]; sT[0] = sT[w]; }
+                sel[q] = sP[0] >= 0.0f ? sJ[0] : -1;
+                sT[0] = sP[0] >= 0.0f ? sT[0] : -1;
+            }
+            __syncthreads();
+            if (sT[0] == (int)threadIdx.x) ++head;
+            __syncthreads();
         }
-        __syncthreads();
+        int M = 1;
+        while (M < cd.n) M <<= 1;
+        const Prefix C = prefix_layout(work, M, cd.n);
+        const bool fast = runs_positive(cd, reinterpret_cast<float*>(red));
+        for (int q = 0; q < K; ++q) {
+            DevPeak* out = &p.peaks[(size_t)c * K + q];
+            const int j = sel[q];
+            if (j < 0) {
+                if (threadIdx.x == 0) { DevPeak z = {}; z.j = -1; *out = z; }
+                continue;
+            }
+            const double f = cd.freqs ? cd.freqs[j] : __dadd_rn(cd.fmin, __dmul_rn((double)j, cd.df));
+            sort_keys(cd, f, keys, M, reinterpret_cast<int*>(C.wh), p.err);
+            prefix_sums(cd, keys, C, red);
+            const Bounds Bq = make_bounds(p.qmin, p.qmax, f);
+            const int2 run = p.sign ? best_run<1>(cd, keys, C, cd.n, Bq, fast, bzs, bss, bls)
+                                    : best_run<0>(cd, keys, C, cd.n, Bq, fast, bzs, bss, bls);
+            if (threadIdx.x == 0) {
+                const int a = run.x, len = run.y;
+                DevPeak pk = {};
+                pk.j = j; pk.i1 = a; pk.k = len;
+                pk.freq = f;
+                pk.period = 1.0 / f;
+                if (len > 0) {
+                    double r = 0.0, s = 0.0;
+                    for (int l = 0; l < len; ++l) {
+                        int qq = a + l;
+                        if (qq >= cd.n) qq -= cd.n;
+                        const int i = (int)(keys[qq] & 0xffffffffu);
+                        double inv = 1.0;
+                        if (cd.dy) { const double dd = (double)cd.dy[i]; inv = __ddiv_rn(1.0, __dmul_rn(dd, dd)); }
+                        const double w = __ddiv_rn(inv, cd.W);
+                        r = __dadd_rn(r, w);
+                        s = __dadd_rn(s, __dmul_rn(w, __dsub_rn((double)cd.y[i], cd.ybar)));
+                    }
+                    // extent and mid-box phase as the definition computes them
+                    const double E = exact_extent(cd, keys, cd.n, a, a + len - 1, f);
+                    const double ph0 = point_phase(cd, (int)(keys[a] & 0xffffffffu), f);
+                    double mid = __dadd_rn(ph0, __dmul_rn(0.5, E));
+                    mid = __dsub_rn(mid, floor(mid));
+                    pk.epoch = __dadd_rn(cd.t_ref, __ddiv_rn(mid, f));
+                    pk.duration = __ddiv_rn(E, f);
+                    if (r > 0.0 && r < 1.0 && (p.sign || s < 0.0)) {
+                        pk.power = s * s / (r * (1.0 - r));
+                        pk.depth = -s / (r * (1.0 - r));
+                        pk.sr = sqrt(pk.power);
+                        pk.snr = pk.sr * sqrt(cd.W);
+                    }
+                }
+                pk.sde = srsd > 0.0 ? (pk.sr - srmean) / srsd : 0.0;
+                *out = pk;
+            }
+            __syncthreads();
+        }
+    __syncthreads();
     }
 }
 
 }  // namespace
 
-size_t ubls_smem_bytes(int nmax)
+size_t ubls_work_bytes(int nmax)
 {
     int M = 1;
     while (M < nmax) M <<= 1;
@@ -786,23 +810,25 @@ size_t ubls_smem_bytes(int nmax)
 
 int ubls_tile() { return kTile; }
 
-cudaError_t launch_ubls(const UblsParams& p, long long nitems, cudaStream_t s)
+cudaError_t launch_ubls(const UblsParams& p, cudaStream_t s)
 {
-    if (nitems <= 0) return cudaSuccess;
-    const size_t smem = ubls_smem_bytes(p.nmax);
+    if (p.nitems <= 0) return cudaSuccess;
+    const size_t smem = p.scratch ? 0 : ubls_work_bytes(p.nmax);
     cudaError_t e = cudaFuncSetAttribute(ubls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    ubls_kernel<<<(unsigned)nitems, kUThreads, smem, s>>>(p);
+    const long long grid = p.scratch ? (p.grid < p.nitems ? p.grid : p.nitems) : p.nitems;
+    ubls_kernel<<<(unsigned)grid, kUThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ubls_reduce(const UblsParams& p, cudaStream_t s)
 {
     if (p.ncurves <= 0) return cudaSuccess;
-    const size_t smem = ubls_smem_bytes(p.nmax);
+    const size_t smem = p.scratch ? 0 : ubls_work_bytes(p.nmax);
     cudaError_t e = cudaFuncSetAttribute(ubls_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    ubls_reduce_kernel<<<p.ncurves, kUThreads, smem, s>>>(p);
+    const int grid = p.scratch ? (p.grid < p.ncurves ? p.grid : p.ncurves) : p.ncurves;
+    ubls_reduce_kernel<<<grid, kUThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -140,9 +140,30 @@ def test_tiny_and_edge_cases():
     assert np.all(spec == 0) and pk[0, 0]["power"] == 0.0
 
 
+def test_long_curves_in_global_scratch():
+    """Curves above the shared-memory size (a 20,000-point curve, the serving workload's
+    longest, searched together with a 3000-point one): the working arrays live in a global
+    scratch slice per persistent block; the search is the oracle's, as for short curves."""
+    rng = np.random.default_rng(21)
+    cis = []
+    for n, P0 in ((20000, 1.7), (3000, 0.9)):
+        t = synth.T0 + np.sort(rng.uniform(0, 60, n))
+        y = (1 + rng.normal(0, 0.01, n)
+             - 0.015 * (np.mod(t - synth.T0 - 0.2, P0) < 0.06)).astype(np.float32)
+        dy = rng.uniform(0.008, 0.012, n).astype(np.float32)
+        freqs = np.sort(np.concatenate([rng.uniform(0.3, 2.0, 23), [1 / P0]]))
+        cis.append(bls.CurveInput(t, y, dy, freqs=freqs, nb=200, qmin=0.005, qmax=0.05))
+    for sign, sg in (("dips", 0), ("both", 1)):
+        pk, spec = _run(cis, sign=sign, qmin=0.005, qmax=0.05)
+        o = 0
+        for c, ci in enumerate(cis):
+            _check(ci, pk[c, 0], spec[o:o + 24], sign=sg, qmin=0.005, qmax=0.05)
+            o += 24
+
+
 def test_limits_and_unsupported():
     rng = np.random.default_rng(1)
-    n = 9000
+    n = 40000
     t = synth.T0 + np.sort(rng.uniform(0, 10, n))
     ci = bls.CurveInput(t, np.ones(n, np.float32), None, nf=3, fmin=0.5, df=0.1, nb=50,
                         qmin=QMIN, qmax=QMAX)
