@@ -677,13 +677,14 @@ def roofline(units, evals, launches_per_step, fold_ms, sms, clk_mhz, run_mhz, ke
     return out
 
 
-def measure(batch, topk, args, ctx, tune=True, e2e=True, steps=None):
+def measure(batch, topk, args, ctx, tune=True, e2e=True, steps=None, warmup=None, sums="f32"):
     """Device-timed and end-to-end search of one batch: warm-up, then `steps` searches of
     the device-resident packed batch between barriers (CUDA events on the plan's stream,
     L2 flushed before each), then the same through pinned host buffers (wall clock)."""
     import torch
     from paper_1112_1701_b300 import autotune, bls
     steps = steps or args.steps
+    warmup = args.warmup if warmup is None else warmup
     nb = batch.nb[0]
     stream = ctx["stream"]
     units = batch.point_freqs()
@@ -693,14 +694,14 @@ def measure(batch, topk, args, ctx, tune=True, e2e=True, steps=None):
     if tune and not args.no_autotune:
         t0 = time.perf_counter()
         res = autotune.tune(dev, nb, batch.qmin, batch.qmax, stream=stream.cuda_stream,
-                            cache=autotune.TuneCache(None))
+                            cache=autotune.TuneCache(None), sums=sums)
         tuned = dict(res.to_json(), tuning_s=time.perf_counter() - t0)
         launch_kw = res.best.plan_kwargs()
-    plan = bls.Plan(nb=nb, qmin=batch.qmin, qmax=batch.qmax, topk=topk,
+    plan = bls.Plan(nb=nb, qmin=batch.qmin, qmax=batch.qmax, topk=topk, sum=sums,
                     stream=stream.cuda_stream, **launch_kw)
     flush = ctx["flush"]
     devp = bls.packed_from_batch(batch, device="cuda")
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.zero_()
         plan.search(devp)
     plan.profile(reset=True)
@@ -739,7 +740,7 @@ def measure(batch, topk, args, ctx, tune=True, e2e=True, steps=None):
                                else "fold_sweep_kernel")
     if e2e and not args.no_e2e:
         hostc = bls.packed_from_batch(batch, pinned=True)
-        for _ in range(max(1, min(args.warmup, 2))):
+        for _ in range(max(1, min(warmup, 2))):
             plan.search(hostc)
         ctx["barrier"]()
         t0 = time.perf_counter()
@@ -770,6 +771,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-shapes", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload object")
+    ap.add_argument("--no-kahan", action="store_true", help="skip the Kahan-sums object")
+    ap.add_argument("--kahan-steps", type=int, default=3)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving object")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's launch rules instead of the autotuner's choice")
@@ -877,6 +880,19 @@ def main():
     if args.plain_curves > 0 and rank == 0:
         line["plain_f64_gpu"] = plain_f64_sample(batch, args.plain_curves, m["value"] / world)
     del m
+
+    # ---- the same workload with Kahan-compensated FP32 histograms and box sums
+    if not args.no_kahan:
+        mk = measure(batch, topk, args, ctx, e2e=False, steps=args.kahan_steps, warmup=1,
+                     sums="kahan")
+        line["kahan_sums"] = {"value": mk["value"], "unit": UNIT, "ms_per_step": mk["ms_per_step"],
+                              "steps": args.kahan_steps, "warmup": 1,
+                              "roofline_frac": mk["roofline"]["frac"],
+                              "kernel_ms": mk["kernel_ms"], "launch": mk["launch"],
+                              "note": "same roofline model (16 B per point x frequency counted "
+                                      "as for plain sums; the Kahan entries move 32 B)"}
+        mk["plan"].close()
+        del mk
 
     # ---- secondary: the batched workload (1024 curves x 50,000 frequencies, nb = 200)
     if not args.no_batched:

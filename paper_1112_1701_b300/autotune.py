@@ -72,8 +72,8 @@ def candidates(nb: int, kmin: int, kmax: int, sums: str = "f32",
                smem_optin: int = 232448, reserve: int = 2048) -> List[Candidate]:
     """Feasible candidates for one nb: for each chunk size, the tile widths (multiples of 16)
     from the widest that fits shared memory down to half of it (at least 32), in both kernels
-    where the warp-specialised one can take the width (a multiple of 8, at most 128, plain
-    sums); plus the library's own choice."""
+    where the warp-specialised one can take the width (a multiple of 8, at most 128); plus
+    the library's own choice."""
     esz = 16 if sums == "kahan" else 8
     out = [DEFAULT]
     for chunk in CHUNKS:
@@ -89,7 +89,7 @@ def candidates(nb: int, kmin: int, kmax: int, sums: str = "f32",
                         reverse=True)
         for T in widths:
             out.append(Candidate(T, chunk, "one_group"))
-            if sums != "kahan" and T % 8 == 0 and T <= 128:
+            if T % 8 == 0 and T <= 128:
                 out.append(Candidate(T, chunk, "ws"))
     return out
 

@@ -648,6 +648,24 @@ __device__ __forceinline__ void sts64(unsigned addr, u64 v)
 {
     asm volatile("st.shared.b64 [%0], %1;" ::"r"(addr), "l"(v));
 }
+// A Kahan histogram entry (sum w, sum w x, comp w, comp w x) as two packed pairs.
+__device__ __forceinline__ void lds128(unsigned addr, u64& h, u64& c)
+{
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(h), "=l"(c) : "r"(addr));
+}
+__device__ __forceinline__ void sts128(unsigned addr, u64 h, u64 c)
+{
+    asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(addr), "l"(h), "l"(c));
+}
+// Kahan-compensated addition of q to the pair sums h with compensations c (both components
+// at once, as kahan_add does for one): y = q - c, t = h + y, c = (t - h) - y, h = t.
+__device__ __forceinline__ void kahan2(u64& h, u64& c, u64 q)
+{
+    const u64 y = sub2(q, c);
+    const u64 t = add2(h, y);
+    c = sub2(sub2(t, h), y);
+    h = t;
+}
 
 // Bins of the 8 point pairs of a 16-point sub-chunk, with their weight pairs; returns
 // whether any bin is not certain (then fix_sub must run before the bins are used).
@@ -723,13 +741,47 @@ __device__ __forceinline__ void rmw_sub(unsigned hbase, unsigned rowb, const uns
     }
 }
 
+// As rmw_sub for a Kahan histogram (16-byte entries): the merged addend of each point is
+// added with compensation.
+__device__ __forceinline__ void rmw_sub_k(unsigned hbase, unsigned rowb, const unsigned* b,
+                                          const float4* Bw, unsigned nbu, int* err)
+{
+    constexpr int G = kRmwGroup;
+#pragma unroll
+    for (int g = 0; g < 16 / G; ++g) {
+        const unsigned* bg = b + G * g;
+        unsigned a[G];
+        u64 h[G], c[G], q[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            a[i] = hbase + (bls_ok(bg[i] < nbu, err) ? bg[i] : 0u) * rowb;
+            lds128(a[i], h[i], c[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const float4& w = Bw[(G * g + i) >> 1];
+            q[i] = (i & 1) ? pk(w.z, w.w) : pk(w.x, w.y);
+        }
+#pragma unroll
+        for (int i = G - 1; i > 0; --i) {
+#pragma unroll
+            for (int j = 0; j < i; ++j) q[i] = add2_if_eq(q[i], q[j], bg[i], bg[j]);
+        }
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            kahan2(h[i], c[i], q[i]);
+            sts128(a[i], h[i], c[i]);
+        }
+    }
+}
+
 // Bins nsub staged 16-point sub-chunks into this thread's histogram (FP32 sums, point
 // order).  Software pipeline: the next sub-chunk's points are loaded and folded (8
 // independent pairs) in the same basic block as the current sub-chunk's read-modify-write
 // chain, so the fold arithmetic fills the shared-memory latency of the chain; the rare
 // FP64 re-fold runs after the stores.  hbase is the shared-memory address of this
 // thread's bin 0, rowb the byte stride between bins.
-template <int PHASE, bool PINGPONG, bool INC>
+template <int PHASE, bool PINGPONG, bool INC, bool KAHAN = false>
 __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int nsub,
                                          unsigned hbase, unsigned rowb, const FoldConst& fc,
                                          const FoldPacked& fq, int* err)
@@ -746,29 +798,29 @@ __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int
         for (; sc + 2 < nsub; sc += 2) {
             const float4* n1 = cp + 16 * (sc + 1);
             const bool e1 = fold_sub<PHASE, INC>(n1, fc, fq, b1, W1);
-            rmw_sub(hbase, rowb, b0, W0, nbu, err);
+            if (KAHAN) rmw_sub_k(hbase, rowb, b0, W0, nbu, err); else rmw_sub(hbase, rowb, b0, W0, nbu, err);
             if (e1) fix_sub<PHASE, INC>(n1, cd + 16 * (sc + 1), fc, fq, b1);
             const float4* n2 = cp + 16 * (sc + 2);
             const bool e2 = fold_sub<PHASE, INC>(n2, fc, fq, b0, W0);
-            rmw_sub(hbase, rowb, b1, W1, nbu, err);
+            if (KAHAN) rmw_sub_k(hbase, rowb, b1, W1, nbu, err); else rmw_sub(hbase, rowb, b1, W1, nbu, err);
             if (e2) fix_sub<PHASE, INC>(n2, cd + 16 * (sc + 2), fc, fq, b0);
         }
     }
     for (; sc + 1 < nsub; ++sc) {
         const float4* n1 = cp + 16 * (sc + 1);
         const bool e1 = fold_sub<PHASE, INC>(n1, fc, fq, b1, W1);
-        rmw_sub(hbase, rowb, b0, W0, nbu, err);
+        if (KAHAN) rmw_sub_k(hbase, rowb, b0, W0, nbu, err); else rmw_sub(hbase, rowb, b0, W0, nbu, err);
         if (e1) fix_sub<PHASE, INC>(n1, cd + 16 * (sc + 1), fc, fq, b1);
 #pragma unroll
         for (int i = 0; i < 16; ++i) b0[i] = b1[i];
 #pragma unroll
         for (int q = 0; q < 8; ++q) W0[q] = W1[q];
     }
-    rmw_sub(hbase, rowb, b0, W0, nbu, err);
+    if (KAHAN) rmw_sub_k(hbase, rowb, b0, W0, nbu, err); else rmw_sub(hbase, rowb, b0, W0, nbu, err);
 }
 
 // Generic binning (FP64 or FP32 phase modes, precision studies): pair by pair.
-template <int PHASE>
+template <int PHASE, bool KAHAN = false>
 __device__ __forceinline__ void bin_generic(const float4* cp, const double* cd, int npairs,
                                             unsigned hbase, unsigned rowb, const FoldConst& fc,
                                             const FoldPacked& fq, int* err)
@@ -780,8 +832,18 @@ __device__ __forceinline__ void bin_generic(const float4* cp, const double* cd, 
         const unsigned nbu = (unsigned)fc.nb;
         const unsigned a0 = hbase + (bls_ok(b0 < nbu, err) ? b0 : 0u) * rowb;
         const unsigned a1 = hbase + (bls_ok(b1 < nbu, err) ? b1 : 0u) * rowb;
-        sts64(a0, add2(lds64(a0), pk(B.x, B.y)));
-        sts64(a1, add2(lds64(a1), pk(B.z, B.w)));
+        if (KAHAN) {
+            u64 h, c;
+            lds128(a0, h, c);
+            kahan2(h, c, pk(B.x, B.y));
+            sts128(a0, h, c);
+            lds128(a1, h, c);
+            kahan2(h, c, pk(B.z, B.w));
+            sts128(a1, h, c);
+        } else {
+            sts64(a0, add2(lds64(a0), pk(B.x, B.y)));
+            sts64(a1, add2(lds64(a1), pk(B.z, B.w)));
+        }
     }
 }
 
@@ -1711,7 +1773,7 @@ __device__ void fetch_tile(const FoldParams& p, TileSlot* slot, int lane)
 // hands them back (the binning group zeroes them) and sweeps the boxes from TMEM.
 constexpr int kWsBinThreads = 128, kWsSweepThreads = 256, kWsSweep0 = 128;
 
-template <int SIGN>
+template <int SIGN, int KAHAN>
 __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_ok, int col,
                                                  unsigned s_tmem, TileSlot* s_slot,
                                                  unsigned full_bar, unsigned empty_bar,
@@ -1761,9 +1823,18 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
                 const unsigned ag = hbase + (unsigned)g * rowb;
                 u64 h[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    h[i] = bls_ok(g + i < 2 * nb, p.err)
-                               ? lds64(ag + (unsigned)i * rowb - (g + i >= nb ? wrapb : 0u)) : 0ull;
+                for (int i = 0; i < 8; ++i) {
+                    const unsigned ai = ag + (unsigned)i * rowb - (g + i >= nb ? wrapb : 0u);
+                    if (!bls_ok(g + i < 2 * nb, p.err)) {
+                        h[i] = 0ull;
+                    } else if (KAHAN) {   // the compensated sums (sum - compensation)
+                        u64 hh, cc;
+                        lds128(ai, hh, cc);
+                        h[i] = sub2(hh, cc);
+                    } else {
+                        h[i] = lds64(ai);
+                    }
+                }
                 unsigned r[16];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -1780,9 +1851,9 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         } else if (part == 0) {
             if (active)
-                v = SB == 4 ? sweep_max<0, SIGN, 4>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err)
-                    : SB == 10 ? sweep_max<0, SIGN, 10>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err)
-                               : sweep_max<0, SIGN, 8>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err);
+                v = SB == 4 ? sweep_max<KAHAN, SIGN, 4>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err)
+                    : SB == 10 ? sweep_max<KAHAN, SIGN, 10>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err)
+                               : sweep_max<KAHAN, SIGN, 8>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err);
         }
         // the histograms are only read here: the binning group zeroes them when it starts
         // the next tile (after this hand-over)
@@ -1846,7 +1917,7 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
 
 constexpr int kWsMaxThreads = 384;
 
-template <int PHASE, int SIGN>
+template <int PHASE, int KAHAN, int SIGN>
 __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1871,10 +1942,11 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
     float4* cpts = reinterpret_cast<float4*>(smem);             // [2][CH]: point pairs
     double* cdt = reinterpret_cast<double*>(cpts + 2 * CH);     // [2][CH]: FP64 offsets
     unsigned char* hist_all = reinterpret_cast<unsigned char*>(cdt + 2 * CH);
-    unsigned char* hist = hist_all + (size_t)col * sizeof(float2);
+    constexpr size_t ESZ = KAHAN ? sizeof(float4) : sizeof(float2);   // histogram entry
+    unsigned char* hist = hist_all + (size_t)col * ESZ;
     const size_t S = (size_t)p.stride;
     const unsigned hbase = (unsigned)__cvta_generic_to_shared(hist);
-    const unsigned rowb = (unsigned)(S * sizeof(float2));
+    const unsigned rowb = (unsigned)(S * ESZ);
     const unsigned full_bar = (unsigned)__cvta_generic_to_shared(&s_bar[0]);
     const unsigned empty_bar = (unsigned)__cvta_generic_to_shared(&s_bar[1]);
 
@@ -1884,7 +1956,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
         const size_t rows = (dyn - (size_t)2 * CH * (sizeof(float4) + sizeof(double))) / rowb;
         u64* h = reinterpret_cast<u64*>(hist_all);
-        for (size_t e = tid; e < rows * S; e += blockDim.x) h[e] = 0ull;
+        for (size_t e = tid; e < rows * S * (ESZ / 8); e += blockDim.x) h[e] = 0ull;
     }
     if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -1919,7 +1991,10 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             const int n = cdr.n, nf = cdr.nf, nb = cdr.nb;
             if (lane_ok) {   // zero this thread's histogram column; the sweep group has
                              // finished reading it (the empty hand-over above)
-                for (int b = 0; b < nb; ++b) sts64(hbase + (unsigned)b * rowb, 0ull);
+                for (int b = 0; b < nb; ++b) {
+                    if (KAHAN) sts128(hbase + (unsigned)b * rowb, 0ull, 0ull);
+                    else sts64(hbase + (unsigned)b * rowb, 0ull);
+                }
             }
             __syncwarp();
             const float4* gpts = cdr.pts;
@@ -1983,18 +2058,18 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                 if (active) {   // a3 + a4
                     if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
                         if (inc)
-                            bin_fast<PHASE, true, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
+                            bin_fast<PHASE, true, true, KAHAN>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                         else
-                            bin_fast<PHASE, true, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
+                            bin_fast<PHASE, true, false, KAHAN>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                     } else
-                        bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq, p.err);
+                        bin_generic<PHASE, KAHAN>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq, p.err);
                 }
                 group_sync(kBarBin, kWsBinThreads);
             }
             if (tid == 0) mbar_arrive(full_bar);
         }
     } else {
-        sweep_group_loop<SIGN>(p, lane_ok, col, s_tmem, s_slot, full_bar, empty_bar, s_wpart,
+        sweep_group_loop<SIGN, KAHAN>(p, lane_ok, col, s_tmem, s_slot, full_bar, empty_bar, s_wpart,
                                s_wpart2, hist, hbase, rowb);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -2006,7 +2081,8 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
     }
 }
 
-// Tile geometries the warp-specialised kernel can take: plain sums, T a multiple of 8, at
+// Tile geometries the warp-specialised kernel can take: plain or Kahan sums (16-byte
+// entries, whose compensated values the sweep group copies into TMEM), T a multiple of 8, at
 // most 128 (T/4 columns per TMEM lane quadrant).  BLS_FOLD_WS=0 in the environment selects
 // fold_sweep_kernel for every class.
 static bool use_ws(int T, int kahan)
@@ -2015,7 +2091,8 @@ static bool use_ws(int T, int kahan)
         const char* e = getenv("BLS_FOLD_WS");
         return (e && e[0] == '0') ? 0 : 1;
     }();
-    return env && !kahan && T % 8 == 0 && T >= 8 && T <= 128;
+    (void)kahan;   // plain and Kahan histograms alike
+    return env && T % 8 == 0 && T >= 8 && T <= 128;
 }
 
 // Threads of a warp-specialised block: binning warps 0-3, sweep warps 4-11, whatever the
@@ -2075,7 +2152,7 @@ static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t sm
     FoldParams q = p;
     q.cols = T;
     if (ws && use_ws(T, KAHAN)) {
-        auto k = fold_sweep_ws_kernel<PHASE, SIGN>;
+        auto k = fold_sweep_ws_kernel<PHASE, KAHAN, SIGN>;
         const size_t sm = ws_smem(smem);
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sm);
@@ -2096,7 +2173,7 @@ static int blocks_t(int T, size_t smem, int ws)
 {
     if (ws && use_ws(T, KAHAN)) {
         // one block per SM: all of TMEM and (nearly) all of shared memory
-        auto k = fold_sweep_ws_kernel<PHASE, SIGN>;
+        auto k = fold_sweep_ws_kernel<PHASE, KAHAN, SIGN>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem(smem)) != cudaSuccess) {
             cudaGetLastError();
             return 1;

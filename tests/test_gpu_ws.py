@@ -160,3 +160,24 @@ def test_bounded_handover_wait_runs_out_and_plan_recovers(monkeypatch):
         pk2 = p2.search([ci], spectrum=spec2)
     assert np.array_equal(spec, spec2)
     assert np.array_equal(pk, pk2)
+
+
+@pytest.mark.parametrize("nb", [200, 256])
+def test_kahan_sums_in_both_kernels(nb):
+    """Kahan-compensated histograms (16-byte entries) in the warp-specialised kernel (the
+    default for such plans) and in the one-group kernel: both within the parity tolerance
+    of the oracle, and within FP32 rounding of each other (the warp-specialised kernel
+    adds the pre-merged weights of points sharing a bin in one compensated addition)."""
+    b = synth.config2(ncurves=3, nf=900, seed=44)
+    cis = [bls.CurveInput(ci.t, ci.y, ci.dy, nf=ci.nf, fmin=ci.fmin, df=ci.df, nb=nb,
+                          qmin=ci.qmin, qmax=ci.qmax) for ci in bls.curves_from_batch(b)]
+    out = {}
+    for kern in ("auto", "one_group"):
+        spec = np.zeros(3 * 900, np.float32)
+        with bls.Plan(nb=nb, qmin=b.qmin, qmax=b.qmax, topk=2, sum="kahan",
+                      fold_kernel=kern) as p:
+            pk = p.search(cis, spectrum=spec)
+        _oracle_check(cis, spec, nb, b.qmin, b.qmax, 0)
+        out[kern] = (spec, pk)
+    np.testing.assert_allclose(out["auto"][0], out["one_group"][0], rtol=1e-6, atol=0)
+    assert np.array_equal(out["auto"][1]["j"][:, 0], out["one_group"][1]["j"][:, 0])
