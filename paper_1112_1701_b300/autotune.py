@@ -16,12 +16,14 @@ For a batch of curves that share nb and the duration range it:
   * returns the fastest, and caches it per (device, nb, kmin, kmax, phase mode, sums, sign,
     curve-length class) in memory and, when a path is given, in a JSON file.
 
-Curves per launch are not tuned: one persistent launch per class of curves is the design,
-and the plan's memory budget splits a batch only when it does not fit.  Mixed-nb workloads
-(serving) keep the per-class rules, since a plan's tile width applies to all its curves.
+A second stage tunes the curves per launch: with the best of the above, the sample is
+searched in one, two and four launches (max_curves_per_launch), and the fastest split
+(ties to fewer launches) is applied to the whole batch.  Mixed-nb workloads (serving) keep
+the per-class rules, since a plan's tile width applies to all its curves.
 """
 from __future__ import annotations
 
+import dataclasses
 import json
 import math
 import os
@@ -35,6 +37,7 @@ from . import bls
 
 CHUNKS = (512, 256)
 MAX_T = 256          # fold_sweep_max_threads()
+SPLITS = (2, 4)      # launches per batch tried by the second stage (besides one)
 
 
 @dataclass(frozen=True)
@@ -42,10 +45,11 @@ class Candidate:
     freqs_per_block: int   # 0 = the library's rule
     point_chunk: int       # 0 = the library's rule
     fold_kernel: str       # key of bls.FOLD
+    curves_per_launch: int = 0   # 0 = every curve of a class in one launch
 
     def plan_kwargs(self) -> dict:
         return dict(freqs_per_block=self.freqs_per_block, point_chunk=self.point_chunk,
-                    fold_kernel=self.fold_kernel)
+                    fold_kernel=self.fold_kernel, max_curves_per_launch=self.curves_per_launch)
 
 
 DEFAULT = Candidate(0, 0, "auto")
@@ -60,10 +64,13 @@ class TuneResult:
     key: str = ""
     sample: str = ""
     cached: bool = False
+    splits: int = 1                 # launches the batch is split into
 
     def to_json(self) -> dict:
         return {"freqs_per_block": self.best.freqs_per_block,
                 "point_chunk": self.best.point_chunk, "fold_kernel": self.best.fold_kernel,
+                "launch_splits": self.splits,
+                "curves_per_launch": self.best.curves_per_launch,
                 "best_ms": self.best_ms, "default_ms": self.default_ms, "key": self.key,
                 "sample": self.sample, "candidates": len(self.table)}
 
@@ -132,12 +139,14 @@ class TuneCache:
             with open(path) as f:
                 self._d = json.load(f)
 
-    def get(self, key: str) -> Optional[Candidate]:
+    def get(self, key: str) -> Optional[tuple]:
+        """(Candidate without the batch's curves per launch, launch splits) or None."""
         with self._lock:
             v = self._d.get(key)
         if v is None:
             return None
-        return Candidate(int(v["freqs_per_block"]), int(v["point_chunk"]), str(v["fold_kernel"]))
+        return (Candidate(int(v["freqs_per_block"]), int(v["point_chunk"]), str(v["fold_kernel"])),
+                int(v.get("launch_splits", 1)))
 
     def put(self, key: str, res: TuneResult):
         with self._lock:
@@ -196,10 +205,16 @@ def tune(curves: Sequence[bls.CurveInput], nb: int, qmin: float, qmax: float, *,
     name, sms = device
     kmin, kmax = bls.kminmax(nb, qmin, qmax)
     key = cache_key(name, sms, nb, kmin, kmax, phase, sums, sign, length_class(curves))
+    def for_batch(c: Candidate, splits: int) -> Candidate:
+        return dataclasses.replace(
+            c, curves_per_launch=0 if splits == 1 else int(math.ceil(len(curves) / splits)))
+
     if use_cache:
         hit = cache.get(key)
         if hit is not None:
-            return TuneResult(hit, float("nan"), float("nan"), [], key, "cache", True)
+            c, splits = hit
+            return TuneResult(for_batch(c, splits), float("nan"), float("nan"), [], key, "cache",
+                              True, splits)
     cands = candidates(nb, kmin, kmax, sums)
     widest = max(c.freqs_per_block for c in cands if c.freqs_per_block) if len(cands) > 1 else 128
     smp = sample_curves(curves, sample, tiles_per_sm * sms, widest)
@@ -212,10 +227,20 @@ def tune(curves: Sequence[bls.CurveInput], nb: int, qmin: float, qmax: float, *,
         raise RuntimeError("no feasible launch configuration for nb = %d" % nb)
     best, best_ms = min(ok, key=lambda x: (x[1], x[0] != DEFAULT))
     default_ms = dict(table).get(DEFAULT) or float("nan")
+    # second stage: the sample in 1, 2 or 4 launches
+    splits = 1
+    for sp in SPLITS:
+        if len(smp) < sp:
+            break
+        c2 = dataclasses.replace(best, curves_per_launch=int(math.ceil(len(smp) / sp)))
+        ms = timer(c2, smp, nb, qmin, qmax, phase, sums, sign, reps, stream=stream)
+        table.append((c2, ms))
+        if ms is not None and ms < best_ms:
+            best_ms, splits = ms, sp
     nfs = [len(c.freqs) if c.freqs is not None else c.nf for c in smp]
-    res = TuneResult(best, best_ms, default_ms, table, key,
+    res = TuneResult(for_batch(best, splits), best_ms, default_ms, table, key,
                      f"{len(smp)} curves (length quantiles), {min(nfs)}-{max(nfs)} frequencies "
-                     f"each, {reps} timed searches per candidate")
+                     f"each, {reps} timed searches per candidate", False, splits)
     cache.put(key, res)
     return res
 

@@ -76,7 +76,9 @@ def test_tune_picks_fastest_skips_infeasible_and_caches(tmp_path):
     assert res.best == at.Candidate(96, 512, "ws") and res.best_ms == 5.0
     assert res.default_ms == 10.0 and not res.cached
     assert any(ms is None for _, ms in res.table)
-    assert len(calls) == len(at.candidates(200, 1, 30))
+    # every candidate, then the best one in two and four launches (no gain: one launch kept)
+    assert len(calls) == len(at.candidates(200, 1, 30)) + len(at.SPLITS)
+    assert res.splits == 1 and res.best.curves_per_launch == 0
     saved = json.load(open(path))
     assert res.key in saved and saved[res.key]["freqs_per_block"] == 96
     # a second run hits the cache (in a fresh cache object reading the file)
@@ -88,6 +90,29 @@ def test_tune_picks_fastest_skips_infeasible_and_caches(tmp_path):
     res3 = at.tune(cis, 200, 0.005, 0.15, timer=timer2, cache=at.TuneCache(path),
                    device=("B300", 132))
     assert not res3.cached
+
+
+def test_second_stage_picks_the_launch_split():
+    """When the sample runs faster in four launches, the whole batch is split into four:
+    curves_per_launch = ceil(N / 4) for the batch (not the sample), and the cache keeps the
+    split, not the count."""
+    b = synth.config2(ncurves=50, nf=2000, seed=5)
+    cis = bls.curves_from_batch(b)
+
+    def cost(c):
+        if c.freqs_per_block == 0:
+            return 10.0
+        if c.curves_per_launch:
+            return 4.0 if c.curves_per_launch <= 8 else 6.0
+        return 9.0 if (c.freqs_per_block, c.point_chunk) == (128, 512) else 20.0
+    timer, calls = _fake_timer(cost)
+    cache = at.TuneCache(None)
+    res = at.tune(cis, 200, 0.005, 0.15, timer=timer, cache=cache, device=("B300", 148))
+    assert res.splits == 4 and res.best_ms == 4.0
+    assert res.best.curves_per_launch == 13                      # ceil(50 / 4)
+    assert res.best.plan_kwargs()["max_curves_per_launch"] == 13
+    hit = at.tune(cis[:20], 200, 0.005, 0.15, timer=timer, cache=cache, device=("B300", 148))
+    assert hit.cached and hit.splits == 4 and hit.best.curves_per_launch == 5   # ceil(20 / 4)
 
 
 def test_ties_keep_the_library_rule():
