@@ -270,6 +270,29 @@ typedef struct {
 /* Serving statistics.  Errors: BLS_ERR_INVALID. */
 bls_status bls_server_stats_get(bls_plan* plan, bls_server_stats* out);
 
+/* Signal detection efficiency across frequency shards (the SDE of Kovacs, Zucker & Mazeh
+ * 2002 that Sec. 2.2.2 cites: (SR_peak - mean SR) / sd SR over a curve's whole spectrum,
+ * population sd).  When one curve's grid is searched in slices (one per GPU or per call),
+ * each slice's SR spectrum is reduced to its moments, the moments are merged (Chan, Golub
+ * and LeVeque's pairwise update), and the best peak's SDE is computed from the merged ones.
+ * Host-side arithmetic in FP64. */
+typedef struct {
+    long long count;        /* number of SR values */
+    double mean;            /* their mean */
+    double m2;              /* sum of squared deviations from the mean */
+} bls_moments;
+
+/* Moments of sr[0..n) (host or device memory of the current device), two passes in FP64.
+ * Errors: BLS_ERR_INVALID (NULL pointers, n < 0), BLS_ERR_CUDA, BLS_ERR_NOMEM. */
+bls_status bls_moments_of(const float* sr, long long n, bls_moments* out);
+
+/* Moments of the union of nparts disjoint parts.  Errors: BLS_ERR_INVALID. */
+bls_status bls_moments_merge(const bls_moments* parts, int nparts, bls_moments* out);
+
+/* SDE of a peak of signal residue sr against a spectrum's moments: 0 for a flat or empty
+ * spectrum.  Errors: BLS_ERR_INVALID. */
+bls_status bls_sde(double sr, const bls_moments* m, double* sde);
+
 /* Box widths from the fractional duration range (reading of the paper's "range of
  * durations"): kmin = max(1, floor(qmin nb + 1e-9)), kmax = min(nb-1, ceil(qmax nb - 1e-9)).
  * Errors: BLS_ERR_INVALID. */

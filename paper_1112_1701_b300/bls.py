@@ -116,7 +116,7 @@ _lock = threading.Lock()
 EXPORTS = ["bls_plan_create", "bls_plan_destroy", "bls_search", "bls_submit", "bls_poll",
            "bls_cancel", "bls_server_stats_get", "bls_kminmax", "bls_debug_fold",
            "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_window_efficiency", "bls_refine", "bls_search_shapes", "bls_variability",
-           "bls_last_error"]
+           "bls_moments_of", "bls_moments_merge", "bls_sde", "bls_last_error"]
 
 
 def lib():
@@ -138,6 +138,9 @@ def lib():
             L.bls_cancel.argtypes = [P, C.c_uint64]
             L.bls_server_stats_get.argtypes = [P, C.POINTER(ServerStats)]
             L.bls_kminmax.argtypes = [I, D, D, C.POINTER(I), C.POINTER(I)]
+            L.bls_moments_of.argtypes = [P, C.c_longlong, C.POINTER(Moments)]
+            L.bls_moments_merge.argtypes = [C.POINTER(Moments), I, C.POINTER(Moments)]
+            L.bls_sde.argtypes = [D, C.POINTER(Moments), C.POINTER(D)]
             L.bls_debug_fold.argtypes = [P, C.POINTER(CurveStruct), P, I, P]
             L.bls_debug_powers.argtypes = [P, C.POINTER(CurveStruct), P, P, P]
             L.bls_profile_get.argtypes = [P, C.POINTER(Profile), I]
@@ -163,6 +166,36 @@ def kminmax(nb: int, qmin: float, qmax: float):
     a, b = C.c_int(), C.c_int()
     _check(lib().bls_kminmax(nb, qmin, qmax, C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+class Moments(C.Structure):
+    _fields_ = [("count", C.c_longlong), ("mean", C.c_double), ("m2", C.c_double)]
+
+
+def moments_of(sr) -> tuple:
+    """``bls_moments_of``: (count, mean, M2) of an SR spectrum (FP32, host or device)."""
+    a = _host(sr, np.float32, "sr")
+    m = Moments()
+    _check(lib().bls_moments_of(_ptr(a), _len(a), C.byref(m)))
+    return m.count, m.mean, m.m2
+
+
+def moments_merge(parts) -> tuple:
+    """``bls_moments_merge``: moments of the union of disjoint parts' (count, mean, M2)."""
+    arr = (Moments * max(1, len(parts)))(*[Moments(int(n), float(mu), float(m2))
+                                             for n, mu, m2 in parts])
+    m = Moments()
+    _check(lib().bls_moments_merge(arr, len(parts), C.byref(m)))
+    return m.count, m.mean, m.m2
+
+
+def sde(sr: float, moments) -> float:
+    """``bls_sde``: signal detection efficiency of a peak against merged moments."""
+    n, mu, m2 = moments
+    m = Moments(int(n), float(mu), float(m2))
+    out = C.c_double()
+    _check(lib().bls_sde(float(sr), C.byref(m), C.byref(out)))
+    return out.value
 
 
 def _ptr(a):

@@ -758,6 +758,62 @@ extern "C" {
 
 const char* bls_last_error(void) { return g_last_error.c_str(); }
 
+bls_status bls_moments_of(const float* sr, long long n, bls_moments* out)
+{
+    if (!out || n < 0 || (n > 0 && !sr)) return set_error(BLS_ERR_INVALID, "bad argument");
+    *out = bls_moments{0, 0.0, 0.0};
+    if (n == 0) return BLS_OK;
+    std::vector<float> host;
+    const float* v = sr;
+    if (ptr_kind(sr) == 2) {
+        try {
+            host.resize((size_t)n);
+        } catch (const std::bad_alloc&) {
+            return set_error(BLS_ERR_NOMEM, "host copy of the spectrum");
+        }
+        cudaError_t e = cudaMemcpy(host.data(), sr, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "copying the spectrum");
+        v = host.data();
+    }
+    double s = 0.0;
+    for (long long i = 0; i < n; ++i) s += (double)v[i];
+    const double m = s / (double)n;
+    double m2 = 0.0;
+    for (long long i = 0; i < n; ++i) {
+        const double d = (double)v[i] - m;
+        m2 += d * d;
+    }
+    *out = bls_moments{n, m, m2};
+    return BLS_OK;
+}
+
+bls_status bls_moments_merge(const bls_moments* parts, int nparts, bls_moments* out)
+{
+    if (!out || nparts < 0 || (nparts > 0 && !parts)) return set_error(BLS_ERR_INVALID, "bad argument");
+    long long n = 0;
+    double m = 0.0, m2 = 0.0;
+    for (int q = 0; q < nparts; ++q) {
+        const bls_moments& b = parts[q];
+        if (b.count < 0) return set_error(BLS_ERR_INVALID, "parts[%d].count = %lld", q, b.count);
+        if (b.count == 0) continue;
+        const double d = b.mean - m;
+        const double tot = (double)(n + b.count);
+        m = m + d * (double)b.count / tot;
+        m2 = m2 + b.m2 + d * d * (double)n * (double)b.count / tot;
+        n += b.count;
+    }
+    *out = bls_moments{n, m, m2};
+    return BLS_OK;
+}
+
+bls_status bls_sde(double sr, const bls_moments* m, double* sde)
+{
+    if (!m || !sde || m->count < 0) return set_error(BLS_ERR_INVALID, "bad argument");
+    const double sd = m->count > 0 ? sqrt(m->m2 / (double)m->count) : 0.0;
+    *sde = sd > 0.0 ? (sr - m->mean) / sd : 0.0;
+    return BLS_OK;
+}
+
 bls_status bls_kminmax(int nb, double qmin, double qmax, int* kmin, int* kmax)
 {
     if (!kmin || !kmax) return set_error(BLS_ERR_INVALID, "NULL output");

@@ -24,6 +24,7 @@ from typing import Callable, List, Optional, Sequence, Tuple
 
 import numpy as np
 
+from . import bls
 from .bls import PEAK_DTYPE
 
 
@@ -109,27 +110,15 @@ def merge_best(peaks: Sequence[np.void]) -> np.ndarray:
 
 
 def spectrum_moments(sr: np.ndarray) -> Tuple[int, float, float]:
-    """(count, mean, sum of squared deviations) of an SR spectrum, two-pass in FP64."""
-    sr = np.asarray(sr, np.float64)
-    if sr.size == 0:
-        return 0, 0.0, 0.0
-    m = float(sr.mean())
-    return int(sr.size), m, float(((sr - m) ** 2).sum())
+    """(count, mean, sum of squared deviations) of an SR spectrum (``bls_moments_of``:
+    two passes in FP64 over the FP32 values)."""
+    return bls.moments_of(np.ascontiguousarray(sr, dtype=np.float32))
 
 
 def merge_moments(parts) -> Tuple[int, float, float]:
-    """Combines (count, mean, M2) of disjoint parts (pairwise update of Chan, Golub and
-    LeVeque)."""
-    n, m, m2 = 0, 0.0, 0.0
-    for nb, mb, m2b in parts:
-        if nb == 0:
-            continue
-        d = mb - m
-        tot = n + nb
-        m = m + d * nb / tot
-        m2 = m2 + m2b + d * d * n * nb / tot
-        n = tot
-    return n, m, m2
+    """Moments of the union of disjoint parts (``bls_moments_merge``: the pairwise update of
+    Chan, Golub and LeVeque)."""
+    return bls.moments_merge(list(parts))
 
 
 def search_freq_shards(nf: int, fmin: float, df: float,
@@ -155,9 +144,7 @@ def search_freq_shards(nf: int, fmin: float, df: float,
     if rank != 0:
         return None
     best = merge_best([p[0] for p in parts if p[0] is not None])
-    n, m, m2 = merge_moments([p[1] for p in parts])
-    sd = (m2 / n) ** 0.5 if n > 0 else 0.0
-    best["sde"] = (best["sr"] - m) / sd if sd > 0.0 else 0.0
+    best["sde"] = bls.sde(float(best["sr"][0]), merge_moments([p[1] for p in parts]))
     return best
 
 
