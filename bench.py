@@ -327,6 +327,59 @@ def run_serving(args):
     return 0
 
 
+def plain_curve_measurement(reps=20):
+    """The plain workload: one light curve (500 times in 20 of 30 nightly windows, a 2%
+    box at P = 0.40 d), 2000 frequencies in [0.2, 5] 1/d, nb = 100, q 0.01-0.10: the median
+    time of a search (device-resident inputs, and from host arrays), the plain FP64 GPU
+    kernel, the FP64 oracle on one thread and on all host threads, and the recovered period."""
+    import torch
+    import oracle
+    from paper_1112_1701_b300 import bls
+    b = synth.config1()
+    c, g = b.curves[0], b.grids[0]
+    units = len(c.t) * g.nf
+    dev = bls.curves_from_batch(b, device="cuda")
+    host = bls.curves_from_batch(b)
+    stream = torch.cuda.current_stream()
+
+    def timed(plan, cis):
+        plan.search(cis)
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pk = plan.search(cis)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts), pk
+
+    with bls.Plan(nb=100, qmin=b.qmin, qmax=b.qmax, topk=1, stream=stream.cuda_stream) as p:
+        t_dev, pk = timed(p, dev)
+        t_host, _ = timed(p, host)
+    with bls.Plan(nb=100, qmin=b.qmin, qmax=b.qmax, topk=1, algo="plain_f64",
+                  stream=stream.cuda_stream) as p:
+        t_plain, _ = timed(p, dev)
+    kmin, kmax = oracle.kminmax(100, b.qmin, b.qmax)
+    cur = [dict(t=c.t, y=c.y, dy=c.dy, nb=100, kmin=kmin, kmax=kmax, fmin=g.fmin, df=g.df,
+                nf=g.nf)]
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.bls_many(cur, nthreads=1, topk=1)
+    t_o1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.bls_many(cur, nthreads=cores, topk=1)
+    t_on = time.perf_counter() - t0
+    return {"workload": "plain: one curve, 500 points in 20 of 30 nights, 2000 freqs in "
+                        "[0.2, 5]/d, nb=100, q 0.01-0.10, injected box P = 0.40 d",
+            "value": units / t_dev, "unit": UNIT, "latency_ms": 1000 * t_dev,
+            "from_host_arrays": {"value": units / t_host, "latency_ms": 1000 * t_host},
+            "plain_f64_gpu": {"value": units / t_plain, "latency_ms": 1000 * t_plain},
+            "oracle_one_thread": {"value": units / t_o1, "ms": 1000 * t_o1},
+            "oracle_all_threads": {"value": units / t_on, "ms": 1000 * t_on, "cores": cores},
+            "best_period_d": float(pk[0, 0]["period"]), "injected_period_d": 0.40,
+            "timing": f"median of {reps} searches, wall clock with the stream synchronised"}
+
+
 def plain_f64_sample(batch, ncurves, value):
     """The plain FP64 one-curve-per-launch GPU kernel (the paper's decomposition without
     redesign) on the first ncurves curves of a batch, full grid each."""
@@ -355,10 +408,20 @@ def run_precision(args):
     Reports the phase-bin mismatch rate (sampled frequencies, all points), the SR relative
     error over the spectrum, the peak-depth error, and best-frequency disagreements."""
     import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    st = precision_study(args.prec_curves, args.nf_prec, args.prec_bin_curves,
+                         args.prec_bin_freqs)
+    line = {"metric": "BLS precision study", "data": "synthetic", "n_gpus": 1,
+            "config": st.pop("config"), **st}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def precision_study(ncurves, nf_grid, bin_curves, bin_freqs):
+    """The precision study's measurements (see run_precision) as one object."""
     import oracle
     from paper_1112_1701_b300 import bls
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    b = synth.config3(ncurves=args.prec_curves, nf=args.nf_prec)
+    b = synth.config3(ncurves=ncurves, nf=nf_grid)
     nb = b.nb[0]
     kmin, kmax = oracle.kminmax(nb, b.qmin, b.qmax)
     cis = bls.curves_from_batch(b)
@@ -372,11 +435,10 @@ def run_precision(args):
     osr = np.sqrt(oP).reshape(len(b), nf)
     sumwx2 = np.array([oracle.prep(c.t, c.y, c.dy)[3][3] for c in b.curves])
     # frequencies for the bin comparison: spread over the grid, the top 1% dense
-    js = sorted(set(np.linspace(0, nf - 1, args.prec_bin_freqs // 2).astype(int).tolist()
-                    + np.linspace(int(0.99 * nf), nf - 1,
-                                  args.prec_bin_freqs // 2).astype(int).tolist()))
+    js = sorted(set(np.linspace(0, nf - 1, bin_freqs // 2).astype(int).tolist()
+                    + np.linspace(int(0.99 * nf), nf - 1, bin_freqs // 2).astype(int).tolist()))
     freqs = [oracle.freq(j, b.grids[0].fmin, b.grids[0].df) for j in js]
-    obins = [oracle.bins(c.t, freqs, nb) for c in b.curves[:args.prec_bin_curves]]
+    obins = [oracle.bins(c.t, freqs, nb) for c in b.curves[:bin_curves]]
     rows = []
     for phase in ("f64", "df32", "fx64", "f32"):
         for sm in ("f32", "kahan"):
@@ -412,16 +474,13 @@ def run_precision(args):
                          "frac_outside_parity_tol": float((np.abs(gsr - osr) > tol).mean()),
                          "depth_abs_err_max_same_j": max(ddepth) if ddepth else None,
                          "best_j_disagree": dj, "best_j_disagree_separated": dj_sep})
-    line = {"metric": "BLS precision study", "data": "synthetic", "n_gpus": 1,
-            "config": {"workload": f"three-year baseline: {len(b)} curves x 3000 points over "
+    return {"config": {"workload": f"three-year baseline: {len(b)} curves x 3000 points over "
                                    f"1095 d, seasonal gaps, {nf} freqs uniform in [0.05, 5]/d, "
                                    f"nb={nb}, q {b.qmin}-{b.qmax}",
                        "bin_check": f"{len(obins)} curves x {len(js)} frequencies x all points",
                        "oracle_s": round(t_oracle, 1), "oracle_threads": cores},
             "sr_rel_err_over": "frequencies with oracle SR > 1e-3 of the curve's maximum",
             "modes": rows}
-    print(json.dumps(line), flush=True)
-    return 0
 
 
 def run_efficiency(args):
@@ -772,6 +831,8 @@ def main():
     ap.add_argument("--no-shapes", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload object")
     ap.add_argument("--no-kahan", action="store_true", help="skip the Kahan-sums object")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the single-curve and precision objects")
     ap.add_argument("--kahan-steps", type=int, default=3)
     ap.add_argument("--no-serving", action="store_true", help="skip the serving object")
     ap.add_argument("--no-autotune", action="store_true",
@@ -935,6 +996,11 @@ def main():
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = serving_measurement(args.requests, args.plain_requests, args.loads,
                                               args.step_units)
+
+    # ---- the plain single-curve workload and a reduced precision study
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["plain_curve"] = plain_curve_measurement()
+        line["precision"] = precision_study(2, 200000, 2, 200)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch)
