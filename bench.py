@@ -784,8 +784,8 @@ def measure(batch, topk, args, ctx, tune=True, e2e=True, steps=None, warmup=None
            "box_evals_per_s": evals * world / (ms_step / 1000.0),
            "kernel_ms": {"prep": prof["prep_ms"] / steps, "fold_sweep": prof["fold_ms"] / steps,
                          "reduce": prof["reduce_ms"] / steps},
-           "launch": (dict(launch_kw, source="autotuner") if tuned else
-                      {"source": "library rules"}),
+           "launch": dict(launch_kw, source="autotuner", tile_shape=plan.tile_shape()) if tuned else
+                     {"source": "library rules", "tile_shape": plan.tile_shape()},
            "plan": plan, "dev": dev, "units": units, "evals": evals}
     if tuned:
         out["autotune"] = tuned
@@ -795,7 +795,7 @@ def measure(batch, topk, args, ctx, tune=True, e2e=True, steps=None, warmup=None
     out["roofline"] = roofline(units, evals, prof["fold_launches"] / max(1, steps), fold_ms,
                                props.multi_processor_count, float(peaks.get("sm_max_mhz", 2032.0)),
                                clk.get("sm_mhz"),
-                               "fold_sweep_ws_kernel" if os.environ.get("BLS_FOLD_WS", "1") != "0"
+                               "fold_sweep_ws_kernel" if out["launch"]["tile_shape"]["fold_kernel"] == "ws"
                                else "fold_sweep_kernel")
     if e2e and not args.no_e2e:
         hostc = bls.packed_from_batch(batch, pinned=True)

@@ -308,6 +308,14 @@ bls_status bls_kminmax(int nb, double qmin, double qmax, int* kmin, int* kmax);
 bls_status bls_debug_fold(bls_plan* plan, const bls_curve* curve, const int* js, int nj,
                           int* bins_out);
 
+/* Diagnostic: the launch shape the plan's tiled search uses for curves of nb bins (0: the
+ * plan's nb and widths) and the plan's duration range -- the plan's freqs_per_block and
+ * point_chunk where given, else its rules: *cols trial frequencies per tile, *chunk points
+ * per staged chunk, *ws = 1 for the warp-specialised fold-sweep kernel, 0 for the one-group
+ * kernel.  Errors: BLS_ERR_INVALID (bad argument, an unbinned or baseline plan, nb outside
+ * 2..4096, or no shape fits shared memory). */
+bls_status bls_tile_shape(bls_plan* plan, int nb, int* cols, int* chunk, int* ws);
+
 /* Diagnostic: the per-frequency best box of one curve as the search kernels leave it
  * before the peak reduction: power_out[j] (FP32 P), i1_out[j], k_out[j] (host).
  * Errors: as bls_search. */
@@ -411,7 +419,7 @@ bls_status bls_variability(const bls_var_desc* desc, void* cuda_stream, bls_var_
  * GPU that loads this library holds until the process exits; curves needing more
  * (about 24 bytes per point plus 4 per frequency) are rejected with BLS_ERR_INVALID.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * and caches it; make that first call before any stream capture.  Every call shares the
+ * and caches it.  Every call shares the
  * array and leaves its contents behind, so calls that overlap on the GPU (other threads,
  * other streams) race: serialise them.  Blocks until the results are written.
  * Errors: BLS_ERR_INVALID (bad argument, host memory given, too large, bad input values),

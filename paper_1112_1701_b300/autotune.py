@@ -76,19 +76,22 @@ class TuneResult:
 
 
 def candidates(nb: int, kmin: int, kmax: int, sums: str = "f32",
-               smem_optin: int = 232448, reserve: int = 2048) -> List[Candidate]:
+               smem_optin: int = 231424, reserve: int = 2048) -> List[Candidate]:
     """Feasible candidates for one nb: for each chunk size, the tile widths (multiples of 16)
     from the widest that fits shared memory down to half of it (at least 32), in both kernels
-    where the warp-specialised one can take the width (a multiple of 8, at most 128); plus
-    the library's own choice."""
+    where the warp-specialised one can take the width (a multiple of 8, at most 128); then
+    the widest warp-specialised width that is not a multiple of 16 (its histograms packed at
+    that stride) with the largest chunk of 256..512 points that fits it; plus the library's
+    own choice.  smem_optin is the dynamic shared memory a block may use (the device's
+    opt-in limit less the kernels' static shared memory)."""
     esz = 16 if sums == "kahan" else 8
+
+    def fits(T, stride, chunk):
+        return 2 * chunk * 24 + nb * stride * esz + reserve <= smem_optin
+
     out = [DEFAULT]
     for chunk in CHUNKS:
-        stage = 2 * chunk * 24
-        avail = smem_optin - stage - reserve
-        if avail <= 0:
-            continue
-        tmax = min(avail // (nb * esz), MAX_T) & ~15
+        tmax = min((smem_optin - 2 * chunk * 24 - reserve) // (nb * esz), MAX_T) & ~15
         if tmax < 16:
             continue
         lo = max(16, (tmax // 2) & ~15)
@@ -98,6 +101,11 @@ def candidates(nb: int, kmin: int, kmax: int, sums: str = "f32",
             out.append(Candidate(T, chunk, "one_group"))
             if T % 8 == 0 and T <= 128:
                 out.append(Candidate(T, chunk, "ws"))
+    for T in range(120, 7, -16):   # 120, 104, ..., 8
+        ch = next((c for c in range(max(CHUNKS), min(CHUNKS) - 1, -16) if fits(T, T, c)), None)
+        if ch is not None:
+            out.append(Candidate(T, ch, "ws"))
+            break
     return out
 
 

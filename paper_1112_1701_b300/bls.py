@@ -115,7 +115,7 @@ _lock = threading.Lock()
 
 EXPORTS = ["bls_plan_create", "bls_plan_destroy", "bls_search", "bls_submit", "bls_poll",
            "bls_cancel", "bls_server_stats_get", "bls_kminmax", "bls_debug_fold",
-           "bls_debug_powers", "bls_profile_get", "bls_search_static", "bls_window_efficiency", "bls_refine", "bls_search_shapes", "bls_variability",
+           "bls_debug_powers", "bls_tile_shape", "bls_profile_get", "bls_search_static", "bls_window_efficiency", "bls_refine", "bls_search_shapes", "bls_variability",
            "bls_moments_of", "bls_moments_merge", "bls_sde", "bls_last_error"]
 
 
@@ -138,6 +138,7 @@ def lib():
             L.bls_cancel.argtypes = [P, C.c_uint64]
             L.bls_server_stats_get.argtypes = [P, C.POINTER(ServerStats)]
             L.bls_kminmax.argtypes = [I, D, D, C.POINTER(I), C.POINTER(I)]
+            L.bls_tile_shape.argtypes = [P, I, C.POINTER(I), C.POINTER(I), C.POINTER(I)]
             L.bls_moments_of.argtypes = [P, C.c_longlong, C.POINTER(Moments)]
             L.bls_moments_merge.argtypes = [C.POINTER(Moments), I, C.POINTER(Moments)]
             L.bls_sde.argtypes = [D, C.POINTER(Moments), C.POINTER(D)]
@@ -537,6 +538,14 @@ class Plan:
         _check(lib().bls_debug_fold(self._h, C.byref(cs), js.ctypes.data, len(js),
                                     out.ctypes.data))
         return out
+
+    def tile_shape(self, nb: int = 0) -> dict:
+        """The launch shape this plan's tiled search uses for curves of `nb` bins (0: the
+        plan's own): frequencies per tile, points per staged chunk and the fold-sweep kernel."""
+        cols, chunk, ws = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().bls_tile_shape(self._h, int(nb), C.byref(cols), C.byref(chunk), C.byref(ws)))
+        return {"cols": cols.value, "chunk": chunk.value,
+                "fold_kernel": "ws" if ws.value else "one_group"}
 
     def debug_powers(self, curve: CurveInput):
         keep: list = []

@@ -191,18 +191,47 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, int kmin, int kmax, Fol
         while (T >= 16 && fold_smem_bytes(T, (T + 15) & ~15, nb, chunk, kahan) + kFoldSmemReserve > P->smem_optin) T -= 16;
         return T;
     };
+    // histogram stride: the warp-specialised kernel packs its columns at any multiple of 8,
+    // the one-group kernel rounds up to 16
+    auto stride_of = [&](int T) {
+        return fold_ws_mode(T, kahan, nb, kmin, kmax, P->d.fold_kernel) ? (T + 7) & ~7 : (T + 15) & ~15;
+    };
+    auto fits = [&](int T, int chunk) {
+        return fold_smem_bytes(T, stride_of(T), nb, chunk, kahan) + kFoldSmemReserve <= P->smem_optin;
+    };
     // (at least 32 points: the staging buffers then also hold the sweep's 2 x 256 partial
     // maxima at the end of a tile)
-    if (P->d.point_chunk > 0) g->chunk = std::max(32, (P->d.point_chunk + 15) & ~15);
+    const bool chunk_given = P->d.point_chunk > 0, width_given = P->d.freqs_per_block > 0;
+    if (chunk_given) g->chunk = std::max(32, (P->d.point_chunk + 15) & ~15);
     else g->chunk = tmax(512) >= tmax(256) ? 512 : 256;
-    int T = P->d.freqs_per_block > 0 ? P->d.freqs_per_block
-                                     : fold_preferred_cols(tmax(g->chunk), kahan, nb, kmin, kmax,
-                                                           P->d.fold_kernel);
-    if (T < 16) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", nb);
+    int T = width_given ? P->d.freqs_per_block
+                        : fold_preferred_cols(tmax(g->chunk), kahan, nb, kmin, kmax, P->d.fold_kernel);
     if (T > maxT) T = maxT;
+    if (width_given && !chunk_given && !fits(T, g->chunk)) {
+        // the largest chunk (a multiple of 16, at least 32) with which the given width fits
+        int c = g->chunk;
+        while (c > 32 && !fits(T, c)) c -= 16;
+        g->chunk = c;
+    } else if (!width_given && T % 16 == 0 && T + 8 <= 128 &&
+               fold_ws_mode(T, kahan, nb, kmin, kmax, P->d.fold_kernel) &&
+               fold_ws_mode(T + 8, kahan, nb, kmin, kmax, P->d.fold_kernel)) {
+        // eight more columns in the warp-specialised kernel where a staging chunk of 256 or
+        // more points (the one given, else the largest) leaves room: fewer tiles per curve
+        // outweigh shorter chunks (survey sweep, nb = 256: 104 columns with 336-point chunks
+        // 416 ms per 512 curves, against 444 ms at 96 columns with 512-point chunks)
+        for (int c = g->chunk; c >= (chunk_given ? g->chunk : 256); c -= 16)
+            if (fits(T + 8, c)) {
+                T += 8;
+                g->chunk = c;
+                break;
+            }
+    }
+    if (T < 8 || (T < 16 && !width_given)) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", nb);
     g->T = T;
-    g->stride = (T + 15) & ~15;
     g->ws = fold_ws_mode(T, kahan, nb, kmin, kmax, P->d.fold_kernel);
+    g->stride = stride_of(T);
+    if (!g->ws && T % 16 != 0)   // the one-group kernel runs 2 T threads: whole warps
+        return set_error(BLS_ERR_INVALID, "freqs_per_block = %d: the one-group kernel needs a multiple of 16", T);
     g->smem = fold_smem_bytes(T, g->stride, nb, g->chunk, kahan);
     if (g->smem + kFoldSmemReserve > P->smem_optin)
         return set_error(BLS_ERR_INVALID, "nb = %d with %d frequencies per block needs %zu B of shared memory (> %zu)",
@@ -839,8 +868,8 @@ bls_status bls_plan_create(const bls_plan_desc* desc, void* cuda_stream, bls_pla
     if (d.sum < 0 || d.sum > 1) return set_error(BLS_ERR_INVALID, "sum = %d", d.sum);
     if (d.sign < 0 || d.sign > 1) return set_error(BLS_ERR_INVALID, "sign = %d", d.sign);
     if (d.algo < 0 || d.algo > 2) return set_error(BLS_ERR_INVALID, "algo = %d", d.algo);
-    if (d.freqs_per_block < 0 || d.freqs_per_block > fold_sweep_max_threads() || (d.freqs_per_block % 16) != 0)
-        return set_error(BLS_ERR_INVALID, "freqs_per_block = %d, need a multiple of 16 up to %d", d.freqs_per_block,
+    if (d.freqs_per_block < 0 || d.freqs_per_block > fold_sweep_max_threads() || (d.freqs_per_block % 8) != 0)
+        return set_error(BLS_ERR_INVALID, "freqs_per_block = %d, need a multiple of 8 up to %d", d.freqs_per_block,
                          fold_sweep_max_threads());
     if (d.point_chunk < 0 || d.point_chunk > 4096) return set_error(BLS_ERR_INVALID, "point_chunk = %d", d.point_chunk);
     if (d.fold_kernel < BLS_FOLD_AUTO || d.fold_kernel > BLS_FOLD_ONE_GROUP)
@@ -1041,6 +1070,29 @@ bls_status bls_debug_powers(bls_plan* P, const bls_curve* curve, float* power_ou
         (e = cudaMemcpyAsync(k_out, dk, (size_t)nf * 4, cudaMemcpyDeviceToHost, P->stream)) != cudaSuccess)
         return cuda_fail(e, "copy");
     if ((e = cudaStreamSynchronize(P->stream)) != cudaSuccess) return cuda_fail(e, "best box");
+    return BLS_OK;
+}
+
+bls_status bls_tile_shape(bls_plan* P, int nb, int* cols, int* chunk, int* ws)
+{
+    if (!P || !cols || !chunk || !ws) return set_error(BLS_ERR_INVALID, "bad argument");
+    std::lock_guard<std::mutex> lk(P->mu);
+    if (P->d.algo != BLS_ALGO_TILED) return set_error(BLS_ERR_INVALID, "the plan's search has no tiles");
+    const bool own = nb == 0;
+    if (own) nb = P->d.nb;
+    if (nb < 2 || nb > 4096) return set_error(BLS_ERR_INVALID, "nb = %d, need 2..4096", nb);
+    // the widths as bls_search resolves them for a curve with this nb and the plan's q range
+    int kmin = P->d.kmin, kmax = P->d.kmax;
+    if (!(own && kmin > 0)) {
+        bls_status st = kminmax_impl(nb, P->d.qmin, P->d.qmax, &kmin, &kmax);
+        if (st != BLS_OK) return st;
+    }
+    FoldGeom g;
+    bls_status st = fold_geometry(P, nb, kmin, kmax, &g);
+    if (st != BLS_OK) return st;
+    *cols = g.T;
+    *chunk = g.chunk;
+    *ws = g.ws;
     return BLS_OK;
 }
 

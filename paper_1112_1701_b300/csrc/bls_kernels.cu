@@ -63,6 +63,7 @@ struct FoldConst {
     unsigned tau;        // j - jc (two's complement): this column's offset from the reference
     unsigned Fclo, Fchi; // Fc = RN_int(f_jc 2^(64 - fxs))
     unsigned dFlo, dFhi; // dF = RN_int(df 2^(96 - fxs)) < 2^63
+    unsigned sh;         // log2 nb when nb is a power of two (the bin is then a shift)
 };
 
 // Fixed-point scale of a curve's offsets: DT = RN_int(dt 2^s) with dt < 2^L.  The fold
@@ -114,6 +115,7 @@ __device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dt
     }
     fc.f = f;
     fc.nb = nb;
+    fc.sh = (nb & (nb - 1)) == 0 ? 31u - (unsigned)__clz(nb) : 0u;
     fc.fh = __double2float_rn(f);
     fc.fl = __double2float_rn(__dsub_rn(f, (double)fc.fh));
     fc.nbf = (float)nb;
@@ -360,7 +362,7 @@ __device__ __forceinline__ void fold_df32_pair(const float4& A, const FoldPacked
 // the carry word of lo*Flo (mod 2^32): three integer multiply-adds per point.  Incremental
 // (INC = true, a uniform-grid tile after its staging step): A = (Q0, Q1, D0, D1) and the
 // phase word is Q + tau D, one multiply-add.  Then one multiply-add for the bin.
-template <bool INC = false>
+template <bool INC = false, bool POW2 = false>
 __device__ __forceinline__ void fold_fx_pair(const float4& A, const FoldConst& fc,
                                              unsigned& b0, unsigned& b1, bool& e0, bool& e1)
 {
@@ -375,10 +377,17 @@ __device__ __forceinline__ void fold_fx_pair(const float4& A, const FoldConst& f
         q1 = __umulhi(lo1, fc.Flo) + lo1 * fc.Fhi + hi1 * fc.Flo;
     }
     const unsigned nbu = (unsigned)fc.nb;
-    b0 = __umulhi(q0, nbu);
-    b1 = __umulhi(q1, nbu);
-    e0 = q0 * nbu - fc.ftol >= fc.fspan;
-    e1 = q1 * nbu - fc.ftol >= fc.fspan;
+    if (POW2) {   // nb = 2^sh: bin and in-bin place are the phase word's top and low bits
+        b0 = q0 >> (32u - fc.sh);
+        b1 = q1 >> (32u - fc.sh);
+        e0 = (q0 << fc.sh) - fc.ftol >= fc.fspan;
+        e1 = (q1 << fc.sh) - fc.ftol >= fc.fspan;
+    } else {
+        b0 = __umulhi(q0, nbu);
+        b1 = __umulhi(q1, nbu);
+        e0 = q0 * nbu - fc.ftol >= fc.fspan;
+        e1 = q1 * nbu - fc.ftol >= fc.fspan;
+    }
 }
 
 // Fold of the point pair (2p, 2p+1) in a given phase mode; A = (dh0, dh1, dl0, dl1), or
@@ -669,7 +678,7 @@ __device__ __forceinline__ void kahan2(u64& h, u64& c, u64 q)
 
 // Bins of the 8 point pairs of a 16-point sub-chunk, with their weight pairs; returns
 // whether any bin is not certain (then fix_sub must run before the bins are used).
-template <int PHASE, bool INC>
+template <int PHASE, bool INC, bool POW2 = false>
 __device__ __forceinline__ bool fold_sub(const float4* cp, const FoldConst& fc, const FoldPacked& fq,
                                          unsigned* b, float4* Bw)
 {
@@ -679,7 +688,7 @@ __device__ __forceinline__ bool fold_sub(const float4* cp, const FoldConst& fc, 
         const float4 A = cp[2 * q];
         Bw[q] = cp[2 * q + 1];
         bool e0, e1;
-        if (PHASE == kPhaseFX64) fold_fx_pair<INC>(A, fc, b[2 * q], b[2 * q + 1], e0, e1);
+        if (PHASE == kPhaseFX64) fold_fx_pair<INC, POW2>(A, fc, b[2 * q], b[2 * q + 1], e0, e1);
         else fold_df32_pair(A, fq, b[2 * q], b[2 * q + 1], e0, e1);
         edge = edge | e0 | e1;
     }
@@ -687,7 +696,7 @@ __device__ __forceinline__ bool fold_sub(const float4* cp, const FoldConst& fc, 
 }
 
 // Rare path: re-fold in FP64 the points of a sub-chunk whose bin is not certain.
-template <int PHASE, bool INC>
+template <int PHASE, bool INC, bool POW2 = false>
 __device__ __forceinline__ void fix_sub(const float4* cp, const double* cd, const FoldConst& fc,
                                      const FoldPacked& fq, unsigned* b)
 {
@@ -695,7 +704,7 @@ __device__ __forceinline__ void fix_sub(const float4* cp, const double* cd, cons
     for (int q = 0; q < 8; ++q) {
         unsigned b0, b1;
         bool e0, e1;
-        if (PHASE == kPhaseFX64) fold_fx_pair<INC>(cp[2 * q], fc, b0, b1, e0, e1);
+        if (PHASE == kPhaseFX64) fold_fx_pair<INC, POW2>(cp[2 * q], fc, b0, b1, e0, e1);
         else fold_df32_pair(cp[2 * q], fq, b0, b1, e0, e1);
         if (e0) b[2 * q] = fold_exact(cd[2 * q], fc.f, fc.nb);
         if (e1) b[2 * q + 1] = fold_exact(cd[2 * q + 1], fc.f, fc.nb);
@@ -781,7 +790,7 @@ __device__ __forceinline__ void rmw_sub_k(unsigned hbase, unsigned rowb, const u
 // chain, so the fold arithmetic fills the shared-memory latency of the chain; the rare
 // FP64 re-fold runs after the stores.  hbase is the shared-memory address of this
 // thread's bin 0, rowb the byte stride between bins.
-template <int PHASE, bool PINGPONG, bool INC, bool KAHAN = false>
+template <int PHASE, bool PINGPONG, bool INC, bool KAHAN = false, bool POW2 = false>
 __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int nsub,
                                          unsigned hbase, unsigned rowb, const FoldConst& fc,
                                          const FoldPacked& fq, int* err)
@@ -789,7 +798,7 @@ __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int
     const unsigned nbu = (unsigned)fc.nb;
     unsigned b0[16], b1[16];
     float4 W0[8], W1[8];
-    if (fold_sub<PHASE, INC>(cp, fc, fq, b0, W0)) fix_sub<PHASE, INC>(cp, cd, fc, fq, b0);
+    if (fold_sub<PHASE, INC, POW2>(cp, fc, fq, b0, W0)) fix_sub<PHASE, INC, POW2>(cp, cd, fc, fq, b0);
     int sc = 0;
     if (PINGPONG) {
         // the two buffers used in turn (the loop body covers two sub-chunks): no register
@@ -797,20 +806,20 @@ __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int
         // warps are the critical path; slower in the one-group kernel)
         for (; sc + 2 < nsub; sc += 2) {
             const float4* n1 = cp + 16 * (sc + 1);
-            const bool e1 = fold_sub<PHASE, INC>(n1, fc, fq, b1, W1);
+            const bool e1 = fold_sub<PHASE, INC, POW2>(n1, fc, fq, b1, W1);
             if (KAHAN) rmw_sub_k(hbase, rowb, b0, W0, nbu, err); else rmw_sub(hbase, rowb, b0, W0, nbu, err);
-            if (e1) fix_sub<PHASE, INC>(n1, cd + 16 * (sc + 1), fc, fq, b1);
+            if (e1) fix_sub<PHASE, INC, POW2>(n1, cd + 16 * (sc + 1), fc, fq, b1);
             const float4* n2 = cp + 16 * (sc + 2);
-            const bool e2 = fold_sub<PHASE, INC>(n2, fc, fq, b0, W0);
+            const bool e2 = fold_sub<PHASE, INC, POW2>(n2, fc, fq, b0, W0);
             if (KAHAN) rmw_sub_k(hbase, rowb, b1, W1, nbu, err); else rmw_sub(hbase, rowb, b1, W1, nbu, err);
-            if (e2) fix_sub<PHASE, INC>(n2, cd + 16 * (sc + 2), fc, fq, b0);
+            if (e2) fix_sub<PHASE, INC, POW2>(n2, cd + 16 * (sc + 2), fc, fq, b0);
         }
     }
     for (; sc + 1 < nsub; ++sc) {
         const float4* n1 = cp + 16 * (sc + 1);
-        const bool e1 = fold_sub<PHASE, INC>(n1, fc, fq, b1, W1);
+        const bool e1 = fold_sub<PHASE, INC, POW2>(n1, fc, fq, b1, W1);
         if (KAHAN) rmw_sub_k(hbase, rowb, b0, W0, nbu, err); else rmw_sub(hbase, rowb, b0, W0, nbu, err);
-        if (e1) fix_sub<PHASE, INC>(n1, cd + 16 * (sc + 1), fc, fq, b1);
+        if (e1) fix_sub<PHASE, INC, POW2>(n1, cd + 16 * (sc + 1), fc, fq, b1);
 #pragma unroll
         for (int i = 0; i < 16; ++i) b0[i] = b1[i];
 #pragma unroll
@@ -1527,7 +1536,9 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
                         kahan_add(reinterpret_cast<float4*>(hist) + b1 * S, B.z, B.w);
                     }
                 } else if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
-                    if (inc)
+                    if (inc && fc.sh != 0u)
+                        bin_fast<PHASE, false, true, false, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
+                    else if (inc)
                         bin_fast<PHASE, false, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                     else
                         bin_fast<PHASE, false, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
@@ -2057,7 +2068,9 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                 const double* cd = cdt + (ci & 1) * CH;
                 if (active) {   // a3 + a4
                     if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
-                        if (inc)
+                        if (inc && fc.sh != 0u)   // nb a power of two: shifts, not multiplies
+                            bin_fast<PHASE, true, true, KAHAN, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
+                        else if (inc)
                             bin_fast<PHASE, true, true, KAHAN>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                         else
                             bin_fast<PHASE, true, false, KAHAN>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
@@ -2494,8 +2507,9 @@ cudaError_t launch_reduce(const ReduceParams& p, int ncurves, cudaStream_t s)
 
 // Per-point bins of one curve at frequencies js, by the fold of the given phase mode.  In
 // FX64 mode on a uniform grid (plain sums) the incremental fold of the search kernels is
-// run as well, for the frequency's place in a tile of T columns -- the tile width the
-// plan's search uses for this curve, so the reference column jc is the search's; a point
+// run as well (with the search's shift form when nb is a power of two), for the
+// frequency's place in a tile of T columns -- the tile width the plan's search uses for
+// this curve, so the reference column jc is the search's; a point
 // where the two folds disagree is reported as -1 - bin.
 template <int PHASE>
 __global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bins, int T, int kahan)
@@ -2521,9 +2535,12 @@ __global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bi
             bool e0, e1;
             inc_point(__float_as_uint(A.x), __float_as_uint(A.z), fi, Q0, D0);
             inc_point(__float_as_uint(A.y), __float_as_uint(A.w), fi, Q1, D1);
-            fold_fx_pair<true>(make_float4(__uint_as_float(Q0), __uint_as_float(Q1),
-                                           __uint_as_float(D0), __uint_as_float(D1)),
-                               fi, c0, c1, e0, e1);
+            const float4 QD = make_float4(__uint_as_float(Q0), __uint_as_float(Q1),
+                                          __uint_as_float(D0), __uint_as_float(D1));
+            if (fi.sh != 0u)   // as the search: shifts when nb is a power of two
+                fold_fx_pair<true, true>(QD, fi, c0, c1, e0, e1);
+            else
+                fold_fx_pair<true>(QD, fi, c0, c1, e0, e1);
             if (e0) c0 = fold_exact(cd.dt64[2 * pi], f, cd.nb);
             if (e1) c1 = fold_exact(cd.dt64[2 * pi + 1], f, cd.nb);
             if (c0 != b0) b0 = (unsigned)(-1 - (int)b0);

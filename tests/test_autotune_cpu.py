@@ -19,10 +19,21 @@ def test_candidates_fit_shared_memory_and_kernel_rules():
     cands = at.candidates(200, 1, 30)
     assert cands[0] == at.DEFAULT
     for c in cands[1:]:
-        assert c.freqs_per_block % 16 == 0 and 16 <= c.freqs_per_block <= 256
-        assert 2 * c.point_chunk * 24 + 2048 + c.freqs_per_block * 200 * 8 <= 232448
+        assert 8 <= c.freqs_per_block <= 256
+        # the one-group kernel's histograms are strided at a multiple of 16 columns, the
+        # warp-specialised kernel's at the width itself (a multiple of 8)
+        stride = c.freqs_per_block if c.fold_kernel == "ws" else (c.freqs_per_block + 15) & ~15
+        assert 2 * c.point_chunk * 24 + 2048 + stride * 200 * 8 <= 231424
         if c.fold_kernel == "ws":
             assert c.freqs_per_block % 8 == 0 and c.freqs_per_block <= 128
+        else:
+            assert c.freqs_per_block % 16 == 0
+    # one warp-specialised width between the multiples of 16: the widest that fits with a
+    # chunk of 256..512 points (nb = 200: 120 columns; nb = 256: 104 columns, 336 points)
+    odd = [c for c in cands[1:] if c.freqs_per_block % 16]
+    assert [(c.freqs_per_block, c.point_chunk, c.fold_kernel) for c in odd] == [(120, 512, "ws")]
+    odd256 = [c for c in at.candidates(256, 1, 39)[1:] if c.freqs_per_block % 16]
+    assert [(c.freqs_per_block, c.point_chunk) for c in odd256] == [(104, 336)]
     widths = {c.freqs_per_block for c in cands if c.point_chunk == 512}
     assert max(widths) == 128 and 96 in widths and 64 in widths
     assert any(c.fold_kernel == "ws" and c.freqs_per_block == 128 for c in cands)

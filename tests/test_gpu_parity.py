@@ -111,21 +111,25 @@ def test_bins_bit_exact_on_exact_edges(phase, grid):
 @pytest.mark.parametrize("T", [0, 80, 48])
 def test_bins_bit_exact_at_survey_tile_geometry(T):
     """The survey sweep's shape (2000 points over 90 nights, 200,000 frequencies, nb = 256):
-    the search runs 96-frequency tiles there (T = 0: the plan's rules), or the width given.
-    Bins of the first, reference (middle), last and ragged-tile columns of such tiles, in
-    the incremental fold with the search's reference column, equal the FP64 oracle's."""
+    the search runs 104-frequency tiles there (T = 0: the plan's rules; histograms packed at
+    a stride of 104 columns, 336-point staging chunks), or the width given.  Bins of the
+    first, reference (middle), last and ragged-tile columns of such tiles, in the incremental
+    fold with the search's reference column, equal the FP64 oracle's."""
     b = synth.config5(ncurves=2)
     nb = 256
     for c, g in zip(b.curves, b.grids):
         ci = _ci(c, g, nb, b.qmin, b.qmax)
-        Tw = T or 96
-        js = []
-        for tile in (0, 1, 1041, (g.nf - 1) // Tw - 1, (g.nf - 1) // Tw):
-            t0 = tile * Tw
-            js += [t0, t0 + Tw // 2 - 1, t0 + Tw // 2, t0 + Tw - 1]
-        js = sorted({j for j in js if 0 <= j < g.nf} | {g.nf - 1})
         kw = dict(freqs_per_block=T, point_chunk=256) if T else {}
         with _plan(nb, b.qmin, b.qmax, **kw) as p:
+            shape = p.tile_shape()
+            if not T:
+                assert shape == {"cols": 104, "chunk": 336, "fold_kernel": "ws"}, shape
+            Tw = shape["cols"]
+            js = []
+            for tile in (0, 1, 1041, (g.nf - 1) // Tw - 1, (g.nf - 1) // Tw):
+                t0 = tile * Tw
+                js += [t0, t0 + Tw // 2 - 1, t0 + Tw // 2, t0 + Tw - 1]
+            js = sorted({j for j in js if 0 <= j < g.nf} | {g.nf - 1})
             bg = p.debug_fold(ci, js)
         bo = oracle.bins(c.t, [oracle.freq(j, g.fmin, g.df) for j in js], nb)
         assert np.array_equal(bg, bo), f"T={Tw}: {int((bg != bo).sum())} of {bg.size} differ"

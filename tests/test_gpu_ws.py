@@ -1,6 +1,7 @@
 """The warp-specialised fold-sweep kernel (marked gpu).
 
-Tiles of any multiple of 8 frequencies up to 128 run in the warp-specialised kernel (a
+Tiles of any multiple of 8 frequencies up to 128 (histograms strided at the width itself)
+run in the warp-specialised kernel (a
 binning warp group and a sweep warp group that takes each tile's histograms over through
 TMEM; T/4 columns per SM sub-partition, two sweep threads per column); BLS_FOLD_WS=0 or
 fold_kernel="one_group" select the one-group kernel.  Checked here:
@@ -94,7 +95,7 @@ def _oracle_check(cis, spec, nb, qmin, qmax, sign):
 def test_spectrum_matches_oracle_every_tile_width(case, sign):
     name, cis, nb, qmin, qmax = _cases()[case]
     ref = None
-    for T in (128, 96, 64, 32, 48, 80, 112):
+    for T in (128, 96, 64, 32, 48, 80, 112, 104, 120, 72, 24):   # 104 .. 24: packed strides
         try:
             spec, pk = _search(cis, nb, qmin, qmax, T=T, sign=sign)
         except bls.BLSError as e:   # T columns of nb bins exceed shared memory
