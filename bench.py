@@ -441,7 +441,7 @@ def precision_study(ncurves, nf_grid, bin_curves, bin_freqs):
     obins = [oracle.bins(c.t, freqs, nb) for c in b.curves[:bin_curves]]
     rows = []
     for phase in ("f64", "df32", "fx64", "f32"):
-        for sm in ("f32", "kahan"):
+        for sm in ("fixed", "f32", "kahan"):
             with bls.Plan(nb=nb, qmin=b.qmin, qmax=b.qmax, topk=1, phase=phase, sum=sm) as p:
                 spec = np.zeros(len(b) * nf, np.float32)
                 pk = p.search(cis, spectrum=spec)
@@ -736,7 +736,7 @@ def roofline(units, evals, launches_per_step, fold_ms, sms, clk_mhz, run_mhz, ke
     return out
 
 
-def measure(batch, topk, args, ctx, tune=True, e2e=True, steps=None, warmup=None, sums="f32"):
+def measure(batch, topk, args, ctx, tune=True, e2e=True, steps=None, warmup=None, sums="fixed"):
     """Device-timed and end-to-end search of one batch: warm-up, then `steps` searches of
     the device-resident packed batch between barriers (CUDA events on the plan's stream,
     L2 flushed before each), then the same through pinned host buffers (wall clock)."""

@@ -63,8 +63,13 @@ enum {
 
 /* Accumulation of the phase histograms and box sums. */
 enum {
-    BLS_SUM_F32 = 0,     /* default: FP32 */
-    BLS_SUM_KAHAN = 1    /* FP32 with Kahan compensation (bins and box sums) */
+    BLS_SUM_FIXED = 0,   /* default: each point's w and w x are rounded once to 32-bit fixed
+                            point (w to 2^-32 of the curve's total weight, w x to 2^-31 of
+                            sum |w x|), every bin sums them exactly with integer additions
+                            (independent of order), and each bin sum is converted to FP32
+                            for the box sweep (FP32 box sums) */
+    BLS_SUM_F32 = 1,     /* FP32 bin and box sums */
+    BLS_SUM_KAHAN = 2    /* FP32 with Kahan compensation (bins and box sums) */
 };
 
 /* Which boxes count. */
@@ -92,12 +97,11 @@ enum {
 
 /* Fold-sweep kernel of the tiled search.  BLS_FOLD_AUTO chooses per class of curves: the
  * warp-specialised kernel (a binning warp group and a sweep warp group that takes each
- * tile's histograms over through tensor memory) where the tile width is 32, 64, 96 or 128
- * frequencies, the sums are plain FP32, the fast sweep covers the widths (kmax - kmin + 1 >=
+ * tile's histograms over through tensor memory) where the tile width is a multiple of 8 up
+ * to 128 frequencies (any sum mode), the fast sweep covers the widths (kmax - kmin + 1 >=
  * SB - 1, SB = 4 for kmax - kmin < 14, else 8 or 10) and nb <= 256 (the bins fit the TMEM
  * copy), otherwise the one-group kernel (every thread bins, then every thread sweeps).
- * BLS_FOLD_WS asks for the warp-specialised kernel wherever the tile width and the sums
- * allow it (tiles whose copy does not fit are then swept from shared memory by the sweep
+ * BLS_FOLD_WS asks for the warp-specialised kernel wherever the tile width allows it (tiles whose copy does not fit are then swept from shared memory by the sweep
  * group); BLS_FOLD_ONE_GROUP always takes the one-group kernel.  The environment variable
  * BLS_FOLD_WS=0 forces the one-group kernel for every plan.  All give the FP64 bins; the
  * per-frequency powers of the two kernels agree within the sweep's 2^-22 approximation. */
@@ -300,7 +304,7 @@ bls_status bls_kminmax(int nb, double qmin, double qmax, int* kmin, int* kmax);
 
 /* Diagnostic: the phase bin of every point of one curve at frequencies js[0..nj), as
  * the search kernels compute them (plan's phase mode); bins_out[q*n + i] (host).  In the
- * FX64 mode on a uniform grid with plain sums the incremental fold of the search kernels
+ * FX64 mode on a uniform grid with fixed-point or FP32 sums the incremental fold of the search kernels
  * is evaluated too, for frequency js[q] at its place in a tile of the width the plan's
  * search uses for this curve (so with the search's reference column); a point where it
  * disagrees with the direct fold is reported as -1 - bin, so every value is a valid bin

@@ -75,7 +75,7 @@ class TuneResult:
                 "sample": self.sample, "candidates": len(self.table)}
 
 
-def candidates(nb: int, kmin: int, kmax: int, sums: str = "f32",
+def candidates(nb: int, kmin: int, kmax: int, sums: str = "fixed",
                smem_optin: int = 231424, reserve: int = 2048) -> List[Candidate]:
     """Feasible candidates for one nb: for each chunk size, the tile widths (multiples of 16)
     from the widest that fits shared memory down to half of it (at least 32), in both kernels
@@ -197,7 +197,7 @@ def time_candidate(cand: Candidate, sample: Sequence[bls.CurveInput], nb: int, q
 
 
 def tune(curves: Sequence[bls.CurveInput], nb: int, qmin: float, qmax: float, *,
-         phase: str = "fx64", sums: str = "f32", sign: str = "dips", sample: int = 32,
+         phase: str = "fx64", sums: str = "fixed", sign: str = "dips", sample: int = 32,
          tiles_per_sm: int = 16, reps: int = 3, cache: Optional[TuneCache] = None,
          use_cache: bool = True, stream=None,
          timer: Optional[Callable[..., Optional[float]]] = None,

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_PKG, "libbls_debug.so" if os.environ.get("BLS_DEBUG") =
 OK, PENDING = 0, 1
 ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL, ERR_CANCELLED = -1, -2, -3, -4, -5, -6
 PHASE = {"fx64": 0, "f64": 1, "f32": 2, "df32": 3}
-SUM = {"f32": 0, "kahan": 1}
+SUM = {"fixed": 0, "f32": 1, "kahan": 2}
 SIGN = {"dips": 0, "both": 1}
 ALGO = {"tiled": 0, "plain_f64": 1, "unbinned": 2}
 FOLD = {"auto": 0, "ws": 1, "one_group": 2}
@@ -433,7 +433,7 @@ class Plan:
     """A search plan on the current CUDA device (``bls_plan_create``)."""
 
     def __init__(self, nb=200, qmin=0.005, qmax=0.15, kmin=0, kmax=0, topk=1, phase="fx64",
-                 sum="f32", sign="dips", algo="tiled", max_device_bytes=0,
+                 sum="fixed", sign="dips", algo="tiled", max_device_bytes=0,
                  max_curves_per_launch=0, freqs_per_block=0, point_chunk=0,
                  max_active_requests=0, step_point_freqs=0, fold_kernel="auto", stream=None):
         self.desc = PlanDesc(nb, qmin, qmax, kmin, kmax, topk, PHASE[phase], SUM[sum],

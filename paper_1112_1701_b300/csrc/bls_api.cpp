@@ -14,6 +14,9 @@
 
 using namespace blsgpu;
 
+static_assert(kSumFixed == BLS_SUM_FIXED && kSumF32 == BLS_SUM_F32 && kSumKahan == BLS_SUM_KAHAN,
+              "internal sum modes are the ABI's values");
+
 namespace blsgpu {
 
 static thread_local std::string g_last_error;
@@ -178,8 +181,8 @@ bls_status resolve_curve(const bls_plan_impl* P, const bls_curve* c, int index, 
 
 bls_status fold_geometry(const bls_plan_impl* P, int nb, int kmin, int kmax, FoldGeom* g)
 {
-    const int kahan = P->d.sum == BLS_SUM_KAHAN;
-    const size_t esz = kahan ? 16 : 8;
+    const int sums = P->d.sum;
+    const size_t esz = hist_entry_bytes(sums);
     const int maxT = fold_sweep_max_threads();
     // chunk: a multiple of 16 points; by default the larger of 512/256 that leaves the
     // block size (frequencies per block) as large as 256 allows.  tmax: the most columns
@@ -188,16 +191,16 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, int kmin, int kmax, Fol
         const size_t stage = (size_t)2 * chunk * 24;
         const size_t avail = P->smem_optin > stage + kFoldSmemReserve ? P->smem_optin - stage - kFoldSmemReserve : 0;
         int T = (int)std::min<size_t>(avail / ((size_t)nb * esz), (size_t)maxT) & ~15;
-        while (T >= 16 && fold_smem_bytes(T, (T + 15) & ~15, nb, chunk, kahan) + kFoldSmemReserve > P->smem_optin) T -= 16;
+        while (T >= 16 && fold_smem_bytes(T, (T + 15) & ~15, nb, chunk, sums) + kFoldSmemReserve > P->smem_optin) T -= 16;
         return T;
     };
     // histogram stride: the warp-specialised kernel packs its columns at any multiple of 8,
     // the one-group kernel rounds up to 16
     auto stride_of = [&](int T) {
-        return fold_ws_mode(T, kahan, nb, kmin, kmax, P->d.fold_kernel) ? (T + 7) & ~7 : (T + 15) & ~15;
+        return fold_ws_mode(T, sums, nb, kmin, kmax, P->d.fold_kernel) ? (T + 7) & ~7 : (T + 15) & ~15;
     };
     auto fits = [&](int T, int chunk) {
-        return fold_smem_bytes(T, stride_of(T), nb, chunk, kahan) + kFoldSmemReserve <= P->smem_optin;
+        return fold_smem_bytes(T, stride_of(T), nb, chunk, sums) + kFoldSmemReserve <= P->smem_optin;
     };
     // (at least 32 points: the staging buffers then also hold the sweep's 2 x 256 partial
     // maxima at the end of a tile)
@@ -205,7 +208,7 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, int kmin, int kmax, Fol
     if (chunk_given) g->chunk = std::max(32, (P->d.point_chunk + 15) & ~15);
     else g->chunk = tmax(512) >= tmax(256) ? 512 : 256;
     int T = width_given ? P->d.freqs_per_block
-                        : fold_preferred_cols(tmax(g->chunk), kahan, nb, kmin, kmax, P->d.fold_kernel);
+                        : fold_preferred_cols(tmax(g->chunk), sums, nb, kmin, kmax, P->d.fold_kernel);
     if (T > maxT) T = maxT;
     if (width_given && !chunk_given && !fits(T, g->chunk)) {
         // the largest chunk (a multiple of 16, at least 32) with which the given width fits
@@ -213,8 +216,8 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, int kmin, int kmax, Fol
         while (c > 32 && !fits(T, c)) c -= 16;
         g->chunk = c;
     } else if (!width_given && T % 16 == 0 && T + 8 <= 128 &&
-               fold_ws_mode(T, kahan, nb, kmin, kmax, P->d.fold_kernel) &&
-               fold_ws_mode(T + 8, kahan, nb, kmin, kmax, P->d.fold_kernel)) {
+               fold_ws_mode(T, sums, nb, kmin, kmax, P->d.fold_kernel) &&
+               fold_ws_mode(T + 8, sums, nb, kmin, kmax, P->d.fold_kernel)) {
         // eight more columns in the warp-specialised kernel where a staging chunk of 256 or
         // more points (the one given, else the largest) leaves room: fewer tiles per curve
         // outweigh shorter chunks (survey sweep, nb = 256: 104 columns with 336-point chunks
@@ -228,11 +231,11 @@ bls_status fold_geometry(const bls_plan_impl* P, int nb, int kmin, int kmax, Fol
     }
     if (T < 8 || (T < 16 && !width_given)) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", nb);
     g->T = T;
-    g->ws = fold_ws_mode(T, kahan, nb, kmin, kmax, P->d.fold_kernel);
+    g->ws = fold_ws_mode(T, sums, nb, kmin, kmax, P->d.fold_kernel);
     g->stride = stride_of(T);
     if (!g->ws && T % 16 != 0)   // the one-group kernel runs 2 T threads: whole warps
         return set_error(BLS_ERR_INVALID, "freqs_per_block = %d: the one-group kernel needs a multiple of 16", T);
-    g->smem = fold_smem_bytes(T, g->stride, nb, g->chunk, kahan);
+    g->smem = fold_smem_bytes(T, g->stride, nb, g->chunk, sums);
     if (g->smem + kFoldSmemReserve > P->smem_optin)
         return set_error(BLS_ERR_INVALID, "nb = %d with %d frequencies per block needs %zu B of shared memory (> %zu)",
                          nb, T, g->smem, P->smem_optin);
@@ -502,7 +505,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     std::vector<int> grids(cls.size());
     for (size_t q = 0; q < cls.size(); ++q) {
         const int bps = fold_blocks_per_sm(geoms[q].T, geoms[q].smem, P->d.phase,
-                                           P->d.sum == BLS_SUM_KAHAN, P->d.sign, geoms[q].ws);
+                                           P->d.sum, P->d.sign, geoms[q].ws);
         long long grid = std::min<long long>((long long)P->sm_count * bps, totals[q]);
         grids[q] = (int)std::max<long long>(grid, 1);
     }
@@ -513,11 +516,11 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
     rp.topk = topk;
     rp.sign = P->d.sign;
     rp.phase = P->d.phase;
-    rp.kahan = P->d.sum == BLS_SUM_KAHAN;
+    rp.sums = P->d.sum;
     {
         int nbmax = 2;
         for (int c = 0; c < nc; ++c) nbmax = std::max(nbmax, specs[g0 + c].nb);
-        rp.smem_bytes = reduce_smem_bytes(nbmax, topk, rp.kahan);
+        rp.smem_bytes = reduce_smem_bytes(nbmax, topk, rp.sums);
         rp.err = P->err.as<int>();
     }
     rp.spectrum = spectrum ? (spectrum_dev ? spectrum : P->spec.as<float>()) : nullptr;
@@ -544,8 +547,10 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
         if ((x = cudaMemsetAsync(P->err.p, 0, 64, st)) != cudaSuccess) return x;
         if (prof) record(P->ev[0]);
         NvtxRange r_prep("bls.prep");   // then fold_sweep, reduce (host enqueue spans)
+        // (the unbinned kernels read FP32 weights)
         if ((x = launch_prep(P->cdesc.as<CurveDesc>(), nullptr, nc, P->err.as<int>(),
-                             unbinned ? kPhaseFX64 : P->d.phase, st)) != cudaSuccess)
+                             unbinned ? kPhaseFX64 : P->d.phase, unbinned ? kSumF32 : P->d.sum,
+                             st)) != cudaSuccess)
             return x;
         ++launches;
         if (prof) record(P->ev[1]);
@@ -567,7 +572,7 @@ bls_status run_group(bls_plan_impl* P, const std::vector<CurveSpec>& specs, int 
                 fp.chunk = geoms[q].chunk;
                 fp.stride = geoms[q].stride;
                 fp.wait_ns = wait_ns;
-                if ((x = launch_fold_sweep(fp, geoms[q].T, grids[q], P->d.phase, P->d.sum == BLS_SUM_KAHAN,
+                if ((x = launch_fold_sweep(fp, geoms[q].T, grids[q], P->d.phase, P->d.sum,
                                            geoms[q].ws, P->d.sign, geoms[q].smem, st)) != cudaSuccess)
                     return x;
                 ++launches;
@@ -865,7 +870,7 @@ bls_status bls_plan_create(const bls_plan_desc* desc, void* cuda_stream, bls_pla
     }
     if (d.topk < 1 || d.topk > kMaxTopK) return set_error(BLS_ERR_INVALID, "topk = %d, need 1..%d", d.topk, kMaxTopK);
     if (d.phase < 0 || d.phase > 3) return set_error(BLS_ERR_INVALID, "phase = %d", d.phase);
-    if (d.sum < 0 || d.sum > 1) return set_error(BLS_ERR_INVALID, "sum = %d", d.sum);
+    if (d.sum < 0 || d.sum > 2) return set_error(BLS_ERR_INVALID, "sum = %d", d.sum);
     if (d.sign < 0 || d.sign > 1) return set_error(BLS_ERR_INVALID, "sign = %d", d.sign);
     if (d.algo < 0 || d.algo > 2) return set_error(BLS_ERR_INVALID, "algo = %d", d.algo);
     if (d.freqs_per_block < 0 || d.freqs_per_block > fold_sweep_max_threads() || (d.freqs_per_block % 8) != 0)
@@ -1063,7 +1068,7 @@ bls_status bls_debug_powers(bls_plan* P, const bls_curve* curve, float* power_ou
     float* dP = P->jsbuf.as<float>();
     int* di1 = reinterpret_cast<int*>(dP + nf);
     int* dk = di1 + nf;
-    if ((e = launch_argmax(P->cdesc.as<CurveDesc>(), nb, nf, P->d.phase, P->d.sum == BLS_SUM_KAHAN,
+    if ((e = launch_argmax(P->cdesc.as<CurveDesc>(), nb, nf, P->d.phase, P->d.sum,
                            P->d.sign, dP, di1, dk, P->stream)) != cudaSuccess)
         return cuda_fail(e, "best-box launch");
     if ((e = cudaMemcpyAsync(i1_out, di1, (size_t)nf * 4, cudaMemcpyDeviceToHost, P->stream)) != cudaSuccess ||
@@ -1128,7 +1133,7 @@ bls_status bls_debug_fold(bls_plan* P, const bls_curve* curve, const int* js, in
         g.T = 1;   // no tiles: the incremental fold is not used
     }
     if ((e = launch_debug_fold(P->cdesc.as<CurveDesc>(), P->jsbuf.as<int>(), nj, P->d.phase, g.T,
-                               P->d.algo == BLS_ALGO_TILED ? P->d.sum == BLS_SUM_KAHAN : 1,
+                               P->d.algo == BLS_ALGO_TILED ? P->d.sum : kSumKahan,
                                P->binsbuf.as<int>(), P->stream)) != cudaSuccess)
         return cuda_fail(e, "debug fold launch");
     if ((e = cudaMemcpyAsync(bins_out, P->binsbuf.p, (size_t)nj * s.n * 4, cudaMemcpyDeviceToHost, P->stream)) != cudaSuccess)

@@ -3,7 +3,8 @@
 // HBM layout (one search launch):
 //   CurveDesc[ncurves]          per-curve scalars and pointers (inputs, prepared points,
 //                               per-frequency results)
-//   float4 pts[n]               prepared points (dt_hi, dt_lo, w, w*x), 16 B per point
+//   float4 pts[n]               prepared points (dt_hi, dt_lo, w, w*x), 16 B per point; in
+//                               the fixed-point sum mode w and w*x are 32-bit integers
 //   double dt64[n]              exact FP64 time offsets, read only by the exact re-fold
 //   float res[nf]               per-frequency largest box power P (FP32)
 //   DevPeak peaks[ncurves*topk] reduced peaks (FP64)
@@ -19,6 +20,10 @@ namespace blsgpu {
 
 constexpr int kMaxTopK = 16;
 constexpr int kPhaseFX64 = 0, kPhaseF64 = 1, kPhaseF32 = 2, kPhaseDF32 = 3;
+// Sum modes (the values of BLS_SUM_*): histogram entries are (W, X) integer pairs (fixed,
+// 8 B), FP32 pairs (8 B) or FP32 pairs with their compensations (Kahan, 16 B).
+constexpr int kSumFixed = 0, kSumF32 = 1, kSumKahan = 2;
+__host__ __device__ constexpr int hist_entry_bytes(int sums) { return sums == kSumKahan ? 16 : 8; }
 
 struct CurveDesc {
     const double* t;       // raw times (device)
@@ -35,6 +40,9 @@ struct CurveDesc {
     int n, nf, nb, kmin, kmax;
     int T;                 // frequencies per tile of this curve (block size of its class)
     int fxs;               // fixed-point scale of the FX64 fold: DT = dt 2^fxs (prep kernel)
+    // fixed-point sums (prep kernel): a bin's integer sums (W, X) stand for
+    // r = W * wq and s = X * xq (wq = 1 / sum of all W, xq = 1 / the scale of w x)
+    float wq, xq;
 };
 
 // A run of frequency tiles of one curve processed by one fold-sweep launch.
@@ -141,26 +149,27 @@ struct ReduceParams {
     int topk;
     int sign;
     int phase;                 // fold mode of the search (for the best-box recomputation)
-    int kahan;                 // Kahan histograms
+    int sums;                  // sum mode of the search (kSum*)
     size_t smem_bytes;         // dynamic shared memory of the launch (reduce_smem_bytes)
     int* err;                  // error word (index checks of the BLS_DEBUG build)
 };
 
 // Shared memory a fold-sweep block needs.
-size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int kahan);
+size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int sums);
 
+// sums: the sum mode whose point layout the prep kernel writes (kSum*).
 cudaError_t launch_prep(CurveDesc* d_curves, const int* slots, int ncurves, int* err, int phase,
-                        cudaStream_t s);
-cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan, int ws,
+                        int sums, cudaStream_t s);
+cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int sums, int ws,
                               int sign, size_t smem, cudaStream_t s);
 cudaError_t launch_reduce(const ReduceParams& p, int ncurves, cudaStream_t s);
-size_t reduce_smem_bytes(int nb_max, int topk, int kahan);
+size_t reduce_smem_bytes(int nb_max, int topk, int sums);
 // Diagnostics: (P, i1, k) of the best box at every frequency of one prepared curve.
-cudaError_t launch_argmax(const CurveDesc* d_curve, int nb, int nf, int phase, int kahan,
+cudaError_t launch_argmax(const CurveDesc* d_curve, int nb, int nf, int phase, int sums,
                           int sign, float* P, int* i1, int* k, cudaStream_t s);
-// T, kahan: the tile width and sum mode the plan's search uses for this curve.
+// T, sums: the tile width and sum mode the plan's search uses for this curve.
 cudaError_t launch_debug_fold(const CurveDesc* d_curve, const int* js, int nj, int phase,
-                              int T, int kahan, int* bins, cudaStream_t s);
+                              int T, int sums, int* bins, cudaStream_t s);
 // Baseline: one curve, one thread per frequency, FP64 histograms in global scratch.
 cudaError_t launch_plain_f64(const CurveDesc* d_curve, const double* w64, const double* wx64,
                              int nf, double* hist, int sign, cudaStream_t s);
@@ -170,11 +179,11 @@ int fold_sweep_max_threads();
 // Whether a class of curves (tile width T, nb, widths kmin..kmax) runs in the
 // warp-specialised fold-sweep kernel under the plan's choice (BLS_FOLD_*), and the tile
 // width preferred for it.
-bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax, int choice);
-int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax, int choice);
-int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, int ws);
+bool fold_use_ws(int T, int sums, int nb, int kmin, int kmax, int choice);
+int fold_preferred_cols(int tmax, int sums, int nb, int kmin, int kmax, int choice);
+int fold_blocks_per_sm(int T, size_t smem, int phase, int sums, int sign, int ws);
 // Kernel of a class: 0 one-group, 1 warp-specialised.
-int fold_ws_mode(int T, int kahan, int nb, int kmin, int kmax, int choice);
+int fold_ws_mode(int T, int sums, int nb, int kmin, int kmax, int choice);
 int fold_block_threads(int cols);   // threads of a fold-sweep block with `cols` columns
 
 }  // namespace blsgpu

@@ -505,10 +505,15 @@ constexpr int kPrepThreads = 256;
 // x = y - ybar, dt = t - min t.  Points are stored in pairs (2p, 2p+1) as two float4:
 // (dt_hi0, dt_hi1, dt_lo0, dt_lo1) and (w0, wx0, w1, wx1), dt in FP64 beside them; an odd
 // curve gets a pad point of zero weight.  In the FX64 phase mode the first float4 holds
-// the bit patterns of DT = RN_int(dt 2^fxs) instead: (lo0, lo1, hi0, hi1).  Validates the inputs (finite t and y, finite
-// dy > 0, frequencies > 0).
+// the bit patterns of DT = RN_int(dt 2^fxs) instead: (lo0, lo1, hi0, hi1).  In the
+// fixed-point sum mode the second float4 holds the bit patterns of the integers
+// W = RN(w Sw) (unsigned) and X = RN(w x Sx) (signed) instead of w and w x, with
+// Sw = 2^32 - 2n - 16 and Sx = (2^31 - n - 16) / sum |w x|: every subset's W sum is below
+// 2^32 and its |X sum| below 2^31, so a bin's integer sums never overflow; the curve's
+// wq = 1 / sum W and xq = 1 / Sx turn them back into r and s.  Validates the inputs (finite
+// t and y, finite dy > 0, frequencies > 0).
 __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, const int* slots,
-                                                             int* err, int phase)
+                                                             int* err, int phase, int sums)
 {
     __shared__ double red[kPrepThreads];
     CurveDesc* cd = &curves[slots ? slots[blockIdx.x] : (int)blockIdx.x];
@@ -557,7 +562,21 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, c
     const double ybar = __dadd_rn(y0, acc);
     const int fxs = fx_shift(__dsub_rn(tmax, tmin));
     const bool fx = phase == kPhaseFX64;
-    double swx2 = 0.0;
+    const bool fixs = sums == kSumFixed;
+    double Sw = 0.0, Sx = 1.0;
+    if (fixs) {
+        double ax = 0.0;   // sum |w x|
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double inv = 1.0;
+            if (dy) { double dd = (double)dy[i]; inv = __ddiv_rn(1.0, __dmul_rn(dd, dd)); }
+            const double w = __ddiv_rn(inv, W);
+            ax = __dadd_rn(ax, fabs(__dmul_rn(w, __dsub_rn((double)y[i], ybar))));
+        }
+        ax = block_sum(ax, red);
+        Sw = 4294967296.0 - 2.0 * n - 16.0;
+        if (ax > 0.0) Sx = __ddiv_rn(2147483648.0 - (double)n - 16.0, ax);
+    }
+    double swx2 = 0.0, wtot = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double inv = 1.0;
         if (dy) { double dd = (double)dy[i]; inv = __ddiv_rn(1.0, __dmul_rn(dd, dd)); }
@@ -577,8 +596,15 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, c
             A[l] = dh;
             A[2 + l] = __double2float_rn(__dsub_rn(dt, (double)dh));
         }
-        B[2 * l] = __double2float_rn(w);
-        B[2 * l + 1] = __double2float_rn(wx);
+        if (fixs) {
+            const unsigned Wi = __double2uint_rn(__dmul_rn(w, Sw));
+            B[2 * l] = __uint_as_float(Wi);
+            B[2 * l + 1] = __int_as_float(__double2int_rn(__dmul_rn(wx, Sx)));
+            wtot = __dadd_rn(wtot, (double)Wi);   // integers below 2^32: exact
+        } else {
+            B[2 * l] = __double2float_rn(w);
+            B[2 * l + 1] = __double2float_rn(wx);
+        }
         dt64[i] = dt;
         swx2 = __dadd_rn(swx2, __dmul_rn(wx, x));
     }
@@ -588,7 +614,10 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, c
         dt64[n] = 0.0;
     }
     swx2 = block_sum(swx2, red);
+    if (fixs) wtot = block_sum(wtot, red);
     if (threadIdx.x == 0) {
+        cd->wq = fixs && wtot > 0.0 ? __double2float_rn(__ddiv_rn(1.0, wtot)) : 0.0f;
+        cd->xq = fixs ? __double2float_rn(__ddiv_rn(1.0, Sx)) : 0.0f;
         cd->t_ref = tmin;
         cd->W = W;
         cd->ybar = ybar;
@@ -599,10 +628,10 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, c
 }
 
 cudaError_t launch_prep(CurveDesc* d_curves, const int* slots, int ncurves, int* err, int phase,
-                        cudaStream_t s)
+                        int sums, cudaStream_t s)
 {
     if (ncurves <= 0) return cudaSuccess;
-    prep_kernel<<<ncurves, kPrepThreads, 0, s>>>(d_curves, slots, err, phase);
+    prep_kernel<<<ncurves, kPrepThreads, 0, s>>>(d_curves, slots, err, phase, sums);
     return cudaGetLastError();
 }
 
@@ -631,7 +660,8 @@ cudaError_t launch_prep_f64(const CurveDesc* d_curves, int ncurves, double* w64,
 // ------------------------------------------------------------------------- a4: binning
 
 // Histogram entry of one thread: (sum w, sum w x) as an FP32 pair, 8 bytes; the Kahan
-// variant adds the two compensation terms, 16 bytes.  Thread t's bin b lives at entry
+// variant adds the two compensation terms, 16 bytes; the fixed-point variant holds the
+// integer sums (sum W, sum X) as two 32-bit words, 8 bytes.  Thread t's bin b lives at entry
 // b * stride + t, so the 32 lanes of a warp touch 32 consecutive entries whatever their
 // bins are (no bank conflicts).
 
@@ -708,6 +738,47 @@ __device__ __forceinline__ void fix_sub(const float4* cp, const double* cd, cons
         else fold_df32_pair(cp[2 * q], fq, b0, b1, e0, e1);
         if (e0) b[2 * q] = fold_exact(cd[2 * q], fc.f, fc.nb);
         if (e1) b[2 * q + 1] = fold_exact(cd[2 * q + 1], fc.f, fc.nb);
+    }
+}
+
+// Shared-memory integer reduction (no value returned).  Integer additions are exact and
+// commutative, so the sums of a bin do not depend on the order of its points.
+__device__ __forceinline__ void red_u32(unsigned addr, unsigned v)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+// Fixed-point sums: each of the 16 points of a sub-chunk adds its (W, X) words to its bin
+// with two shared-memory reductions.  A point's addition does not wait for the bin's
+// previous value, and points that share a bin need no merging.
+__device__ __forceinline__ void red_sub(unsigned hbase, unsigned rowb, const unsigned* b,
+                                        const float4* Bw, unsigned nbu, int* err)
+{
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const unsigned a = hbase + (bls_ok(b[i] < nbu, err) ? b[i] : 0u) * rowb;
+        const float4& w = Bw[i >> 1];
+        red_u32(a, __float_as_uint((i & 1) ? w.z : w.x));
+        red_u32(a + 4u, __float_as_uint((i & 1) ? w.w : w.y));
+    }
+}
+
+// The FP32 pair (r, s) of a fixed-point bin entry (W, X): r = W wq, s = X xq.
+__device__ __forceinline__ void fixed_pair(u64 h, float wq, float xq, float& r, float& s)
+{
+    r = __fmul_rn(__uint2float_rn((unsigned)h), wq);
+    s = __fmul_rn(__int2float_rn((int)(unsigned)(h >> 32)), xq);
+}
+
+// Rewrites one histogram column of nb fixed-point entries as FP32 pairs, in place.
+__device__ __forceinline__ void fixed_to_f32(unsigned hbase, unsigned rowb, int nb, float wq,
+                                             float xq)
+{
+    for (int b = 0; b < nb; ++b) {
+        const unsigned a = hbase + (unsigned)b * rowb;
+        float r, sx;
+        fixed_pair(lds64(a), wq, xq, r, sx);
+        sts64(a, pk(r, sx));
     }
 }
 
@@ -790,7 +861,16 @@ __device__ __forceinline__ void rmw_sub_k(unsigned hbase, unsigned rowb, const u
 // chain, so the fold arithmetic fills the shared-memory latency of the chain; the rare
 // FP64 re-fold runs after the stores.  hbase is the shared-memory address of this
 // thread's bin 0, rowb the byte stride between bins.
-template <int PHASE, bool PINGPONG, bool INC, bool KAHAN = false, bool POW2 = false>
+template <int SUMS>
+__device__ __forceinline__ void hist_sub(unsigned hbase, unsigned rowb, const unsigned* b,
+                                         const float4* Bw, unsigned nbu, int* err)
+{
+    if (SUMS == kSumKahan) rmw_sub_k(hbase, rowb, b, Bw, nbu, err);
+    else if (SUMS == kSumFixed) red_sub(hbase, rowb, b, Bw, nbu, err);
+    else rmw_sub(hbase, rowb, b, Bw, nbu, err);
+}
+
+template <int PHASE, bool PINGPONG, bool INC, int SUMS = kSumF32, bool POW2 = false>
 __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int nsub,
                                          unsigned hbase, unsigned rowb, const FoldConst& fc,
                                          const FoldPacked& fq, int* err)
@@ -807,29 +887,29 @@ __device__ __forceinline__ void bin_fast(const float4* cp, const double* cd, int
         for (; sc + 2 < nsub; sc += 2) {
             const float4* n1 = cp + 16 * (sc + 1);
             const bool e1 = fold_sub<PHASE, INC, POW2>(n1, fc, fq, b1, W1);
-            if (KAHAN) rmw_sub_k(hbase, rowb, b0, W0, nbu, err); else rmw_sub(hbase, rowb, b0, W0, nbu, err);
+            hist_sub<SUMS>(hbase, rowb, b0, W0, nbu, err);
             if (e1) fix_sub<PHASE, INC, POW2>(n1, cd + 16 * (sc + 1), fc, fq, b1);
             const float4* n2 = cp + 16 * (sc + 2);
             const bool e2 = fold_sub<PHASE, INC, POW2>(n2, fc, fq, b0, W0);
-            if (KAHAN) rmw_sub_k(hbase, rowb, b1, W1, nbu, err); else rmw_sub(hbase, rowb, b1, W1, nbu, err);
+            hist_sub<SUMS>(hbase, rowb, b1, W1, nbu, err);
             if (e2) fix_sub<PHASE, INC, POW2>(n2, cd + 16 * (sc + 2), fc, fq, b0);
         }
     }
     for (; sc + 1 < nsub; ++sc) {
         const float4* n1 = cp + 16 * (sc + 1);
         const bool e1 = fold_sub<PHASE, INC, POW2>(n1, fc, fq, b1, W1);
-        if (KAHAN) rmw_sub_k(hbase, rowb, b0, W0, nbu, err); else rmw_sub(hbase, rowb, b0, W0, nbu, err);
+        hist_sub<SUMS>(hbase, rowb, b0, W0, nbu, err);
         if (e1) fix_sub<PHASE, INC, POW2>(n1, cd + 16 * (sc + 1), fc, fq, b1);
 #pragma unroll
         for (int i = 0; i < 16; ++i) b0[i] = b1[i];
 #pragma unroll
         for (int q = 0; q < 8; ++q) W0[q] = W1[q];
     }
-    if (KAHAN) rmw_sub_k(hbase, rowb, b0, W0, nbu, err); else rmw_sub(hbase, rowb, b0, W0, nbu, err);
+    hist_sub<SUMS>(hbase, rowb, b0, W0, nbu, err);
 }
 
 // Generic binning (FP64 or FP32 phase modes, precision studies): pair by pair.
-template <int PHASE, bool KAHAN = false>
+template <int PHASE, int SUMS = kSumF32>
 __device__ __forceinline__ void bin_generic(const float4* cp, const double* cd, int npairs,
                                             unsigned hbase, unsigned rowb, const FoldConst& fc,
                                             const FoldPacked& fq, int* err)
@@ -841,7 +921,12 @@ __device__ __forceinline__ void bin_generic(const float4* cp, const double* cd, 
         const unsigned nbu = (unsigned)fc.nb;
         const unsigned a0 = hbase + (bls_ok(b0 < nbu, err) ? b0 : 0u) * rowb;
         const unsigned a1 = hbase + (bls_ok(b1 < nbu, err) ? b1 : 0u) * rowb;
-        if (KAHAN) {
+        if (SUMS == kSumFixed) {
+            red_u32(a0, __float_as_uint(B.x));
+            red_u32(a0 + 4u, __float_as_uint(B.y));
+            red_u32(a1, __float_as_uint(B.z));
+            red_u32(a1 + 4u, __float_as_uint(B.w));
+        } else if (SUMS == kSumKahan) {
             u64 h, c;
             lds128(a0, h, c);
             kahan2(h, c, pk(B.x, B.y));
@@ -1412,11 +1497,11 @@ constexpr int kFoldMaxThreads = 256;
 
 // Shared memory of a fold-sweep block: [staging: 2 x chunk point pairs + FP64 offsets]
 // [histograms: nb_max rows x stride entries].
-size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int kahan)
+size_t fold_smem_bytes(int T, int stride, int nb_max, int chunk, int sums)
 {
     (void)T;
     size_t stage = (size_t)2 * chunk * (sizeof(float4) + sizeof(double));
-    size_t hist = (size_t)nb_max * stride * (kahan ? sizeof(float4) : sizeof(float2));
+    size_t hist = (size_t)nb_max * stride * hist_entry_bytes(sums);
     return stage + hist;
 }
 
@@ -1432,9 +1517,10 @@ int fold_block_threads(int cols)
     return (BLS_SWEEP_SPLIT == 2 && 2 * cols <= kFoldMaxThreads) ? 2 * cols : cols;
 }
 
-template <int PHASE, int KAHAN, int SIGN>
+template <int PHASE, int SUMS, int SIGN>
 __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldParams p)
 {
+    constexpr int KAHAN = SUMS == kSumKahan;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
     // p.cols frequencies per tile, one histogram column each; blockDim.x is cols or
@@ -1537,15 +1623,19 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
                     }
                 } else if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
                     if (inc && fc.sh != 0u)
-                        bin_fast<PHASE, false, true, false, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
+                        bin_fast<PHASE, false, true, SUMS, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                     else if (inc)
-                        bin_fast<PHASE, false, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
+                        bin_fast<PHASE, false, true, SUMS>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                     else
-                        bin_fast<PHASE, false, false>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
+                        bin_fast<PHASE, false, false, SUMS>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                 } else {
-                    bin_generic<PHASE>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq, p.err);
+                    bin_generic<PHASE, SUMS>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq, p.err);
                 }
             }
+            __syncthreads();
+        }
+        if (SUMS == kSumFixed) {   // integer sums -> FP32 (r, s), each binning thread its column
+            if (active && part == 0) fixed_to_f32(hbase, rowb, nb, cdr.wq, cdr.xq);
             __syncthreads();
         }
 
@@ -1784,7 +1874,7 @@ __device__ void fetch_tile(const FoldParams& p, TileSlot* slot, int lane)
 // hands them back (the binning group zeroes them) and sweeps the boxes from TMEM.
 constexpr int kWsBinThreads = 128, kWsSweepThreads = 256, kWsSweep0 = 128;
 
-template <int SIGN, int KAHAN>
+template <int SIGN, int SUMS>
 __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_ok, int col,
                                                  unsigned s_tmem, TileSlot* s_slot,
                                                  unsigned full_bar, unsigned empty_bar,
@@ -1819,6 +1909,7 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
         const int tile = sl.tile;
         const int nf = sl.cd.nf, nb = sl.cd.nb, kmin = sl.cd.kmin, kmax = sl.cd.kmax;
         float* const res = sl.cd.res;
+        const float wq = sl.cd.wq, xq = sl.cd.xq;
         const int j = tile * T + col;
         const bool active = lane_ok && j < nf;
         const int SB = sweep_block(nb, kmin, kmax);
@@ -1838,7 +1929,7 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
                     const unsigned ai = ag + (unsigned)i * rowb - (g + i >= nb ? wrapb : 0u);
                     if (!bls_ok(g + i < 2 * nb, p.err)) {
                         h[i] = 0ull;
-                    } else if (KAHAN) {   // the compensated sums (sum - compensation)
+                    } else if (SUMS == kSumKahan) {   // the compensated sums (sum - compensation)
                         u64 hh, cc;
                         lds128(ai, hh, cc);
                         h[i] = sub2(hh, cc);
@@ -1850,7 +1941,8 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     float hw, hx;
-                    upk(h[i], hw, hx);
+                    if (SUMS == kSumFixed) fixed_pair(h[i], wq, xq, hw, hx);   // integer sums
+                    else upk(h[i], hw, hx);
                     if (g + i < nb) wmax = fmaxf(wmax, hw);
                     r[2 * i] = __float_as_uint(hw);
                     r[2 * i + 1] = __float_as_uint(hx);
@@ -1861,6 +1953,8 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
             tmem_wait_st();
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         } else if (part == 0) {
+            constexpr int KAHAN = SUMS == kSumKahan;
+            if (SUMS == kSumFixed && active) fixed_to_f32(hbase, rowb, nb, wq, xq);
             if (active)
                 v = SB == 4 ? sweep_max<KAHAN, SIGN, 4>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err)
                     : SB == 10 ? sweep_max<KAHAN, SIGN, 10>(hist, p.stride, nb, kmin, kmax, 0, 1, p.err)
@@ -1928,9 +2022,10 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
 
 constexpr int kWsMaxThreads = 384;
 
-template <int PHASE, int KAHAN, int SIGN>
+template <int PHASE, int SUMS, int SIGN>
 __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldParams p)
 {
+    constexpr int KAHAN = SUMS == kSumKahan;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) unsigned long long s_bar[2];   // [0] histograms full, [1] empty
     __shared__ TileSlot s_slot[2];                          // descriptor of tile k at [k & 1]
@@ -2069,20 +2164,20 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                 if (active) {   // a3 + a4
                     if ((PHASE == kPhaseDF32 && fc.fast) || (PHASE == kPhaseFX64 && fc.fxok)) {
                         if (inc && fc.sh != 0u)   // nb a power of two: shifts, not multiplies
-                            bin_fast<PHASE, true, true, KAHAN, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
+                            bin_fast<PHASE, true, true, SUMS, true>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                         else if (inc)
-                            bin_fast<PHASE, true, true, KAHAN>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
+                            bin_fast<PHASE, true, true, SUMS>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                         else
-                            bin_fast<PHASE, true, false, KAHAN>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
+                            bin_fast<PHASE, true, false, SUMS>(cp, cd, (cnum + 15) >> 4, hbase, rowb, fc, fq, p.err);
                     } else
-                        bin_generic<PHASE, KAHAN>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq, p.err);
+                        bin_generic<PHASE, SUMS>(cp, cd, (cnum + 1) >> 1, hbase, rowb, fc, fq, p.err);
                 }
                 group_sync(kBarBin, kWsBinThreads);
             }
             if (tid == 0) mbar_arrive(full_bar);
         }
     } else {
-        sweep_group_loop<SIGN, KAHAN>(p, lane_ok, col, s_tmem, s_slot, full_bar, empty_bar, s_wpart,
+        sweep_group_loop<SIGN, SUMS>(p, lane_ok, col, s_tmem, s_slot, full_bar, empty_bar, s_wpart,
                                s_wpart2, hist, hbase, rowb);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -2098,13 +2193,13 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
 // entries, whose compensated values the sweep group copies into TMEM), T a multiple of 8, at
 // most 128 (T/4 columns per TMEM lane quadrant).  BLS_FOLD_WS=0 in the environment selects
 // fold_sweep_kernel for every class.
-static bool use_ws(int T, int kahan)
+static bool use_ws(int T, int sums)
 {
     static const int env = [] {
         const char* e = getenv("BLS_FOLD_WS");
         return (e && e[0] == '0') ? 0 : 1;
     }();
-    (void)kahan;   // plain and Kahan histograms alike
+    (void)sums;   // every sum mode
     return env && T % 8 == 0 && T >= 8 && T <= 128;
 }
 
@@ -2118,11 +2213,11 @@ static int ws_threads(int) { return kWsMaxThreads; }
 // thread per column) 21.8 ms against 14.8 ms at 128 (warp-specialised).  256 columns
 // (nb <= 100) keep the one-group kernel, whose eight binning warps then win (11.5 ms
 // against 13.1 ms at nb = 100).
-int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax, int choice)
+int fold_preferred_cols(int tmax, int sums, int nb, int kmin, int kmax, int choice)
 {
     if (tmax >= 256) return tmax;
     const int Tw = tmax > 128 ? 128 : tmax & ~7;
-    if (Tw >= 8 && fold_use_ws(Tw, kahan, nb, kmin, kmax, choice)) return Tw;
+    if (Tw >= 8 && fold_use_ws(Tw, sums, nb, kmin, kmax, choice)) return Tw;
     return tmax;
 }
 
@@ -2131,15 +2226,15 @@ int fold_preferred_cols(int tmax, int kahan, int nb, int kmin, int kmax, int cho
 // shared memory while the binning group waits, and the one-group kernel, whose threads all
 // bin and then all sweep, is faster (nb = 400: 81.7 ms at 48 columns against 97.3 ms at
 // 64, 256 curves x 20k frequencies).
-bool fold_use_ws(int T, int kahan, int nb, int kmin, int kmax, int choice)
+bool fold_use_ws(int T, int sums, int nb, int kmin, int kmax, int choice)
 {
-    if (choice == BLS_FOLD_ONE_GROUP || !use_ws(T, kahan)) return false;
+    if (choice == BLS_FOLD_ONE_GROUP || !use_ws(T, sums)) return false;
     return choice == BLS_FOLD_WS || ws_tmem_mode(nb, kmin, kmax) != 0;
 }
 
-int fold_ws_mode(int T, int kahan, int nb, int kmin, int kmax, int choice)
+int fold_ws_mode(int T, int sums, int nb, int kmin, int kmax, int choice)
 {
-    return fold_use_ws(T, kahan, nb, kmin, kmax, choice) ? 1 : 0;
+    return fold_use_ws(T, sums, nb, kmin, kmax, choice) ? 1 : 0;
 }
 
 // Dynamic shared memory of a warp-specialised block: at least half of an SM's shared memory,
@@ -2158,14 +2253,14 @@ static size_t ws_smem(size_t smem)
     return smem > half ? smem : half;
 }
 
-template <int PHASE, int KAHAN, int SIGN>
+template <int PHASE, int SUMS, int SIGN>
 static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t smem,
                                  cudaStream_t s, int ws)
 {
     FoldParams q = p;
     q.cols = T;
-    if (ws && use_ws(T, KAHAN)) {
-        auto k = fold_sweep_ws_kernel<PHASE, KAHAN, SIGN>;
+    if (ws && use_ws(T, SUMS)) {
+        auto k = fold_sweep_ws_kernel<PHASE, SUMS, SIGN>;
         const size_t sm = ws_smem(smem);
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sm);
@@ -2173,7 +2268,7 @@ static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t sm
         k<<<grid, ws_threads(T), sm, s>>>(q);
         return cudaGetLastError();
     }
-    auto k = fold_sweep_kernel<PHASE, KAHAN, SIGN>;
+    auto k = fold_sweep_kernel<PHASE, SUMS, SIGN>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -2181,19 +2276,19 @@ static cudaError_t launch_fold_t(const FoldParams& p, int T, int grid, size_t sm
     return cudaGetLastError();
 }
 
-template <int PHASE, int KAHAN, int SIGN>
+template <int PHASE, int SUMS, int SIGN>
 static int blocks_t(int T, size_t smem, int ws)
 {
-    if (ws && use_ws(T, KAHAN)) {
+    if (ws && use_ws(T, SUMS)) {
         // one block per SM: all of TMEM and (nearly) all of shared memory
-        auto k = fold_sweep_ws_kernel<PHASE, KAHAN, SIGN>;
+        auto k = fold_sweep_ws_kernel<PHASE, SUMS, SIGN>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem(smem)) != cudaSuccess) {
             cudaGetLastError();
             return 1;
         }
         return 1;
     }
-    auto k = fold_sweep_kernel<PHASE, KAHAN, SIGN>;
+    auto k = fold_sweep_kernel<PHASE, SUMS, SIGN>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -2206,12 +2301,15 @@ static int blocks_t(int T, size_t smem, int ws)
     return nb > 0 ? nb : 1;
 }
 
-int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, int ws)
+int fold_blocks_per_sm(int T, size_t smem, int phase, int sums, int sign, int ws)
 {
 #define BLS_OCC(PH)                                                                   \
     if (phase == PH) {                                                                \
-        if (kahan) return sign ? blocks_t<PH, 1, 1>(T, smem, ws) : blocks_t<PH, 1, 0>(T, smem, ws); \
-        return sign ? blocks_t<PH, 0, 1>(T, smem, ws) : blocks_t<PH, 0, 0>(T, smem, ws);      \
+        if (sums == kSumKahan)                                                        \
+            return sign ? blocks_t<PH, kSumKahan, 1>(T, smem, ws) : blocks_t<PH, kSumKahan, 0>(T, smem, ws); \
+        if (sums == kSumF32)                                                          \
+            return sign ? blocks_t<PH, kSumF32, 1>(T, smem, ws) : blocks_t<PH, kSumF32, 0>(T, smem, ws); \
+        return sign ? blocks_t<PH, kSumFixed, 1>(T, smem, ws) : blocks_t<PH, kSumFixed, 0>(T, smem, ws); \
     }
     BLS_OCC(kPhaseDF32)
     BLS_OCC(kPhaseF64)
@@ -2221,15 +2319,19 @@ int fold_blocks_per_sm(int T, size_t smem, int phase, int kahan, int sign, int w
     return 1;
 }
 
-cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int kahan, int ws,
+cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, int sums, int ws,
                               int sign, size_t smem, cudaStream_t s)
 {
 #define BLS_DISPATCH(PH)                                                              \
     if (phase == PH) {                                                                \
-        if (kahan) return sign ? launch_fold_t<PH, 1, 1>(p, T, grid, smem, s, ws)         \
-                               : launch_fold_t<PH, 1, 0>(p, T, grid, smem, s, ws);        \
-        return sign ? launch_fold_t<PH, 0, 1>(p, T, grid, smem, s, ws)                    \
-                    : launch_fold_t<PH, 0, 0>(p, T, grid, smem, s, ws);                   \
+        if (sums == kSumKahan)                                                        \
+            return sign ? launch_fold_t<PH, kSumKahan, 1>(p, T, grid, smem, s, ws)    \
+                        : launch_fold_t<PH, kSumKahan, 0>(p, T, grid, smem, s, ws);   \
+        if (sums == kSumF32)                                                          \
+            return sign ? launch_fold_t<PH, kSumF32, 1>(p, T, grid, smem, s, ws)      \
+                        : launch_fold_t<PH, kSumF32, 0>(p, T, grid, smem, s, ws);     \
+        return sign ? launch_fold_t<PH, kSumFixed, 1>(p, T, grid, smem, s, ws)        \
+                    : launch_fold_t<PH, kSumFixed, 0>(p, T, grid, smem, s, ws);       \
     }
     BLS_DISPATCH(kPhaseDF32)
     BLS_DISPATCH(kPhaseF64)
@@ -2244,10 +2346,13 @@ cudaError_t launch_fold_sweep(const FoldParams& p, int T, int grid, int phase, i
 // One frequency's histogram of a curve, binned point by point into a private histogram
 // column with the hot kernel's fold.  The FP32 bin sums follow point order; where points of
 // one read-modify-write group of the hot kernel share a bin, that kernel adds their
-// pre-summed weights, so such a bin can differ from this one in its last bit.
+// pre-summed weights, so such a bin can differ from this one in its last bit.  Fixed-point
+// sums are exact integers, converted to FP32 as the hot kernels convert them: those bins
+// equal the hot kernels' bit for bit.
 __device__ void bin_column(const CurveDesc& cd, double f, unsigned char* hist, int stride,
-                           int phase, int kahan, int* err = nullptr)
+                           int phase, int sums, int* err = nullptr)
 {
+    const bool kahan = sums == kSumKahan;
     const size_t S = (size_t)stride;
     const FoldConst fc = make_fold_const(f, cd.nb, cd.dtmax, cd.fxs);
     const FoldPacked fq = make_fold_packed(fc);
@@ -2263,51 +2368,66 @@ __device__ void bin_column(const CurveDesc& cd, double f, unsigned char* hist, i
         if (kahan) {
             kahan_add(reinterpret_cast<float4*>(hist) + b0 * S, B.x, B.y);
             kahan_add(reinterpret_cast<float4*>(hist) + b1 * S, B.z, B.w);
+        } else if (sums == kSumFixed) {
+            unsigned* H = reinterpret_cast<unsigned*>(hist);
+            H[2 * b0 * S] += __float_as_uint(B.x);
+            H[2 * b0 * S + 1] += __float_as_uint(B.y);
+            H[2 * b1 * S] += __float_as_uint(B.z);
+            H[2 * b1 * S + 1] += __float_as_uint(B.w);
         } else {
             u64* H = reinterpret_cast<u64*>(hist);
             H[b0 * S] = add2(H[b0 * S], pk(B.x, B.y));
             H[b1 * S] = add2(H[b1 * S], pk(B.z, B.w));
         }
     }
+    if (sums == kSumFixed) {
+        u64* H = reinterpret_cast<u64*>(hist);
+        for (int b = 0; b < cd.nb; ++b) {
+            float r, sx;
+            fixed_pair(H[(size_t)b * S], cd.wq, cd.xq, r, sx);
+            H[(size_t)b * S] = pk(r, sx);
+        }
+    }
 }
 
 // The best box (exact tie-break) of one frequency, by one thread.
 __device__ Best best_box_at(const CurveDesc& cd, double f, unsigned char* hist, int stride,
-                            int phase, int kahan, int sign)
+                            int phase, int sums, int sign)
 {
-    bin_column(cd, f, hist, stride, phase, kahan);
-    return sweep_exact_rt(sign, hist, stride, kahan, cd.nb, cd.kmin, cd.kmax);
+    bin_column(cd, f, hist, stride, phase, sums);
+    return sweep_exact_rt(sign, hist, stride, sums == kSumKahan, cd.nb, cd.kmin, cd.kmax);
 }
 
 // The same by the 32 lanes of a warp: lane 0 bins, the lanes share the exact sweep.
 __device__ Best best_box_warp(const CurveDesc& cd, double f, unsigned char* hist, int stride,
-                              int phase, int kahan, int sign, int lane, int* err)
+                              int phase, int sums, int sign, int lane, int* err)
 {
-    if (lane == 0) bin_column(cd, f, hist, stride, phase, kahan, err);
+    if (lane == 0) bin_column(cd, f, hist, stride, phase, sums, err);
     __syncwarp();
+    const int kahan = sums == kSumKahan;
     return sign ? sweep_exact_warp<1>(hist, stride, kahan, cd.nb, cd.kmin, cd.kmax, lane)
                 : sweep_exact_warp<0>(hist, stride, kahan, cd.nb, cd.kmin, cd.kmax, lane);
 }
 
 // Diagnostics: (P, i1, k) of the best box at frequencies j0 .. j0 + count of one curve.
-__global__ void argmax_kernel(const CurveDesc* curve, int j0, int count, int phase, int kahan,
+__global__ void argmax_kernel(const CurveDesc* curve, int j0, int count, int phase, int sums,
                               int sign, float* P, int* i1, int* k)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const CurveDesc cd = *curve;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= count) return;
-    unsigned char* hist = smem + (size_t)threadIdx.x * (kahan ? 16 : 8);
-    const Best g = best_box_at(cd, grid_freq(cd, j0 + q), hist, blockDim.x, phase, kahan, sign);
+    unsigned char* hist = smem + (size_t)threadIdx.x * hist_entry_bytes(sums);
+    const Best g = best_box_at(cd, grid_freq(cd, j0 + q), hist, blockDim.x, phase, sums, sign);
     P[q] = g.num > 0.0f ? __fdiv_rn(g.num, g.den) : 0.0f;
     i1[q] = g.i1;
     k[q] = g.k;
 }
 
-cudaError_t launch_argmax(const CurveDesc* d_curve, int nb, int nf, int phase, int kahan,
+cudaError_t launch_argmax(const CurveDesc* d_curve, int nb, int nf, int phase, int sums,
                           int sign, float* P, int* i1, int* k, cudaStream_t s)
 {
-    const int esz = kahan ? 16 : 8;
+    const int esz = hist_entry_bytes(sums);
     int T = 64;
     while (T > 1 && (size_t)T * nb * esz > 200 * 1024) T >>= 1;
     const size_t smem = (size_t)T * nb * esz;
@@ -2316,7 +2436,7 @@ cudaError_t launch_argmax(const CurveDesc* d_curve, int nb, int nf, int phase, i
     if (e != cudaSuccess) return e;
     for (int j0 = 0; j0 < nf; j0 += 65536) {
         const int cnt = min(65536, nf - j0);
-        argmax_kernel<<<(cnt + T - 1) / T, T, smem, s>>>(d_curve, j0, cnt, phase, kahan, sign,
+        argmax_kernel<<<(cnt + T - 1) / T, T, smem, s>>>(d_curve, j0, cnt, phase, sums, sign,
                                                          P + j0, i1 + j0, k + j0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -2409,7 +2529,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
     // best box of each kept frequency, one warp per frequency (lane 0 bins, the lanes share
     // the exact sweep), in rounds of at most one frequency per warp that fit the histograms
     {
-        const int esz = p.kahan ? 16 : 8;
+        const int esz = hist_entry_bytes(p.sums);
         const int nwarps = (int)(blockDim.x >> 5);
         int R = (int)(p.smem_bytes / ((size_t)cd.nb * esz));
         R = R < 1 ? 1 : (R > K ? K : (R > nwarps ? nwarps : R));
@@ -2418,7 +2538,7 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
             if (warp < R && q < K) {
                 if (sel[q] >= 0) {
                     const Best g = best_box_warp(cd, grid_freq(cd, sel[q]), smem + (size_t)warp * esz,
-                                                 R, p.phase, p.kahan, p.sign, lane, p.err);
+                                                 R, p.phase, p.sums, p.sign, lane, p.err);
                     if (lane == 0) {
                         sel_i1[q] = g.i1;
                         sel_k[q] = g.k;
@@ -2486,9 +2606,9 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(ReduceParams p)
     }
 }
 
-size_t reduce_smem_bytes(int nb_max, int topk, int kahan)
+size_t reduce_smem_bytes(int nb_max, int topk, int sums)
 {
-    size_t need = (size_t)nb_max * topk * (kahan ? 16 : 8);
+    size_t need = (size_t)nb_max * topk * hist_entry_bytes(sums);
     const size_t cap = 160 * 1024;
     return need < cap ? need : cap;
 }
@@ -2506,7 +2626,7 @@ cudaError_t launch_reduce(const ReduceParams& p, int ncurves, cudaStream_t s)
 // ------------------------------------------------------------------------- diagnostics
 
 // Per-point bins of one curve at frequencies js, by the fold of the given phase mode.  In
-// FX64 mode on a uniform grid (plain sums) the incremental fold of the search kernels is
+// FX64 mode on a uniform grid (fixed-point or FP32 sums) the incremental fold of the search kernels is
 // run as well (with the search's shift form when nb is a power of two), for the
 // frequency's place in a tile of T columns -- the tile width the plan's search uses for
 // this curve, so the reference column jc is the search's; a point
@@ -2552,9 +2672,10 @@ __global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bi
 }
 
 cudaError_t launch_debug_fold(const CurveDesc* d_curve, const int* js, int nj, int phase,
-                              int T, int kahan, int* bins, cudaStream_t s)
+                              int T, int sums, int* bins, cudaStream_t s)
 {
     if (nj <= 0) return cudaSuccess;
+    const int kahan = sums == kSumKahan;
     if (T < 1) return cudaErrorInvalidValue;
     if (phase == kPhaseF64)
         debug_fold_kernel<kPhaseF64><<<nj, 256, 0, s>>>(d_curve, js, bins, T, kahan);

@@ -298,7 +298,7 @@ bool Server::step()
         cudaMemsetAsync(err.p, 0, sizeof(int), stream);
         enq = true;
         cudaMemcpyAsync(dsl, hs, sizeof(int) * nadm, cudaMemcpyHostToDevice, stream);
-        if ((e = launch_prep(cdesc.as<CurveDesc>(), dsl, nadm, err.as<int>(), P->d.phase, stream)) != cudaSuccess) {
+        if ((e = launch_prep(cdesc.as<CurveDesc>(), dsl, nadm, err.as<int>(), P->d.phase, P->d.sum, stream)) != cudaSuccess) {
             fail_all(std::string("prep launch: ") + cudaGetErrorString(e));
             return false;
         }
@@ -369,11 +369,11 @@ bool Server::step()
             fp.stride = geoms[q].stride;
             fp.wait_ns = handoff_limit_ns();
             const int bps = fold_blocks_per_sm(geoms[q].T, geoms[q].smem, P->d.phase,
-                                               P->d.sum == BLS_SUM_KAHAN, P->d.sign, geoms[q].ws);
+                                               P->d.sum, P->d.sign, geoms[q].ws);
             long long grid = std::min<long long>((long long)P->sm_count * bps, tot[q]);
             cudaStream_t sq = nstr > 1 ? cls_stream[q % nstr] : stream;
             if ((e = launch_fold_sweep(fp, geoms[q].T, (int)std::max<long long>(grid, 1), P->d.phase,
-                                       P->d.sum == BLS_SUM_KAHAN, geoms[q].ws, P->d.sign, geoms[q].smem,
+                                       P->d.sum, geoms[q].ws, P->d.sign, geoms[q].smem,
                                        sq)) != cudaSuccess) {
                 fail_all(std::string("fold-sweep launch: ") + cudaGetErrorString(e));
                 return false;
@@ -401,8 +401,8 @@ bool Server::step()
         rp.topk = topk;
         rp.sign = P->d.sign;
         rp.phase = P->d.phase;
-        rp.kahan = P->d.sum == BLS_SUM_KAHAN;
-        rp.smem_bytes = reduce_smem_bytes(nbmax, topk, rp.kahan);
+        rp.sums = P->d.sum;
+        rp.smem_bytes = reduce_smem_bytes(nbmax, topk, rp.sums);
         rp.err = err.as<int>();
         if ((e = launch_reduce(rp, nf, stream)) != cudaSuccess) {
             fail_all(std::string("reduce launch: ") + cudaGetErrorString(e));

@@ -122,14 +122,14 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
         const size_t avail = avail_all > stage ? avail_all - stage : 0;
         const size_t cap = avail / ((size_t)c->nb * 8);
         int T = (int)std::min<size_t>(cap, (size_t)fold_sweep_max_threads()) & ~15;
-        while (T >= 16 && fold_smem_bytes(T, T, c->nb, chunk, 0) > avail_all) T -= 16;
+        while (T >= 16 && fold_smem_bytes(T, T, c->nb, chunk, kSumF32) > avail_all) T -= 16;
         return T;
     };
     const int chunk = tmax(512) >= tmax(256) ? 512 : 256;
-    const int T = fold_preferred_cols(tmax(chunk), 0, c->nb, kmin, kmax, BLS_FOLD_AUTO);
-    const int ws = fold_ws_mode(T, 0, c->nb, kmin, kmax, BLS_FOLD_AUTO);
+    const int T = fold_preferred_cols(tmax(chunk), kSumF32, c->nb, kmin, kmax, BLS_FOLD_AUTO);
+    const int ws = fold_ws_mode(T, kSumF32, c->nb, kmin, kmax, BLS_FOLD_AUTO);
     if (T < 16) return set_error(BLS_ERR_INVALID, "nb = %d needs more shared memory than a block has", c->nb);
-    const size_t smem = fold_smem_bytes(T, T, c->nb, chunk, 0);
+    const size_t smem = fold_smem_bytes(T, T, c->nb, chunk, kSumF32);
 
     CurveDesc d;
     memset(&d, 0, sizeof(d));
@@ -150,7 +150,7 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
 
     static_init_kernel<<<1, 1, 0, s>>>(d, cdesc, range, prefix, ntiles, counter, err);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "static init launch");
-    if ((e = launch_prep(cdesc, nullptr, 1, err, kPhaseFX64, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
+    if ((e = launch_prep(cdesc, nullptr, 1, err, kPhaseFX64, kSumF32, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
     FoldParams fp;
     fp.curves = cdesc;
     fp.ranges = range;
@@ -162,9 +162,9 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
     fp.chunk = chunk;
     fp.stride = T;
     fp.wait_ns = 0;
-    long long grid = (long long)sms * fold_blocks_per_sm(T, smem, kPhaseFX64, 0, sign, ws);
+    long long grid = (long long)sms * fold_blocks_per_sm(T, smem, kPhaseFX64, kSumF32, sign, ws);
     if (grid > ntiles) grid = ntiles;
-    if ((e = launch_fold_sweep(fp, T, (int)grid, kPhaseFX64, 0, ws, sign, smem, s)) != cudaSuccess)
+    if ((e = launch_fold_sweep(fp, T, (int)grid, kPhaseFX64, kSumF32, ws, sign, smem, s)) != cudaSuccess)
         return cuda_fail(e, "fold-sweep launch");
     ReduceParams rp;
     rp.curves = cdesc;
@@ -190,8 +190,8 @@ extern "C" bls_status bls_search_static(const bls_curve* c, int topk, int sign, 
     rp.topk = topk;
     rp.sign = sign;
     rp.phase = kPhaseFX64;
-    rp.kahan = 0;
-    rp.smem_bytes = reduce_smem_bytes(c->nb, topk, 0);
+    rp.sums = kSumF32;
+    rp.smem_bytes = reduce_smem_bytes(c->nb, topk, kSumF32);
     rp.err = err;
     if ((e = launch_reduce(rp, 1, s)) != cudaSuccess) return cuda_fail(e, "reduce launch");
     int host_err = 0;

@@ -182,3 +182,26 @@ def test_kahan_sums_in_both_kernels(nb):
         out[kern] = (spec, pk)
     np.testing.assert_allclose(out["auto"][0], out["one_group"][0], rtol=1e-6, atol=0)
     assert np.array_equal(out["auto"][1]["j"][:, 0], out["one_group"][1]["j"][:, 0])
+
+
+@pytest.mark.parametrize("nb", [200, 256])
+@pytest.mark.parametrize("sums", ["fixed", "f32"])
+def test_fixed_and_f32_sums_in_both_kernels(sums, nb):
+    """Fixed-point sums (the default: exact integer bin sums, converted to FP32 for the
+    sweep) and plain FP32 sums, in the warp-specialised and the one-group kernel: both
+    within the parity tolerance of the oracle.  With fixed-point sums the two kernels bin
+    into identical integers, so their spectra differ only by the sweeps' approximations."""
+    b = synth.config2(ncurves=3, nf=900, seed=45)
+    cis = [bls.CurveInput(ci.t, ci.y, ci.dy, nf=ci.nf, fmin=ci.fmin, df=ci.df, nb=nb,
+                          qmin=ci.qmin, qmax=ci.qmax) for ci in bls.curves_from_batch(b)]
+    out = {}
+    for kern in ("auto", "one_group"):
+        spec = np.zeros(3 * 900, np.float32)
+        with bls.Plan(nb=nb, qmin=b.qmin, qmax=b.qmax, topk=2, sum=sums,
+                      fold_kernel=kern) as p:
+            pk = p.search(cis, spectrum=spec)
+            assert p.tile_shape()["fold_kernel"] == ("ws" if kern == "auto" else "one_group")
+        _oracle_check(cis, spec, nb, b.qmin, b.qmax, 0)
+        out[kern] = (spec, pk)
+    np.testing.assert_allclose(out["auto"][0], out["one_group"][0], rtol=1e-6, atol=0)
+    assert np.array_equal(out["auto"][1]["j"][:, 0], out["one_group"][1]["j"][:, 0])

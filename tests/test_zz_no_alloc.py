@@ -42,7 +42,8 @@ def test_static_search_matches_search_on_two_calls_in_a_row():
         host = bls.CurveInput(c.t, c.y, c.dy, nf=g.nf, fmin=g.fmin, df=g.df, nb=200,
                               qmin=b.qmin, qmax=b.qmax)
         ref_spec = np.zeros(g.nf, np.float32)
-        with bls.Plan(nb=200, qmin=b.qmin, qmax=b.qmax, topk=topk) as p:
+        # the static search sums in FP32: the regular search in the same sum mode
+        with bls.Plan(nb=200, qmin=b.qmin, qmax=b.qmax, topk=topk, sum="f32") as p:
             ref = p.search([host], spectrum=ref_spec)[0]
         _, _, _, scal = oracle.prep(c.t, c.y, c.dy)
         tol = _sr_tol(ref_spec.astype(np.float64), scal[3])
