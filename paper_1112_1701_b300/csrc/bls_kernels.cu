@@ -79,6 +79,14 @@ __host__ __device__ __forceinline__ int fx_shift(double dtmax)
     return s < 1 ? 1 : s;
 }
 
+// 2^e as an FP64 number built from its exponent field, for -1022 <= e <= 1023: x * pow2(e)
+// equals ldexp(x, e) whenever the result is a normal number (every use below), at the cost
+// of one FP64 multiply.
+__device__ __forceinline__ double pow2(int e)
+{
+    return __hiloint2double((e + 1023) << 20, 0);
+}
+
 // Error bound of the double-FP32 fold, in bins.  With D = dt, F = f, DF = D*F and
 // u = 2^-24 (FP32 unit roundoff):
 //   split errors |D - dh - dl| <= u^2 D, |F - fh - fl| <= u^2 F, dropped dl*fl <= u^2 DF,
@@ -96,17 +104,25 @@ __host__ __device__ __forceinline__ int fx_shift(double dtmax)
 // 2^-52 (DF + 1) nb bins of nb*frac(dt f), so b is the definition's bin whenever r is at
 // least tol = (E + 2^-52 (DF + 1)) nb 2^32 (with margin) from both ends of the bin:
 // tol <= r < 2^32 - tol - nb.
-__device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dtmax, int fxs)
+//
+// The hot kernels ask only for the parts their fold uses: `direct` (the FX64 constants of
+// the direct fold; a tile on the incremental fold sets its own) and `df32` (the double-FP32
+// and FP32 folds' constants); the per-tile constants are FP64 arithmetic, a slow pipe on
+// this GPU.
+__device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dtmax, int fxs,
+                                                     bool direct = true, bool df32 = true)
 {
     FoldConst fc;
-    {
-        const double Fd = ldexp(f, 64 - fxs);
+    fc.fxok = false;
+    fc.Flo = fc.Fhi = fc.ftol = fc.fspan = 0u;
+    if (direct) {
+        const double Fd = f * pow2(64 - fxs);
         fc.fxok = Fd < 18446744073709551616.0;   // F < 2^64
         const unsigned long long F = fc.fxok ? __double2ull_rn(Fd) : 0ull;
         fc.Flo = (unsigned)F;
         fc.Fhi = (unsigned)(F >> 32);
-        const double E = f * ldexp(1.0, -(fxs + 1)) + dtmax * ldexp(1.0, fxs - 65) + ldexp(1.0, -66)
-                       + ldexp(1.0, -52) * (dtmax * f + 1.0);
+        const double E = f * pow2(-(fxs + 1)) + dtmax * pow2(fxs - 65) + pow2(-66)
+                       + pow2(-52) * (dtmax * f + 1.0);
         const double tolu = E * nb * 4294967296.0 * 1.01 + 4.0;
         fc.fxok = fc.fxok && tolu < 1.0e9;
         const unsigned tol = fc.fxok ? (unsigned)ceil(tolu) : 0u;
@@ -116,9 +132,13 @@ __device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dt
     fc.f = f;
     fc.nb = nb;
     fc.sh = (nb & (nb - 1)) == 0 ? 31u - (unsigned)__clz(nb) : 0u;
+    fc.nbf = (float)nb;
+    fc.fh = fc.fl = 0.0f;
+    fc.fast = false;
+    fc.lim = 0.0f;
+    if (!df32) return fc;
     fc.fh = __double2float_rn(f);
     fc.fl = __double2float_rn(__dsub_rn(f, (double)fc.fh));
-    fc.nbf = (float)nb;
     double DF = dtmax * f;
     fc.fast = DF < 1048576.0;
     double cmax = 3.0 * 5.9604644775390625e-8 * DF;          // 3 u DF
@@ -147,15 +167,15 @@ __device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dt
 // the typical workloads for the exact re-fold.
 __device__ __forceinline__ bool inc_tile_ok(double fc, double df, int fxs)
 {
-    return df > 0.0 && fc >= 0.0 && ldexp(fc, 64 - fxs) < 18446744073709551616.0 &&
-           ldexp(df, 96 - fxs) < 9223372036854775808.0;
+    return df > 0.0 && fc >= 0.0 && fc * pow2(64 - fxs) < 18446744073709551616.0 &&
+           df * pow2(96 - fxs) < 9223372036854775808.0;
 }
 
 __device__ __forceinline__ void make_fold_const_inc(FoldConst& fc, double f, double fcen, int tau,
                                                     double df, int nb, double dtmax, int fxs)
 {
-    const unsigned long long Fc = __double2ull_rn(ldexp(fcen, 64 - fxs));
-    const unsigned long long dF = __double2ull_rn(ldexp(df, 96 - fxs));
+    const unsigned long long Fc = __double2ull_rn(fcen * pow2(64 - fxs));
+    const unsigned long long dF = __double2ull_rn(df * pow2(96 - fxs));
     fc.Fclo = (unsigned)Fc;
     fc.Fchi = (unsigned)(Fc >> 32);
     fc.dFlo = (unsigned)dF;
@@ -163,11 +183,11 @@ __device__ __forceinline__ void make_fold_const_inc(FoldConst& fc, double f, dou
     fc.tau = (unsigned)tau;
     const double at = fabs((double)tau);
     const double fhi = fmax(f, fcen);
-    const double E = fcen * ldexp(1.0, -(fxs + 1)) + dtmax * ldexp(1.0, fxs - 65) + ldexp(1.0, -66)
-                   + at * (ldexp(1.0, -33) + df * ldexp(1.0, -(fxs + 1)) + dtmax * ldexp(1.0, fxs - 97)
-                           + ldexp(1.0, -98))
-                   + dtmax * fhi * ldexp(1.0, -51) * 1.01
-                   + ldexp(1.0, -52) * (dtmax * f + 1.0);
+    const double E = fcen * pow2(-(fxs + 1)) + dtmax * pow2(fxs - 65) + pow2(-66)
+                   + at * (pow2(-33) + df * pow2(-(fxs + 1)) + dtmax * pow2(fxs - 97)
+                           + pow2(-98))
+                   + dtmax * fhi * pow2(-51) * 1.01
+                   + pow2(-52) * (dtmax * f + 1.0);
     const double tolu = E * nb * 4294967296.0 * 1.01 + 4.0;
     fc.fxok = tolu < 1.0e9;
     const unsigned tol = fc.fxok ? (unsigned)ceil(tolu) : 0u;
@@ -1562,13 +1582,14 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
         const bool active = j < nf;
         const int jt = active ? j : nf - 1;
         const double f = grid_freq(cdr, jt);
-        FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs);
         // FX64 tiles of a uniform grid (plain sums) take the incremental fold, with the
         // tile's middle column (at most its last frequency) as the reference column
         const int jc = min(tile * T + T / 2, nf - 1);
         const double fcen = grid_freq(cdr, jc);
         const bool inc = PHASE == kPhaseFX64 && !KAHAN && cdr.freqs == nullptr &&
                          inc_tile_ok(fcen, cdr.df, cdr.fxs);
+        FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs, !inc,
+                                       PHASE == kPhaseDF32 || PHASE == kPhaseF32);
         if (inc) make_fold_const_inc(fc, f, fcen, jt - jc, cdr.df, nb, cdr.dtmax, cdr.fxs);
         const FoldPacked fq = make_fold_packed(fc);
 
@@ -2109,13 +2130,14 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             const bool active = lane_ok && j < nf;
             const int jt = j < nf ? j : nf - 1;
             const double f = grid_freq(cdr, jt);
-            FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs);
             // FX64 tiles of a uniform grid take the incremental fold, with the tile's middle
             // column (at most its last frequency) as the reference column
             const int jc = min(tile * T + T / 2, nf - 1);
             const double fcen = grid_freq(cdr, jc);
             const bool inc = PHASE == kPhaseFX64 && cdr.freqs == nullptr &&
                              inc_tile_ok(fcen, cdr.df, cdr.fxs);
+            FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs, !inc,
+                                           PHASE == kPhaseDF32 || PHASE == kPhaseF32);
             if (inc) make_fold_const_inc(fc, f, fcen, jt - jc, cdr.df, nb, cdr.dtmax, cdr.fxs);
             const FoldPacked fq = make_fold_packed(fc);
 

@@ -12,6 +12,8 @@
 //   smem_red     private-column update with two shared-memory float atomic adds
 //   smem_ired32  private-column update with two shared-memory 32-bit integer reductions
 //   smem_ired64  private-column update with one shared-memory 64-bit integer reduction
+//   smem_ired32p two 32-bit integer reductions per point into separate W and X planes
+//                (4-byte entries, stride = threads: the 32 lanes of a warp hit 32 banks)
 //   lds64        private-column 8-byte loads only
 //   mufu_rcp     approximate reciprocals (8 chains per thread)
 //   lds*/sts*_bw shared-memory bytes per SM per clock for 4, 8 and 16 bytes per lane
@@ -236,6 +238,15 @@ __global__ void smem_hist(int iters, float* out, Stamp* st)
             const unsigned long long v = ((unsigned long long)(x >> 20) << 32) | (x & 0xffffu);
             asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
         }
+    } else if (MODE == 6) {     // two 32-bit reductions per point, W and X planes
+        const unsigned base = (unsigned)__cvta_generic_to_shared(H);
+        const unsigned plane = 128u * T * 4u;
+        for (int i = 0; i < iters; ++i) {
+            x = x * 1664525u + 1013904223u;
+            const unsigned a = base + ((x >> 25) * T + t) * 4u;
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(x & 0xffffu) : "memory");
+            asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a + plane), "r"(x >> 20) : "memory");
+        }
     } else {                    // loads only
         for (int i = 0; i < iters; ++i) {
             x = x * 1664525u + 1013904223u;
@@ -334,16 +345,17 @@ int main(int argc, char** argv)
         runbw("sts64_bw", 8, smem_bw<8, 1>);
         runbw("sts128_bw", 16, smem_bw<16, 1>);
     }
-    const char* names[6] = {"smem_rmw", "smem_rmw2", "smem_red", "lds64", "smem_ired32",
-                            "smem_ired64"};
+    const char* names[7] = {"smem_rmw", "smem_rmw2", "smem_red", "lds64", "smem_ired32",
+                            "smem_ired64", "smem_ired32p"};
     const int Ts[3] = {64, 128, 192};
-    for (int mode = 0; mode < 6; ++mode) {
+    for (int mode = 0; mode < 7; ++mode) {
         for (int ti = 0; ti < 3; ++ti) {
             const int T = Ts[ti];
             const size_t smem = (size_t)128 * T * sizeof(float2);
             const int blocks = sms, it = (int)(40000 * scale);
             auto k = mode == 0 ? smem_hist<0> : mode == 1 ? smem_hist<1> : mode == 2 ? smem_hist<2>
-                   : mode == 3 ? smem_hist<3> : mode == 4 ? smem_hist<4> : smem_hist<5>;
+                   : mode == 3 ? smem_hist<3> : mode == 4 ? smem_hist<4> : mode == 5 ? smem_hist<5>
+                   : smem_hist<6>;
             CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             Result r = run([&] { k<<<blocks, T, smem>>>(it, out, st); }, blocks, (double)blocks * T * it, st, sms);
             printf("{\"probe\": \"%s\", \"threads_per_sm\": %d, \"ms\": %.3f, \"clk_mhz\": %.0f, \"points_per_sm_clk\": %.3f}\n",
