@@ -784,8 +784,9 @@ def measure(batch, topk, args, ctx, tune=True, e2e=True, steps=None, warmup=None
            "box_evals_per_s": evals * world / (ms_step / 1000.0),
            "kernel_ms": {"prep": prof["prep_ms"] / steps, "fold_sweep": prof["fold_ms"] / steps,
                          "reduce": prof["reduce_ms"] / steps},
-           "launch": dict(launch_kw, source="autotuner", tile_shape=plan.tile_shape()) if tuned else
-                     {"source": "library rules", "tile_shape": plan.tile_shape()},
+           "launch": dict(launch_kw, source="autotuner", tile_shape=plan.tile_shape(), sums=sums)
+                     if tuned else {"source": "library rules", "tile_shape": plan.tile_shape(),
+                                    "sums": sums},
            "plan": plan, "dev": dev, "units": units, "evals": evals}
     if tuned:
         out["autotune"] = tuned
