@@ -43,6 +43,12 @@ struct CurveDesc {
     // fixed-point sums (prep kernel): a bin's integer sums (W, X) stand for
     // r = W * wq and s = X * xq (wq = 1 / sum of all W, xq = 1 / the scale of w x)
     float wq, xq;
+    // incremental fold of uniform-grid tiles (prep kernel): incok if the grid is uniform and
+    // dF = RN_int(df 2^(96 - fxs)) < 2^63; the edge window's error bound of a column is
+    // E = fcen ewc + ew0 + |tau| ewt + max(f, fcen) ewh + f ewf (coefficients rounded up)
+    unsigned long long dF;
+    float ewc, ew0, ewt, ewh, ewf;
+    int incok;
 };
 
 // A run of frequency tiles of one curve processed by one fold-sweep launch.

@@ -165,34 +165,35 @@ __device__ __forceinline__ FoldConst make_fold_const(double f, int nb, double dt
 // direct fold applies with tol = (sum of these) nb 2^32 (1.01) + 4.  Valid (fxok) while
 // Fc < 2^64, dF < 2^63 and tol < 10^9; the window keeps fewer than 10^-5 of the points of
 // the typical workloads for the exact re-fold.
-__device__ __forceinline__ bool inc_tile_ok(double fc, double df, int fxs)
+__device__ __forceinline__ bool inc_tile_ok(double fcen, const CurveDesc& cd)
 {
-    return df > 0.0 && fc >= 0.0 && fc * pow2(64 - fxs) < 18446744073709551616.0 &&
-           df * pow2(96 - fxs) < 9223372036854775808.0;
+    return cd.incok && fcen >= 0.0 && fcen * pow2(64 - cd.fxs) < 18446744073709551616.0;
 }
 
+// The per-curve terms (dF, the coefficients of E) come from the prep kernel; a tile computes
+// Fc in FP64 and its columns' windows in FP32 with every operation rounded up, so the window
+// is never narrower than the bound (and the FP64 pipe, slow on this GPU, does little).
 __device__ __forceinline__ void make_fold_const_inc(FoldConst& fc, double f, double fcen, int tau,
-                                                    double df, int nb, double dtmax, int fxs)
+                                                    const CurveDesc& cd, int nb)
 {
-    const unsigned long long Fc = __double2ull_rn(fcen * pow2(64 - fxs));
-    const unsigned long long dF = __double2ull_rn(df * pow2(96 - fxs));
+    const unsigned long long Fc = __double2ull_rn(fcen * pow2(64 - cd.fxs));
     fc.Fclo = (unsigned)Fc;
     fc.Fchi = (unsigned)(Fc >> 32);
-    fc.dFlo = (unsigned)dF;
-    fc.dFhi = (unsigned)(dF >> 32);
+    fc.dFlo = (unsigned)cd.dF;
+    fc.dFhi = (unsigned)(cd.dF >> 32);
     fc.tau = (unsigned)tau;
-    const double at = fabs((double)tau);
-    const double fhi = fmax(f, fcen);
-    const double E = fcen * pow2(-(fxs + 1)) + dtmax * pow2(fxs - 65) + pow2(-66)
-                   + at * (pow2(-33) + df * pow2(-(fxs + 1)) + dtmax * pow2(fxs - 97)
-                           + pow2(-98))
-                   + dtmax * fhi * pow2(-51) * 1.01
-                   + pow2(-52) * (dtmax * f + 1.0);
-    const double tolu = E * nb * 4294967296.0 * 1.01 + 4.0;
-    fc.fxok = tolu < 1.0e9;
-    const unsigned tol = fc.fxok ? (unsigned)ceil(tolu) : 0u;
+    const float ff = __double2float_ru(f), fcf = __double2float_ru(fcen);
+    const float at = (float)(tau < 0 ? -tau : tau);   // exact: |tau| < 2^24
+    float E = __fmaf_ru(fcf, cd.ewc, cd.ew0);
+    E = __fmaf_ru(at, cd.ewt, E);
+    E = __fmaf_ru(fmaxf(ff, fcf), cd.ewh, E);
+    E = __fmaf_ru(ff, cd.ewf, E);
+    // tol = E nb 2^32 (1.01) + 4, rounded up
+    const float tolu = __fadd_ru(__fmul_ru(__fmul_ru(__fmul_ru(E, (float)nb), 4294967296.0f), 1.0101f), 4.0f);
+    fc.fxok = tolu < 1.0e9f;
+    const unsigned tol = fc.fxok ? __float2uint_ru(tolu) : 0u;
     fc.ftol = tol;
-    fc.fspan = fc.fxok ? (unsigned)(4294967296.0 - 2.0 * tol - nb) : 0u;
+    fc.fspan = fc.fxok ? 0u - 2u * tol - (unsigned)nb : 0u;   // 2^32 - 2 tol - nb
 }
 
 // (Qi, Di) of one point from DT = (hi:lo) and the tile's Fc, dF (see make_fold_const_inc).
@@ -636,6 +637,19 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(CurveDesc* curves, c
     swx2 = block_sum(swx2, red);
     if (fixs) wtot = block_sum(wtot, red);
     if (threadIdx.x == 0) {
+        // per-curve terms of the incremental fold's window (see make_fold_const_inc),
+        // coefficients of E rounded up to FP32
+        const double dtm = __dsub_rn(tmax, tmin), df = cd->df;
+        const bool uni = cd->freqs == nullptr && df > 0.0 && isfinite(df);
+        const double dFd = uni ? df * pow2(96 - fxs) : 0.0;
+        cd->incok = uni && dFd < 9223372036854775808.0;
+        cd->dF = cd->incok ? __double2ull_rn(dFd) : 0ull;
+        cd->ewc = __double2float_ru(pow2(-(fxs + 1)));
+        cd->ew0 = __double2float_ru(dtm * pow2(fxs - 65) + pow2(-66) + pow2(-52));
+        cd->ewt = __double2float_ru(pow2(-33) + (uni ? df : 0.0) * pow2(-(fxs + 1)) +
+                                    dtm * pow2(fxs - 97) + pow2(-98));
+        cd->ewh = __double2float_ru(dtm * pow2(-51) * 1.0101);
+        cd->ewf = __double2float_ru(dtm * pow2(-52));
         cd->wq = fixs && wtot > 0.0 ? __double2float_rn(__ddiv_rn(1.0, wtot)) : 0.0f;
         cd->xq = fixs ? __double2float_rn(__ddiv_rn(1.0, Sx)) : 0.0f;
         cd->t_ref = tmin;
@@ -1587,10 +1601,10 @@ __global__ void __launch_bounds__(kFoldMaxThreads, 1) fold_sweep_kernel(FoldPara
         const int jc = min(tile * T + T / 2, nf - 1);
         const double fcen = grid_freq(cdr, jc);
         const bool inc = PHASE == kPhaseFX64 && !KAHAN && cdr.freqs == nullptr &&
-                         inc_tile_ok(fcen, cdr.df, cdr.fxs);
+                         inc_tile_ok(fcen, cdr);
         FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs, !inc,
                                        PHASE == kPhaseDF32 || PHASE == kPhaseF32);
-        if (inc) make_fold_const_inc(fc, f, fcen, jt - jc, cdr.df, nb, cdr.dtmax, cdr.fxs);
+        if (inc) make_fold_const_inc(fc, f, fcen, jt - jc, cdr, nb);
         const FoldPacked fq = make_fold_packed(fc);
 
         for (int b = 0; b < nb && part == 0; ++b) {
@@ -2135,10 +2149,10 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             const int jc = min(tile * T + T / 2, nf - 1);
             const double fcen = grid_freq(cdr, jc);
             const bool inc = PHASE == kPhaseFX64 && cdr.freqs == nullptr &&
-                             inc_tile_ok(fcen, cdr.df, cdr.fxs);
+                             inc_tile_ok(fcen, cdr);
             FoldConst fc = make_fold_const(f, nb, cdr.dtmax, cdr.fxs, !inc,
                                            PHASE == kPhaseDF32 || PHASE == kPhaseF32);
-            if (inc) make_fold_const_inc(fc, f, fcen, jt - jc, cdr.df, nb, cdr.dtmax, cdr.fxs);
+            if (inc) make_fold_const_inc(fc, f, fcen, jt - jc, cdr, nb);
             const FoldPacked fq = make_fold_packed(fc);
 
             // a2: chunks of CH points through shared memory (as in fold_sweep_kernel)
@@ -2666,8 +2680,8 @@ __global__ void debug_fold_kernel(const CurveDesc* curve, const int* js, int* bi
     const int jc = min(j / T * T + T / 2, cd.nf - 1);
     const double fcen = grid_freq(cd, jc);
     const bool inc = PHASE == kPhaseFX64 && !kahan && cd.freqs == nullptr &&
-                     inc_tile_ok(fcen, cd.df, cd.fxs);
-    if (inc) make_fold_const_inc(fi, f, fcen, j - jc, cd.df, cd.nb, cd.dtmax, cd.fxs);
+                     inc_tile_ok(fcen, cd);
+    if (inc) make_fold_const_inc(fi, f, fcen, j - jc, cd, cd.nb);
     for (int pi = threadIdx.x; 2 * pi < cd.n; pi += blockDim.x) {
         unsigned b0, b1;
         fold_pair<PHASE>(cd.pts[2 * pi], &cd.dt64[2 * pi], fc, fq, b0, b1);
