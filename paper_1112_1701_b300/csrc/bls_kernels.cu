@@ -462,6 +462,7 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 __device__ __forceinline__ float rcp_approx(float x)
 {
@@ -1913,7 +1914,7 @@ template <int SIGN, int SUMS>
 __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_ok, int col,
                                                  unsigned s_tmem, TileSlot* s_slot,
                                                  unsigned full_bar, unsigned empty_bar,
-                                                 float* s_wpart, float* s_wpart2,
+                                                 unsigned slot_bar, float* s_wpart, float* s_wpart2,
                                                  unsigned char* hist, unsigned hbase,
                                                  unsigned rowb)
 {
@@ -1926,11 +1927,18 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
     const unsigned tbase = s_tmem + ((unsigned)((warp & 3) * 32) << 16);
     const bool fetcher = warp == sg0 / 32;
     unsigned ph = 0;
-    // descriptors of tiles 0 and 1; the histograms start empty
-    if (fetcher) fetch_tile(p, &s_slot[0], lane);
+    // descriptors of tiles 0 and 1 (each published on its slot's barrier by the 32 lanes
+    // that wrote it); the histograms start empty
+    if (fetcher) {
+        fetch_tile(p, &s_slot[0], lane);
+        mbar_arrive(slot_bar);
+    }
     group_sync(kBarSweep, NS);
     if (tid == sg0) mbar_arrive(empty_bar);
-    if (fetcher) fetch_tile(p, &s_slot[1], lane);
+    if (fetcher) {
+        fetch_tile(p, &s_slot[1], lane);
+        mbar_arrive(slot_bar + 8u);
+    }
     for (int k = 0;; ++k) {
         int give_up = 0;
         if (tid == sg0) {
@@ -1999,6 +2007,13 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
         // the next tile (after this hand-over)
         group_sync(kBarSweep, NS);
         if (tid == sg0) mbar_arrive(empty_bar);
+        // descriptor of tile k + 2 into slot k & 1, published on the slot's barrier: every
+        // thread of this group has read the slot into registers above, and the binning
+        // group read it before binning tile k
+        if (fetcher) {
+            fetch_tile(p, &s_slot[k & 1], lane);
+            mbar_arrive(slot_bar + 8u * (unsigned)(k & 1));
+        }
         if (use_tmem) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             bool fast = true;
@@ -2049,9 +2064,6 @@ __device__ __forceinline__ void sweep_group_loop(const FoldParams& p, bool lane_
             if (fast) v = vf;
         }
         if (part == 0 && active) res[j] = v;
-        // descriptor of tile k + 2 (slot k & 1 is no longer read: the binning group
-        // copied it before binning tile k, this group above)
-        if (fetcher) fetch_tile(p, &s_slot[k & 1], lane);
     }
 }
 
@@ -2062,7 +2074,8 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
 {
     constexpr int KAHAN = SUMS == kSumKahan;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long s_bar[2];   // [0] histograms full, [1] empty
+    // [0] histograms full, [1] empty, [2 + s] the descriptor in slot s written
+    __shared__ __align__(8) unsigned long long s_bar[4];
     __shared__ TileSlot s_slot[2];                          // descriptor of tile k at [k & 1]
     __shared__ float s_wpart[128], s_wpart2[128];           // second sweep part's partials
     __shared__ unsigned s_tmem;
@@ -2090,6 +2103,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
     const unsigned rowb = (unsigned)(S * ESZ);
     const unsigned full_bar = (unsigned)__cvta_generic_to_shared(&s_bar[0]);
     const unsigned empty_bar = (unsigned)__cvta_generic_to_shared(&s_bar[1]);
+    const unsigned slot_bar = (unsigned)__cvta_generic_to_shared(&s_bar[2]);   // slot s: + 8 s
 
     {   // every histogram row starts at zero (afterwards each binning warp re-zeroes its
         // columns at the start of every tile)
@@ -2107,6 +2121,8 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
     if (tid == 0) {
         mbar_init(full_bar, 1);
         mbar_init(empty_bar, 1);
+        mbar_init(slot_bar, 32);        // arrived by the 32 lanes that write the slot
+        mbar_init(slot_bar + 8u, 32);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -2114,30 +2130,25 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
 
     if (binner) {
         unsigned ph = 0;
+        const unsigned long long wlim = p.wait_ns ? p.wait_ns : kHandoffTimeoutNs;
         for (int k = 0;; ++k) {
             int give_up = 0;
-            if (tid == 0) {
-                give_up = !mbar_wait(empty_bar, ph, p.wait_ns ? p.wait_ns : kHandoffTimeoutNs);
+            if (tid == 0) {   // tile k's descriptor, written ahead by the sweep group
+                give_up = !mbar_wait(slot_bar + 8u * (unsigned)(k & 1), (unsigned)(k >> 1) & 1u, wlim);
                 if (give_up) atomicOr(p.err, kErrTimeout);
             }
-            ph ^= 1u;
             give_up = group_or(kBarBin, kWsBinThreads, give_up);
             const TileSlot& sl = s_slot[k & 1];
             if (give_up || sl.stop) {
+                // the stop is handed over once the sweep group has taken the previous tile
+                if (tid == 0 && !give_up && !mbar_wait(empty_bar, ph, wlim)) atomicOr(p.err, kErrTimeout);
+                group_sync(kBarBin, kWsBinThreads);
                 if (tid == 0) mbar_arrive(full_bar);   // the sweep group reads the stop
                 break;
             }
             const CurveDesc cdr = sl.cd;
             const int tile = sl.tile;
             const int n = cdr.n, nf = cdr.nf, nb = cdr.nb;
-            if (lane_ok) {   // zero this thread's histogram column; the sweep group has
-                             // finished reading it (the empty hand-over above)
-                for (int b = 0; b < nb; ++b) {
-                    if (KAHAN) sts128(hbase + (unsigned)b * rowb, 0ull, 0ull);
-                    else sts64(hbase + (unsigned)b * rowb, 0ull);
-                }
-            }
-            __syncwarp();
             const float4* gpts = cdr.pts;
             const double* gdt = cdr.dt64;
             const int j = tile * T + col;
@@ -2173,7 +2184,28 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                 }
                 cp_async_commit();
             };
+            // the tile's constants and its first chunk are prepared while the sweep group may
+            // still be copying the previous tile's histograms out
             stage(0);
+            if (tid == 0) {
+                give_up = !mbar_wait(empty_bar, ph, wlim);
+                if (give_up) atomicOr(p.err, kErrTimeout);
+            }
+            ph ^= 1u;
+            give_up = group_or(kBarBin, kWsBinThreads, give_up);
+            if (give_up) {
+                cp_async_wait_all();
+                if (tid == 0) mbar_arrive(full_bar);
+                break;
+            }
+            if (lane_ok) {   // zero this thread's histogram column; the sweep group has
+                             // finished reading it (the empty hand-over above)
+                for (int b = 0; b < nb; ++b) {
+                    if (KAHAN) sts128(hbase + (unsigned)b * rowb, 0ull, 0ull);
+                    else sts64(hbase + (unsigned)b * rowb, 0ull);
+                }
+            }
+            __syncwarp();
             for (int ci = 0; ci < nchunks; ++ci) {
                 if (ci + 1 < nchunks) stage(ci + 1); else cp_async_commit();
                 cp_async_wait1();
@@ -2213,7 +2245,7 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             if (tid == 0) mbar_arrive(full_bar);
         }
     } else {
-        sweep_group_loop<SIGN, SUMS>(p, lane_ok, col, s_tmem, s_slot, full_bar, empty_bar, s_wpart,
+        sweep_group_loop<SIGN, SUMS>(p, lane_ok, col, s_tmem, s_slot, full_bar, empty_bar, slot_bar, s_wpart,
                                s_wpart2, hist, hbase, rowb);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
