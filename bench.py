@@ -59,8 +59,8 @@ NB, QMIN, QMAX = 200, 0.005, 0.15
 # profiles/fold_sweep_survey_2048x200k_dram.md), valid for the kernel source with the given
 # SHA-256; reported as null once the source changes.
 NCU_TRAFFIC = {"workload": "survey", "ncurves": 2048,
-               "kernel_sha256": "b11b87626abbc88a75dba51bd1498a36e11da83d259eeb172132c5f987ff5957",
-               "bytes_per_launch": 175595264 + 1626031616}
+               "kernel_sha256": "9375a80d89c7a68659b74104f1ed35817d45c30e9872fb90779bdb28e713c809",
+               "bytes_per_launch": 169564672 + 1619356672}
 
 
 def kernel_sha():
