@@ -401,8 +401,8 @@ __device__ __forceinline__ void fold_fx_pair(const float4& A, const FoldConst& f
     if (POW2) {   // nb = 2^sh: bin and in-bin place are the phase word's top and low bits
         b0 = q0 >> (32u - fc.sh);
         b1 = q1 >> (32u - fc.sh);
-        e0 = (q0 << fc.sh) - fc.ftol >= fc.fspan;
-        e1 = (q1 << fc.sh) - fc.ftol >= fc.fspan;
+        e0 = q0 * nbu - fc.ftol >= fc.fspan;   // q nb = q << sh: one multiply-add
+        e1 = q1 * nbu - fc.ftol >= fc.fspan;
     } else {
         b0 = __umulhi(q0, nbu);
         b1 = __umulhi(q1, nbu);
