@@ -2178,9 +2178,12 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
                 const int cpad = (cn + 15) & ~15;
                 float4* dp = cpts + (ci & 1) * CH;
                 double* dd = cdt + (ci & 1) * CH;
-                for (int i = tid; i < cn; i += kWsBinThreads) {
+                // thread t copies point pairs t, t + 128, ...: both float4 slots of a pair and
+                // its two FP64 offsets (16-byte aligned: curves start at even points)
+                for (int i = 2 * tid; i < cn; i += 2 * kWsBinThreads) {
                     cp_async16(&dp[i], &gpts[c0 + i]);
-                    cp_async8(&dd[i], &gdt[c0 + i]);
+                    cp_async16(&dp[i + 1], &gpts[c0 + i + 1]);
+                    cp_async16(&dd[i], &gdt[c0 + i]);
                 }
                 for (int i = cn + tid; i < cpad; i += kWsBinThreads) {
                     dp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -2213,14 +2216,14 @@ __global__ void __launch_bounds__(kWsMaxThreads, 1) fold_sweep_ws_kernel(FoldPar
             for (int ci = 0; ci < nchunks; ++ci) {
                 if (ci + 1 < nchunks) stage(ci + 1); else cp_async_commit();
                 cp_async_wait1();
-                if (inc && !(tid & 1)) {
+                if (inc) {
                     // staging step of the incremental fold, on this thread's own copies (the
-                    // even slots, DT of a point pair): (lo0, lo1, hi0, hi1) -> (Q0, Q1, D0, D1)
-                    // (written out here rather than through inc_stage: the binning loop
-                    // below is measurably faster with this form)
+                    // DT slot of each of its point pairs): (lo0, lo1, hi0, hi1) ->
+                    // (Q0, Q1, D0, D1) (written out here rather than through inc_stage: the
+                    // binning loop below is measurably faster with this form)
                     float4* dp = cpts + (ci & 1) * CH;
                     const int cn = (min(CH, n - ci * CH) + 1) & ~1;
-                    for (int i = tid; i < cn; i += kWsBinThreads) {
+                    for (int i = 2 * tid; i < cn; i += 2 * kWsBinThreads) {
                         const float4 A = dp[i];
                         unsigned Q0, D0, Q1, D1;
                         inc_point(__float_as_uint(A.x), __float_as_uint(A.z), fc, Q0, D0);
