@@ -59,8 +59,8 @@ NB, QMIN, QMAX = 200, 0.005, 0.15
 # profiles/fold_sweep_survey_2048x200k_dram.md), valid for the kernel source with the given
 # SHA-256; reported as null once the source changes.
 NCU_TRAFFIC = {"workload": "survey", "ncurves": 2048,
-               "kernel_sha256": "509abc3727488e97ff4918fa922528252e71da31c468eaa1ce13f5b56da607c7",
-               "bytes_per_launch": 169681408 + 1620271360}
+               "kernel_sha256": "dcf2a2ab73413f1f73f9a446ef059607beb54f2bd2cde447510583f65b7eebd6",
+               "bytes_per_launch": 163674368 + 1615719168}
 
 
 def kernel_sha():
