@@ -467,7 +467,40 @@ __device__ __forceinline__ float start_best(const Prefix& C, float4 T, int n, in
         const u64* WL = reinterpret_cast<const u64*>(C.wl);
         const u64* XH = reinterpret_cast<const u64*>(C.xh);
         const u64* XL = reinterpret_cast<const u64*>(C.xl);
+        if ((u & 2) && u + 1 <= u1) {   // to a multiple of four
+            const int h = u >> 1;
+            const u64 NR = add2(sub2(AWH, WH[h]), sub2(AWL, WL[h]));
+            const u64 S = add2(sub2(XH[h], AXH), sub2(XL[h], AXL));
+            float nd0, nd1;
+            upk2(fma2(NR, NR, NR), nd0, nd1);
+            float z0, z1;
+            upk2(mul2(S, pk2(rsqrt_apx(-nd0), rsqrt_apx(-nd1))), z0, z1);
+            b = SIGN ? fmax3f(b, fabsf(z0), fabsf(z1)) : fmin3f(b, z0, z1);
+            u += 2;
+        }
+        // four ends at a time: one 16-byte read of each prefix array (arrays 16-byte aligned,
+        // see prefix_layout), two packed pairs, the same per-lane arithmetic
+        const ulonglong2* WH4 = reinterpret_cast<const ulonglong2*>(C.wh);
+        const ulonglong2* WL4 = reinterpret_cast<const ulonglong2*>(C.wl);
+        const ulonglong2* XH4 = reinterpret_cast<const ulonglong2*>(C.xh);
+        const ulonglong2* XL4 = reinterpret_cast<const ulonglong2*>(C.xl);
 #pragma unroll 2
+        for (; u + 3 <= u1; u += 4) {
+            const int h = u >> 2;
+            const ulonglong2 wh = WH4[h], wl = WL4[h], xh = XH4[h], xl = XL4[h];
+            const u64 NR0 = add2(sub2(AWH, wh.x), sub2(AWL, wl.x));
+            const u64 NR1 = add2(sub2(AWH, wh.y), sub2(AWL, wl.y));
+            const u64 S0 = add2(sub2(xh.x, AXH), sub2(xl.x, AXL));
+            const u64 S1 = add2(sub2(xh.y, AXH), sub2(xl.y, AXL));
+            float nd0, nd1, nd2, nd3;
+            upk2(fma2(NR0, NR0, NR0), nd0, nd1);
+            upk2(fma2(NR1, NR1, NR1), nd2, nd3);
+            float z0, z1, z2, z3;
+            upk2(mul2(S0, pk2(rsqrt_apx(-nd0), rsqrt_apx(-nd1))), z0, z1);
+            upk2(mul2(S1, pk2(rsqrt_apx(-nd2), rsqrt_apx(-nd3))), z2, z3);
+            b = SIGN ? fmax3f(b, fabsf(z0), fabsf(z1)) : fmin3f(b, z0, z1);
+            b = SIGN ? fmax3f(b, fabsf(z2), fabsf(z3)) : fmin3f(b, z2, z3);
+        }
         for (; u + 1 <= u1; u += 2) {
             const int h = u >> 1;
             const u64 NR = add2(sub2(AWH, WH[h]), sub2(AWL, WL[h]));
@@ -493,11 +526,12 @@ __device__ __forceinline__ float start_best(const Prefix& C, float4 T, int n, in
     return b;
 }
 
-// Shared-memory layout of both kernels: keys [M] (8 B), then the four prefix arrays of
-// n1 = n + 1 rounded up to even entries each (so that 8-byte pair reads stay aligned).
+// Shared-memory layout of both kernels: keys [M] (8 B, M >= 2), then the four prefix arrays
+// of n1 = n + 1 rounded up to a multiple of four entries each (so that 16-byte reads of four
+// entries stay aligned).
 __device__ __forceinline__ Prefix prefix_layout(unsigned char* dsm, int M, int n)
 {
-    const int n1 = (n + 2) & ~1;
+    const int n1 = (n + 4) & ~3;
     float* base = reinterpret_cast<float*>(dsm + (size_t)M * sizeof(unsigned long long));
     Prefix C;
     C.wh = base;
@@ -805,7 +839,7 @@ size_t ubls_work_bytes(int nmax)
 {
     int M = 1;
     while (M < nmax) M <<= 1;
-    return (size_t)M * sizeof(unsigned long long) + (size_t)4 * ((nmax + 2) & ~1) * sizeof(float);
+    return (size_t)M * sizeof(unsigned long long) + (size_t)4 * ((nmax + 4) & ~3) * sizeof(float);
 }
 
 int ubls_tile() { return kTile; }
