@@ -24,8 +24,8 @@
 // double-float pairs in four arrays).  Run starts are dealt round-robin to the threads; a
 // start's admissible ends (extent within [qmin, qmax]) come from two binary searches, and
 // every run's sums are independent prefix differences.  Runs are ranked by the signed
-// residue z = s / sqrt(r(1-r)) (P = z^2), evaluated two ends at a time as packed FP32 pairs
-// where every run of the curve is known to have 0 < r < 1; only the best z of each
+// residue z = s / sqrt(r(1-r)) (P = z^2), evaluated four ends at a time as two packed FP32
+// pairs where every run of the curve is known to have 0 < r < 1; only the best z of each
 // frequency is kept, P(f_j) = z^2.
 //
 // Reduce kernel: one block per curve: the top-k local maxima of P(f_j) (as in the binned
