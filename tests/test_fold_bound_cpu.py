@@ -12,6 +12,10 @@ checks, against the oracle's FP64 bins, that no point outside the window has ano
     tau = j - jc, and the window widened by |tau| times D's error, the grid's two FP64
     roundings and the FP64 definition's own rounding.
 
+The kernels evaluate the incremental window in FP32 with upward rounding from per-curve
+coefficients (prep kernel); a model of that evaluation is checked never to give a narrower
+window than the FP64 bound (dropping the tile-offset term makes it fail).
+
 Inputs: long baselines at high frequencies, and points on exact bin edges.  Dropping the
 dominant term of the incremental window (|tau| times D's rounding) makes the exact-edge case
 fail; the smaller terms (the floor's one-sided nb, the grid roundings) are margins these
@@ -127,3 +131,71 @@ def test_incremental_window_is_small_on_the_batched_workload():
     for c, g in zip(b.curves, b.grids):
         js = [0, 64, 127, 25000, 49983, 49999]
         assert _check(c.t, g.fmin, g.df, g.nf, 200, js) < 2e-3
+
+
+def _up32(x):
+    """The smallest FP32 number >= the exact rational x (upward rounding)."""
+    from fractions import Fraction
+    v = np.float32(float(x))
+    while Fraction(float(v)) < x:
+        v = np.nextafter(v, np.float32(np.inf))
+    while True:
+        w = np.nextafter(v, np.float32(-np.inf))
+        if Fraction(float(w)) >= x:
+            v = w
+        else:
+            return v
+
+
+def _window_fp32(dtm, df, s, f, fc, tau, nb):
+    """The kernels' per-column window: per-curve coefficients formed in FP64 and rounded up
+    to FP32, then the column's bound with every FP32 operation rounded up."""
+    from fractions import Fraction as Fr
+    ewc = _up32(Fr(2.0 ** -(s + 1)))
+    ew0 = _up32(Fr(dtm * 2.0 ** (s - 65) + 2.0 ** -66 + 2.0 ** -52))
+    ewt = _up32(Fr(2.0 ** -33 + df * 2.0 ** -(s + 1) + dtm * 2.0 ** (s - 97) + 2.0 ** -98))
+    ewh = _up32(Fr(dtm * 2.0 ** -51 * 1.0101))
+    ewf = _up32(Fr(dtm * 2.0 ** -52))
+    ff, fcf = _up32(Fr(f)), _up32(Fr(fc))
+    at = np.float32(abs(tau))
+
+    def fma(a, b, c):
+        return _up32(Fr(float(a)) * Fr(float(b)) + Fr(float(c)))
+
+    E = fma(fcf, ewc, ew0)
+    E = fma(at, ewt, E)
+    E = fma(max(ff, fcf), ewh, E)
+    E = fma(ff, ewf, E)
+    t = _up32(Fr(float(E)) * nb)
+    t = _up32(Fr(float(t)) * 2 ** 32)
+    t = _up32(Fr(float(t)) * Fr(float(np.float32(1.0101))))
+    t = _up32(Fr(float(t)) + 4)
+    return float(t)
+
+
+def test_fp32_windows_never_narrower_than_the_fp64_bound():
+    """The incremental fold's window is computed in FP32 with upward rounding from per-curve
+    coefficients; over baselines of days to years, grids up to 20 cycles per day, tile
+    offsets up to 64 and bin counts 2-4096, it is never below the FP64 bound's window."""
+    rng = np.random.default_rng(21)
+    checked = 0
+    for _ in range(300):
+        dtm = float(10.0 ** rng.uniform(0, 3.1))
+        s = _shift(dtm)
+        df = float(10.0 ** rng.uniform(-7, -2))
+        f = float(rng.uniform(0.01, 20.0))
+        tau = int(rng.integers(-64, 65))
+        fc = f - tau * df
+        if fc <= 0:
+            continue
+        nb = int(rng.choice([2, 7, 100, 200, 256, 400, 4096]))
+        E64 = (fc * 2.0 ** -(s + 1) + dtm * 2.0 ** (s - 65) + 2.0 ** -66
+               + abs(tau) * (2.0 ** -33 + df * 2.0 ** -(s + 1) + dtm * 2.0 ** (s - 97) + 2.0 ** -98)
+               + dtm * max(f, fc) * 2.0 ** -51 * 1.01 + 2.0 ** -52 * (dtm * f + 1.0))
+        tol64 = math.ceil(E64 * nb * 4294967296.0 * 1.01 + 4.0)
+        tolu = _window_fp32(dtm, df, s, f, fc, tau, nb)
+        if tolu >= 1.0e9:
+            continue   # the fold falls back to FP64 for the tile
+        assert math.ceil(tolu) >= tol64, (dtm, df, f, tau, nb, tolu, tol64)
+        checked += 1
+    assert checked > 200
